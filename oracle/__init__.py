@@ -1,0 +1,148 @@
+"""FP64 CPU oracle for PCPM PageRank (arXiv 1709.07122).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline / reference arm may import this; the product path
+(``paper_1709_07122_gb300``) never does, and this package never imports it.
+
+The arithmetic lives in ``pcpm_oracle.c`` (plain sequential C, FP64), compiled
+with gcc on first use; this file only marshals numpy arrays. Functions and the
+passages they follow:
+
+* :func:`pagerank` - Eq. 1 / Algorithm 1 (pull direction), plus the dangling
+  reading (uniform redistribution by default, or leak).
+* :func:`png` - Partition-Node Graph of Sec. 3.3: per (source partition,
+  destination partition) update and edge counts, the write offsets of Sec. 3.1,
+  and the bins in canonical order (source partitions in ID order, nodes in ID
+  order, destination IDs in adjacency order; MSB marks a message's first ID).
+* :func:`scatter_gather` - Algorithm 3 followed by Algorithm 4 in FP64.
+
+Parity of :func:`pagerank` is pinned by closed forms, a dense linear solve and
+invariants; :func:`png` by brute-force enumeration and the paper's offset
+example; :func:`scatter_gather` by a dense matrix product (see tests/).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pcpm_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_pcpm_oracle.so")
+_lib = None
+_lock = threading.Lock()
+
+_u32p = np.ctypeslib.ndpointer(dtype=np.uint32, flags="C_CONTIGUOUS")
+_f64p = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+
+
+def build(force: bool = False) -> str:
+    """Compiles pcpm_oracle.c into a shared library next to it."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        subprocess.run(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"], check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            vp = ctypes.c_void_p
+            lib.oracle_pagerank.argtypes = [ctypes.c_uint32, _u32p, _u32p, ctypes.c_double, ctypes.c_int,
+                                            ctypes.c_int, vp, vp, vp, vp]
+            lib.oracle_pagerank.restype = ctypes.c_int
+            lib.oracle_png_count.argtypes = [ctypes.c_uint32, _u32p, _u32p, ctypes.c_uint32, _u32p, _u32p]
+            lib.oracle_png_count.restype = None
+            lib.oracle_png_fill.argtypes = [ctypes.c_uint32, _u32p, _u32p, ctypes.c_uint32, _u32p, _u32p,
+                                            _u32p, _u32p, _u32p, _u32p, _u32p, _u32p]
+            lib.oracle_png_fill.restype = None
+            lib.oracle_scatter_gather.argtypes = [ctypes.c_uint32, ctypes.c_uint32, _u32p, _u32p, _u32p, _u32p,
+                                                  _f64p, _f64p]
+            lib.oracle_scatter_gather.restype = None
+            _lib = lib
+    return _lib
+
+
+def _csr(row_ptr, col):
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.uint32)
+    col = np.ascontiguousarray(col, dtype=np.uint32)
+    if col.size == 0:
+        col = np.zeros(1, dtype=np.uint32)  # valid pointer; row_ptr[n] = 0 says no edges
+    return row_ptr, col
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def pagerank(row_ptr, col, d: float = 0.85, iters: int = 20, x0=None, dangling: str = "uniform",
+             history: bool = False):
+    """Iterates Eq. 1 ``iters`` times from ``x0`` (uniform 1/n if None).
+
+    Returns a dict with ``x`` (final vector), ``resid`` (L1 change per
+    iteration) and, if ``history``, ``hist`` of shape (iters+1, n)."""
+    if dangling not in ("uniform", "leak"):
+        raise ValueError("dangling must be 'uniform' or 'leak'")
+    lib = _load()
+    row_ptr, col = _csr(row_ptr, col)
+    n = row_ptr.size - 1
+    x0a = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float64)
+    if x0a is not None and x0a.size != n:
+        raise ValueError("x0 has the wrong length")
+    hist = np.empty((iters + 1, n), dtype=np.float64) if history else None
+    x = np.empty(n, dtype=np.float64)
+    resid = np.empty(max(iters, 1), dtype=np.float64)
+    rc = lib.oracle_pagerank(n, row_ptr, col, float(d), 1 if dangling == "uniform" else 0, int(iters),
+                             _ptr(x0a), _ptr(hist), _ptr(x), _ptr(resid))
+    if rc != 0:
+        raise MemoryError("oracle_pagerank could not allocate")
+    out = {"x": x, "resid": resid[:iters]}
+    if history:
+        out["hist"] = hist
+    return out
+
+
+def png(row_ptr, col, q: int):
+    """Partition-Node Graph for partition size ``q`` (nodes per partition)."""
+    lib = _load()
+    row_ptr, col = _csr(row_ptr, col)
+    n = row_ptr.size - 1
+    k = (n + q - 1) // q
+    cnt_u = np.empty(k * k, dtype=np.uint32)
+    cnt_e = np.empty(k * k, dtype=np.uint32)
+    lib.oracle_png_count(n, row_ptr, col, int(q), cnt_u, cnt_e)
+    ne = int(cnt_u.sum(dtype=np.uint64))
+    m = int(row_ptr[n])
+    off_u = np.empty(k * k, dtype=np.uint32)
+    off_e = np.empty(k * k, dtype=np.uint32)
+    bin_u = np.empty(k + 1, dtype=np.uint32)
+    bin_e = np.empty(k + 1, dtype=np.uint32)
+    src_idx = np.empty(max(ne, 1), dtype=np.uint32)
+    dest_ids = np.empty(max(m, 1), dtype=np.uint32)
+    lib.oracle_png_fill(n, row_ptr, col, int(q), cnt_u, cnt_e, off_u, off_e, bin_u, bin_e, src_idx, dest_ids)
+    return {
+        "n": n, "q": int(q), "k": k, "m": m, "ne": ne,
+        "cnt_u": cnt_u.reshape(k, k), "cnt_e": cnt_e.reshape(k, k),
+        "off_u": off_u.reshape(k, k), "off_e": off_e.reshape(k, k),
+        "bin_u": bin_u, "bin_e": bin_e,
+        "src_idx": src_idx[:ne], "dest_ids": dest_ids[:m],
+    }
+
+
+def scatter_gather(g: dict, spr) -> np.ndarray:
+    """Algorithm 3 + Algorithm 4 in FP64 over the bins of :func:`png`:
+    returns y[v] = sum of spr[u] over in-neighbours u of v."""
+    lib = _load()
+    spr = np.ascontiguousarray(spr, dtype=np.float64)
+    y = np.empty(g["n"], dtype=np.float64)
+    src = g["src_idx"] if g["ne"] else np.zeros(1, dtype=np.uint32)
+    dst = g["dest_ids"] if g["m"] else np.zeros(1, dtype=np.uint32)
+    lib.oracle_scatter_gather(g["n"], g["k"], g["bin_u"], g["bin_e"], np.ascontiguousarray(src),
+                              np.ascontiguousarray(dst), spr, y)
+    return y

@@ -1,0 +1,202 @@
+/*
+ * pcpm_oracle.c - plain, slow, sequential FP64 reference for PCPM PageRank.
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the tests, the package's smoke check and the
+ * benchmark's CPU-baseline / reference arm may load this. The CUDA library
+ * shares no code, header, table or helper with this file.
+ *
+ * What it computes, with the passage of Lakhotia, Kannan and Prasanna,
+ * "Accelerating PageRank using Partition-Centric Processing" (arXiv 1709.07122)
+ * that each function follows:
+ *
+ *   oracle_pagerank     Eq. 1 (Sec. 2.1) iterated in the pull direction of
+ *                       Algorithm 1, keeping PR and the scaled vector SPR
+ *                       (Table 1: SPR(v) = PR(v)/|N_o(v)|) apart. Dangling nodes
+ *                       (no out-edges) are a reading: the paper is silent, so
+ *                       either their mass is spread uniformly over all nodes
+ *                       (default) or it leaks, as Eq. 1 literally does.
+ *   oracle_png_count    first scan of the PNG construction (Sec. 3.3): for each
+ *                       source partition p and destination partition p', the
+ *                       number of nodes of p with at least one out-neighbour in
+ *                       p' (|N_i^p(p')|, one update each, Sec. 3.2) and the
+ *                       number of edges from p into p'.
+ *   oracle_png_fill     offsets (Sec. 3.1: a partition's offset into a bin is
+ *                       what all lower-ID partitions write there) and the second
+ *                       PNG scan, which fills the bins: the source node of every
+ *                       update in update-bin order, and the destination IDs with
+ *                       the most significant bit set on the first ID of every
+ *                       message (Sec. 3.2).
+ *   oracle_scatter_gather  Algorithm 3 (scatter over the PNG) followed by the
+ *                       branch-avoiding gather of Algorithm 4, in FP64, giving
+ *                       the sum of SPR over in-neighbours for every node.
+ *
+ * Partitions are index ranges [i*q, (i+1)*q) (Sec. 3.1); the last one may be
+ * shorter. Inputs are a CSR out-adjacency (row_ptr[n+1], col[m]) whose rows are
+ * sorted ascending.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define MSB 0x80000000u
+#define ID_MASK 0x7FFFFFFFu
+
+/* Eq. 1 iterated `iters` times from x0 (uniform 1/n when x0 is NULL).
+ * x_hist, when not NULL, receives (iters+1) vectors of n doubles: x_0 .. x_iters.
+ * resid[i-1] = sum_v |x_i(v) - x_{i-1}(v)|. Returns 0, or -1 on allocation failure. */
+int oracle_pagerank(uint32_t n, const uint32_t* row_ptr, const uint32_t* col, double d,
+                    int dangling_uniform, int iters, const double* x0,
+                    double* x_hist, double* x_out, double* resid) {
+    uint64_t m = row_ptr[n];
+    uint32_t* in_start = (uint32_t*)calloc((size_t)n + 1, sizeof(uint32_t));
+    uint32_t* in_src = (uint32_t*)malloc((size_t)(m ? m : 1) * sizeof(uint32_t));
+    uint32_t* fill = (uint32_t*)malloc((size_t)(n ? n : 1) * sizeof(uint32_t));
+    double* x = (double*)malloc((size_t)(n ? n : 1) * sizeof(double));
+    double* y = (double*)malloc((size_t)(n ? n : 1) * sizeof(double));
+    if (!in_start || !in_src || !fill || !x || !y) {
+        free(in_start); free(in_src); free(fill); free(x); free(y);
+        return -1;
+    }
+
+    /* In-neighbour lists N_i(v), built from the out-adjacency. */
+    for (uint32_t u = 0; u < n; ++u)
+        for (uint32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) in_start[col[e] + 1] += 1;
+    for (uint32_t v = 0; v < n; ++v) in_start[v + 1] += in_start[v];
+    memcpy(fill, in_start, (size_t)n * sizeof(uint32_t));
+    for (uint32_t u = 0; u < n; ++u)
+        for (uint32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) in_src[fill[col[e]]++] = u;
+
+    for (uint32_t v = 0; v < n; ++v) x[v] = x0 ? x0[v] : 1.0 / (double)n;
+    if (x_hist) memcpy(x_hist, x, (size_t)n * sizeof(double));
+
+    for (int it = 1; it <= iters; ++it) {
+        /* Mass sitting on dangling nodes, handed back uniformly. */
+        double dangling = 0.0;
+        if (dangling_uniform)
+            for (uint32_t u = 0; u < n; ++u)
+                if (row_ptr[u + 1] == row_ptr[u]) dangling += x[u];
+        double r = 0.0;
+        for (uint32_t v = 0; v < n; ++v) {
+            double temp = 0.0; /* sum of SPR over in-neighbours (Algorithm 1) */
+            for (uint32_t j = in_start[v]; j < in_start[v + 1]; ++j) {
+                uint32_t u = in_src[j];
+                temp += x[u] / (double)(row_ptr[u + 1] - row_ptr[u]);
+            }
+            y[v] = (1.0 - d) / (double)n + d * (temp + dangling / (double)n);
+            r += fabs(y[v] - x[v]);
+        }
+        if (resid) resid[it - 1] = r;
+        double* t = x; x = y; y = t;
+        if (x_hist) memcpy(x_hist + (size_t)it * n, x, (size_t)n * sizeof(double));
+    }
+    if (x_out) memcpy(x_out, x, (size_t)n * sizeof(double));
+    free(in_start); free(in_src); free(fill); free(x); free(y);
+    return 0;
+}
+
+/* First PNG scan. cnt_u and cnt_e are k*k arrays (row = source partition p,
+ * column = destination partition p'), zeroed here. A node contributes one
+ * update to p' for its first out-edge into p'; the other edges into p' are the
+ * "unused" ones of Sec. 3.2 and only add destination IDs. */
+void oracle_png_count(uint32_t n, const uint32_t* row_ptr, const uint32_t* col, uint32_t q,
+                      uint32_t* cnt_u, uint32_t* cnt_e) {
+    uint32_t k = (n + q - 1) / q;
+    memset(cnt_u, 0, (size_t)k * k * sizeof(uint32_t));
+    memset(cnt_e, 0, (size_t)k * k * sizeof(uint32_t));
+    for (uint32_t p = 0; p < k; ++p) {
+        uint32_t u_end = (p + 1) * (uint64_t)q < n ? (p + 1) * q : n;
+        for (uint32_t u = p * q; u < u_end; ++u) {
+            uint32_t prev_bin = UINT32_MAX;
+            for (uint32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
+                uint32_t bin = col[e] / q;
+                if (bin != prev_bin) { cnt_u[(size_t)p * k + bin] += 1; prev_bin = bin; }
+                cnt_e[(size_t)p * k + bin] += 1;
+            }
+        }
+    }
+}
+
+/* Offsets and the second PNG scan.
+ *   off_u[p][p'] = sum over partitions p~ < p of cnt_u[p~][p']  (Sec. 3.1)
+ *   bin_u[p']    = start of update_bins[p'] in one array holding all bins in
+ *                  partition order; bin_u[k] = |E'|. off_e and bin_e likewise for
+ *                  the destination-ID bins, bin_e[k] = m.
+ *   src_idx[bin_u[p'] + off_u[p][p'] + j] = the j-th node of partition p (in ID
+ *                  order) with an out-neighbour in p': the node whose value the
+ *                  scatter inserts at that position.
+ *   dest_ids       for each such node, its out-neighbours in p' in adjacency
+ *                  order, the first with the MSB set.                        */
+void oracle_png_fill(uint32_t n, const uint32_t* row_ptr, const uint32_t* col, uint32_t q,
+                     const uint32_t* cnt_u, const uint32_t* cnt_e,
+                     uint32_t* off_u, uint32_t* off_e, uint32_t* bin_u, uint32_t* bin_e,
+                     uint32_t* src_idx, uint32_t* dest_ids) {
+    uint32_t k = (n + q - 1) / q;
+    /* Offsets: partitions write to every bin in the order of their IDs. */
+    for (uint32_t pd = 0; pd < k; ++pd) {
+        uint32_t su = 0, se = 0;
+        for (uint32_t p = 0; p < k; ++p) {
+            off_u[(size_t)p * k + pd] = su;
+            off_e[(size_t)p * k + pd] = se;
+            su += cnt_u[(size_t)p * k + pd];
+            se += cnt_e[(size_t)p * k + pd];
+        }
+        bin_u[pd + 1] = su; /* bin sizes for now, prefix-summed below */
+        bin_e[pd + 1] = se;
+    }
+    bin_u[0] = 0;
+    bin_e[0] = 0;
+    for (uint32_t pd = 0; pd < k; ++pd) {
+        bin_u[pd + 1] += bin_u[pd];
+        bin_e[pd + 1] += bin_e[pd];
+    }
+    /* Second scan: write cursors start at each partition's offsets. */
+    uint32_t* cur_u = (uint32_t*)malloc((size_t)k * sizeof(uint32_t));
+    uint32_t* cur_e = (uint32_t*)malloc((size_t)k * sizeof(uint32_t));
+    for (uint32_t p = 0; p < k; ++p) {
+        for (uint32_t pd = 0; pd < k; ++pd) {
+            cur_u[pd] = bin_u[pd] + off_u[(size_t)p * k + pd];
+            cur_e[pd] = bin_e[pd] + off_e[(size_t)p * k + pd];
+        }
+        uint32_t u_end = (p + 1) * (uint64_t)q < n ? (p + 1) * q : n;
+        for (uint32_t u = p * q; u < u_end; ++u) {
+            uint32_t prev_bin = UINT32_MAX;
+            for (uint32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
+                uint32_t v = col[e];
+                uint32_t bin = v / q;
+                if (bin != prev_bin) {
+                    src_idx[cur_u[bin]++] = u;
+                    dest_ids[cur_e[bin]++] = v | MSB;
+                    prev_bin = bin;
+                } else {
+                    dest_ids[cur_e[bin]++] = v;
+                }
+            }
+        }
+    }
+    free(cur_u);
+    free(cur_e);
+}
+
+/* Algorithm 3 then Algorithm 4 over the bins above, in FP64.
+ * update[t] = spr[src_idx[t]]; then for every bin, walk its destination IDs,
+ * advancing the update pointer by the MSB of each ID (branch avoidance). The
+ * pointer starts one before the bin's first update, so the first (flagged) ID
+ * reads the bin's first update. y[v] receives sum over in-neighbours u of spr[u]. */
+void oracle_scatter_gather(uint32_t n, uint32_t k, const uint32_t* bin_u, const uint32_t* bin_e,
+                           const uint32_t* src_idx, const uint32_t* dest_ids,
+                           const double* spr, double* y) {
+    uint32_t ne = bin_u[k];
+    double* update = (double*)malloc((size_t)(ne ? ne : 1) * sizeof(double));
+    for (uint32_t t = 0; t < ne; ++t) update[t] = spr[src_idx[t]]; /* scatter */
+    for (uint32_t v = 0; v < n; ++v) y[v] = 0.0;
+    for (uint32_t p = 0; p < k; ++p) { /* gather */
+        int64_t update_ptr = (int64_t)bin_u[p] - 1;
+        for (uint32_t j = bin_e[p]; j < bin_e[p + 1]; ++j) {
+            uint32_t id = dest_ids[j];
+            update_ptr += id >> 31;
+            y[id & ID_MASK] += update[update_ptr];
+        }
+    }
+    free(update);
+}
