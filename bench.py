@@ -1,0 +1,397 @@
+#!/usr/bin/env python
+"""PCPM PageRank benchmark: per-iteration GTEPS on one GB300 (or N replicas).
+
+Workload (default): RMAT scale 24 (16,777,216 nodes), edge factor 16,
+a, b, c = 0.57, 0.19, 0.19, random node labels, duplicates and self-loops
+removed, uint32 CSR, partition size 32,768 nodes (k = 512), d = 0.85, FP32
+ranks with FP64 reductions. A step is one PCPM iteration: scatter, gather +
+apply, reduce. Inputs (about 3 GB per iteration) are far larger than the
+129 MB L2, so no flush is needed between steps.
+
+Prints one JSON line. `value` = edges / (device time of one iteration) in
+GTEPS, from CUDA events recorded by the library on the launching stream;
+`roofline` covers the kernel with the largest share of the time; `e2e` is the
+same metric through the host-memory entry point pcpm_pagerank_host (H2D copy
+of the CSR from pinned memory, PNG build, 20 iterations, D2H of the ranks);
+`cpu_baseline` times the FP64 CPU oracle on the host on one full iteration of
+the same graph. `--impl reference` times only the oracle (rank 0), each step a
+bounded slice of that iteration.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GTEPS per iter & achieved HBM GB/s; time to L1 residual 1e-7 vs plain FP32"
+PHASES = ("scatter", "gather_apply", "reduce")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400, help="timed iterations")
+    ap.add_argument("--warmup", type=int, default=5, help="untimed iterations before timing (>= 3)")
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--graph", choices=("rmat", "er"), default="rmat")
+    ap.add_argument("--scale", type=int, default=24)
+    ap.add_argument("--edge-factor", type=float, default=16.0)
+    ap.add_argument("--labels", choices=("random", "bfs"), default="random")
+    ap.add_argument("--part-size", type=int, default=32768)
+    ap.add_argument("--d", type=float, default=0.85)
+    ap.add_argument("--seed", type=int, default=1710)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-converge", action="store_true", help="skip the time-to-residual run")
+    ap.add_argument("--ref-budget-s", type=float, default=120.0, help="reference arm: timed seconds target")
+    return ap.parse_args()
+
+
+def workload_name(a):
+    if a.graph == "rmat":
+        g = f"rmat-s{a.scale}-ef{a.edge_factor:g}-abc0.57/0.19/0.19"
+    else:
+        g = f"er-n{1 << a.scale}-deg{a.edge_factor:g}"
+    return f"{g}-{a.labels}-labels-q{a.part_size}"
+
+
+def make_graph(a):
+    import graphgen
+    if a.graph == "rmat":
+        return graphgen.rmat(a.scale, a.edge_factor, 0.57, 0.19, 0.19, seed=a.seed, relabel=a.labels)
+    return graphgen.erdos_renyi(1 << a.scale, a.edge_factor, seed=a.seed, relabel=a.labels)
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling in the background (read-only)."""
+
+    FIELDS = ("index,timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "50", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def stop(self, t0: float, t1: float):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 10:
+                    continue
+                try:
+                    ts = time.mktime(time.strptime(parts[1].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                    frac = float("0." + parts[1].split(".")[1]) if "." in parts[1] else 0.0
+                    rows.append((ts + frac, float(parts[2]), float(parts[3]), parts[6:10]))
+                except (ValueError, IndexError):
+                    continue
+        os.unlink(self.path)
+        inside = [r for r in rows if t0 - 0.06 <= r[0] <= t1 + 0.06]
+        used = inside or rows
+        if not used:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[i] for r in used for i, v in enumerate(r[3]) if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[1] for r in used), "sm_max_mhz": max(r[2] for r in used),
+                "reasons": reasons, "samples": len(used), "samples_in_timed_region": len(inside)}
+
+
+# --------------------------------------------------------------- roofline
+def algorithmic_bytes(info, mode="fused"):
+    """Bytes each kernel must move per launch (4-byte indices and values)."""
+    n, m, ne, k = info["n"], info["num_edges"], info["num_updates"], info["num_partitions"]
+    nchunks = -(-m // 256)
+    gather = 4 * m + 4 * ne + 4 * nchunks + 8 * (k + 1) + 8 * k  # destIDs, updates, chunk bases, bins, hubs
+    apply = 12 * n  # PR_old and 1/outdeg read, PR' written
+    scatter = 8 * ne + 8 * k * k  # srcIdx read + update write, segment starts/counts
+    if mode == "fused":
+        return {"scatter": 0, "gather_apply": gather + apply + scatter, "reduce": 16 * k}
+    return {"scatter": scatter + 8 * n, "gather_apply": gather + apply, "reduce": 16 * k}
+
+
+def eq5_bytes(info):
+    """The paper's PCPM communication model, Eq. 5, with d_i = d_v = 4."""
+    n, m, ne, k = info["n"], info["num_edges"], info["num_updates"], info["num_partitions"]
+    r = m / ne if ne else 1.0
+    return m * (4 * (1 + 1 / r) + 8 / r) + k * k * 4 + 2 * n * 4
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def recorded_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from a committed ncu summary, valid only while the
+    kernel source is unchanged since the capture (sha256 recorded there)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f)
+    for name, sha in rec.get("source_sha256", {}).items():
+        src = os.path.join(ROOT, "paper_1709_07122_gb300", "csrc", name)
+        if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest() != sha:
+            return None
+    entry = rec.get("kernels", {}).get(kernel)
+    if not entry or rec.get("workload") != workload:
+        return None
+    return entry.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------- CPU side
+def cpu_oracle_iteration(rp, col, d, slices=16):
+    """One full FP64 oracle iteration on the host, as `slices` destination
+    ranges; returns (GTEPS, seconds, edges)."""
+    import oracle
+    pull = oracle.Pull(rp, col)
+    n = pull.n
+    x = np.full(n, 1.0 / n)
+    y = np.empty(n)
+    t0 = time.perf_counter()
+    for i in range(slices):
+        pull.step(x, y, d, v_begin=n * i // slices, v_end=n * (i + 1) // slices)
+    dt = time.perf_counter() - t0
+    m = int(rp[-1])
+    return m / dt / 1e9, dt, m
+
+
+def run_reference(a):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    if a.warmup < 0 or a.steps < 1:
+        raise SystemExit("steps must be >= 1")
+    rp, col = make_graph(a)
+    n, m = rp.size - 1, int(rp[-1])
+    pull = oracle.Pull(rp, col)
+    x = np.full(n, 1.0 / n)
+    y = np.empty(n)
+    # Size each step so the whole run stays near the time budget.
+    probe = max(1, n // 256)
+    t0 = time.perf_counter()
+    pull.step(x, y, a.d, v_begin=0, v_end=probe)
+    per_edge = (time.perf_counter() - t0) / max(1, pull.in_edges(0, probe))
+    budget_edges = a.ref_budget_s / max(per_edge, 1e-12) / (a.steps + a.warmup)
+    width = int(min(n, max(1024, budget_edges / max(m / n, 1e-9))))
+    starts = [(i * width) % n for i in range(a.steps + a.warmup)]
+    for s in starts[:a.warmup]:
+        pull.step(x, y, a.d, v_begin=s, v_end=min(n, s + width))
+    edges = 0
+    t0 = time.perf_counter()
+    for s in starts[a.warmup:]:
+        e = min(n, s + width)
+        pull.step(x, y, a.d, v_begin=s, v_end=e)
+        edges += pull.in_edges(s, e)
+    dt = time.perf_counter() - t0
+    gteps = edges / dt / 1e9
+    sample = (f"FP64 pull step (Eq. 1) of the oracle over {a.steps} slices of {width} destination nodes "
+              f"of the full graph ({edges} in-edges in total), one thread")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": gteps, "unit": "GTEPS", "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": dt * 1e3 / a.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(a), "n": n, "m": m, "part_size": a.part_size, "d": a.d},
+        "cpu_baseline": {"value": gteps, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": gteps, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU side
+def run_ours(a):
+    import torch
+    import paper_1709_07122_gb300 as pcpm
+
+    rank, world, local = dist_env()
+    if a.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    pcpm.build()
+    pcpm.lib()
+    rp, col = make_graph(a)
+    n, m = rp.size - 1, int(rp[-1])
+    stream = torch.cuda.current_stream()
+
+    d_rp, d_col = pcpm.to_device_csr(rp, col)
+    torch.cuda.synchronize()
+    b0 = time.perf_counter()
+    g = pcpm.PNG(d_rp, d_col, a.part_size)
+    build_ms = (time.perf_counter() - b0) * 1e3
+    del d_rp, d_col
+    info = g.info
+
+    g.reset()
+    g.iterate(a.d, a.warmup, sync=False)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local).start()
+    time.sleep(0.2)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.time()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    kms = g.iterate_timed(a.d, a.steps)  # per-kernel CUDA events on `stream`
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    barrier()
+    clocks = sampler.stop(t0, t1)
+    bracket_ms = ev0.elapsed_time(ev1)
+    iter_ms = max_over_ranks(kms["span"] / a.steps)
+    value = world * m / (iter_ms * 1e-3) / 1e9
+
+    # roofline of the kernel with the largest share of the time
+    ab = algorithmic_bytes(info, "fused")
+    dom = max(PHASES, key=lambda p: kms[p])
+    dom_ms = kms[dom] / a.steps
+    peak, peak_src = measured_peaks()
+    achieved = ab[dom] / (dom_ms * 1e-3) / 1e9
+    wl = workload_name(a)
+    roofline = {"bound": "hbm", "kernel": dom + " (fused: gather, apply, next scatter)", "achieved": achieved,
+                "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
+                "traffic": recorded_traffic(dom, wl), "algorithmic_bytes": ab[dom]}
+    iter_bytes = sum(ab.values())
+
+    # The paper's two phases as separate kernels (Table execTime analogue).
+    tp_steps = max(3, min(a.steps, 50))
+    g.iterate(a.d, 3, sync=False, mode="two_phase")
+    tms = g.iterate_timed(a.d, tp_steps, mode="two_phase")
+    tab = algorithmic_bytes(info, "two_phase")
+    two_phase = {"iters": tp_steps, "ms_per_iter": tms["span"] / tp_steps,
+                 "gteps": m / (tms["span"] / tp_steps * 1e-3) / 1e9}
+    for ph in PHASES:
+        ms = tms[ph] / tp_steps
+        two_phase[ph] = {"ms": ms, "gbs": tab[ph] / (ms * 1e-3) / 1e9 if ms > 0 else None,
+                         "frac": tab[ph] / (ms * 1e-3) / 1e9 / peak if ms > 0 else None}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": iter_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl, "n": n, "m": m, "part_size": a.part_size, "k": info["num_partitions"],
+                   "num_updates": info["num_updates"], "r": info["compression_ratio"], "d": a.d,
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "no flush: each iteration moves ~%.2f GB, > 129 MB L2" % (iter_bytes / 1e9)},
+        "roofline": roofline,
+        "phase_ms_per_iter": {p: kms[p] / a.steps for p in PHASES},
+        "hbm_gbs_achieved": iter_bytes / (iter_ms * 1e-3) / 1e9,
+        "bytes_per_edge": {"algorithmic": iter_bytes / m, "eq5_model": eq5_bytes(info) / m},
+        "two_phase": two_phase,
+        "bracket_ms_per_step": bracket_ms / a.steps,
+        "build_ms": build_ms,
+        "clocks": clocks,
+        "gpu_launches": 2 * a.steps,
+    }
+
+    if not a.no_converge:
+        torch.cuda.synchronize()
+        c0 = time.perf_counter()
+        _, its, res = g.pagerank(a.d, max_iters=300, tol=1e-7)
+        torch.cuda.synchronize()
+        out["time_to_residual"] = {"tol": 1e-7, "iters": its, "ms": (time.perf_counter() - c0) * 1e3,
+                                   "final_residual": res, "reached": res < 1e-7, "start": "uniform"}
+    g.close()
+
+    if not a.no_e2e:
+        e2e_iters = 20
+        prp = torch.empty(n + 1, dtype=torch.int32, pin_memory=True)
+        pcol = torch.empty(max(m, 1), dtype=torch.int32, pin_memory=True)
+        pout = torch.empty(n, dtype=torch.float32, pin_memory=True)
+        prp.numpy()[:] = rp.view(np.int32)
+        pcol.numpy()[:m] = col.view(np.int32)
+        hrp, hcol, hout = prp.numpy().view(np.uint32), pcol.numpy().view(np.uint32)[:m], pout.numpy()
+        pcpm.pagerank_host(hrp, hcol, a.part_size, a.d, 3, pr_out=hout)  # warm-up call
+        barrier()
+        walls = []
+        for _ in range(3):
+            e0 = time.perf_counter()
+            pcpm.pagerank_host(hrp, hcol, a.part_size, a.d, e2e_iters, pr_out=hout)
+            walls.append(time.perf_counter() - e0)
+        wall = max_over_ranks(statistics.median(walls))
+        out["e2e"] = {"value": world * m * e2e_iters / wall / 1e9, "unit": "GTEPS",
+                      "h2d_bytes_per_step": (n + 1 + m) * 4 / e2e_iters, "d2h_bytes_per_step": n * 4 / e2e_iters,
+                      "call": "pcpm_pagerank_host: H2D CSR (pinned) + PNG build + %d iterations + D2H ranks"
+                              % e2e_iters, "wall_ms_per_call": wall * 1e3}
+
+    if rank == 0 and not a.no_cpu_baseline:
+        gt, dt, _ = cpu_oracle_iteration(rp, col, a.d)
+        out["cpu_baseline"] = {"value": gt, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                               "sample": "one full FP64 pull iteration (Eq. 1) of the same graph as 16 "
+                                         "destination-range steps, %.1f s, single thread" % dt}
+    if dist is not None:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    return 0
+
+
+def main():
+    a = parse_args()
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_ours(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

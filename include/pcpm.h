@@ -1,0 +1,205 @@
+/*
+ * pcpm.h - C ABI of the GB300 (sm_103a) Partition-Centric PageRank library.
+ *
+ * Method: Lakhotia, Kannan, Prasanna, "Accelerating PageRank using
+ * Partition-Centric Processing" (arXiv 1709.07122). One PageRank iteration is
+ * Eq. 1 of Sec. 2.1,
+ *     PR_{i+1}(v) = (1-d)/|V| + d * sum_{u in N_i(v)} PR_i(u)/|N_o(u)|,
+ * computed as the sparse product A^T * SPR of Eq. 2 (SPR(u) = PR(u)/|N_o(u)|,
+ * Table 1) in two phases over index-range partitions of q nodes (Sec. 3.1):
+ *   scatter (Algorithm 3): every node sends at most one update to each
+ *     destination partition (Sec. 3.2), laid out by the Partition-Node Graph
+ *     (PNG, Sec. 3.3) into contiguous per-partition bins at static offsets;
+ *   gather (Algorithm 4) + apply (Algorithm 2, apply loop): every destination
+ *     partition accumulates its bin; a destination ID with its most
+ *     significant bit set starts the next update's message.
+ *
+ * Conventions for every entry point:
+ *   - Device pointers are CUDA global-memory addresses on the current device;
+ *     host pointers are ordinary CPU memory. Each argument says which.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream). Work is enqueued on it; calls return after enqueueing unless the
+ *     entry point says it synchronises.
+ *   - Return value: PCPM_OK (0), a positive informational code, or a negative
+ *     error code (see pcpm_strerror). On error no output argument is written
+ *     and no memory is leaked. Invalid arguments are rejected on the host
+ *     before anything is launched.
+ *   - A pcpm_png handle owns its device memory and one solver state; calls on
+ *     the same handle must not run concurrently.
+ *   - Dangling nodes (no out-edges): the paper does not say what happens to
+ *     their rank. By default their mass is spread uniformly over all nodes
+ *     (ranks keep summing to 1); PCPM_DANGLING_LEAK drops it, as Eq. 1 read
+ *     literally does.
+ */
+#ifndef PCPM_H
+#define PCPM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define PCPM_OK 0
+#define PCPM_NOT_CONVERGED 1   /* tol > 0 and max_iters reached first */
+#define PCPM_EINVAL (-1)       /* bad argument (null, size or range) */
+#define PCPM_ECUDA (-2)        /* a CUDA runtime call failed */
+#define PCPM_ENOMEM (-3)       /* device or host allocation failed */
+#define PCPM_ETIMEOUT (-4)     /* a bounded device-side wait gave up */
+#define PCPM_EDEVICE (-5)      /* a device-side consistency check failed */
+#define PCPM_EBADGRAPH (-6)    /* CSR invalid: column >= n or a row not sorted */
+
+/* ------------------------------------------------------------------ limits */
+/* Node IDs keep their most significant bit free for the message flag
+ * (Sec. 3.2), so n < 2^31. */
+#define PCPM_MAX_NODES 0x7FFFFFFFu
+/* One partition's FP32 accumulator lives in shared memory (<= 227 KB/CTA). */
+#define PCPM_MAX_PART_SIZE 32768u
+/* Bounded by the builder's per-warp counting tables in shared memory. */
+#define PCPM_MAX_PARTITIONS 8192u
+
+/* ------------------------------------------------------------------- flags */
+#define PCPM_DANGLING_LEAK 0x1u /* drop dangling mass instead of spreading it */
+/* Run every iteration as the paper's two phases: a scatter kernel (Algorithm
+ * 3), then a gather + apply kernel (Algorithm 4 and the apply loop). Without
+ * this flag an iteration is one fused kernel per partition: gather, apply, and
+ * the scatter of that partition's new values into a second set of update bins
+ * for the next iteration (a standalone scatter runs first when those bins do
+ * not yet hold the current ranks). Both compute the same iteration. */
+#define PCPM_TWO_PHASE 0x2u
+
+/* Kernels timed by pcpm_iterate_timed, in this order. In fused mode the
+ * standalone scatter runs only when needed and the gather phase includes the
+ * next iteration's scatter. */
+#define PCPM_PHASE_SCATTER 0
+#define PCPM_PHASE_GATHER_APPLY 1
+#define PCPM_PHASE_REDUCE 2
+#define PCPM_NUM_PHASES 3
+
+typedef struct pcpm_png pcpm_png; /* opaque, device-resident */
+
+typedef struct pcpm_png_info {
+    uint32_t n;               /* |V| */
+    uint32_t part_size;       /* q, nodes per partition (Sec. 3.1) */
+    uint32_t num_partitions;  /* k = ceil(n / q) */
+    uint32_t reserved;
+    uint64_t num_edges;       /* m = |E| */
+    uint64_t num_updates;     /* |E'|: edges of the PNG = updates per iteration (Sec. 3.3) */
+    double compression_ratio; /* r = |E| / |E'| (Sec. 4, Table params) */
+    uint64_t device_bytes;    /* device memory held by the handle */
+    int32_t iterations_done;  /* iterations applied since the last reset */
+    int32_t reserved2;
+} pcpm_png_info;
+
+/* Builds the Partition-Node Graph of Sec. 3.3 from a CSR out-adjacency:
+ * partitions of `part_size` consecutive node IDs (Sec. 3.1); for every
+ * (source partition p, destination partition p') the number of nodes of p with
+ * an out-neighbour in p' (one update each, Sec. 3.2) and the number of edges
+ * p -> p'; the write offsets of Sec. 3.1 (each partition writes into a bin after
+ * all lower-ID partitions); and the bins themselves: in update order, the
+ * source node of every update, and in destination-ID order, the out-neighbours
+ * of that node in p' with the first one's MSB set (Sec. 3.2). Within a bin,
+ * source partitions appear in ID order, nodes in ID order and destinations in
+ * adjacency order.
+ *
+ *   row_ptr  device, uint32[n+1]; row_ptr[0] = 0, non-decreasing, row_ptr[n] = m.
+ *   col_idx  device, uint32[m]; out-neighbours of node u in
+ *            col_idx[row_ptr[u] .. row_ptr[u+1]), each < n, sorted
+ *            non-decreasing within the row. Duplicates and self-loops are
+ *            kept as ordinary edges. Both arrays are only read, and only
+ *            during this call.
+ *   n        1 <= n <= PCPM_MAX_NODES.    m  < 2^32 and equal to row_ptr[n].
+ *   part_size  1 <= q <= PCPM_MAX_PART_SIZE and ceil(n/q) <= PCPM_MAX_PARTITIONS.
+ *   out      host; receives the new handle (free with pcpm_free).
+ * Synchronises `stream`. Returns PCPM_EBADGRAPH, and no handle, if a column is
+ * >= n or a row is not sorted; PCPM_EINVAL if row_ptr[n] != m. */
+int pcpm_build(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t n, uint64_t m,
+               uint32_t part_size, void* stream, pcpm_png** out);
+
+/* Releases the handle and all its device memory. NULL is a no-op. Waits for
+ * work the library enqueued on the handle's last stream. */
+void pcpm_free(pcpm_png* png);
+
+/* Sizes of the handle (host struct). */
+int pcpm_png_get_info(const pcpm_png* png, pcpm_png_info* info);
+
+/* Copies the PNG to host buffers; any pointer may be NULL to skip it.
+ * Synchronises. Layout (k = num_partitions, row = source partition p,
+ * column = destination partition p'):
+ *   cnt_u[k*k]  updates p -> p'            cnt_e[k*k]  edges p -> p'
+ *   off_u[k*k]  offset of p in update_bins[p'] (Sec. 3.1)  off_e[k*k] same for IDs
+ *   bin_u[k+1]  start of update_bins[p'] in the concatenated bins; bin_u[k] = |E'|
+ *   bin_e[k+1]  start of destID_bins[p'];                      bin_e[k] = m
+ *   src_idx[|E'|]  source node of each update, in bin order
+ *   dest_ids[m]    destination IDs in bin order, MSB = first of a message */
+int pcpm_png_export(const pcpm_png* png, uint32_t* cnt_u, uint32_t* cnt_e, uint32_t* off_u,
+                    uint32_t* off_e, uint32_t* bin_u, uint32_t* bin_e, uint32_t* src_idx,
+                    uint32_t* dest_ids);
+
+/* Starts a new solve: PR_0 = pr_init (device, float[n], read during the call;
+ * NULL = uniform 1/n), SPR_0 = PR_0/|N_o| (0 for dangling nodes), and the
+ * dangling mass of PR_0. Resets iterations_done to 0. */
+int pcpm_reset(pcpm_png* png, const float* pr_init, void* stream);
+
+/* Applies up to `iters` iterations of Eq. 1 to the handle's current ranks,
+ * each one a scatter (Algorithm 3), a gather + apply (Algorithm 4 and the apply
+ * loop of Algorithm 2) and an FP64 reduction of the L1 change
+ * sum_v |PR_{i+1}(v) - PR_i(v)| and of the next dangling mass.
+ *   d     damping factor, 0 <= d < 1.      iters >= 0.
+ *   tol   > 0: stop after the first iteration whose L1 change is < tol;
+ *         <= 0: run exactly `iters` iterations.
+ *   flags PCPM_DANGLING_LEAK and/or PCPM_TWO_PHASE, or 0.
+ *   iters_run, last_residual  host, nullable: iterations applied by this call
+ *         and the L1 change of the last one (0 if none). If either is
+ *         requested, or tol > 0, the call synchronises.
+ * Returns PCPM_NOT_CONVERGED if tol > 0 was not reached. */
+int pcpm_iterate(pcpm_png* png, float d, int iters, double tol, uint32_t flags, int* iters_run,
+                 double* last_residual, void* stream);
+
+/* Same as pcpm_iterate with tol <= 0, and also records CUDA events around
+ * every kernel on `stream`. kernel_ms (host, PCPM_NUM_PHASES + 1 floats)
+ * receives the total milliseconds spent in each phase over the `iters`
+ * iterations, then the span from the event before the first kernel to the
+ * event after the last one. Synchronises. */
+int pcpm_iterate_timed(pcpm_png* png, float d, int iters, uint32_t flags, float* kernel_ms,
+                       void* stream);
+
+/* Copies the current ranks PR_i to pr_out (device, float[n], caller-owned). */
+int pcpm_ranks(const pcpm_png* png, float* pr_out, void* stream);
+
+/* L1 changes of the iterations since the last reset (host double[max_count]);
+ * writes min(max_count, iterations_done) values and returns that count (or a
+ * negative error). Synchronises. */
+int pcpm_residual_history(const pcpm_png* png, double* out, int max_count);
+
+/* pcpm_reset + pcpm_iterate + pcpm_ranks. pr_out (device, float[n]) receives
+ * PR after the last iteration; pr_init as in pcpm_reset. Synchronises when
+ * tol > 0 or when iters_run / final_residual are requested. */
+int pcpm_pagerank(pcpm_png* png, float d, int max_iters, double tol, uint32_t flags,
+                  const float* pr_init, float* pr_out, int* iters_run, double* final_residual,
+                  void* stream);
+
+/* End-to-end solve from host memory: copies the CSR (host row_ptr[n+1],
+ * col_idx[m], rules of pcpm_build) to the device, builds the PNG, runs
+ * pcpm_pagerank with a uniform start and copies the ranks to pr_out (host,
+ * float[n]). Allocates and frees its own device memory; synchronises. */
+int pcpm_pagerank_host(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t n, uint64_t m,
+                       uint32_t part_size, float d, int max_iters, double tol, uint32_t flags,
+                       float* pr_out, int* iters_run, double* final_residual);
+
+/* Test hooks. pcpm_scatter_only runs one scatter (Algorithm 3) of the current
+ * ranks into the current update bins without advancing the solve.
+ * pcpm_export_state copies the current state to host buffers (nullable):
+ * pr[n], spr[n] (= pr/outdeg, recomputed on the device), updates[|E'|] (the
+ * current update bins, bin order) and the dangling mass of pr. Synchronises. */
+int pcpm_scatter_only(pcpm_png* png, void* stream);
+int pcpm_export_state(const pcpm_png* png, float* pr, float* spr, float* updates, double* dangling);
+
+/* Message for a status code (static string). */
+const char* pcpm_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PCPM_H */

@@ -10,6 +10,8 @@ passages they follow:
 
 * :func:`pagerank` - Eq. 1 / Algorithm 1 (pull direction), plus the dangling
   reading (uniform redistribution by default, or leak).
+* :class:`Pull` - the same step over a range of destination nodes, with the
+  in-neighbour lists built once (used to time bounded samples).
 * :func:`png` - Partition-Node Graph of Sec. 3.3: per (source partition,
   destination partition) update and edge counts, the write offsets of Sec. 3.1,
   and the bins in canonical order (source partitions in ID order, nodes in ID
@@ -57,6 +59,13 @@ def _load():
             lib.oracle_pagerank.argtypes = [ctypes.c_uint32, _u32p, _u32p, ctypes.c_double, ctypes.c_int,
                                             ctypes.c_int, vp, vp, vp, vp]
             lib.oracle_pagerank.restype = ctypes.c_int
+            lib.oracle_in_adjacency.argtypes = [ctypes.c_uint32, _u32p, _u32p, _u32p, _u32p]
+            lib.oracle_in_adjacency.restype = None
+            lib.oracle_dangling_mass.argtypes = [ctypes.c_uint32, _u32p, _f64p]
+            lib.oracle_dangling_mass.restype = ctypes.c_double
+            lib.oracle_pull_step.argtypes = [ctypes.c_uint32, _u32p, _u32p, _u32p, ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_uint32, ctypes.c_uint32, _f64p, _f64p]
+            lib.oracle_pull_step.restype = ctypes.c_double
             lib.oracle_png_count.argtypes = [ctypes.c_uint32, _u32p, _u32p, ctypes.c_uint32, _u32p, _u32p]
             lib.oracle_png_count.restype = None
             lib.oracle_png_fill.argtypes = [ctypes.c_uint32, _u32p, _u32p, ctypes.c_uint32, _u32p, _u32p,
@@ -106,6 +115,34 @@ def pagerank(row_ptr, col, d: float = 0.85, iters: int = 20, x0=None, dangling: 
     if history:
         out["hist"] = hist
     return out
+
+
+class Pull:
+    """In-neighbour lists of a graph, for single Eq. 1 steps over node ranges."""
+
+    def __init__(self, row_ptr, col):
+        lib = _load()
+        self.row_ptr, self.col = _csr(row_ptr, col)
+        self.n = self.row_ptr.size - 1
+        m = int(self.row_ptr[self.n])
+        self.in_start = np.empty(self.n + 1, dtype=np.uint32)
+        self.in_src = np.empty(max(m, 1), dtype=np.uint32)
+        lib.oracle_in_adjacency(self.n, self.row_ptr, self.col, self.in_start, self.in_src)
+
+    def in_edges(self, v_begin: int, v_end: int) -> int:
+        return int(self.in_start[v_end]) - int(self.in_start[v_begin])
+
+    def dangling_mass(self, x) -> float:
+        return _load().oracle_dangling_mass(self.n, self.row_ptr, np.ascontiguousarray(x, dtype=np.float64))
+
+    def step(self, x, y, d: float = 0.85, dangling: str = "uniform", v_begin: int = 0, v_end=None) -> float:
+        """y[v] = Eq. 1 applied to x for v in [v_begin, v_end); returns the L1
+        change over that range. x and y are float64 arrays of length n."""
+        lib = _load()
+        v_end = self.n if v_end is None else v_end
+        dmass = self.dangling_mass(x) if dangling == "uniform" else 0.0
+        return lib.oracle_pull_step(self.n, self.row_ptr, self.in_start, self.in_src, float(d), dmass,
+                                    int(v_begin), int(v_end), x, y)
 
 
 def png(row_ptr, col, q: int):

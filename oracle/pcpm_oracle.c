@@ -9,12 +9,14 @@
  * "Accelerating PageRank using Partition-Centric Processing" (arXiv 1709.07122)
  * that each function follows:
  *
- *   oracle_pagerank     Eq. 1 (Sec. 2.1) iterated in the pull direction of
- *                       Algorithm 1, keeping PR and the scaled vector SPR
- *                       (Table 1: SPR(v) = PR(v)/|N_o(v)|) apart. Dangling nodes
- *                       (no out-edges) are a reading: the paper is silent, so
- *                       either their mass is spread uniformly over all nodes
- *                       (default) or it leaks, as Eq. 1 literally does.
+ *   oracle_pull_step    Eq. 1 (Sec. 2.1) applied in the pull direction of
+ *                       Algorithm 1 to a range of destination nodes, keeping
+ *                       PR and the scaled vector SPR (Table 1: SPR(v) =
+ *                       PR(v)/|N_o(v)|) apart. Dangling nodes (no out-edges)
+ *                       are a reading: the paper is silent, so either their
+ *                       mass is spread uniformly over all nodes (default) or
+ *                       it leaks, as Eq. 1 literally does.
+ *   oracle_pagerank     oracle_pull_step over all nodes, iterated.
  *   oracle_png_count    first scan of the PNG construction (Sec. 3.3): for each
  *                       source partition p and destination partition p', the
  *                       number of nodes of p with at least one out-neighbour in
@@ -42,6 +44,51 @@
 #define MSB 0x80000000u
 #define ID_MASK 0x7FFFFFFFu
 
+/* In-neighbour lists N_i(v) from the out-adjacency: the sources of the edges
+ * into v are in_src[in_start[v] .. in_start[v+1]), in increasing source order.
+ * in_start has n+1 entries, in_src m. */
+void oracle_in_adjacency(uint32_t n, const uint32_t* row_ptr, const uint32_t* col,
+                         uint32_t* in_start, uint32_t* in_src) {
+    memset(in_start, 0, ((size_t)n + 1) * sizeof(uint32_t));
+    for (uint32_t u = 0; u < n; ++u)
+        for (uint32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) in_start[col[e] + 1] += 1;
+    for (uint32_t v = 0; v < n; ++v) in_start[v + 1] += in_start[v];
+    uint32_t* fill = (uint32_t*)malloc((size_t)(n ? n : 1) * sizeof(uint32_t));
+    memcpy(fill, in_start, (size_t)n * sizeof(uint32_t));
+    for (uint32_t u = 0; u < n; ++u)
+        for (uint32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) in_src[fill[col[e]]++] = u;
+    free(fill);
+}
+
+/* Mass sitting on dangling nodes (no out-edges). */
+double oracle_dangling_mass(uint32_t n, const uint32_t* row_ptr, const double* x) {
+    double dangling = 0.0;
+    for (uint32_t u = 0; u < n; ++u)
+        if (row_ptr[u + 1] == row_ptr[u]) dangling += x[u];
+    return dangling;
+}
+
+/* One application of Eq. 1 (pull direction, Algorithm 1) to the destination
+ * nodes v in [v_begin, v_end):
+ *   y[v] = (1-d)/n + d * (sum_{u in N_i(v)} x[u]/|N_o(u)| + dangling/n).
+ * `dangling` is the mass handed back uniformly (0 for the leaking reading).
+ * Returns sum over the range of |y[v] - x[v]|. */
+double oracle_pull_step(uint32_t n, const uint32_t* row_ptr, const uint32_t* in_start,
+                        const uint32_t* in_src, double d, double dangling,
+                        uint32_t v_begin, uint32_t v_end, const double* x, double* y) {
+    double r = 0.0;
+    for (uint32_t v = v_begin; v < v_end; ++v) {
+        double temp = 0.0; /* sum of SPR over in-neighbours */
+        for (uint32_t j = in_start[v]; j < in_start[v + 1]; ++j) {
+            uint32_t u = in_src[j];
+            temp += x[u] / (double)(row_ptr[u + 1] - row_ptr[u]);
+        }
+        y[v] = (1.0 - d) / (double)n + d * (temp + dangling / (double)n);
+        r += fabs(y[v] - x[v]);
+    }
+    return r;
+}
+
 /* Eq. 1 iterated `iters` times from x0 (uniform 1/n when x0 is NULL).
  * x_hist, when not NULL, receives (iters+1) vectors of n doubles: x_0 .. x_iters.
  * resid[i-1] = sum_v |x_i(v) - x_{i-1}(v)|. Returns 0, or -1 on allocation failure. */
@@ -49,49 +96,26 @@ int oracle_pagerank(uint32_t n, const uint32_t* row_ptr, const uint32_t* col, do
                     int dangling_uniform, int iters, const double* x0,
                     double* x_hist, double* x_out, double* resid) {
     uint64_t m = row_ptr[n];
-    uint32_t* in_start = (uint32_t*)calloc((size_t)n + 1, sizeof(uint32_t));
+    uint32_t* in_start = (uint32_t*)malloc(((size_t)n + 1) * sizeof(uint32_t));
     uint32_t* in_src = (uint32_t*)malloc((size_t)(m ? m : 1) * sizeof(uint32_t));
-    uint32_t* fill = (uint32_t*)malloc((size_t)(n ? n : 1) * sizeof(uint32_t));
     double* x = (double*)malloc((size_t)(n ? n : 1) * sizeof(double));
     double* y = (double*)malloc((size_t)(n ? n : 1) * sizeof(double));
-    if (!in_start || !in_src || !fill || !x || !y) {
-        free(in_start); free(in_src); free(fill); free(x); free(y);
+    if (!in_start || !in_src || !x || !y) {
+        free(in_start); free(in_src); free(x); free(y);
         return -1;
     }
-
-    /* In-neighbour lists N_i(v), built from the out-adjacency. */
-    for (uint32_t u = 0; u < n; ++u)
-        for (uint32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) in_start[col[e] + 1] += 1;
-    for (uint32_t v = 0; v < n; ++v) in_start[v + 1] += in_start[v];
-    memcpy(fill, in_start, (size_t)n * sizeof(uint32_t));
-    for (uint32_t u = 0; u < n; ++u)
-        for (uint32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) in_src[fill[col[e]]++] = u;
-
+    oracle_in_adjacency(n, row_ptr, col, in_start, in_src);
     for (uint32_t v = 0; v < n; ++v) x[v] = x0 ? x0[v] : 1.0 / (double)n;
     if (x_hist) memcpy(x_hist, x, (size_t)n * sizeof(double));
-
     for (int it = 1; it <= iters; ++it) {
-        /* Mass sitting on dangling nodes, handed back uniformly. */
-        double dangling = 0.0;
-        if (dangling_uniform)
-            for (uint32_t u = 0; u < n; ++u)
-                if (row_ptr[u + 1] == row_ptr[u]) dangling += x[u];
-        double r = 0.0;
-        for (uint32_t v = 0; v < n; ++v) {
-            double temp = 0.0; /* sum of SPR over in-neighbours (Algorithm 1) */
-            for (uint32_t j = in_start[v]; j < in_start[v + 1]; ++j) {
-                uint32_t u = in_src[j];
-                temp += x[u] / (double)(row_ptr[u + 1] - row_ptr[u]);
-            }
-            y[v] = (1.0 - d) / (double)n + d * (temp + dangling / (double)n);
-            r += fabs(y[v] - x[v]);
-        }
+        double dangling = dangling_uniform ? oracle_dangling_mass(n, row_ptr, x) : 0.0;
+        double r = oracle_pull_step(n, row_ptr, in_start, in_src, d, dangling, 0, n, x, y);
         if (resid) resid[it - 1] = r;
         double* t = x; x = y; y = t;
         if (x_hist) memcpy(x_hist + (size_t)it * n, x, (size_t)n * sizeof(double));
     }
     if (x_out) memcpy(x_out, x, (size_t)n * sizeof(double));
-    free(in_start); free(in_src); free(fill); free(x); free(y);
+    free(in_start); free(in_src); free(x); free(y);
     return 0;
 }
 

@@ -1,0 +1,277 @@
+"""Partition-Centric PageRank (PCPM, arXiv 1709.07122) on GB300 (sm_103a).
+
+Thin Python binding over the C ABI of ``include/pcpm.h`` (``libpcpm.so``,
+built in-tree by :func:`build`). Everything here is argument marshalling:
+PyTorch provides device memory and the current CUDA stream; every step of the
+method (PNG construction, scatter, gather/apply, reductions) runs in the
+library's own kernels. There is no CPU fallback: if the library is missing the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+__all__ = ["build", "lib", "PNG", "pagerank_host", "PcpmError", "DANGLING_LEAK", "TWO_PHASE"]
+
+PCPM_OK = 0
+PCPM_NOT_CONVERGED = 1
+DANGLING_LEAK = 0x1
+TWO_PHASE = 0x2
+NUM_PHASES = 3
+PHASES = ("scatter", "gather_apply", "reduce")
+
+_lib = None
+_lock = threading.Lock()
+
+
+class PcpmError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        msg = lib().pcpm_strerror(code).decode() if _lib is not None else str(code)
+        super().__init__(f"{where} failed: {msg} (status {code})")
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint32), ("part_size", ctypes.c_uint32), ("num_partitions", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("num_edges", ctypes.c_uint64), ("num_updates", ctypes.c_uint64),
+                ("compression_ratio", ctypes.c_double), ("device_bytes", ctypes.c_uint64),
+                ("iterations_done", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compiles libpcpm.so for sm_103a (no-op when up to date)."""
+    return _build.build(force=force, verbose=verbose)
+
+
+def lib(path: str | None = None):
+    """Loads libpcpm.so and declares its signatures; raises if it is absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = path or _build.LIB_PATH
+            if not os.path.exists(path):
+                raise RuntimeError(f"CUDA library not built: {path} is missing (run __graft_entry__.build())")
+            L = ctypes.CDLL(path)
+            vp, u32, u64, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+            f32, f64 = ctypes.c_float, ctypes.c_double
+            pi, pd, pf = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float)
+            sig = {
+                "pcpm_build": (i32, [vp, vp, u32, u64, u32, vp, ctypes.POINTER(vp)]),
+                "pcpm_free": (None, [vp]),
+                "pcpm_png_get_info": (i32, [vp, ctypes.POINTER(_Info)]),
+                "pcpm_png_export": (i32, [vp] + [vp] * 8),
+                "pcpm_reset": (i32, [vp, vp, vp]),
+                "pcpm_iterate": (i32, [vp, f32, i32, f64, u32, pi, pd, vp]),
+                "pcpm_iterate_timed": (i32, [vp, f32, i32, u32, pf, vp]),
+                "pcpm_ranks": (i32, [vp, vp, vp]),
+                "pcpm_residual_history": (i32, [vp, vp, i32]),
+                "pcpm_pagerank": (i32, [vp, f32, i32, f64, u32, vp, vp, pi, pd, vp]),
+                "pcpm_pagerank_host": (i32, [vp, vp, u32, u64, u32, f32, i32, f64, u32, vp, pi, pd]),
+                "pcpm_scatter_only": (i32, [vp, vp]),
+                "pcpm_export_state": (i32, [vp, vp, vp, vp, pd]),
+                "pcpm_strerror": (ctypes.c_char_p, [i32]),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(code: int, where: str, allow=(PCPM_OK,)) -> int:
+    if code not in allow:
+        raise PcpmError(code, where)
+    return code
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_u32(t):
+    """A CUDA tensor of 32-bit integers (int32 or uint32) viewed for the ABI."""
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda):
+        raise TypeError("expected a CUDA tensor")
+    if t.dtype not in (torch.int32, getattr(torch, "uint32", torch.int32)):
+        raise TypeError("expected a 32-bit integer tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _flags(dangling: str, mode: str = "fused") -> int:
+    if dangling not in ("uniform", "leak"):
+        raise ValueError("dangling must be 'uniform' or 'leak'")
+    if mode not in ("fused", "two_phase"):
+        raise ValueError("mode must be 'fused' or 'two_phase'")
+    return (DANGLING_LEAK if dangling == "leak" else 0) | (TWO_PHASE if mode == "two_phase" else 0)
+
+
+def to_device_csr(row_ptr: np.ndarray, col: np.ndarray, device="cuda"):
+    """Copies a host CSR (uint32 arrays) to CUDA int32 tensors (same bits)."""
+    import torch
+    rp = torch.from_numpy(np.ascontiguousarray(row_ptr, dtype=np.uint32).view(np.int32)).to(device)
+    c = np.ascontiguousarray(col, dtype=np.uint32)
+    ct = torch.from_numpy((c if c.size else np.zeros(1, np.uint32)).view(np.int32)).to(device)
+    return rp, ct
+
+
+class PNG:
+    """A device-resident Partition-Node Graph and its solver state."""
+
+    def __init__(self, row_ptr, col, part_size: int, stream=None):
+        """row_ptr, col: CUDA int32/uint32 tensors (CSR out-adjacency, rows sorted)."""
+        L = lib()
+        n = row_ptr.numel() - 1
+        m = int(row_ptr[-1].item()) & 0xFFFFFFFF
+        h = ctypes.c_void_p()
+        _check(L.pcpm_build(_dev_u32(row_ptr), _dev_u32(col), n, m, int(part_size), _stream(stream),
+                            ctypes.byref(h)), "pcpm_build")
+        self._h = h
+        self.n = n
+
+    @classmethod
+    def from_host(cls, row_ptr: np.ndarray, col: np.ndarray, part_size: int, stream=None):
+        rp, c = to_device_csr(row_ptr, col)
+        return cls(rp, c, part_size, stream)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().pcpm_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def info(self) -> dict:
+        i = _Info()
+        _check(lib().pcpm_png_get_info(self._h, ctypes.byref(i)), "pcpm_png_get_info")
+        return {f: getattr(i, f) for f, _ in _Info._fields_ if not f.startswith("reserved")}
+
+    def export(self) -> dict:
+        """Host copies of counts, offsets, bin starts and bins (see pcpm.h)."""
+        inf = self.info
+        k, ne, m = inf["num_partitions"], inf["num_updates"], inf["num_edges"]
+        out = {key: np.empty(k * k, np.uint32) for key in ("cnt_u", "cnt_e", "off_u", "off_e")}
+        out["bin_u"] = np.empty(k + 1, np.uint32)
+        out["bin_e"] = np.empty(k + 1, np.uint32)
+        out["src_idx"] = np.empty(max(ne, 1), np.uint32)
+        out["dest_ids"] = np.empty(max(m, 1), np.uint32)
+        order = ("cnt_u", "cnt_e", "off_u", "off_e", "bin_u", "bin_e", "src_idx", "dest_ids")
+        _check(lib().pcpm_png_export(self._h, *[out[x].ctypes.data_as(ctypes.c_void_p) for x in order]),
+               "pcpm_png_export")
+        for key in ("cnt_u", "cnt_e", "off_u", "off_e"):
+            out[key] = out[key].reshape(k, k)
+        out["src_idx"] = out["src_idx"][:ne]
+        out["dest_ids"] = out["dest_ids"][:m]
+        out.update(k=k, ne=ne, m=m, n=inf["n"], q=inf["part_size"])
+        return out
+
+    def reset(self, pr_init=None, stream=None):
+        p = None if pr_init is None else ctypes.c_void_p(_f32_dev(pr_init, self.n).data_ptr())
+        _check(lib().pcpm_reset(self._h, p, _stream(stream)), "pcpm_reset")
+
+    def iterate(self, d: float = 0.85, iters: int = 1, tol: float = 0.0, dangling: str = "uniform",
+                stream=None, sync: bool = True, mode: str = "fused"):
+        """Advances the state; returns (iterations run, last L1 change) when sync."""
+        it, res = ctypes.c_int(0), ctypes.c_double(0.0)
+        code = lib().pcpm_iterate(self._h, float(d), int(iters), float(tol), _flags(dangling, mode),
+                                  ctypes.byref(it) if sync else None, ctypes.byref(res) if sync else None,
+                                  _stream(stream))
+        _check(code, "pcpm_iterate", allow=(PCPM_OK, PCPM_NOT_CONVERGED))
+        return (it.value, res.value) if sync else None
+
+    def iterate_timed(self, d: float = 0.85, iters: int = 1, dangling: str = "uniform", stream=None,
+                      mode: str = "fused") -> dict:
+        ms = (ctypes.c_float * (NUM_PHASES + 1))()
+        _check(lib().pcpm_iterate_timed(self._h, float(d), int(iters), _flags(dangling, mode), ms, _stream(stream)),
+               "pcpm_iterate_timed")
+        return dict(zip(PHASES + ("span",), list(ms)))
+
+    def ranks(self, out=None, stream=None):
+        import torch
+        out = torch.empty(self.n, dtype=torch.float32, device="cuda") if out is None else _f32_dev(out, self.n)
+        _check(lib().pcpm_ranks(self._h, ctypes.c_void_p(out.data_ptr()), _stream(stream)), "pcpm_ranks")
+        return out
+
+    def residual_history(self) -> np.ndarray:
+        cnt = self.info["iterations_done"]
+        buf = np.empty(max(cnt, 1), np.float64)
+        got = lib().pcpm_residual_history(self._h, buf.ctypes.data_as(ctypes.c_void_p), cnt)
+        if got < 0:
+            raise PcpmError(got, "pcpm_residual_history")
+        return buf[:got]
+
+    def pagerank(self, d: float = 0.85, max_iters: int = 20, tol: float = 0.0, pr_init=None,
+                 dangling: str = "uniform", out=None, stream=None, mode: str = "fused"):
+        """Full solve; returns (ranks tensor, iterations run, last L1 change)."""
+        import torch
+        out = torch.empty(self.n, dtype=torch.float32, device="cuda") if out is None else _f32_dev(out, self.n)
+        p = None if pr_init is None else ctypes.c_void_p(_f32_dev(pr_init, self.n).data_ptr())
+        it, res = ctypes.c_int(0), ctypes.c_double(0.0)
+        code = lib().pcpm_pagerank(self._h, float(d), int(max_iters), float(tol), _flags(dangling, mode), p,
+                                   ctypes.c_void_p(out.data_ptr()), ctypes.byref(it), ctypes.byref(res),
+                                   _stream(stream))
+        _check(code, "pcpm_pagerank", allow=(PCPM_OK, PCPM_NOT_CONVERGED))
+        return out, it.value, res.value
+
+    def scatter_only(self, stream=None):
+        _check(lib().pcpm_scatter_only(self._h, _stream(stream)), "pcpm_scatter_only")
+
+    def export_state(self) -> dict:
+        inf = self.info
+        pr = np.empty(self.n, np.float32)
+        spr = np.empty(self.n, np.float32)
+        upd = np.empty(max(inf["num_updates"], 1), np.float32)
+        dang = ctypes.c_double(0.0)
+        _check(lib().pcpm_export_state(self._h, pr.ctypes.data_as(ctypes.c_void_p),
+                                       spr.ctypes.data_as(ctypes.c_void_p), upd.ctypes.data_as(ctypes.c_void_p),
+                                       ctypes.byref(dang)), "pcpm_export_state")
+        return {"pr": pr, "spr": spr, "updates": upd[:inf["num_updates"]], "dangling": dang.value}
+
+
+def _f32_dev(t, n):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise TypeError("expected a contiguous CUDA float32 tensor")
+    if t.numel() != n:
+        raise ValueError(f"expected {n} elements, got {t.numel()}")
+    return t
+
+
+def pagerank_host(row_ptr: np.ndarray, col: np.ndarray, part_size: int, d: float = 0.85, max_iters: int = 20,
+                  tol: float = 0.0, dangling: str = "uniform", pr_out: np.ndarray | None = None,
+                  mode: str = "fused"):
+    """End-to-end solve from host arrays through pcpm_pagerank_host.
+    Returns (ranks float32 array, iterations run, last L1 change)."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.uint32)
+    c = np.ascontiguousarray(col, dtype=np.uint32)
+    n = rp.size - 1
+    out = np.empty(n, np.float32) if pr_out is None else pr_out
+    it, res = ctypes.c_int(0), ctypes.c_double(0.0)
+    code = lib().pcpm_pagerank_host(rp.ctypes.data_as(ctypes.c_void_p),
+                                    c.ctypes.data_as(ctypes.c_void_p) if c.size else None, n, int(rp[-1]),
+                                    int(part_size), float(d), int(max_iters), float(tol), _flags(dangling, mode),
+                                    out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(it), ctypes.byref(res))
+    _check(code, "pcpm_pagerank_host", allow=(PCPM_OK, PCPM_NOT_CONVERGED))
+    return out, it.value, res.value

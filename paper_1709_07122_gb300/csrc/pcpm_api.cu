@@ -1,0 +1,452 @@
+// pcpm_api.cu - the extern "C" boundary: argument checks, handle lifetime,
+// the iteration loop and host-side copies. All arithmetic of the method runs
+// in the kernels of png_build.cu and pcpm_iter.cu.
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "pcpm_internal.cuh"
+
+namespace pcpm {
+
+
+cudaError_t dev_alloc(pcpm_png* g, void** p, size_t bytes) {
+    bytes = std::max<size_t>(bytes, 16);
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) g->device_bytes += bytes;
+    return e;
+}
+
+namespace {
+
+#define CK(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) return e_ == cudaErrorMemoryAllocation ? PCPM_ENOMEM : PCPM_ECUDA; \
+    } while (0)
+
+#define RC(call)                          \
+    do {                                  \
+        int r_ = (call);                  \
+        if (r_ != PCPM_OK) return r_;     \
+    } while (0)
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void release(pcpm_png* g) {
+    if (!g) return;
+    void* ptrs[] = {g->dest, g->src, g->bin_u, g->bin_e, g->seg_u, g->cnt_u, g->seg_e, g->cnt_e,
+                    g->chunk_base, g->hubs, g->bin_order, g->src_order, g->inv_deg, g->pr[0], g->pr[1],
+                    g->upd[0], g->upd[1], g->partials, g->hist, g->state};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (g->state_host) cudaFreeHost(g->state_host);
+    delete g;
+}
+
+int alloc_state(pcpm_png* g) {
+    const uint32_t n = g->n;
+    CK(dev_alloc(g, (void**)&g->pr[0], (size_t)n * sizeof(float)));
+    CK(dev_alloc(g, (void**)&g->pr[1], (size_t)n * sizeof(float)));
+    // Update bins: two buffers (the fused iteration gathers one and scatters
+    // the next), padded so a chunk's update slice may round up past the end.
+    CK(dev_alloc(g, (void**)&g->upd[0], (g->ne + 8) * sizeof(float)));
+    CK(dev_alloc(g, (void**)&g->upd[1], (g->ne + 8) * sizeof(float)));
+    CK(cudaMemset(g->upd[0], 0, (g->ne + 8) * sizeof(float)));
+    CK(cudaMemset(g->upd[1], 0, (g->ne + 8) * sizeof(float)));
+    CK(dev_alloc(g, (void**)&g->partials, 2 * partial_slots(g) * sizeof(double)));
+    g->hist_cap = 1024;
+    CK(dev_alloc(g, (void**)&g->hist, (size_t)g->hist_cap * sizeof(double)));
+    CK(dev_alloc(g, (void**)&g->state, sizeof(DevState)));
+    CK(cudaMallocHost((void**)&g->state_host, sizeof(DevState)));
+    std::memset(g->state_host, 0, sizeof(DevState));
+    CK(cudaMemset(g->state, 0, sizeof(DevState)));
+    return PCPM_OK;
+}
+
+int ensure_hist(pcpm_png* g, int needed, cudaStream_t s) {
+    if (needed <= g->hist_cap) return PCPM_OK;
+    int cap = g->hist_cap;
+    while (cap < needed) cap *= 2;
+    double* h = nullptr;
+    CK(cudaMalloc((void**)&h, (size_t)cap * sizeof(double)));
+    cudaError_t e = cudaMemcpyAsync(h, g->hist, (size_t)g->hist_cap * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaFree(h);
+        return PCPM_ECUDA;
+    }
+    cudaFree(g->hist);
+    g->device_bytes += (size_t)(cap - g->hist_cap) * sizeof(double);
+    g->hist = h;
+    g->hist_cap = cap;
+    return PCPM_OK;
+}
+
+int check_device_err(const DevState& st) {
+    if (st.err & kErrTimeout) return PCPM_ETIMEOUT;
+    if (st.err) return PCPM_EDEVICE;
+    return PCPM_OK;
+}
+
+int sync_state(pcpm_png* g, cudaStream_t s) {
+    CK(cudaMemcpyAsync(g->state_host, g->state, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return check_device_err(*g->state_host);
+}
+
+// Launches iterations [0, iters) with optional event records around kernels.
+// Two-phase: scatter, gather + apply, reduce (the paper's phases). Fused: the
+// gather kernel also scatters the next iteration's updates into the other
+// buffer, so a standalone scatter runs only when no valid bins exist yet.
+int run_iterations(pcpm_png* g, float d, int iters, double tol, uint32_t flags, cudaStream_t s,
+                   std::vector<cudaEvent_t>* ev) {
+    RC(ensure_hist(g, g->iters_done + iters, s));
+    const bool fused = !(flags & PCPM_TWO_PHASE);
+    for (int i = 0; i < iters; ++i) {
+        if (ev) CK(cudaEventRecord((*ev)[4 * i], s));
+        if (!fused || !g->upd_valid) RC(launch_scatter(g, s));
+        if (ev) CK(cudaEventRecord((*ev)[4 * i + 1], s));
+        RC(launch_gather(g, d, flags, fused, s));
+        if (ev) CK(cudaEventRecord((*ev)[4 * i + 2], s));
+        RC(launch_reduce(g, tol, g->iters_done + i, s));
+        if (ev) CK(cudaEventRecord((*ev)[4 * i + 3], s));
+        g->cur ^= 1;
+        if (fused) {
+            g->ucur ^= 1;
+            g->upd_valid = 1;
+        } else {
+            g->upd_valid = 0;
+        }
+    }
+    return PCPM_OK;
+}
+
+int iterate_impl(pcpm_png* g, float d, int iters, double tol, uint32_t flags, int* iters_run, double* last_residual,
+                 cudaStream_t s) {
+    g->last_stream = s;
+    CK(cudaMemsetAsync(&g->state->stop, 0, sizeof(int), s));
+    const int start_done = g->iters_done;
+    const int start_cur = g->cur;
+    const int start_ucur = g->ucur;
+    const int start_valid = g->upd_valid;
+    const bool need_sync = tol > 0.0 || iters_run || last_residual;
+    if (tol > 0.0) {
+        // Batches of iterations; kernels after convergence return at once.
+        const int batch = 8;
+        int launched = 0;
+        while (launched < iters) {
+            const int b = std::min(batch, iters - launched);
+            RC(run_iterations(g, d, b, tol, flags, s, nullptr));
+            g->iters_done += b;  // provisional, corrected below
+            launched += b;
+            RC(sync_state(g, s));
+            if (g->state_host->stop) break;
+        }
+    } else {
+        RC(run_iterations(g, d, iters, tol, flags, s, nullptr));
+        g->iters_done += iters;
+        if (need_sync) RC(sync_state(g, s));
+    }
+    if (need_sync) {
+        const int done = g->state_host->iters_done - start_done;
+        g->iters_done = g->state_host->iters_done;
+        g->cur = start_cur ^ (done & 1);
+        if (!(flags & PCPM_TWO_PHASE)) {
+            g->ucur = start_ucur ^ (done & 1);
+            g->upd_valid = done > 0 ? 1 : start_valid;
+        } else if (done > 0) {
+            g->upd_valid = 0;
+        }
+        if (iters_run) *iters_run = done;
+        if (last_residual) *last_residual = done > 0 ? g->state_host->residual : 0.0;
+        if (tol > 0.0 && !g->state_host->stop) return PCPM_NOT_CONVERGED;
+    }
+    return PCPM_OK;
+}
+
+bool bad_damping(float d) { return !(d >= 0.0f && d < 1.0f); }
+
+constexpr uint32_t kAllFlags = PCPM_DANGLING_LEAK | PCPM_TWO_PHASE;
+
+}  // namespace
+}  // namespace pcpm
+
+using namespace pcpm;
+
+extern "C" {
+
+int pcpm_build(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t n, uint64_t m, uint32_t part_size,
+               void* stream, pcpm_png** out) {
+    if (!out || !row_ptr || n == 0 || n > PCPM_MAX_NODES || part_size == 0 || part_size > PCPM_MAX_PART_SIZE)
+        return PCPM_EINVAL;
+    if (m > 0xFFFFFF00ull) return PCPM_EINVAL;
+    const uint64_t k = ((uint64_t)n + part_size - 1) / part_size;
+    if (k > PCPM_MAX_PARTITIONS) return PCPM_EINVAL;
+    if (!is_device_ptr(row_ptr)) return PCPM_EINVAL;
+    if (m > 0 && !is_device_ptr(col_idx)) return PCPM_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint32_t ends[2] = {1, 0};
+    CK(cudaMemcpyAsync(&ends[0], row_ptr, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&ends[1], row_ptr + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (ends[0] != 0 || ends[1] != m) return PCPM_EINVAL;
+
+    pcpm_png* g = new (std::nothrow) pcpm_png;
+    if (!g) return PCPM_ENOMEM;
+    std::memset(g, 0, sizeof(*g));
+    if (cudaGetDevice(&g->device) != cudaSuccess) {
+        delete g;
+        return PCPM_ECUDA;
+    }
+    g->n = n;
+    g->q = part_size;
+    g->k = (uint32_t)k;
+    g->m = m;
+    g->last_stream = s;
+    int rc = PCPM_OK;
+    if (cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess) rc = PCPM_ECUDA;
+    if (rc == PCPM_OK) rc = build_png(g, row_ptr, col_idx ? col_idx : row_ptr, s);
+    if (rc == PCPM_OK) rc = alloc_state(g);
+    if (rc == PCPM_OK) rc = configure_kernels(g);
+    if (rc == PCPM_OK) {
+        if (cudaStreamSynchronize(s) != cudaSuccess) rc = PCPM_ECUDA;
+    }
+    if (rc != PCPM_OK) {
+        cudaStreamSynchronize(s);
+        cudaGetLastError();
+        release(g);
+        return rc;
+    }
+    *out = g;
+    return PCPM_OK;
+}
+
+void pcpm_free(pcpm_png* png) {
+    if (!png) return;
+    cudaStreamSynchronize(png->last_stream);
+    cudaGetLastError();
+    release(png);
+}
+
+int pcpm_png_get_info(const pcpm_png* g, pcpm_png_info* info) {
+    if (!g || !info) return PCPM_EINVAL;
+    std::memset(info, 0, sizeof(*info));
+    info->n = g->n;
+    info->part_size = g->q;
+    info->num_partitions = g->k;
+    info->num_edges = g->m;
+    info->num_updates = g->ne;
+    info->compression_ratio = g->ne ? (double)g->m / (double)g->ne : 0.0;
+    info->device_bytes = g->device_bytes;
+    info->iterations_done = g->iters_done;
+    return PCPM_OK;
+}
+
+int pcpm_png_export(const pcpm_png* g, uint32_t* cnt_u, uint32_t* cnt_e, uint32_t* off_u, uint32_t* off_e,
+                    uint32_t* bin_u, uint32_t* bin_e, uint32_t* src_idx, uint32_t* dest_ids) {
+    if (!g) return PCPM_EINVAL;
+    CK(cudaStreamSynchronize(g->last_stream));
+    const size_t kk = (size_t)g->k * g->k;
+    std::vector<uint32_t> hb_u(g->k + 1), hb_e(g->k + 1);
+    CK(cudaMemcpy(hb_u.data(), g->bin_u, (g->k + 1) * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(hb_e.data(), g->bin_e, (g->k + 1) * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    if (cnt_u) CK(cudaMemcpy(cnt_u, g->cnt_u, kk * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    if (cnt_e) CK(cudaMemcpy(cnt_e, g->cnt_e, kk * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    if (off_u || off_e) {
+        std::vector<uint32_t> seg(kk);
+        if (off_u) {
+            CK(cudaMemcpy(seg.data(), g->seg_u, kk * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+            for (size_t i = 0; i < kk; ++i) off_u[i] = seg[i] - hb_u[i % g->k];
+        }
+        if (off_e) {
+            CK(cudaMemcpy(seg.data(), g->seg_e, kk * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+            for (size_t i = 0; i < kk; ++i) off_e[i] = seg[i] - hb_e[i % g->k];
+        }
+    }
+    if (bin_u) std::memcpy(bin_u, hb_u.data(), (g->k + 1) * sizeof(uint32_t));
+    if (bin_e) std::memcpy(bin_e, hb_e.data(), (g->k + 1) * sizeof(uint32_t));
+    if (src_idx && g->ne) CK(cudaMemcpy(src_idx, g->src, g->ne * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    if (dest_ids && g->m) CK(cudaMemcpy(dest_ids, g->dest, g->m * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    return PCPM_OK;
+}
+
+int pcpm_reset(pcpm_png* g, const float* pr_init, void* stream) {
+    if (!g) return PCPM_EINVAL;
+    if (pr_init && !is_device_ptr(pr_init)) return PCPM_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    g->last_stream = s;
+    CK(cudaMemsetAsync(g->state, 0, sizeof(DevState), s));
+    g->cur = 0;
+    g->iters_done = 0;
+    g->upd_valid = 0;
+    RC(launch_init(g, pr_init, s));
+    RC(launch_reduce(g, 0.0, -1, s));
+    return PCPM_OK;
+}
+
+int pcpm_iterate(pcpm_png* g, float d, int iters, double tol, uint32_t flags, int* iters_run, double* last_residual,
+                 void* stream) {
+    if (!g || iters < 0 || bad_damping(d) || (flags & ~kAllFlags)) return PCPM_EINVAL;
+    return iterate_impl(g, d, iters, tol, flags, iters_run, last_residual, (cudaStream_t)stream);
+}
+
+int pcpm_iterate_timed(pcpm_png* g, float d, int iters, uint32_t flags, float* kernel_ms, void* stream) {
+    if (!g || iters < 0 || bad_damping(d) || !kernel_ms || (flags & ~kAllFlags)) return PCPM_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    g->last_stream = s;
+    std::vector<cudaEvent_t> ev((size_t)4 * iters);
+    int rc = PCPM_OK;
+    size_t made = 0;
+    for (; made < ev.size(); ++made)
+        if (cudaEventCreate(&ev[made]) != cudaSuccess) {
+            rc = PCPM_ECUDA;
+            break;
+        }
+    if (rc == PCPM_OK && cudaMemsetAsync(&g->state->stop, 0, sizeof(int), s) != cudaSuccess) rc = PCPM_ECUDA;
+    if (rc == PCPM_OK) rc = run_iterations(g, d, iters, 0.0, flags, s, &ev);
+    if (rc == PCPM_OK) {
+        g->iters_done += iters;
+        rc = sync_state(g, s);
+    }
+    if (rc == PCPM_OK) {
+        for (int p = 0; p <= PCPM_NUM_PHASES; ++p) kernel_ms[p] = 0.0f;
+        if (iters > 0 && cudaEventElapsedTime(&kernel_ms[PCPM_NUM_PHASES], ev[0], ev[4 * iters - 1]) != cudaSuccess)
+            rc = PCPM_ECUDA;
+        for (int i = 0; i < iters && rc == PCPM_OK; ++i)
+            for (int p = 0; p < PCPM_NUM_PHASES; ++p) {
+                float ms = 0.0f;
+                if (cudaEventElapsedTime(&ms, ev[4 * i + p], ev[4 * i + p + 1]) != cudaSuccess) rc = PCPM_ECUDA;
+                kernel_ms[p] += ms;
+            }
+    }
+    for (size_t i = 0; i < made; ++i) cudaEventDestroy(ev[i]);
+    return rc;
+}
+
+int pcpm_ranks(const pcpm_png* g, float* pr_out, void* stream) {
+    if (!g || !is_device_ptr(pr_out)) return PCPM_EINVAL;
+    CK(cudaMemcpyAsync(pr_out, g->pr[g->cur], (size_t)g->n * sizeof(float), cudaMemcpyDeviceToDevice,
+                       (cudaStream_t)stream));
+    return PCPM_OK;
+}
+
+int pcpm_residual_history(const pcpm_png* g, double* out, int max_count) {
+    if (!g || !out || max_count < 0) return PCPM_EINVAL;
+    CK(cudaStreamSynchronize(g->last_stream));
+    const int count = std::min(max_count, std::min(g->iters_done, g->hist_cap));
+    if (count > 0) CK(cudaMemcpy(out, g->hist, (size_t)count * sizeof(double), cudaMemcpyDeviceToHost));
+    return count;
+}
+
+int pcpm_pagerank(pcpm_png* g, float d, int max_iters, double tol, uint32_t flags, const float* pr_init,
+                  float* pr_out, int* iters_run, double* final_residual, void* stream) {
+    if (!g || max_iters < 0 || bad_damping(d) || (flags & ~kAllFlags)) return PCPM_EINVAL;
+    if (!is_device_ptr(pr_out)) return PCPM_EINVAL;
+    if (pr_init && !is_device_ptr(pr_init)) return PCPM_EINVAL;
+    RC(pcpm_reset(g, pr_init, stream));
+    const int rc = iterate_impl(g, d, max_iters, tol, flags, iters_run, final_residual, (cudaStream_t)stream);
+    if (rc < 0) return rc;
+    RC(pcpm_ranks(g, pr_out, stream));
+    return rc;
+}
+
+int pcpm_pagerank_host(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t n, uint64_t m,
+                       uint32_t part_size, float d, int max_iters, double tol, uint32_t flags, float* pr_out,
+                       int* iters_run, double* final_residual) {
+    if (!row_ptr || !pr_out || (m > 0 && !col_idx) || n == 0 || n > PCPM_MAX_NODES || m > 0xFFFFFF00ull)
+        return PCPM_EINVAL;
+    if (max_iters < 0 || bad_damping(d) || (flags & ~kAllFlags)) return PCPM_EINVAL;
+    uint32_t *d_rp = nullptr, *d_col = nullptr;
+    float* d_pr = nullptr;
+    pcpm_png* g = nullptr;
+    int rc = PCPM_OK;
+    cudaStream_t s = nullptr;
+    auto fail = [&](cudaError_t e) { return e == cudaErrorMemoryAllocation ? PCPM_ENOMEM : PCPM_ECUDA; };
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_rp, ((size_t)n + 1) * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_col, std::max<size_t>(m, 1) * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_pr, (size_t)n * sizeof(float));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_rp, row_ptr, ((size_t)n + 1) * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && m)
+        e = cudaMemcpyAsync(d_col, col_idx, (size_t)m * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) rc = fail(e);
+    if (rc == PCPM_OK) rc = pcpm_build(d_rp, d_col, n, m, part_size, s, &g);
+    if (rc == PCPM_OK) rc = pcpm_pagerank(g, d, max_iters, tol, flags, nullptr, d_pr, iters_run, final_residual, s);
+    if (rc >= 0) {
+        e = cudaMemcpyAsync(pr_out, d_pr, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = fail(e);
+    }
+    if (s) cudaStreamSynchronize(s);
+    if (g) pcpm_free(g);
+    cudaFree(d_rp);
+    cudaFree(d_col);
+    cudaFree(d_pr);
+    if (s) cudaStreamDestroy(s);
+    cudaGetLastError();
+    return rc;
+}
+
+int pcpm_scatter_only(pcpm_png* g, void* stream) {
+    if (!g) return PCPM_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    g->last_stream = s;
+    CK(cudaMemsetAsync(&g->state->stop, 0, sizeof(int), s));
+    RC(launch_scatter(g, s));
+    g->upd_valid = 1;
+    return PCPM_OK;
+}
+
+int pcpm_export_state(const pcpm_png* g, float* pr, float* spr, float* updates, double* dangling) {
+    if (!g) return PCPM_EINVAL;
+    CK(cudaStreamSynchronize(g->last_stream));
+    if (pr) CK(cudaMemcpy(pr, g->pr[g->cur], (size_t)g->n * sizeof(float), cudaMemcpyDeviceToHost));
+    if (spr) {
+        float* tmp = nullptr;
+        CK(cudaMalloc((void**)&tmp, (size_t)g->n * sizeof(float)));
+        int rc = launch_spr(const_cast<pcpm_png*>(g), tmp, g->last_stream);
+        cudaError_t e = cudaStreamSynchronize(g->last_stream);
+        if (rc == PCPM_OK && e == cudaSuccess)
+            e = cudaMemcpy(spr, tmp, (size_t)g->n * sizeof(float), cudaMemcpyDeviceToHost);
+        cudaFree(tmp);
+        if (rc != PCPM_OK) return rc;
+        if (e != cudaSuccess) return PCPM_ECUDA;
+    }
+    if (updates && g->ne) CK(cudaMemcpy(updates, g->upd[g->ucur], g->ne * sizeof(float), cudaMemcpyDeviceToHost));
+    if (dangling) {
+        DevState st;
+        CK(cudaMemcpy(&st, g->state, sizeof(DevState), cudaMemcpyDeviceToHost));
+        *dangling = st.dangling;
+        const int rc = check_device_err(st);
+        if (rc != PCPM_OK) return rc;
+    }
+    return PCPM_OK;
+}
+
+const char* pcpm_strerror(int code) {
+    switch (code) {
+        case PCPM_OK: return "success";
+        case PCPM_NOT_CONVERGED: return "tolerance not reached within max_iters";
+        case PCPM_EINVAL: return "invalid argument";
+        case PCPM_ECUDA: return "CUDA runtime error";
+        case PCPM_ENOMEM: return "out of memory";
+        case PCPM_ETIMEOUT: return "bounded device wait timed out";
+        case PCPM_EDEVICE: return "device-side consistency check failed";
+        case PCPM_EBADGRAPH: return "invalid CSR: column out of range or row not sorted";
+        default: return "unknown status code";
+    }
+}
+
+}  // extern "C"

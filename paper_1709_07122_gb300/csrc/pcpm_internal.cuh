@@ -1,0 +1,118 @@
+// pcpm_internal.cuh - shared definitions of the CUDA library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pcpm.h"
+
+namespace pcpm {
+
+// ---------------------------------------------------------------- layout
+// Destination IDs carry the message flag in bit 31 (Sec. 3.2).
+constexpr uint32_t kMsb = 0x80000000u;
+constexpr uint32_t kIdMask = 0x7FFFFFFFu;
+constexpr uint32_t kNoHub = 0xFFFFFFFFu;
+
+// Builder: edges per warp tile (each tile lies inside one source partition).
+constexpr uint32_t kTileEdges = 8192;
+// Builder: a destination needs this many in-edges inside its bin before the
+// gather keeps it in registers instead of shared-memory atomics.
+constexpr uint32_t kHubMinInDegree = 64;
+// Gather: destination IDs per chunk. Every chunk of the concatenated bins
+// starts at a multiple of kChunk entries and has a precomputed update base
+// (the number of flagged IDs before it), so any warp can decode any chunk.
+constexpr uint32_t kChunk = 256;
+// Gather: a chunk needs the updates [base-1, next base) (the first ID may
+// continue the previous message), widened to 16-byte boundaries.
+constexpr uint32_t kUpdSlot = kChunk + 8;
+// Gather: warps per CTA and pipeline depth of each warp's private ring.
+constexpr int kGatherWarps = 16;
+constexpr int kGatherStages = 3;
+// Scatter: threads per CTA and 4-entry groups in flight per thread.
+constexpr int kScatterThreads = 1024;
+constexpr int kScatterUnroll = 4;
+// Apply / reduce threads.
+constexpr int kReduceThreads = 512;
+// Largest thread-block cluster used for one bin.
+constexpr int kMaxCluster = 8;
+
+// Upper bound for a device-side wait on an mbarrier, in SM clock cycles
+// (about one second at 2 GHz). A wait that runs out sets kErrTimeout.
+constexpr long long kWaitLimitCycles = 2000000000LL;
+
+// Device error bits (DevState::err).
+constexpr int kErrTimeout = 1;
+constexpr int kErrBounds = 2;
+constexpr int kErrBadGraph = 4;
+
+// Solver scalars kept on the device.
+struct DevState {
+    double dangling;  // sum of PR over dangling nodes for the current ranks
+    double residual;  // L1 change of the last iteration
+    int stop;         // set once residual < tol (tol > 0)
+    int iters_done;   // iterations applied since reset
+    int err;          // kErr* bits
+    int pad;
+};
+
+}  // namespace pcpm
+
+// The handle behind the opaque ABI type.
+struct pcpm_png {
+    int device;
+    int sms;
+    uint32_t n, q, k;
+    uint64_t m, ne;
+    uint64_t nchunks;        // ceil(m / kChunk)
+    // PNG
+    uint32_t* dest;          // m destination IDs in bin order (padded to whole chunks)
+    uint32_t* src;           // ne source IDs in bin order (padded)
+    uint32_t* bin_u;         // k+1 starts of update bins
+    uint32_t* bin_e;         // k+1 starts of destination-ID bins
+    uint32_t* seg_u;         // k*k absolute start of segment (p, p') in the update array
+    uint32_t* cnt_u;         // k*k updates p -> p'
+    uint32_t* seg_e;         // k*k absolute start of segment (p, p') in the ID array
+    uint32_t* cnt_e;         // k*k edges p -> p'
+    uint32_t* chunk_base;    // nchunks+1: flagged IDs before each chunk
+    uint32_t* hubs;          // 2k: per bin, local IDs of its two largest in-degrees (or kNoHub)
+    uint32_t* bin_order;     // k: destination partitions by decreasing bin size
+    uint32_t* src_order;     // k: source partitions by decreasing update count
+    float* inv_deg;          // n: 1/|N_o(u)|, 0 for dangling nodes
+    // solver state
+    float* pr[2];            // ranks ping-pong
+    int cur;                 // pr[cur] holds PR_i
+    float* upd[2];           // update bins (padded); upd[ucur] is the current one
+    int ucur;
+    int upd_valid;           // upd[ucur] holds the scatter of PR_i
+    int cluster;             // CTAs per bin in the gather
+    double* partials;        // 2 * max(k * cluster, init blocks): per-CTA (residual, dangling)
+    int partial_count;       // CTAs that wrote partials for the pending reduce
+    double* hist;            // residual history
+    int hist_cap;
+    pcpm::DevState* state;   // device scalars
+    pcpm::DevState* state_host;  // pinned mirror
+    int iters_done;
+    uint64_t device_bytes;
+    cudaStream_t last_stream;
+};
+
+namespace pcpm {
+
+// Builder entry (png_build.cu). Fills every PNG field of `g` (n, q, k, m set by
+// the caller); returns a PCPM_* status.
+int build_png(pcpm_png* g, const uint32_t* row_ptr, const uint32_t* col, cudaStream_t s);
+
+// Iteration kernels (pcpm_iter.cu).
+int configure_kernels(pcpm_png* g);
+int launch_init(pcpm_png* g, const float* pr_init, cudaStream_t s);
+int launch_scatter(pcpm_png* g, cudaStream_t s);
+int launch_gather(pcpm_png* g, float d, uint32_t flags, bool fused, cudaStream_t s);
+int launch_reduce(pcpm_png* g, double tol, int hist_slot, cudaStream_t s);
+int launch_spr(pcpm_png* g, float* spr, cudaStream_t s);
+size_t partial_slots(const pcpm_png* g);
+
+// Device allocation helper that records sizes.
+cudaError_t dev_alloc(pcpm_png* g, void** p, size_t bytes);
+
+}  // namespace pcpm

@@ -1,0 +1,692 @@
+// pcpm_iter.cu - one PCPM PageRank iteration on sm_103a.
+//
+// Scatter (Algorithm 3 over the PNG): one CTA per source partition p, largest
+// first. The partition's slice of SPR = PR/outdeg (q floats) is staged in shared
+// memory - the paper's cached vertex data of p - and, for every destination
+// partition p', the segment of update_bins[p'] that p owns (static offsets,
+// Sec. 3.1) is filled: update[t] = SPR[src[t]]. The k segments are walked as one
+// flattened range of 4-entry groups so every thread has equal work; source IDs
+// stream in and updates stream out as 16-byte vectors, several groups in flight
+// per thread.
+//
+// Gather + apply (Algorithm 4 and the apply loop of Algorithm 2): a thread-block
+// cluster of S CTAs per destination partition p', largest bins first. Every CTA
+// holds a full q-float accumulator in shared memory and takes a contiguous 1/S
+// of the bin's chunks, split again into one contiguous run per warp. Each warp
+// streams its chunks with cp.async.bulk (TMA, non-tensor form) into a private
+// kGatherStages-deep ring: the chunk's kChunk destination IDs and the slice of
+// the update bin they refer to, both landing on one mbarrier; the per-chunk
+// update bases come from the builder. Branch avoidance (Algorithm 4) becomes
+// warp arithmetic: the update of an ID is the chunk's base plus the inclusive
+// count of flagged IDs before it, from ballots. The bin's two largest in-degree
+// destinations are summed in registers instead of contended atomics. Then the
+// cluster synchronises, each CTA adds the S partial sums of its 1/S of the
+// partition over distributed shared memory and applies
+//   PR'(v) = (1-d)/n + d*(acc(v) + D/n)
+// writing PR' and FP64 partial sums of |PR' - PR| and of PR' over dangling
+// nodes. In the fused form the same cluster then assembles SPR' = PR'/outdeg for
+// the whole partition in shared memory and scatters it into the other update
+// buffer for the next iteration: gather, apply and the next scatter of one
+// partition in one launch, without writing SPR to memory.
+#include <algorithm>
+#include <cstdlib>
+
+#include "pcpm_internal.cuh"
+
+namespace pcpm {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t r;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// ------------------------------------------------------------ mbarrier / TMA
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Bulk copy global -> shared completing on an mbarrier. Both addresses 16-byte
+// aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits for the given phase parity, for at most kWaitLimitCycles.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > kWaitLimitCycles) return false;
+    return true;
+}
+
+// ------------------------------------------------------------------- cluster
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t cluster_size() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Address of `p` (this CTA's shared memory) in the shared memory of CTA `rank`.
+__device__ __forceinline__ uint32_t map_rank(const void* p, uint32_t rank) {
+    uint32_t a;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(a) : "r"(smem_addr(p)), "r"(rank));
+    return a;
+}
+
+__device__ __forceinline__ float ld_cluster_f32(uint32_t addr) {
+    float v;
+    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ float4 ld_cluster_f32x4(uint32_t addr) {
+    float4 v;
+    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(addr)
+                 : "memory");
+    return v;
+}
+
+// ------------------------------------------------------------ global memory
+__device__ __forceinline__ uint4 ld_stream_u4(const uint32_t* p) {
+    uint4 r;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+                 : "l"(p));
+    return r;
+}
+
+__device__ __forceinline__ void st_stream_f4(float* p, float4 v) {
+    asm volatile("st.global.cs.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+
+// Deterministic block sum of two doubles; result valid in thread 0.
+template <int kThreads>
+__device__ __forceinline__ void block_sum2(double& a, double& b) {
+    __shared__ double sa[kThreads / 32], sb[kThreads / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(kFull, a, o);
+        b += __shfl_down_sync(kFull, b, o);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        sa[warp] = a;
+        sb[warp] = b;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        a = lane < kThreads / 32 ? sa[lane] : 0.0;
+        b = lane < kThreads / 32 ? sb[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_down_sync(kFull, a, o);
+            b += __shfl_down_sync(kFull, b, o);
+        }
+    }
+}
+
+// ------------------------------------------------------------ scatter body
+// 4-entry groups of a segment [a, a + c): the aligned groups that overlap it.
+__device__ __forceinline__ uint32_t seg_groups(uint32_t a, uint32_t c) {
+    return c ? ((a + c + 3) >> 2) - (a >> 2) : 0;
+}
+
+// gpre[j] = groups of segments < j, gpre[k] = total (whole block).
+__device__ void segment_groups_prefix(const uint32_t* __restrict__ segrow, const uint32_t* __restrict__ cntrow,
+                                      uint32_t k, uint32_t* gpre, uint32_t* sh32) {
+    const uint32_t per = (k + blockDim.x - 1) / blockDim.x;
+    const uint32_t lo = min(k, threadIdx.x * per), hi = min(k, lo + per);
+    uint32_t s = 0;
+    for (uint32_t j = lo; j < hi; ++j) s += seg_groups(segrow[j], cntrow[j]);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t x = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh32[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t t = lane < nw ? sh32[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, t, o);
+            if (lane >= o) t += y;
+        }
+        sh32[lane] = t;
+    }
+    __syncthreads();
+    uint32_t run = (warp ? sh32[warp - 1] : 0) + x - s;
+    for (uint32_t j = lo; j < hi; ++j) {
+        gpre[j] = run;
+        run += seg_groups(segrow[j], cntrow[j]);
+    }
+    if (threadIdx.x == 0) gpre[k] = sh32[nw - 1];
+    __syncthreads();
+}
+
+// update[t] = sspr[src[t] - base] for the groups [f_lo, f_hi) of the
+// partition's flattened segment list (Algorithm 3).
+__device__ __forceinline__ void scatter_groups(const float* sspr, uint32_t base, uint32_t len,
+                                               const uint32_t* gpre, uint32_t k,
+                                               const uint32_t* __restrict__ segrow,
+                                               const uint32_t* __restrict__ cntrow,
+                                               const uint32_t* __restrict__ src, float* __restrict__ upd,
+                                               uint32_t f_lo, uint32_t f_hi, int* err) {
+    uint32_t pd = 0;
+    for (uint32_t f0 = f_lo + threadIdx.x; f0 < f_hi; f0 += kScatterUnroll * blockDim.x) {
+        uint32_t e0[kScatterUnroll], s0[kScatterUnroll], c0[kScatterUnroll];
+        uint4 ids[kScatterUnroll];
+        bool live[kScatterUnroll], full[kScatterUnroll];
+#pragma unroll
+        for (int u = 0; u < kScatterUnroll; ++u) {
+            const uint32_t f = f0 + u * blockDim.x;
+            live[u] = f < f_hi;
+            full[u] = false;
+            if (live[u]) {
+                uint32_t a = pd, b = k;  // last segment whose prefix is <= f
+                while (a + 1 < b) {
+                    const uint32_t mid = (a + b) >> 1;
+                    if (gpre[mid] <= f) a = mid; else b = mid;
+                }
+                pd = a;
+                s0[u] = segrow[pd];
+                c0[u] = cntrow[pd];
+                e0[u] = ((s0[u] >> 2) + (f - gpre[pd])) << 2;
+                full[u] = e0[u] >= s0[u] && e0[u] + 4 <= s0[u] + c0[u];
+                if (full[u]) ids[u] = ld_stream_u4(src + e0[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kScatterUnroll; ++u) {
+            if (!live[u]) continue;
+            if (full[u]) {
+                const uint32_t i0 = ids[u].x - base, i1 = ids[u].y - base, i2 = ids[u].z - base, i3 = ids[u].w - base;
+                if (i0 < len && i1 < len && i2 < len && i3 < len)
+                    st_stream_f4(upd + e0[u], make_float4(sspr[i0], sspr[i1], sspr[i2], sspr[i3]));
+                else
+                    atomicOr(err, kErrBounds);
+            } else {
+#pragma unroll
+                for (uint32_t j = 0; j < 4; ++j) {
+                    const uint32_t e = e0[u] + j;
+                    if (e >= s0[u] && e < s0[u] + c0[u]) {
+                        const uint32_t i = src[e] - base;
+                        if (i < len) upd[e] = sspr[i]; else atomicOr(err, kErrBounds);
+                    }
+                }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ init
+__global__ void __launch_bounds__(kReduceThreads) init_kernel(uint32_t n, const float* __restrict__ pr_init,
+                                                              const float* __restrict__ inv_deg, float* __restrict__ pr,
+                                                              double* __restrict__ partials) {
+    const float uniform = (float)(1.0 / (double)n);
+    double dang = 0.0, zero = 0.0;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const float x = pr_init ? pr_init[v] : uniform;
+        pr[v] = x;
+        if (inv_deg[v] == 0.0f) dang += (double)x;
+    }
+    block_sum2<kReduceThreads>(zero, dang);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = 0.0;
+        partials[2 * blockIdx.x + 1] = dang;
+    }
+}
+
+__global__ void spr_kernel(uint32_t n, const float* __restrict__ pr, const float* __restrict__ inv_deg,
+                           float* __restrict__ spr) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        spr[v] = pr[v] * inv_deg[v];
+}
+
+// --------------------------------------------------------------- scatter
+__global__ void __launch_bounds__(kScatterThreads, 1) scatter_kernel(
+    uint32_t n, uint32_t q, uint32_t k, const float* __restrict__ pr, const float* __restrict__ inv_deg,
+    const uint32_t* __restrict__ src, const uint32_t* __restrict__ seg_u, const uint32_t* __restrict__ cnt_u,
+    const uint32_t* __restrict__ src_order, float* __restrict__ upd, const DevState* __restrict__ st,
+    int* __restrict__ err) {
+    if (st->stop) return;
+    extern __shared__ __align__(128) unsigned char smraw[];
+    __shared__ uint32_t sh32[32];
+    float* sspr = reinterpret_cast<float*>(smraw);
+    uint32_t* gpre = reinterpret_cast<uint32_t*>(smraw + (size_t)((q + 3) & ~3u) * sizeof(float));
+    const uint32_t p = src_order[blockIdx.x];
+    const uint32_t base = p * q, len = min(q, n - base);
+    const uint32_t* segrow = seg_u + (size_t)p * k;
+    const uint32_t* cntrow = cnt_u + (size_t)p * k;
+    // SPR of the partition, staged in shared memory.
+    if ((base & 3) == 0) {
+        const uint32_t v4 = len >> 2;
+        for (uint32_t i = threadIdx.x; i < v4; i += blockDim.x) {
+            const float4 x = __ldg(reinterpret_cast<const float4*>(pr + base) + i);
+            const float4 w = __ldg(reinterpret_cast<const float4*>(inv_deg + base) + i);
+            reinterpret_cast<float4*>(sspr)[i] = make_float4(x.x * w.x, x.y * w.y, x.z * w.z, x.w * w.w);
+        }
+        for (uint32_t i = (v4 << 2) + threadIdx.x; i < len; i += blockDim.x) sspr[i] = pr[base + i] * inv_deg[base + i];
+    } else {
+        for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) sspr[i] = pr[base + i] * inv_deg[base + i];
+    }
+    segment_groups_prefix(segrow, cntrow, k, gpre, sh32);
+    scatter_groups(sspr, base, len, gpre, k, segrow, cntrow, src, upd, 0, gpre[k], err);
+}
+
+// ---------------------------------------------------------- gather+apply
+struct GatherArgs {
+    uint32_t n, q, k;
+    const uint32_t* dest;
+    const uint32_t* bin_e;
+    const uint32_t* chunk_base;
+    const uint32_t* bin_order;
+    const uint32_t* hubs;
+    const float* upd_in;
+    const float* pr_in;
+    const float* inv_deg;
+    float* pr_out;
+    double* partials;
+    const DevState* st;
+    int* err;
+    float d;
+    int uniform_dangling;
+    // fused scatter of the next iteration
+    const uint32_t* src;
+    const uint32_t* seg_u;
+    const uint32_t* cnt_u;
+    float* upd_out;
+};
+
+constexpr uint32_t kIdSlotBytes = kChunk * sizeof(uint32_t);
+constexpr uint32_t kUpdSlotBytes = kUpdSlot * sizeof(float);
+constexpr uint32_t kStageBytes = kIdSlotBytes + kUpdSlotBytes;
+constexpr size_t kRingBytes = (size_t)kGatherWarps * kGatherStages * kStageBytes;
+constexpr size_t kBarBytes = (size_t)kGatherWarps * kGatherStages * sizeof(uint64_t);
+constexpr size_t kMetaBytes = (size_t)kGatherWarps * kGatherStages * 2 * sizeof(uint32_t);
+constexpr size_t kAccOffset = kRingBytes + kBarBytes + kMetaBytes;
+static_assert(kStageBytes % 16 == 0, "ring slots must stay 16-byte aligned");
+static_assert(kAccOffset % 16 == 0, "accumulator must be 16-byte aligned");
+
+__device__ __forceinline__ void gather_one(uint32_t id, uint32_t uoff, uint32_t pos, uint32_t E0, uint32_t E1,
+                                           uint32_t vbase, uint32_t len, const float* ups, float* acc, uint32_t h0,
+                                           uint32_t h1, float& a0, float& a1, int* err) {
+    if (pos >= E0 && pos < E1) {
+        const uint32_t local = (id & kIdMask) - vbase;
+        if (uoff >= kUpdSlot) {
+            atomicOr(err, kErrBounds);
+            return;
+        }
+        const float val = ups[uoff];
+        if (local == h0) a0 += val;
+        else if (local == h1) a1 += val;
+        else if (local < len) atomicAdd(&acc[local], val);
+        else atomicOr(err, kErrBounds);
+    }
+}
+
+template <bool kFused>
+__global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const GatherArgs a) {
+    if (a.st->stop) return;
+    extern __shared__ __align__(128) unsigned char smraw[];
+    __shared__ uint32_t sh32[32];
+    unsigned char* ring = smraw;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smraw + kRingBytes);
+    uint32_t* meta = reinterpret_cast<uint32_t*>(smraw + kRingBytes + kBarBytes);
+    float* acc = reinterpret_cast<float*>(smraw + kAccOffset);
+
+    const uint32_t S = cluster_size(), rank = cluster_rank();
+    const uint32_t pd = a.bin_order[blockIdx.x / S];
+    const uint32_t vbase = pd * a.q, len = min(a.q, a.n - vbase);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    for (uint32_t i = threadIdx.x; i < (len + 3) / 4; i += blockDim.x)
+        reinterpret_cast<float4*>(acc)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (threadIdx.x < kGatherWarps * kGatherStages) mbar_init(&bars[threadIdx.x], 1);
+    fence_mbar_init();
+    __syncthreads();
+
+    const uint32_t h0 = a.hubs[2 * pd], h1 = a.hubs[2 * pd + 1];
+    float hub0 = 0.0f, hub1 = 0.0f;
+    const uint32_t E0 = a.bin_e[pd], E1 = a.bin_e[pd + 1];
+    if (E1 > E0) {
+        const uint32_t c_first = E0 / kChunk;
+        const uint32_t nch = (E1 - 1) / kChunk - c_first + 1;
+        const uint32_t gw = rank * kGatherWarps + warp, GW = S * kGatherWarps;
+        const uint32_t wc0 = c_first + (uint32_t)((uint64_t)nch * gw / GW);
+        const uint32_t nmine = c_first + (uint32_t)((uint64_t)nch * (gw + 1) / GW) - wc0;
+        unsigned char* wring = ring + (size_t)warp * kGatherStages * kStageBytes;
+        uint64_t* wbar = bars + warp * kGatherStages;
+        uint32_t* wmeta = meta + warp * kGatherStages * 2;
+        const uint32_t lt = lanemask_lt();
+
+        // Chunk bases of this warp's run, 32 per register table, two tables ahead.
+        auto load_table = [&](uint32_t t) -> uint32_t {
+            const uint32_t j = 32 * t + lane;
+            return j <= nmine ? a.chunk_base[wc0 + j] : 0u;
+        };
+        uint32_t tb = 0, t0 = load_table(0), t1 = load_table(1), t2 = load_table(2);
+        auto cb_of = [&](uint32_t j) -> uint32_t {  // warp-collective, j in [32 tb, 32 tb + 64)
+            const uint32_t x0 = __shfl_sync(kFull, t0, j & 31);
+            const uint32_t x1 = __shfl_sync(kFull, t1, j & 31);
+            return (j >> 5) == tb ? x0 : x1;
+        };
+        auto issue = [&](uint32_t j) {  // warp-collective
+            if (((j + 1) >> 5) > tb + 1) {
+                ++tb;
+                t0 = t1;
+                t1 = t2;
+                t2 = load_table(tb + 2);
+            }
+            const uint32_t cb0 = cb_of(j), cb1 = cb_of(j + 1);
+            if (lane == 0) {
+                const uint32_t slot = j % kGatherStages;
+                const uint32_t us = (cb0 > 0 ? cb0 - 1 : 0) & ~3u;
+                const uint32_t ue = (cb1 + 3) & ~3u;
+                const uint32_t ubytes = (ue - us) * (uint32_t)sizeof(float);
+                wmeta[2 * slot] = cb0;
+                wmeta[2 * slot + 1] = us;
+                unsigned char* dst = wring + (size_t)slot * kStageBytes;
+                mbar_arrive_expect_tx(&wbar[slot], kIdSlotBytes + ubytes);
+                bulk_load(dst, a.dest + (size_t)(wc0 + j) * kChunk, kIdSlotBytes, &wbar[slot]);
+                if (ubytes) bulk_load(dst + kIdSlotBytes, a.upd_in + us, ubytes, &wbar[slot]);
+            }
+        };
+
+        const uint32_t pre = nmine < (uint32_t)kGatherStages ? nmine : (uint32_t)kGatherStages;
+        for (uint32_t j = 0; j < pre; ++j) issue(j);
+        uint32_t issued = pre;
+        uint32_t j = 0;
+        bool ok = true;
+        for (; j < nmine; ++j) {
+            const uint32_t slot = j % kGatherStages;
+            ok = __all_sync(kFull, mbar_wait_bounded(&wbar[slot], (j / kGatherStages) & 1u));
+            if (!ok) break;
+            const unsigned char* stage = wring + (size_t)slot * kStageBytes;
+            const uint32_t* ids_s = reinterpret_cast<const uint32_t*>(stage);
+            const float* ups = reinterpret_cast<const float*>(stage + kIdSlotBytes);
+            uint32_t fbase = wmeta[2 * slot];
+            const uint32_t us = wmeta[2 * slot + 1];
+            const uint32_t cstart = (wc0 + j) * kChunk;
+#pragma unroll
+            for (int h = 0; h < (int)(kChunk / 128); ++h) {
+                const uint4 ids = *reinterpret_cast<const uint4*>(ids_s + h * 128 + lane * 4);
+                const uint32_t f0 = ids.x >> 31, f1 = ids.y >> 31, f2 = ids.z >> 31, f3 = ids.w >> 31;
+                const uint32_t b0 = __ballot_sync(kFull, f0), b1 = __ballot_sync(kFull, f1);
+                const uint32_t b2 = __ballot_sync(kFull, f2), b3 = __ballot_sync(kFull, f3);
+                const uint32_t before = __popc(b0 & lt) + __popc(b1 & lt) + __popc(b2 & lt) + __popc(b3 & lt);
+                // update index (relative to the slot) of each ID: inclusive flag count - 1
+                const uint32_t u0 = fbase + before + f0 - 1 - us;
+                const uint32_t u1 = u0 + f1, u2 = u1 + f2, u3 = u2 + f3;
+                const uint32_t pos = cstart + h * 128 + lane * 4;
+                gather_one(ids.x, u0, pos, E0, E1, vbase, len, ups, acc, h0, h1, hub0, hub1, a.err);
+                gather_one(ids.y, u1, pos + 1, E0, E1, vbase, len, ups, acc, h0, h1, hub0, hub1, a.err);
+                gather_one(ids.z, u2, pos + 2, E0, E1, vbase, len, ups, acc, h0, h1, hub0, hub1, a.err);
+                gather_one(ids.w, u3, pos + 3, E0, E1, vbase, len, ups, acc, h0, h1, hub0, hub1, a.err);
+                fbase += __popc(b0) + __popc(b1) + __popc(b2) + __popc(b3);
+            }
+            __syncwarp();
+            if (issued < nmine) {
+                issue(issued);
+                ++issued;
+            }
+        }
+        if (!ok) {
+            // A copy did not land in time: record it, then wait (bounded) for
+            // every copy still in flight before shared memory is reused.
+            if (lane == 0) atomicOr(a.err, kErrTimeout);
+            for (uint32_t jj = j; jj < issued; ++jj)
+                (void)mbar_wait_bounded(&wbar[jj % kGatherStages], (jj / kGatherStages) & 1u);
+        }
+    }
+    // Register sums of the two hubs.
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        hub0 += __shfl_xor_sync(kFull, hub0, o);
+        hub1 += __shfl_xor_sync(kFull, hub1, o);
+    }
+    if (lane == 0) {
+        if (h0 < len) atomicAdd(&acc[h0], hub0);
+        if (h1 < len) atomicAdd(&acc[h1], hub1);
+    }
+    cluster_sync();
+
+    // Apply over this CTA's 1/S of the partition (multiples of 4 nodes).
+    const uint32_t per = (((len + S - 1) / S) + 3) & ~3u;
+    const uint32_t lo = min(len, rank * per), hi = min(len, lo + per);
+    const double D = a.uniform_dangling ? a.st->dangling : 0.0;
+    const float cst = (float)((1.0 - (double)a.d) / (double)a.n + (double)a.d * D / (double)a.n);
+    double res = 0.0, dg = 0.0;
+    for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        float s = 0.0f;
+        for (uint32_t r = 0; r < S; ++r) s += ld_cluster_f32(map_rank(acc + i, r));
+        const uint32_t v = vbase + i;
+        const float x = fmaf(a.d, s, cst);
+        const float old = a.pr_in[v];
+        const float inv = a.inv_deg[v];
+        a.pr_out[v] = x;
+        if (kFused) acc[i] = x * inv;
+        res += fabs((double)x - (double)old);
+        if (inv == 0.0f) dg += (double)x;
+    }
+    block_sum2<kGatherWarps * 32>(res, dg);
+    if (threadIdx.x == 0) {
+        a.partials[2 * blockIdx.x] = res;
+        a.partials[2 * blockIdx.x + 1] = dg;
+    }
+    cluster_sync();
+
+    if constexpr (kFused) {
+        // Fused scatter of the next iteration: gather SPR' of the whole
+        // partition into this CTA's shared memory, then write 1/S of its
+        // update segments.
+        for (uint32_t r = 0; r < S; ++r) {
+            if (r == rank) continue;
+            const uint32_t rlo = min(len, r * per), rhi = min(len, rlo + per);
+            const uint32_t q4 = (rhi - rlo) >> 2;
+            for (uint32_t i = threadIdx.x; i < q4; i += blockDim.x)
+                reinterpret_cast<float4*>(acc + rlo)[i] = ld_cluster_f32x4(map_rank(acc + rlo + 4 * i, r));
+            for (uint32_t i = rlo + (q4 << 2) + threadIdx.x; i < rhi; i += blockDim.x)
+                acc[i] = ld_cluster_f32(map_rank(acc + i, r));
+        }
+        cluster_sync();  // no CTA reads another's shared memory after this point
+        uint32_t* gpre = reinterpret_cast<uint32_t*>(ring);
+        const uint32_t* segrow = a.seg_u + (size_t)pd * a.k;
+        const uint32_t* cntrow = a.cnt_u + (size_t)pd * a.k;
+        segment_groups_prefix(segrow, cntrow, a.k, gpre, sh32);
+        const uint32_t G = gpre[a.k];
+        const uint32_t f_lo = (uint32_t)((uint64_t)G * rank / S);
+        const uint32_t f_hi = (uint32_t)((uint64_t)G * (rank + 1) / S);
+        scatter_groups(acc, vbase, len, gpre, a.k, segrow, cntrow, a.src, a.upd_out, f_lo, f_hi, a.err);
+    }
+}
+
+// ---------------------------------------------------------------- reduce
+__global__ void __launch_bounds__(kReduceThreads) reduce_kernel(const double* __restrict__ partials, int count,
+                                                                DevState* __restrict__ st, double* __restrict__ hist,
+                                                                int hist_slot, double tol) {
+    if (st->stop) return;
+    double r = 0.0, dg = 0.0;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) {
+        r += partials[2 * i];
+        dg += partials[2 * i + 1];
+    }
+    block_sum2<kReduceThreads>(r, dg);
+    if (threadIdx.x == 0) {
+        st->dangling = dg;
+        if (hist_slot >= 0) {
+            st->residual = r;
+            hist[hist_slot] = r;
+            st->iters_done += 1;
+            if (tol > 0.0 && r < tol) st->stop = 1;
+        }
+    }
+}
+
+constexpr int kInitBlocks = 1024;
+
+size_t gather_smem_bytes(uint32_t q) { return kAccOffset + (size_t)((q + 3) & ~3u) * sizeof(float); }
+size_t scatter_smem_bytes(uint32_t q, uint32_t k) {
+    return (size_t)((q + 3) & ~3u) * sizeof(float) + (size_t)(k + 1) * sizeof(uint32_t);
+}
+
+}  // namespace
+
+size_t partial_slots(const pcpm_png* g) {
+    return std::max<size_t>((size_t)g->k * kMaxCluster, (size_t)kInitBlocks);
+}
+
+// Picks the cluster size for the gather and sets shared-memory limits.
+int configure_kernels(pcpm_png* g) {
+    const size_t gs = gather_smem_bytes(g->q), ss = scatter_smem_bytes(g->q, g->k);
+    if (cudaFuncSetAttribute(gather_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gs) != cudaSuccess ||
+        cudaFuncSetAttribute(gather_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gs) != cudaSuccess ||
+        cudaFuncSetAttribute(scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss) != cudaSuccess)
+        return PCPM_ECUDA;
+    // Enough CTAs to give every SM about four of them, at least two per bin, at
+    // most kMaxCluster; a PCPM_GATHER_CLUSTER environment variable (1, 2, 4 or
+    // 8) overrides the choice.
+    int want = 2;
+    while (want < kMaxCluster && (uint64_t)g->k * want < (uint64_t)g->sms * 4) want *= 2;
+    if (const char* env = getenv("PCPM_GATHER_CLUSTER")) {
+        const int v = atoi(env);
+        if (v == 1 || v == 2 || v == 4 || v == 8) want = v;
+    }
+    for (int S = want; S >= 1; S /= 2) {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = S;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(g->k * S);
+        cfg.blockDim = dim3(kGatherWarps * 32);
+        cfg.dynamicSmemBytes = gs;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int clusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&clusters, gather_kernel<true>, &cfg) == cudaSuccess && clusters > 0) {
+            g->cluster = S;
+            return PCPM_OK;
+        }
+        cudaGetLastError();
+    }
+    return PCPM_ECUDA;
+}
+
+int launch_init(pcpm_png* g, const float* pr_init, cudaStream_t s) {
+    const int blocks = (int)std::min<uint64_t>(kInitBlocks, (g->n + kReduceThreads - 1) / kReduceThreads);
+    init_kernel<<<blocks, kReduceThreads, 0, s>>>(g->n, pr_init, g->inv_deg, g->pr[g->cur], g->partials);
+    g->partial_count = blocks;
+    return cudaGetLastError() == cudaSuccess ? PCPM_OK : PCPM_ECUDA;
+}
+
+int launch_spr(pcpm_png* g, float* spr, cudaStream_t s) {
+    spr_kernel<<<(int)std::min<uint64_t>(4096, (g->n + 255) / 256), 256, 0, s>>>(g->n, g->pr[g->cur], g->inv_deg,
+                                                                                  spr);
+    return cudaGetLastError() == cudaSuccess ? PCPM_OK : PCPM_ECUDA;
+}
+
+int launch_scatter(pcpm_png* g, cudaStream_t s) {
+    scatter_kernel<<<g->k, kScatterThreads, scatter_smem_bytes(g->q, g->k), s>>>(
+        g->n, g->q, g->k, g->pr[g->cur], g->inv_deg, g->src, g->seg_u, g->cnt_u, g->src_order, g->upd[g->ucur],
+        g->state, &g->state->err);
+    return cudaGetLastError() == cudaSuccess ? PCPM_OK : PCPM_ECUDA;
+}
+
+int launch_gather(pcpm_png* g, float d, uint32_t flags, bool fused, cudaStream_t s) {
+    GatherArgs a;
+    a.n = g->n;
+    a.q = g->q;
+    a.k = g->k;
+    a.dest = g->dest;
+    a.bin_e = g->bin_e;
+    a.chunk_base = g->chunk_base;
+    a.bin_order = g->bin_order;
+    a.hubs = g->hubs;
+    a.upd_in = g->upd[g->ucur];
+    a.pr_in = g->pr[g->cur];
+    a.inv_deg = g->inv_deg;
+    a.pr_out = g->pr[g->cur ^ 1];
+    a.partials = g->partials;
+    a.st = g->state;
+    a.err = &g->state->err;
+    a.d = d;
+    a.uniform_dangling = (flags & PCPM_DANGLING_LEAK) ? 0 : 1;
+    a.src = g->src;
+    a.seg_u = g->seg_u;
+    a.cnt_u = g->cnt_u;
+    a.upd_out = g->upd[g->ucur ^ 1];
+
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = g->cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(g->k * g->cluster);
+    cfg.blockDim = dim3(kGatherWarps * 32);
+    cfg.dynamicSmemBytes = gather_smem_bytes(g->q);
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = fused ? cudaLaunchKernelEx(&cfg, gather_kernel<true>, a)
+                                : cudaLaunchKernelEx(&cfg, gather_kernel<false>, a);
+    g->partial_count = (int)(g->k * g->cluster);
+    return e == cudaSuccess ? PCPM_OK : PCPM_ECUDA;
+}
+
+int launch_reduce(pcpm_png* g, double tol, int hist_slot, cudaStream_t s) {
+    reduce_kernel<<<1, kReduceThreads, 0, s>>>(g->partials, g->partial_count, g->state, g->hist, hist_slot, tol);
+    return cudaGetLastError() == cudaSuccess ? PCPM_OK : PCPM_ECUDA;
+}
+
+}  // namespace pcpm

@@ -1,0 +1,620 @@
+// png_build.cu - device construction of the Partition-Node Graph (Sec. 3.3).
+//
+// The paper builds the PNG with two scans over each source partition's edges:
+// the first counts, per destination partition p', the updates (one per node
+// with a neighbour in p', Sec. 3.2) and the edges; a prefix sum turns the counts
+// into write offsets (Sec. 3.1); the second scan fills the bins. Here the same
+// two scans run as a stable counting sort of all edges keyed by destination
+// partition:
+//   tiles      every source partition's edge range is cut into tiles of
+//              kTileEdges edges (one warp each), so a tile never straddles two
+//              source partitions;
+//   count      each warp counts edges and message starts per key p' over its
+//              tile into warp-private shared-memory tables;
+//   scan       column-wise exclusive scans of the [tile][p'] tables give every
+//              tile its write cursor into every bin, and the column totals give
+//              the bin starts. Because tiles follow CSR order, the cursor of the
+//              first tile of partition p is exactly the Sec. 3.1 offset of p;
+//   fill       each warp replays its tile, ranks equal keys inside a 32-edge
+//              window with match/ballot, and writes destination IDs (first of a
+//              message flagged) and, for message starts, the source node.
+// The result is the canonical bin order: source partitions in ID order, nodes
+// in ID order, destinations in adjacency order. Finally the per-chunk update
+// bases used by the gather (number of flagged IDs before every kChunk-entry
+// chunk), the two largest in-degrees of every bin (kept in registers by the
+// gather), largest-first launch orders of bins and source partitions, and
+// 1/outdegree are computed.
+#include <algorithm>
+#include <vector>
+
+#include "pcpm_internal.cuh"
+
+namespace pcpm {
+namespace {
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t r;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(r));
+    return r;
+}
+
+// First index i in [lo, hi) with a[i] > x (hi if none); a is non-decreasing.
+__device__ __forceinline__ uint32_t upper_bound_u32(const uint32_t* a, uint32_t lo, uint32_t hi, uint32_t x) {
+    while (lo < hi) {
+        uint32_t mid = lo + ((hi - lo) >> 1);
+        if (a[mid] <= x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Exclusive scan of one value per thread over a block of up to 1024 threads.
+__device__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* total, uint32_t* sh32) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh32[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t s = lane < nw ? sh32[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        sh32[lane] = s;
+    }
+    __syncthreads();
+    const uint32_t prefix = warp ? sh32[warp - 1] : 0;
+    *total = sh32[nw - 1];
+    __syncthreads();
+    return prefix + x - v;
+}
+
+// --------------------------------------------------------- small scans
+// out[0..N] = exclusive scan of in[0..N), out[N] = total. One block of 1024
+// threads, N <= 1024 * kSmallScanItems.
+constexpr int kSmallScanItems = 16;
+
+__global__ void __launch_bounds__(1024) scan_small_kernel(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
+                                                          uint32_t N) {
+    __shared__ uint32_t sh32[32];
+    const uint32_t per = (N + blockDim.x - 1) / blockDim.x;
+    const uint32_t lo = min(N, threadIdx.x * per), hi = min(N, lo + per);
+    uint32_t s = 0;
+    for (uint32_t i = lo; i < hi; ++i) s += in[i];
+    uint32_t total;
+    uint32_t run = block_exclusive_scan(s, &total, sh32);
+    for (uint32_t i = lo; i < hi; ++i) {
+        uint32_t x = in[i];
+        out[i] = run;
+        run += x;
+    }
+    if (threadIdx.x == 0) out[N] = total;
+}
+
+// Large exclusive scan: block sums, a small scan of the sums, then the blocks.
+constexpr uint32_t kScanBlockItems = 4096;  // 1024 threads x 4
+
+__global__ void __launch_bounds__(1024) scan_block_sums_kernel(const uint32_t* __restrict__ in, uint32_t N,
+                                                               uint32_t* __restrict__ sums) {
+    const uint32_t base = blockIdx.x * kScanBlockItems + threadIdx.x * 4;
+    uint32_t s = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) s += (base + j < N) ? in[base + j] : 0;
+    s = __reduce_add_sync(0xffffffffu, s);
+    __shared__ uint32_t ws[32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        uint32_t t = ws[threadIdx.x];
+        t = __reduce_add_sync(0xffffffffu, t);
+        if (threadIdx.x == 0) sums[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(1024) scan_block_apply_kernel(const uint32_t* __restrict__ in, uint32_t N,
+                                                                const uint32_t* __restrict__ block_off,
+                                                                uint32_t* __restrict__ out) {
+    __shared__ uint32_t sh32[32];
+    const uint32_t base = blockIdx.x * kScanBlockItems + threadIdx.x * 4;
+    uint32_t x[4];
+    uint32_t s = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        x[j] = (base + j < N) ? in[base + j] : 0;
+        s += x[j];
+    }
+    uint32_t total;
+    uint32_t run = block_off[blockIdx.x] + block_exclusive_scan(s, &total, sh32);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if (base + j < N) out[base + j] = run;
+        run += x[j];
+    }
+}
+
+// ---------------------------------------------------- CSR validation
+__global__ void check_row_ptr_kernel(const uint32_t* __restrict__ row_ptr, uint32_t n, int* __restrict__ err) {
+    for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x)
+        if (row_ptr[u] > row_ptr[u + 1]) atomicOr(err, kErrBadGraph);
+}
+
+// ------------------------------------------------------ partition tiles
+__global__ void partition_tiles_kernel(const uint32_t* __restrict__ row_ptr, uint32_t n, uint32_t q, uint32_t k,
+                                       uint32_t* __restrict__ tiles) {
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < k; p += gridDim.x * blockDim.x) {
+        const uint32_t u0 = p * q, u1 = min(n, u0 + q);
+        const uint32_t edges = row_ptr[u1] - row_ptr[u0];
+        tiles[p] = (edges + kTileEdges - 1) / kTileEdges;
+    }
+}
+
+// ------------------------------------------------ count / fill of tiles
+// One warp per tile. kFill = false: per-tile counts of edges (tab_e) and of
+// message starts (tab_u) for every destination partition. kFill = true: the
+// tables hold scanned cursors; write the bins.
+template <bool kFill>
+__global__ void tile_kernel(const uint32_t* __restrict__ row_ptr, const uint32_t* __restrict__ col, uint32_t n,
+                            uint32_t q, uint32_t k, const uint32_t* __restrict__ tile_start, uint32_t ntiles,
+                            uint32_t* __restrict__ tab_e, uint32_t* __restrict__ tab_u,
+                            const uint32_t* __restrict__ bin_e, const uint32_t* __restrict__ bin_u,
+                            uint32_t* __restrict__ dest, uint32_t* __restrict__ src, int* __restrict__ err) {
+    extern __shared__ uint32_t sh[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+    uint32_t* ce = sh + (size_t)warp * 2 * k;  // edges (count) / ID cursor (fill)
+    uint32_t* cu = ce + k;                      // updates / update cursor
+    const uint32_t lt = lanemask_lt();
+
+    for (uint32_t t = blockIdx.x * wpc + warp; t < ntiles; t += gridDim.x * wpc) {
+        const uint32_t p = upper_bound_u32(tile_start, 0, k + 1, t) - 1;
+        const uint32_t u_begin = p * q, u_end = min(n, u_begin + q);
+        const uint32_t e_begin = row_ptr[u_begin] + (t - tile_start[p]) * kTileEdges;
+        const uint32_t e_end = (uint32_t)min((uint64_t)e_begin + kTileEdges, (uint64_t)row_ptr[u_end]);
+        for (uint32_t j = lane; j < k; j += 32) {
+            if (kFill) {
+                ce[j] = bin_e[j] + tab_e[(size_t)t * k + j];
+                cu[j] = bin_u[j] + tab_u[(size_t)t * k + j];
+            } else {
+                ce[j] = 0;
+                cu[j] = 0;
+            }
+        }
+        __syncwarp();
+        // Rows covering the tile: the last row starting at or before an edge owns it.
+        const uint32_t ulo = upper_bound_u32(row_ptr, u_begin, u_end + 1, e_begin) - 1;
+        const uint32_t uhi = upper_bound_u32(row_ptr, ulo, u_end + 1, e_end - 1) - 1;
+        uint32_t carry_v = (e_begin > row_ptr[ulo]) ? col[e_begin - 1] : 0;
+
+        for (uint32_t w0 = e_begin; w0 < e_end; w0 += 32) {
+            const uint32_t e = w0 + lane;
+            bool valid = e < e_end;
+            uint32_t u = 0, v = 0;
+            if (valid) {
+                u = upper_bound_u32(row_ptr, ulo, uhi + 1, e) - 1;
+                v = col[e];
+            }
+            uint32_t prev_v = __shfl_up_sync(0xffffffffu, v, 1);
+            if (lane == 0) prev_v = carry_v;
+            carry_v = __shfl_sync(0xffffffffu, v, 31);
+            uint32_t key = 0xffffffffu;
+            bool start = false;
+            if (valid) {
+                const bool row_start = (e == row_ptr[u]);
+                if (v >= n || (!row_start && prev_v > v)) {
+                    atomicOr(err, kErrBadGraph);
+                    valid = false;
+                } else {
+                    key = v / q;
+                    start = row_start || (prev_v / q != key);
+                }
+            }
+            const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+            const uint32_t smask = __ballot_sync(0xffffffffu, start);
+            const uint32_t peers = __match_any_sync(0xffffffffu, key) & vmask;
+            if (kFill && valid) {
+                const uint32_t pos_e = ce[key] + __popc(peers & lt);
+                dest[pos_e] = start ? (v | kMsb) : v;
+                if (start) src[cu[key] + __popc(peers & smask & lt)] = u;
+            }
+            __syncwarp();
+            if (valid && lane == __ffs(peers) - 1) {
+                ce[key] += __popc(peers);
+                cu[key] += __popc(peers & smask);
+            }
+            __syncwarp();
+        }
+        if (!kFill) {
+            for (uint32_t j = lane; j < k; j += 32) {
+                tab_e[(size_t)t * k + j] = ce[j];
+                tab_u[(size_t)t * k + j] = cu[j];
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------ column scans of tables
+// A table is [nrows + 1][k]; rows are tiles. After the three kernels, row r
+// holds the exclusive column prefix over rows < r and row nrows the totals.
+constexpr uint32_t kColRows = 256;  // rows per block (multiple of 32)
+
+__global__ void __launch_bounds__(1024) colscan_sums_kernel(const uint32_t* __restrict__ tab, uint32_t nrows,
+                                                            uint32_t k, uint32_t* __restrict__ bsum) {
+    __shared__ uint32_t red[32][33];
+    const uint32_t tx = threadIdx.x, ty = threadIdx.y;
+    const uint32_t key = blockIdx.x * 32 + tx;
+    const uint32_t r0 = blockIdx.y * kColRows, r1 = min(nrows, r0 + kColRows);
+    uint32_t s = 0;
+    if (key < k)
+        for (uint32_t r = r0 + ty; r < r1; r += 32) s += tab[(size_t)r * k + key];
+    red[ty][tx] = s;
+    __syncthreads();
+    if (ty == 0 && key < k) {
+        uint32_t t = 0;
+        for (int i = 0; i < 32; ++i) t += red[i][tx];
+        bsum[(size_t)blockIdx.y * k + key] = t;
+    }
+}
+
+__global__ void colscan_blocks_kernel(uint32_t* __restrict__ bsum, uint32_t nb, uint32_t k,
+                                      uint32_t* __restrict__ tab, uint32_t nrows, uint32_t* __restrict__ totals) {
+    const uint32_t key = blockIdx.x * blockDim.x + threadIdx.x;
+    if (key >= k) return;
+    uint32_t run = 0;
+    for (uint32_t b = 0; b < nb; ++b) {
+        const uint32_t x = bsum[(size_t)b * k + key];
+        bsum[(size_t)b * k + key] = run;
+        run += x;
+    }
+    tab[(size_t)nrows * k + key] = run;
+    totals[key] = run;
+}
+
+__global__ void __launch_bounds__(1024) colscan_apply_kernel(uint32_t* __restrict__ tab, uint32_t nrows, uint32_t k,
+                                                             const uint32_t* __restrict__ boff) {
+    __shared__ uint32_t sm[32][33];
+    __shared__ uint32_t carry[32];
+    const uint32_t tx = threadIdx.x, ty = threadIdx.y;
+    const uint32_t key = blockIdx.x * 32 + tx;
+    const uint32_t r0 = blockIdx.y * kColRows, r1 = min(nrows, r0 + kColRows);
+    if (ty == 0) carry[tx] = key < k ? boff[(size_t)blockIdx.y * k + key] : 0;
+    __syncthreads();
+    for (uint32_t g = r0; g < r1; g += 32) {
+        const uint32_t r = g + ty;
+        const bool ok = key < k && r < r1;
+        sm[ty][tx] = ok ? tab[(size_t)r * k + key] : 0;
+        __syncthreads();
+        // warp ty scans key column ty of this block over rows tx
+        const uint32_t y = sm[tx][ty];
+        uint32_t incl = y;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t z = __shfl_up_sync(0xffffffffu, incl, o);
+            if (tx >= o) incl += z;
+        }
+        const uint32_t c = carry[ty];
+        sm[tx][ty] = c + incl - y;
+        __syncthreads();
+        if (tx == 31) carry[ty] = c + incl;
+        if (ok) tab[(size_t)r * k + key] = sm[ty][tx];
+        __syncthreads();
+    }
+}
+
+// --------------------------------------------------- segments and chunks
+// seg_x[p][p'] = absolute start of the entries partition p writes into bin p';
+// cnt_x[p][p'] = their number. Row tile_start[p] of a scanned table is the
+// Sec. 3.1 offset of partition p (row ntiles = column totals).
+__global__ void segments_kernel(const uint32_t* __restrict__ tab, const uint32_t* __restrict__ tile_start,
+                                const uint32_t* __restrict__ bin, uint32_t k, uint32_t* __restrict__ seg,
+                                uint32_t* __restrict__ cnt) {
+    const uint64_t total = (uint64_t)k * k;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t p = (uint32_t)(i / k), pd = (uint32_t)(i % k);
+        const uint32_t off = tab[(size_t)tile_start[p] * k + pd];
+        const uint32_t nxt = tab[(size_t)tile_start[p + 1] * k + pd];
+        seg[i] = bin[pd] + off;
+        cnt[i] = nxt - off;
+    }
+}
+
+// Flagged IDs per kChunk-entry chunk (one warp per chunk).
+__global__ void chunk_flags_kernel(const uint32_t* __restrict__ dest, uint64_t m, uint64_t nchunks,
+                                   uint32_t* __restrict__ cnt) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    for (uint64_t c = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); c < nchunks; c += warps) {
+        uint32_t s = 0;
+        for (uint32_t j = lane; j < kChunk; j += 32) {
+            const uint64_t pos = c * kChunk + j;
+            if (pos < m) s += dest[pos] >> 31;
+        }
+        s = __reduce_add_sync(0xffffffffu, s);
+        if (lane == 0) cnt[c] = s;
+    }
+}
+
+__global__ void inv_deg_kernel(const uint32_t* __restrict__ row_ptr, uint32_t n, float* __restrict__ inv) {
+    for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
+        const uint32_t deg = row_ptr[u + 1] - row_ptr[u];
+        inv[u] = deg ? 1.0f / (float)deg : 0.0f;
+    }
+}
+
+// In-degree of every node.
+__global__ void indegree_kernel(const uint32_t* __restrict__ col, uint64_t m, uint32_t* __restrict__ indeg) {
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < m; e += (uint64_t)gridDim.x * blockDim.x)
+        atomicAdd(&indeg[col[e]], 1u);
+}
+
+__device__ __forceinline__ unsigned long long block_max_u64(unsigned long long x, unsigned long long* sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = max(x, __shfl_xor_sync(0xffffffffu, x, o));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) sh[warp] = x;
+    __syncthreads();
+    x = lane < nw ? sh[lane] : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = max(x, __shfl_xor_sync(0xffffffffu, x, o));
+    __syncthreads();
+    return x;
+}
+
+// Per destination partition: local IDs of the two nodes with the largest
+// in-degree (ties to the lower ID), kNoHub below kHubMinInDegree. The gather
+// sums their updates in registers instead of contended shared-memory atomics.
+__global__ void __launch_bounds__(1024) hubs_kernel(const uint32_t* __restrict__ indeg, uint32_t n, uint32_t q,
+                                                    uint32_t* __restrict__ hubs) {
+    __shared__ unsigned long long sh[32];
+    const uint32_t p = blockIdx.x, base = p * q, len = min(q, n - base);
+    unsigned long long best = 0;
+    for (uint32_t i = threadIdx.x; i < len; i += blockDim.x)
+        best = max(best, ((unsigned long long)indeg[base + i] << 32) | (0xFFFFFFFFu - i));
+    const unsigned long long b1 = block_max_u64(best, sh);
+    unsigned long long second = 0;
+    for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) {
+        const unsigned long long key = ((unsigned long long)indeg[base + i] << 32) | (0xFFFFFFFFu - i);
+        if (key != b1) second = max(second, key);
+    }
+    const unsigned long long b2 = block_max_u64(second, sh);
+    if (threadIdx.x == 0) {
+        hubs[2 * p] = (b1 >> 32) >= kHubMinInDegree ? 0xFFFFFFFFu - (uint32_t)b1 : kNoHub;
+        hubs[2 * p + 1] = (b2 >> 32) >= kHubMinInDegree ? 0xFFFFFFFFu - (uint32_t)b2 : kNoHub;
+    }
+}
+
+// size[p] for ordering: entries of destination bin p, or 4-entry groups the
+// scatter of source partition p writes.
+__global__ void bin_sizes_kernel(const uint32_t* __restrict__ bin_e, uint32_t k, uint32_t* __restrict__ size) {
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < k; p += gridDim.x * blockDim.x)
+        size[p] = bin_e[p + 1] - bin_e[p];
+}
+
+__global__ void src_groups_kernel(const uint32_t* __restrict__ seg_u, const uint32_t* __restrict__ cnt_u, uint32_t k,
+                                  uint32_t* __restrict__ size) {
+    const uint32_t p = blockIdx.x;
+    uint32_t s = 0;
+    for (uint32_t j = threadIdx.x; j < k; j += blockDim.x) {
+        const uint32_t a = seg_u[(size_t)p * k + j], c = cnt_u[(size_t)p * k + j];
+        s += c ? ((a + c + 3) >> 2) - (a >> 2) : 0;
+    }
+    s = __reduce_add_sync(0xffffffffu, s);
+    __shared__ uint32_t ws[32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        uint32_t t = threadIdx.x < (blockDim.x >> 5) ? ws[threadIdx.x] : 0;
+        t = __reduce_add_sync(0xffffffffu, t);
+        if (threadIdx.x == 0) size[p] = t;
+    }
+}
+
+// order[rank] = p by decreasing size (ties to the lower index): the largest
+// units are launched first so the last wave is made of small ones.
+__global__ void order_kernel(const uint32_t* __restrict__ size, uint32_t k, uint32_t* __restrict__ order) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) {
+        const uint32_t si = size[i];
+        uint32_t rank = 0;
+        for (uint32_t j = 0; j < k; ++j) {
+            const uint32_t sj = size[j];
+            rank += (sj > si) || (sj == si && j < i);
+        }
+        order[rank] = i;
+    }
+}
+
+struct TempBufs {
+    std::vector<void*> ptrs;
+    ~TempBufs() {
+        for (void* p : ptrs) cudaFree(p);
+    }
+    template <class T>
+    cudaError_t alloc(T** p, size_t count) {
+        void* q = nullptr;
+        cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+        if (e == cudaSuccess) {
+            ptrs.push_back(q);
+            *p = (T*)q;
+        }
+        return e;
+    }
+};
+
+#define BCK(call)                                                                    \
+    do {                                                                             \
+        cudaError_t e_ = (call);                                                     \
+        if (e_ != cudaSuccess) return e_ == cudaErrorMemoryAllocation ? PCPM_ENOMEM : PCPM_ECUDA; \
+    } while (0)
+
+int grid_for(uint64_t work, int threads, int cap) {
+    uint64_t b = (work + threads - 1) / threads;
+    return (int)std::max<uint64_t>(1, std::min<uint64_t>(b, (uint64_t)cap));
+}
+
+// Exclusive scan of N values into out[0..N] (out[N] = total).
+int scan_exclusive(const uint32_t* in, uint32_t* out, uint64_t N, TempBufs& tmp, cudaStream_t s) {
+    if (N <= 1024ull * kSmallScanItems) {
+        scan_small_kernel<<<1, 1024, 0, s>>>(in, out, (uint32_t)N);
+        return cudaGetLastError() == cudaSuccess ? PCPM_OK : PCPM_ECUDA;
+    }
+    const uint64_t nb = (N + kScanBlockItems - 1) / kScanBlockItems;
+    if (nb > 1024ull * kSmallScanItems) return PCPM_EINVAL;
+    uint32_t *sums = nullptr, *offs = nullptr;
+    BCK(tmp.alloc(&sums, nb));
+    BCK(tmp.alloc(&offs, nb + 1));
+    scan_block_sums_kernel<<<(unsigned)nb, 1024, 0, s>>>(in, (uint32_t)N, sums);
+    scan_small_kernel<<<1, 1024, 0, s>>>(sums, offs, (uint32_t)nb);
+    scan_block_apply_kernel<<<(unsigned)nb, 1024, 0, s>>>(in, (uint32_t)N, offs, out);
+    BCK(cudaMemcpyAsync(out + N, offs + nb, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    return cudaGetLastError() == cudaSuccess ? PCPM_OK : PCPM_ECUDA;
+}
+
+int colscan(uint32_t* tab, uint32_t nrows, uint32_t k, uint32_t* totals, TempBufs& tmp, cudaStream_t s) {
+    const uint32_t nb = std::max<uint32_t>(1, (nrows + kColRows - 1) / kColRows);
+    uint32_t* bsum = nullptr;
+    BCK(tmp.alloc(&bsum, (size_t)nb * k));
+    dim3 blk(32, 32), grd((k + 31) / 32, nb);
+    colscan_sums_kernel<<<grd, blk, 0, s>>>(tab, nrows, k, bsum);
+    colscan_blocks_kernel<<<(k + 255) / 256, 256, 0, s>>>(bsum, nb, k, tab, nrows, totals);
+    colscan_apply_kernel<<<grd, blk, 0, s>>>(tab, nrows, k, bsum);
+    return cudaGetLastError() == cudaSuccess ? PCPM_OK : PCPM_ECUDA;
+}
+
+int read_err(int* d_err, cudaStream_t s, int* h_err) {
+    BCK(cudaMemcpyAsync(h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BCK(cudaStreamSynchronize(s));
+    return PCPM_OK;
+}
+
+}  // namespace
+
+int build_png(pcpm_png* g, const uint32_t* row_ptr, const uint32_t* col, cudaStream_t s) {
+    const uint32_t n = g->n, q = g->q, k = g->k;
+    const uint64_t m = g->m;
+    TempBufs tmp;
+    int* d_err = nullptr;
+    BCK(tmp.alloc(&d_err, 1));
+    BCK(cudaMemsetAsync(d_err, 0, sizeof(int), s));
+    int h_err = 0;
+    int rc;
+
+    check_row_ptr_kernel<<<grid_for(n, 256, 4096), 256, 0, s>>>(row_ptr, n, d_err);
+    BCK(cudaGetLastError());
+    if ((rc = read_err(d_err, s, &h_err)) != PCPM_OK) return rc;
+    if (h_err) return PCPM_EBADGRAPH;
+
+    // Tiles: kTileEdges edges of one source partition each.
+    uint32_t *tiles = nullptr, *tile_start = nullptr;
+    BCK(tmp.alloc(&tiles, k));
+    BCK(tmp.alloc(&tile_start, k + 1));
+    partition_tiles_kernel<<<grid_for(k, 256, 1024), 256, 0, s>>>(row_ptr, n, q, k, tiles);
+    if ((rc = scan_exclusive(tiles, tile_start, k, tmp, s)) != PCPM_OK) return rc;
+    uint32_t ntiles = 0;
+    BCK(cudaMemcpyAsync(&ntiles, tile_start + k, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    BCK(cudaStreamSynchronize(s));
+
+    // Count pass.
+    uint32_t *tab_e = nullptr, *tab_u = nullptr;
+    BCK(tmp.alloc(&tab_e, (size_t)(ntiles + 1) * k));
+    BCK(tmp.alloc(&tab_u, (size_t)(ntiles + 1) * k));
+    const int wpc = (int)std::max<uint32_t>(1, std::min<uint32_t>(8, 12288u / k));  // <= 96 KB of tables
+    const size_t tile_smem = (size_t)wpc * 2 * k * sizeof(uint32_t);
+    BCK(cudaFuncSetAttribute(tile_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem));
+    BCK(cudaFuncSetAttribute(tile_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem));
+    const int sms = g->sms;
+    const int tile_grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((ntiles + wpc - 1) / wpc, (uint64_t)sms * 16));
+    if (ntiles) {
+        tile_kernel<false><<<tile_grid, wpc * 32, tile_smem, s>>>(row_ptr, col, n, q, k, tile_start, ntiles, tab_e,
+                                                                 tab_u, nullptr, nullptr, nullptr, nullptr, d_err);
+        BCK(cudaGetLastError());
+    }
+    if ((rc = read_err(d_err, s, &h_err)) != PCPM_OK) return rc;
+    if (h_err) return PCPM_EBADGRAPH;
+
+    // Scans: per-tile cursors, bin starts.
+    uint32_t *tot_e = nullptr, *tot_u = nullptr;
+    BCK(tmp.alloc(&tot_e, k));
+    BCK(tmp.alloc(&tot_u, k));
+    if (ntiles) {
+        if ((rc = colscan(tab_e, ntiles, k, tot_e, tmp, s)) != PCPM_OK) return rc;
+        if ((rc = colscan(tab_u, ntiles, k, tot_u, tmp, s)) != PCPM_OK) return rc;
+    } else {
+        BCK(cudaMemsetAsync(tab_e, 0, (size_t)k * sizeof(uint32_t), s));
+        BCK(cudaMemsetAsync(tab_u, 0, (size_t)k * sizeof(uint32_t), s));
+        BCK(cudaMemsetAsync(tot_e, 0, (size_t)k * sizeof(uint32_t), s));
+        BCK(cudaMemsetAsync(tot_u, 0, (size_t)k * sizeof(uint32_t), s));
+    }
+    BCK(dev_alloc(g, (void**)&g->bin_e, (k + 1) * sizeof(uint32_t)));
+    BCK(dev_alloc(g, (void**)&g->bin_u, (k + 1) * sizeof(uint32_t)));
+    if ((rc = scan_exclusive(tot_e, g->bin_e, k, tmp, s)) != PCPM_OK) return rc;
+    if ((rc = scan_exclusive(tot_u, g->bin_u, k, tmp, s)) != PCPM_OK) return rc;
+    uint32_t ends[2] = {0, 0};
+    BCK(cudaMemcpyAsync(&ends[0], g->bin_e + k, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    BCK(cudaMemcpyAsync(&ends[1], g->bin_u + k, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    BCK(cudaStreamSynchronize(s));
+    if (ends[0] != m) return PCPM_EDEVICE;
+    g->ne = ends[1];
+
+    // Fill pass.
+    g->nchunks = (m + kChunk - 1) / kChunk;
+    const size_t dest_len = std::max<uint64_t>(g->nchunks, 1) * kChunk;
+    BCK(dev_alloc(g, (void**)&g->dest, dest_len * sizeof(uint32_t)));
+    BCK(cudaMemsetAsync(g->dest, 0, dest_len * sizeof(uint32_t), s));
+    BCK(dev_alloc(g, (void**)&g->src, (g->ne + 4) * sizeof(uint32_t)));
+    if (ntiles) {
+        tile_kernel<true><<<tile_grid, wpc * 32, tile_smem, s>>>(row_ptr, col, n, q, k, tile_start, ntiles, tab_e,
+                                                                tab_u, g->bin_e, g->bin_u, g->dest, g->src, d_err);
+        BCK(cudaGetLastError());
+    }
+
+    // Segment table for the scatter (and offsets for export).
+    const size_t kk = (size_t)k * k;
+    BCK(dev_alloc(g, (void**)&g->seg_u, kk * sizeof(uint32_t)));
+    BCK(dev_alloc(g, (void**)&g->cnt_u, kk * sizeof(uint32_t)));
+    BCK(dev_alloc(g, (void**)&g->seg_e, kk * sizeof(uint32_t)));
+    BCK(dev_alloc(g, (void**)&g->cnt_e, kk * sizeof(uint32_t)));
+    segments_kernel<<<grid_for(kk, 256, 4096), 256, 0, s>>>(tab_u, tile_start, g->bin_u, k, g->seg_u, g->cnt_u);
+    segments_kernel<<<grid_for(kk, 256, 4096), 256, 0, s>>>(tab_e, tile_start, g->bin_e, k, g->seg_e, g->cnt_e);
+    BCK(cudaGetLastError());
+
+    // Update base of every chunk of the destination-ID array.
+    BCK(dev_alloc(g, (void**)&g->chunk_base, (g->nchunks + 1) * sizeof(uint32_t)));
+    if (g->nchunks) {
+        uint32_t* ccnt = nullptr;
+        BCK(tmp.alloc(&ccnt, g->nchunks));
+        chunk_flags_kernel<<<grid_for(g->nchunks * 32, 256, 8192), 256, 0, s>>>(g->dest, m, g->nchunks, ccnt);
+        BCK(cudaGetLastError());
+        if ((rc = scan_exclusive(ccnt, g->chunk_base, g->nchunks, tmp, s)) != PCPM_OK) return rc;
+    } else {
+        BCK(cudaMemsetAsync(g->chunk_base, 0, sizeof(uint32_t), s));
+    }
+
+    // Hubs per bin and launch orders.
+    uint32_t *indeg = nullptr, *sizes = nullptr;
+    BCK(tmp.alloc(&indeg, n));
+    BCK(tmp.alloc(&sizes, k));
+    BCK(cudaMemsetAsync(indeg, 0, (size_t)n * sizeof(uint32_t), s));
+    if (m) indegree_kernel<<<grid_for(m, 256, sms * 32), 256, 0, s>>>(col, m, indeg);
+    BCK(dev_alloc(g, (void**)&g->hubs, 2 * (size_t)k * sizeof(uint32_t)));
+    hubs_kernel<<<k, 1024, 0, s>>>(indeg, n, q, g->hubs);
+    BCK(dev_alloc(g, (void**)&g->bin_order, (size_t)k * sizeof(uint32_t)));
+    BCK(dev_alloc(g, (void**)&g->src_order, (size_t)k * sizeof(uint32_t)));
+    bin_sizes_kernel<<<grid_for(k, 256, 64), 256, 0, s>>>(g->bin_e, k, sizes);
+    order_kernel<<<grid_for(k, 128, 1024), 128, 0, s>>>(sizes, k, g->bin_order);
+    src_groups_kernel<<<k, 256, 0, s>>>(g->seg_u, g->cnt_u, k, sizes);
+    order_kernel<<<grid_for(k, 128, 1024), 128, 0, s>>>(sizes, k, g->src_order);
+    BCK(cudaGetLastError());
+
+    BCK(dev_alloc(g, (void**)&g->inv_deg, (size_t)n * sizeof(float)));
+    inv_deg_kernel<<<grid_for(n, 256, 4096), 256, 0, s>>>(row_ptr, n, g->inv_deg);
+    BCK(cudaGetLastError());
+    if ((rc = read_err(d_err, s, &h_err)) != PCPM_OK) return rc;
+    if (h_err) return PCPM_EDEVICE;
+    return PCPM_OK;
+}
+
+}  // namespace pcpm

@@ -1,0 +1,82 @@
+"""CPU-only checks of the C ABI: the library builds for sm_103a, loads without
+a GPU, exports every entry point include/pcpm.h declares, and rejects invalid
+arguments on the host before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1709_07122_gb300 as pcpm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for fname in os.listdir(os.path.join(ROOT, "include")):
+        if fname.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fname)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(pcpm_\w+)\s*\(", text))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def L():
+    pcpm.build()
+    return pcpm.lib()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("pcpm_build", "pcpm_pagerank", "pcpm_free", "pcpm_png_export", "pcpm_strerror"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(L):
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_strerror_is_host_only(L):
+    for code in (0, 1, -1, -2, -3, -4, -5, -6, 99):
+        assert isinstance(L.pcpm_strerror(code), bytes)
+    assert b"invalid" in L.pcpm_strerror(-1)
+
+
+def test_invalid_arguments_rejected_before_any_launch(L):
+    h = ctypes.c_void_p()
+    assert L.pcpm_build(None, None, 10, 0, 4, None, ctypes.byref(h)) == -1
+    assert L.pcpm_build(ctypes.c_void_p(16), None, 0, 0, 4, None, ctypes.byref(h)) == -1  # n = 0
+    assert L.pcpm_build(ctypes.c_void_p(16), None, 10, 0, 0, None, ctypes.byref(h)) == -1  # q = 0
+    assert L.pcpm_build(ctypes.c_void_p(16), None, 10, 0, 40000, None, ctypes.byref(h)) == -1  # q too large
+    assert L.pcpm_build(ctypes.c_void_p(16), None, 1 << 31, 0, 4, None, ctypes.byref(h)) == -1  # n >= 2^31
+    assert L.pcpm_build(ctypes.c_void_p(16), None, 10_000_000, 0, 1, None, ctypes.byref(h)) == -1  # k too large
+    assert L.pcpm_build(ctypes.c_void_p(16), None, 10, 0, 4, None, None) == -1
+    assert L.pcpm_png_get_info(None, None) == -1
+    assert L.pcpm_reset(None, None, None) == -1
+    assert L.pcpm_iterate(None, 0.85, 1, 0.0, 0, None, None, None) == -1
+    assert L.pcpm_pagerank(None, 0.85, 1, 0.0, 0, None, None, None, None, None) == -1
+    assert L.pcpm_residual_history(None, None, 0) == -1
+    assert L.pcpm_scatter_only(None, None) == -1
+    assert L.pcpm_export_state(None, None, None, None, None) == -1
+    L.pcpm_free(None)  # null-safe
+    out = (ctypes.c_float * 4)()
+    # host entry: bad damping factor and null pointers fail on the host
+    rp = (ctypes.c_uint32 * 5)(0, 1, 2, 3, 4)
+    col = (ctypes.c_uint32 * 4)(1, 2, 3, 0)
+    assert L.pcpm_pagerank_host(rp, col, 4, 4, 2, 1.0, 5, 0.0, 0, out, None, None) == -1
+    assert L.pcpm_pagerank_host(None, col, 4, 4, 2, 0.85, 5, 0.0, 0, out, None, None) == -1
+    assert L.pcpm_pagerank_host(rp, col, 4, 4, 2, 0.85, -1, 0.0, 0, out, None, None) == -1
+    assert L.pcpm_pagerank_host(rp, col, 4, 4, 2, 0.85, 5, 0.0, 0x80, out, None, None) == -1
+
+
+def test_binding_fails_loudly_without_library(tmp_path):
+    saved = pcpm._lib
+    try:
+        pcpm._lib = None
+        with pytest.raises(RuntimeError, match="not built"):
+            pcpm.lib(str(tmp_path / "missing.so"))
+    finally:
+        pcpm._lib = saved

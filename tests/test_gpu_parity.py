@@ -1,0 +1,251 @@
+"""GPU parity of the CUDA path against the FP64 oracle, through the C ABI.
+
+Bar: PNG counts, offsets, bin starts and bins bit-exact; the scatter's update
+bins bit-exact (a float copy); ranks within L1 1e-6 of the oracle on every
+iteration (FP32 ranks, FP32 shared-memory accumulation, FP64 reductions).
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1709_07122_gb300 as pcpm  # noqa: E402
+
+L1_TOL = 1e-6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pcpm.build()
+    pcpm.lib()
+
+
+def assert_png_matches(g: dict, ref: dict):
+    assert g["k"] == ref["k"] and g["ne"] == ref["ne"] and g["m"] == ref["m"]
+    for key in ("cnt_u", "cnt_e", "off_u", "off_e", "bin_u", "bin_e", "src_idx", "dest_ids"):
+        np.testing.assert_array_equal(g[key], np.asarray(ref[key], dtype=np.uint32), err_msg=key)
+
+
+def l1(a, b):
+    return float(np.abs(np.asarray(a, np.float64) - np.asarray(b, np.float64)).sum())
+
+
+GRAPHS = {
+    "rmat16_q16384": lambda: (graphgen.rmat(16, 16, seed=1709), 16384),
+    "rmat12_q100_ragged": lambda: (graphgen.rmat(12, 16, seed=3), 100),
+    "rmat12_bfs_q512": lambda: (graphgen.rmat(12, 16, seed=4, relabel="bfs"), 512),
+    "er14_q512": lambda: (graphgen.erdos_renyi(1 << 14, 16, seed=5), 512),
+    "random1000_q7": lambda: (graphgen.random_graph(1000, 5000, seed=6), 7),
+    "random300_q1": lambda: (graphgen.random_graph(300, 900, seed=7), 1),
+    "single_partition": lambda: (graphgen.random_graph(500, 3000, seed=8), 32768),
+    "rmat10_q32768_k1": lambda: (graphgen.rmat(10, 8, seed=9), 32768),
+    "rmat14_q_not_multiple": lambda: (graphgen.rmat(14, 16, seed=10), 3000),
+}
+
+
+@pytest.mark.parametrize("name", sorted(GRAPHS))
+def test_png_bit_exact(name):
+    (rp, col), q = GRAPHS[name]()
+    with pcpm.PNG.from_host(rp, col, q) as g:
+        assert_png_matches(g.export(), oracle.png(rp, col, q))
+
+
+def test_png_edge_cases_bit_exact():
+    cases = []
+    # one node, no edges
+    cases.append((np.array([0, 0], np.uint32), np.array([], np.uint32), 1))
+    # no edges at all
+    cases.append((np.zeros(11, np.uint32), np.array([], np.uint32), 3))
+    # hub pointing everywhere, isolated and dangling nodes, empty bins
+    n = 70
+    src = [0] * (n - 1) + list(range(5, n, 3))
+    dst = list(range(1, n)) + [2] * len(range(5, n, 3))
+    cases.append(graphgen.csr_from_edges(n, np.array(src), np.array(dst)) + (8,))
+    # duplicates and self-loops kept as ordinary edges
+    rp, col = graphgen.csr_from_edges(20, np.array([1, 1, 1, 2, 2, 5]), np.array([3, 3, 1, 2, 19, 0]),
+                                      dedupe=False, drop_self_loops=False)
+    cases.append((rp, col, 4))
+    # a tile boundary inside one long row (> 8192 edges from one node)
+    n = 20000
+    rp, col = graphgen.csr_from_edges(n, np.zeros(n - 1, int), np.arange(1, n))
+    cases.append((rp, col, 1024))
+    for rp, col, q in cases:
+        with pcpm.PNG.from_host(rp, col, q) as g:
+            assert_png_matches(g.export(), oracle.png(rp, col, q))
+
+
+def test_paper_offsets_example_on_gpu():
+    rp, col = graphgen.csr_from_edges(9, np.array([0, 0, 3, 6, 7, 8]), np.array([6, 8, 4, 0, 3, 2]))
+    with pcpm.PNG.from_host(rp, col, 3) as g:
+        assert list(g.export()["off_u"][2]) == [0, 1, 1]
+
+
+@pytest.mark.parametrize("name", ["rmat16_q16384", "rmat12_q100_ragged", "random1000_q7", "er14_q512"])
+def test_scatter_bit_exact(name):
+    (rp, col), q = GRAPHS[name]()
+    n = rp.size - 1
+    x0 = torch.from_numpy(graphgen.random_rank_vector(n, seed=21).astype(np.float32)).cuda()
+    ref = oracle.png(rp, col, q)
+    with pcpm.PNG.from_host(rp, col, q) as g:
+        g.reset(x0)
+        g.scatter_only()
+        st = g.export_state()
+        # scatter: update[t] = SPR[src[t]] exactly (Algorithm 3)
+        np.testing.assert_array_equal(st["updates"], st["spr"][ref["src_idx"]])
+        # SPR_0 = PR_0 / outdeg in FP32 (1/outdeg rounded once, then one product)
+        deg = np.diff(rp.astype(np.int64))
+        inv = np.where(deg > 0, np.float32(1) / np.maximum(deg, 1).astype(np.float32), np.float32(0))
+        np.testing.assert_array_equal(st["spr"], (x0.cpu().numpy() * inv.astype(np.float32)).astype(np.float32))
+        np.testing.assert_allclose(st["dangling"], x0.cpu().numpy().astype(np.float64)[deg == 0].sum(), rtol=1e-12)
+
+
+@pytest.mark.parametrize("mode", ["fused", "two_phase"])
+@pytest.mark.parametrize("dangling", ["uniform", "leak"])
+@pytest.mark.parametrize("start", ["uniform", "random"])
+def test_iterations_rmat16_l1_every_iteration(dangling, start, mode):
+    # RMAT scale 16, edge factor 16, q = 16384, d = 0.85, 20 iterations.
+    (rp, col), q = GRAPHS["rmat16_q16384"]()
+    n = rp.size - 1
+    x0 = None if start == "uniform" else graphgen.random_rank_vector(n, seed=33)
+    ref = oracle.pagerank(rp, col, 0.85, iters=20, x0=x0, dangling=dangling, history=True)
+    x0_t = None if x0 is None else torch.from_numpy(x0.astype(np.float32)).cuda()
+    with pcpm.PNG.from_host(rp, col, q) as g:
+        g.reset(x0_t)
+        errs = []
+        for i in range(1, 21):
+            g.iterate(0.85, 1, dangling=dangling, mode=mode)
+            errs.append(l1(g.ranks().cpu().numpy(), ref["hist"][i]))
+        assert max(errs) <= L1_TOL, errs
+        hist = g.residual_history()
+        assert hist.size == 20
+        np.testing.assert_allclose(hist, ref["resid"], rtol=1e-3, atol=2e-7)
+
+
+@pytest.mark.parametrize("mode", ["fused", "two_phase"])
+@pytest.mark.parametrize("name", sorted(GRAPHS))
+def test_pagerank_matches_oracle(name, mode):
+    (rp, col), q = GRAPHS[name]()
+    ref = oracle.pagerank(rp, col, 0.85, iters=20)["x"]
+    with pcpm.PNG.from_host(rp, col, q) as g:
+        pr, iters, res = g.pagerank(0.85, max_iters=20, mode=mode)
+        assert iters == 20
+        assert l1(pr.cpu().numpy(), ref) <= L1_TOL
+
+
+def test_modes_interleave():
+    # Fused and two-phase iterations share one state: any mix of them follows
+    # the oracle, and a fused step after a two-phase one rescatters first.
+    (rp, col), q = GRAPHS["rmat12_q100_ragged"]()
+    ref = oracle.pagerank(rp, col, 0.85, iters=9, history=True)["hist"]
+    with pcpm.PNG.from_host(rp, col, q) as g:
+        g.reset()
+        done = 0
+        for mode, k in [("fused", 2), ("two_phase", 1), ("fused", 3), ("two_phase", 2), ("fused", 1)]:
+            g.iterate(0.85, k, mode=mode)
+            done += k
+            assert l1(g.ranks().cpu().numpy(), ref[done]) <= L1_TOL, (mode, done)
+
+
+def test_fused_scatter_writes_next_bins_bit_exact():
+    # After a fused iteration the current update bins hold SPR of the new ranks
+    # at every PNG position (the fused kernel's scatter half).
+    (rp, col), q = GRAPHS["rmat14_q_not_multiple"]()
+    ref = oracle.png(rp, col, q)
+    with pcpm.PNG.from_host(rp, col, q) as g:
+        g.reset()
+        g.iterate(0.85, 3)
+        st = g.export_state()
+        np.testing.assert_array_equal(st["updates"], st["spr"][ref["src_idx"]])
+
+
+def test_tolerance_stops_at_first_iteration_below():
+    (rp, col), q = GRAPHS["rmat12_q100_ragged"]()
+    ref = oracle.pagerank(rp, col, 0.85, iters=200)
+    first = int(np.argmax(ref["resid"] < 1e-6)) + 1
+    with pcpm.PNG.from_host(rp, col, q) as g:
+        pr, iters, res = g.pagerank(0.85, max_iters=200, tol=1e-6)
+        assert res < 1e-6
+        assert abs(iters - first) <= 1
+        hist = g.residual_history()
+        assert hist.size == iters and hist[-1] == res and (hist[:-1] >= 1e-6).all()
+        # too few iterations: NOT_CONVERGED is reported, ranks still returned
+        pr, iters, res = g.pagerank(0.85, max_iters=3, tol=1e-12)
+        assert iters == 3 and res > 1e-12
+
+
+def test_state_continues_across_calls_and_reset():
+    (rp, col), q = GRAPHS["er14_q512"]()
+    ref = oracle.pagerank(rp, col, 0.9, iters=7, history=True)["hist"]
+    with pcpm.PNG.from_host(rp, col, q) as g:
+        g.reset()
+        g.iterate(0.9, 3)
+        g.iterate(0.9, 4, sync=False)
+        assert l1(g.ranks().cpu().numpy(), ref[7]) <= L1_TOL
+        assert g.info["iterations_done"] == 7
+        g.reset()
+        assert l1(g.ranks().cpu().numpy(), ref[0]) <= 1e-6
+        g.iterate(0.9, 2)
+        assert l1(g.ranks().cpu().numpy(), ref[2]) <= L1_TOL
+
+
+def test_closed_forms_on_gpu():
+    # Directed cycle: 1/n stays fixed; in-star with a dangling centre.
+    n = 5000
+    rp, col = graphgen.csr_from_edges(n, np.arange(n), (np.arange(n) + 1) % n)
+    with pcpm.PNG.from_host(rp, col, 512) as g:
+        pr, _, _ = g.pagerank(0.85, 20)
+        np.testing.assert_allclose(pr.cpu().numpy(), 1.0 / n, rtol=1e-5)
+    rp, col = graphgen.csr_from_edges(n, np.arange(1, n), np.zeros(n - 1, int))
+    d = 0.85
+    with pcpm.PNG.from_host(rp, col, 777) as g:
+        pr, _, _ = g.pagerank(d, 200)
+        x = pr.cpu().numpy()
+        den = n + d * (n - 1)
+        # The centre sums n-1 equal FP32 terms in shared memory every iteration:
+        # a sequential FP32 sum of N terms is within gamma_N = N*2^-24 (relative)
+        # of the exact sum, about 3e-4 here; the leaves inherit it through D/n.
+        gamma = (n - 1) * 2.0 ** -24
+        np.testing.assert_allclose(x[1:], 1 / den, rtol=gamma)
+        np.testing.assert_allclose(x[0], (1 + d * (n - 1)) / den, rtol=gamma)
+        assert abs(x.astype(np.float64).sum() - 1) < 2 * gamma
+
+
+def test_pagerank_host_end_to_end():
+    (rp, col), q = GRAPHS["rmat12_q100_ragged"]()
+    ref = oracle.pagerank(rp, col, 0.85, iters=20)["x"]
+    pr, iters, res = pcpm.pagerank_host(rp, col, q, 0.85, 20)
+    assert iters == 20 and l1(pr, ref) <= L1_TOL
+
+
+def test_errors_from_bad_inputs():
+    rp = np.array([0, 2, 3, 3], np.uint32)
+    unsorted = np.array([2, 1, 0], np.uint32)
+    with pytest.raises(pcpm.PcpmError) as e:
+        pcpm.PNG.from_host(rp, unsorted, 2)
+    assert e.value.code == -6
+    out_of_range = np.array([1, 7, 0], np.uint32)
+    with pytest.raises(pcpm.PcpmError) as e:
+        pcpm.PNG.from_host(rp, out_of_range, 2)
+    assert e.value.code == -6
+    decreasing = np.array([0, 2, 1, 3], np.uint32)
+    with pytest.raises(pcpm.PcpmError) as e:
+        pcpm.PNG.from_host(decreasing, np.array([1, 2, 0], np.uint32), 2)
+    assert e.value.code == -6
+    # host pointers where device pointers are required
+    h = ctypes.c_void_p()
+    host_rp = rp.ctypes.data_as(ctypes.c_void_p)
+    assert pcpm.lib().pcpm_build(host_rp, host_rp, 3, 3, 2, None, ctypes.byref(h)) == -1
+    (rp2, col2), q = GRAPHS["random300_q1"]()
+    with pcpm.PNG.from_host(rp2, col2, q) as g:
+        with pytest.raises(pcpm.PcpmError):
+            g.iterate(1.0, 1)
+        with pytest.raises(ValueError):
+            g.iterate(0.85, 1, dangling="bogus")

@@ -164,3 +164,17 @@ def test_transpose_matters():
     x1 = oracle.pagerank(rp, col, D, iters=1)["x"]
     base = (1 - D) / 3 + D * (1 / 3) / 3  # node 2 is dangling with mass 1/3
     np.testing.assert_allclose(x1, [base, base + D / 3, base + D / 3], rtol=1e-15)
+
+
+def test_pull_step_ranges_compose():
+    # Steps over disjoint destination ranges assemble the full step.
+    rp, col = graphgen.rmat(10, 16, seed=21)
+    n = rp.size - 1
+    x0 = graphgen.random_rank_vector(n, seed=22)
+    full = oracle.pagerank(rp, col, D, iters=1, x0=x0)
+    pull = oracle.Pull(rp, col)
+    y = np.zeros(n)
+    r = sum(pull.step(x0, y, D, v_begin=a, v_end=min(n, a + 100)) for a in range(0, n, 100))
+    np.testing.assert_array_equal(y, full["x"])
+    np.testing.assert_allclose(r, full["resid"][0], rtol=1e-12)
+    assert pull.in_edges(0, n) == rp[-1]
