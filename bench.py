@@ -54,6 +54,9 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-converge", action="store_true", help="skip the time-to-residual run")
+    ap.add_argument("--no-two-phase", action="store_true", help="skip the two-phase (per-phase) leg")
+    ap.add_argument("--mode", choices=("fused", "two_phase"), default="fused",
+                    help="iteration form timed for `value`")
     ap.add_argument("--ref-budget-s", type=float, default=120.0, help="reference arm: timed seconds target")
     return ap.parse_args()
 
@@ -281,7 +284,7 @@ def run_ours(a):
     info = g.info
 
     g.reset()
-    g.iterate(a.d, a.warmup, sync=False)
+    g.iterate(a.d, a.warmup, sync=False, mode=a.mode)
     torch.cuda.synchronize()
 
     sampler = ClockSampler(local).start()
@@ -291,7 +294,7 @@ def run_ours(a):
     t0 = time.time()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    kms = g.iterate_timed(a.d, a.steps)  # per-kernel CUDA events on `stream`
+    kms = g.iterate_timed(a.d, a.steps, mode=a.mode)  # per-kernel CUDA events on `stream`
     ev1.record(stream)
     torch.cuda.synchronize()
     t1 = time.time()
@@ -302,27 +305,32 @@ def run_ours(a):
     value = world * m / (iter_ms * 1e-3) / 1e9
 
     # roofline of the kernel with the largest share of the time
-    ab = algorithmic_bytes(info, "fused")
+    ab = algorithmic_bytes(info, a.mode)
     dom = max(PHASES, key=lambda p: kms[p])
     dom_ms = kms[dom] / a.steps
     peak, peak_src = measured_peaks()
     achieved = ab[dom] / (dom_ms * 1e-3) / 1e9
     wl = workload_name(a)
-    roofline = {"bound": "hbm", "kernel": dom + " (fused: gather, apply, next scatter)", "achieved": achieved,
+    kname = dom + (" (fused: gather, apply, next scatter)" if a.mode == "fused" and dom == "gather_apply" else "")
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved,
                 "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
                 "traffic": recorded_traffic(dom, wl), "algorithmic_bytes": ab[dom]}
     iter_bytes = sum(ab.values())
 
-    # The paper's two phases as separate kernels (Table execTime analogue).
-    tp_steps = max(3, min(a.steps, 50))
-    g.iterate(a.d, 3, sync=False, mode="two_phase")
-    tms = g.iterate_timed(a.d, tp_steps, mode="two_phase")
-    tab = algorithmic_bytes(info, "two_phase")
-    two_phase = {"iters": tp_steps, "ms_per_iter": tms["span"] / tp_steps,
+    # The other iteration form, timed the same way: two-phase gives the
+    # paper's scatter / gather split (Table execTime analogue).
+    other = None
+    if not a.no_two_phase:
+        om = "two_phase" if a.mode == "fused" else "fused"
+        tp_steps = max(3, min(a.steps, 50))
+        g.iterate(a.d, 3, sync=False, mode=om)
+        tms = g.iterate_timed(a.d, tp_steps, mode=om)
+        tab = algorithmic_bytes(info, om)
+        other = {"mode": om, "iters": tp_steps, "ms_per_iter": tms["span"] / tp_steps,
                  "gteps": m / (tms["span"] / tp_steps * 1e-3) / 1e9}
-    for ph in PHASES:
-        ms = tms[ph] / tp_steps
-        two_phase[ph] = {"ms": ms, "gbs": tab[ph] / (ms * 1e-3) / 1e9 if ms > 0 else None,
+        for ph in PHASES:
+            ms = tms[ph] / tp_steps
+            other[ph] = {"ms": ms, "gbs": tab[ph] / (ms * 1e-3) / 1e9 if ms > 0 else None,
                          "frac": tab[ph] / (ms * 1e-3) / 1e9 / peak if ms > 0 else None}
 
     out = {
@@ -337,7 +345,8 @@ def run_ours(a):
         "phase_ms_per_iter": {p: kms[p] / a.steps for p in PHASES},
         "hbm_gbs_achieved": iter_bytes / (iter_ms * 1e-3) / 1e9,
         "bytes_per_edge": {"algorithmic": iter_bytes / m, "eq5_model": eq5_bytes(info) / m},
-        "two_phase": two_phase,
+        "mode": a.mode,
+        "other_mode": other,
         "bracket_ms_per_step": bracket_ms / a.steps,
         "build_ms": build_ms,
         "clocks": clocks,
@@ -347,7 +356,7 @@ def run_ours(a):
     if not a.no_converge:
         torch.cuda.synchronize()
         c0 = time.perf_counter()
-        _, its, res = g.pagerank(a.d, max_iters=300, tol=1e-7)
+        _, its, res = g.pagerank(a.d, max_iters=300, tol=1e-7, mode=a.mode)
         torch.cuda.synchronize()
         out["time_to_residual"] = {"tol": 1e-7, "iters": its, "ms": (time.perf_counter() - c0) * 1e3,
                                    "final_residual": res, "reached": res < 1e-7, "start": "uniform"}

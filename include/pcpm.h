@@ -66,7 +66,10 @@ extern "C" {
  * this flag an iteration is one fused kernel per partition: gather, apply, and
  * the scatter of that partition's new values into a second set of update bins
  * for the next iteration (a standalone scatter runs first when those bins do
- * not yet hold the current ranks). Both compute the same iteration. */
+ * not yet hold the current ranks). Both compute the same iteration. When a
+ * bin is too large for one work unit (skewed graphs; it is then cut into
+ * several units whose partial sums meet in global memory), iterations run in
+ * the two-phase form whatever the flag says. */
 #define PCPM_TWO_PHASE 0x2u
 
 /* Kernels timed by pcpm_iterate_timed, in this order. In fused mode the
@@ -89,8 +92,21 @@ typedef struct pcpm_png_info {
     double compression_ratio; /* r = |E| / |E'| (Sec. 4, Table params) */
     uint64_t device_bytes;    /* device memory held by the handle */
     int32_t iterations_done;  /* iterations applied since the last reset */
-    int32_t reserved2;
+    uint32_t gather_units;    /* gather work units (bins, large ones cut) */
+    uint32_t scatter_units;   /* scatter work units (source partitions, large ones cut) */
+    uint32_t gather_cluster;  /* CTAs (one thread-block cluster) per gather unit */
+    uint32_t fused_ok;        /* 1 if iterations can run fused (no bin was cut) */
+    uint32_t reserved2;
 } pcpm_png_info;
+
+/* Tuning of the work decomposition; zero fields take the automatic choice.
+ * Results do not depend on these, only speed. */
+typedef struct pcpm_build_options {
+    uint32_t gather_unit_chunks;  /* most 256-ID chunks one gather unit takes from a bin */
+    uint32_t scatter_unit_groups; /* most 4-update groups one scatter unit writes */
+    uint32_t gather_cluster;      /* CTAs per gather unit: 1, 2, 4 or 8 */
+    uint32_t reserved;
+} pcpm_build_options;
 
 /* Builds the Partition-Node Graph of Sec. 3.3 from a CSR out-adjacency:
  * partitions of `part_size` consecutive node IDs (Sec. 3.1); for every
@@ -116,6 +132,12 @@ typedef struct pcpm_png_info {
  * >= n or a row is not sorted; PCPM_EINVAL if row_ptr[n] != m. */
 int pcpm_build(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t n, uint64_t m,
                uint32_t part_size, void* stream, pcpm_png** out);
+
+/* pcpm_build with tuning options (host struct, nullable = all automatic).
+ * PCPM_EINVAL if gather_cluster is not 0, 1, 2, 4 or 8. */
+int pcpm_build_ex(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t n, uint64_t m,
+                  uint32_t part_size, const pcpm_build_options* options, void* stream,
+                  pcpm_png** out);
 
 /* Releases the handle and all its device memory. NULL is a no-op. Waits for
  * work the library enqueued on the handle's last stream. */

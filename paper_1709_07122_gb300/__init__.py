@@ -41,7 +41,14 @@ class _Info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_uint32), ("part_size", ctypes.c_uint32), ("num_partitions", ctypes.c_uint32),
                 ("reserved", ctypes.c_uint32), ("num_edges", ctypes.c_uint64), ("num_updates", ctypes.c_uint64),
                 ("compression_ratio", ctypes.c_double), ("device_bytes", ctypes.c_uint64),
-                ("iterations_done", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
+                ("iterations_done", ctypes.c_int32), ("gather_units", ctypes.c_uint32),
+                ("scatter_units", ctypes.c_uint32), ("gather_cluster", ctypes.c_uint32),
+                ("fused_ok", ctypes.c_uint32), ("reserved2", ctypes.c_uint32)]
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("gather_unit_chunks", ctypes.c_uint32), ("scatter_unit_groups", ctypes.c_uint32),
+                ("gather_cluster", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -63,6 +70,7 @@ def lib(path: str | None = None):
             pi, pd, pf = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float)
             sig = {
                 "pcpm_build": (i32, [vp, vp, u32, u64, u32, vp, ctypes.POINTER(vp)]),
+                "pcpm_build_ex": (i32, [vp, vp, u32, u64, u32, ctypes.POINTER(_Options), vp, ctypes.POINTER(vp)]),
                 "pcpm_free": (None, [vp]),
                 "pcpm_png_get_info": (i32, [vp, ctypes.POINTER(_Info)]),
                 "pcpm_png_export": (i32, [vp] + [vp] * 8),
@@ -129,21 +137,23 @@ def to_device_csr(row_ptr: np.ndarray, col: np.ndarray, device="cuda"):
 class PNG:
     """A device-resident Partition-Node Graph and its solver state."""
 
-    def __init__(self, row_ptr, col, part_size: int, stream=None):
-        """row_ptr, col: CUDA int32/uint32 tensors (CSR out-adjacency, rows sorted)."""
+    def __init__(self, row_ptr, col, part_size: int, stream=None, **options):
+        """row_ptr, col: CUDA int32/uint32 tensors (CSR out-adjacency, rows sorted).
+        options: gather_unit_chunks, scatter_unit_groups, gather_cluster (0 = automatic)."""
         L = lib()
         n = row_ptr.numel() - 1
         m = int(row_ptr[-1].item()) & 0xFFFFFFFF
         h = ctypes.c_void_p()
-        _check(L.pcpm_build(_dev_u32(row_ptr), _dev_u32(col), n, m, int(part_size), _stream(stream),
-                            ctypes.byref(h)), "pcpm_build")
+        opt = _Options(**{k: int(v) for k, v in options.items()})
+        _check(L.pcpm_build_ex(_dev_u32(row_ptr), _dev_u32(col), n, m, int(part_size), ctypes.byref(opt),
+                               _stream(stream), ctypes.byref(h)), "pcpm_build")
         self._h = h
         self.n = n
 
     @classmethod
-    def from_host(cls, row_ptr: np.ndarray, col: np.ndarray, part_size: int, stream=None):
+    def from_host(cls, row_ptr: np.ndarray, col: np.ndarray, part_size: int, stream=None, **options):
         rp, c = to_device_csr(row_ptr, col)
-        return cls(rp, c, part_size, stream)
+        return cls(rp, c, part_size, stream, **options)
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -46,8 +46,9 @@ bool is_device_ptr(const void* p) {
 void release(pcpm_png* g) {
     if (!g) return;
     void* ptrs[] = {g->dest, g->src, g->bin_u, g->bin_e, g->seg_u, g->cnt_u, g->seg_e, g->cnt_e,
-                    g->chunk_base, g->hubs, g->bin_order, g->src_order, g->inv_deg, g->pr[0], g->pr[1],
-                    g->upd[0], g->upd[1], g->partials, g->hist, g->state};
+                    g->chunk_base, g->hubs, g->gunits, g->gorder, g->sunits, g->sorder, g->gacc,
+                    g->bin_done, g->inv_deg, g->pr[0], g->pr[1], g->upd[0], g->upd[1], g->partials,
+                    g->hist, g->state};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (g->state_host) cudaFreeHost(g->state_host);
@@ -65,6 +66,10 @@ int alloc_state(pcpm_png* g) {
     CK(cudaMemset(g->upd[0], 0, (g->ne + 8) * sizeof(float)));
     CK(cudaMemset(g->upd[1], 0, (g->ne + 8) * sizeof(float)));
     CK(dev_alloc(g, (void**)&g->partials, 2 * partial_slots(g) * sizeof(double)));
+    CK(dev_alloc(g, (void**)&g->gacc, (size_t)n * sizeof(float)));
+    CK(dev_alloc(g, (void**)&g->bin_done, (size_t)g->k * sizeof(uint32_t)));
+    CK(cudaMemset(g->gacc, 0, (size_t)n * sizeof(float)));
+    CK(cudaMemset(g->bin_done, 0, (size_t)g->k * sizeof(uint32_t)));
     g->hist_cap = 1024;
     CK(dev_alloc(g, (void**)&g->hist, (size_t)g->hist_cap * sizeof(double)));
     CK(dev_alloc(g, (void**)&g->state, sizeof(DevState)));
@@ -112,7 +117,7 @@ int sync_state(pcpm_png* g, cudaStream_t s) {
 int run_iterations(pcpm_png* g, float d, int iters, double tol, uint32_t flags, cudaStream_t s,
                    std::vector<cudaEvent_t>* ev) {
     RC(ensure_hist(g, g->iters_done + iters, s));
-    const bool fused = !(flags & PCPM_TWO_PHASE);
+    const bool fused = !(flags & PCPM_TWO_PHASE) && g->fused_ok;
     for (int i = 0; i < iters; ++i) {
         if (ev) CK(cudaEventRecord((*ev)[4 * i], s));
         if (!fused || !g->upd_valid) RC(launch_scatter(g, s));
@@ -162,7 +167,7 @@ int iterate_impl(pcpm_png* g, float d, int iters, double tol, uint32_t flags, in
         const int done = g->state_host->iters_done - start_done;
         g->iters_done = g->state_host->iters_done;
         g->cur = start_cur ^ (done & 1);
-        if (!(flags & PCPM_TWO_PHASE)) {
+        if (!(flags & PCPM_TWO_PHASE) && g->fused_ok) {
             g->ucur = start_ucur ^ (done & 1);
             g->upd_valid = done > 0 ? 1 : start_valid;
         } else if (done > 0) {
@@ -188,7 +193,17 @@ extern "C" {
 
 int pcpm_build(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t n, uint64_t m, uint32_t part_size,
                void* stream, pcpm_png** out) {
+    return pcpm_build_ex(row_ptr, col_idx, n, m, part_size, nullptr, stream, out);
+}
+
+int pcpm_build_ex(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t n, uint64_t m, uint32_t part_size,
+                  const pcpm_build_options* options, void* stream, pcpm_png** out) {
     if (!out || !row_ptr || n == 0 || n > PCPM_MAX_NODES || part_size == 0 || part_size > PCPM_MAX_PART_SIZE)
+        return PCPM_EINVAL;
+    pcpm_build_options opt = {};
+    if (options) opt = *options;
+    if (opt.gather_cluster != 0 && opt.gather_cluster != 1 && opt.gather_cluster != 2 && opt.gather_cluster != 4 &&
+        opt.gather_cluster != 8)
         return PCPM_EINVAL;
     if (m > 0xFFFFFF00ull) return PCPM_EINVAL;
     const uint64_t k = ((uint64_t)n + part_size - 1) / part_size;
@@ -214,9 +229,10 @@ int pcpm_build(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t n, uin
     g->k = (uint32_t)k;
     g->m = m;
     g->last_stream = s;
+    g->cluster = (int)opt.gather_cluster;
     int rc = PCPM_OK;
     if (cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess) rc = PCPM_ECUDA;
-    if (rc == PCPM_OK) rc = build_png(g, row_ptr, col_idx ? col_idx : row_ptr, s);
+    if (rc == PCPM_OK) rc = build_png(g, row_ptr, col_idx ? col_idx : row_ptr, opt, s);
     if (rc == PCPM_OK) rc = alloc_state(g);
     if (rc == PCPM_OK) rc = configure_kernels(g);
     if (rc == PCPM_OK) {
@@ -250,6 +266,10 @@ int pcpm_png_get_info(const pcpm_png* g, pcpm_png_info* info) {
     info->compression_ratio = g->ne ? (double)g->m / (double)g->ne : 0.0;
     info->device_bytes = g->device_bytes;
     info->iterations_done = g->iters_done;
+    info->gather_units = g->ngunits;
+    info->scatter_units = g->nsunits;
+    info->gather_cluster = (uint32_t)g->cluster;
+    info->fused_ok = (uint32_t)g->fused_ok;
     return PCPM_OK;
 }
 
@@ -287,6 +307,8 @@ int pcpm_reset(pcpm_png* g, const float* pr_init, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     g->last_stream = s;
     CK(cudaMemsetAsync(g->state, 0, sizeof(DevState), s));
+    CK(cudaMemsetAsync(g->gacc, 0, (size_t)g->n * sizeof(float), s));
+    CK(cudaMemsetAsync(g->bin_done, 0, (size_t)g->k * sizeof(uint32_t), s));
     g->cur = 0;
     g->iters_done = 0;
     g->upd_valid = 0;

@@ -76,8 +76,20 @@ struct pcpm_png {
     uint32_t* cnt_e;         // k*k edges p -> p'
     uint32_t* chunk_base;    // nchunks+1: flagged IDs before each chunk
     uint32_t* hubs;          // 2k: per bin, local IDs of its two largest in-degrees (or kNoHub)
-    uint32_t* bin_order;     // k: destination partitions by decreasing bin size
-    uint32_t* src_order;     // k: source partitions by decreasing update count
+    // Work units. A gather unit is a run of chunks of one bin (uint4: bin,
+    // first chunk, end chunk, pieces of that bin); a scatter unit is a range of
+    // 4-entry groups of one source partition (partition, first group, end
+    // group, pieces). Large bins and partitions are cut into several units so
+    // skewed graphs still spread over all SMs; orders list units largest first.
+    uint4* gunits;
+    uint32_t* gorder;
+    uint32_t ngunits;
+    uint4* sunits;
+    uint32_t* sorder;
+    uint32_t nsunits;
+    int fused_ok;            // every bin is a single gather unit
+    float* gacc;             // n: partial sums of bins cut into several units
+    uint32_t* bin_done;      // k: units of a cut bin that have flushed
     float* inv_deg;          // n: 1/|N_o(u)|, 0 for dangling nodes
     // solver state
     float* pr[2];            // ranks ping-pong
@@ -85,8 +97,8 @@ struct pcpm_png {
     float* upd[2];           // update bins (padded); upd[ucur] is the current one
     int ucur;
     int upd_valid;           // upd[ucur] holds the scatter of PR_i
-    int cluster;             // CTAs per bin in the gather
-    double* partials;        // 2 * max(k * cluster, init blocks): per-CTA (residual, dangling)
+    int cluster;             // CTAs per gather unit (a thread-block cluster)
+    double* partials;        // 2 * partial_slots(): per-CTA (residual, dangling)
     int partial_count;       // CTAs that wrote partials for the pending reduce
     double* hist;            // residual history
     int hist_cap;
@@ -101,7 +113,8 @@ namespace pcpm {
 
 // Builder entry (png_build.cu). Fills every PNG field of `g` (n, q, k, m set by
 // the caller); returns a PCPM_* status.
-int build_png(pcpm_png* g, const uint32_t* row_ptr, const uint32_t* col, cudaStream_t s);
+int build_png(pcpm_png* g, const uint32_t* row_ptr, const uint32_t* col, const pcpm_build_options& opt,
+              cudaStream_t s);
 
 // Iteration kernels (pcpm_iter.cu).
 int configure_kernels(pcpm_png* g);

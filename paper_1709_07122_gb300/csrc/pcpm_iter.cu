@@ -29,7 +29,6 @@
 // buffer for the next iteration: gather, apply and the next scatter of one
 // partition in one launch, without writing SPR to memory.
 #include <algorithm>
-#include <cstdlib>
 
 #include "pcpm_internal.cuh"
 
@@ -295,14 +294,15 @@ __global__ void spr_kernel(uint32_t n, const float* __restrict__ pr, const float
 __global__ void __launch_bounds__(kScatterThreads, 1) scatter_kernel(
     uint32_t n, uint32_t q, uint32_t k, const float* __restrict__ pr, const float* __restrict__ inv_deg,
     const uint32_t* __restrict__ src, const uint32_t* __restrict__ seg_u, const uint32_t* __restrict__ cnt_u,
-    const uint32_t* __restrict__ src_order, float* __restrict__ upd, const DevState* __restrict__ st,
-    int* __restrict__ err) {
+    const uint4* __restrict__ units, const uint32_t* __restrict__ order, float* __restrict__ upd,
+    const DevState* __restrict__ st, int* __restrict__ err) {
     if (st->stop) return;
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ uint32_t sh32[32];
     float* sspr = reinterpret_cast<float*>(smraw);
     uint32_t* gpre = reinterpret_cast<uint32_t*>(smraw + (size_t)((q + 3) & ~3u) * sizeof(float));
-    const uint32_t p = src_order[blockIdx.x];
+    const uint4 unit = units[order[blockIdx.x]];  // (partition, first group, end group, pieces)
+    const uint32_t p = unit.x;
     const uint32_t base = p * q, len = min(q, n - base);
     const uint32_t* segrow = seg_u + (size_t)p * k;
     const uint32_t* cntrow = cnt_u + (size_t)p * k;
@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(kScatterThreads, 1) scatter_kernel(
         for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) sspr[i] = pr[base + i] * inv_deg[base + i];
     }
     segment_groups_prefix(segrow, cntrow, k, gpre, sh32);
-    scatter_groups(sspr, base, len, gpre, k, segrow, cntrow, src, upd, 0, gpre[k], err);
+    scatter_groups(sspr, base, len, gpre, k, segrow, cntrow, src, upd, unit.y, min(unit.z, gpre[k]), err);
 }
 
 // ---------------------------------------------------------- gather+apply
@@ -328,8 +328,11 @@ struct GatherArgs {
     const uint32_t* dest;
     const uint32_t* bin_e;
     const uint32_t* chunk_base;
-    const uint32_t* bin_order;
+    const uint4* units;
+    const uint32_t* order;
     const uint32_t* hubs;
+    float* gacc;
+    uint32_t* bin_done;
     const float* upd_in;
     const float* pr_in;
     const float* inv_deg;
@@ -356,23 +359,6 @@ constexpr size_t kAccOffset = kRingBytes + kBarBytes + kMetaBytes;
 static_assert(kStageBytes % 16 == 0, "ring slots must stay 16-byte aligned");
 static_assert(kAccOffset % 16 == 0, "accumulator must be 16-byte aligned");
 
-__device__ __forceinline__ void gather_one(uint32_t id, uint32_t uoff, uint32_t pos, uint32_t E0, uint32_t E1,
-                                           uint32_t vbase, uint32_t len, const float* ups, float* acc, uint32_t h0,
-                                           uint32_t h1, float& a0, float& a1, int* err) {
-    if (pos >= E0 && pos < E1) {
-        const uint32_t local = (id & kIdMask) - vbase;
-        if (uoff >= kUpdSlot) {
-            atomicOr(err, kErrBounds);
-            return;
-        }
-        const float val = ups[uoff];
-        if (local == h0) a0 += val;
-        else if (local == h1) a1 += val;
-        else if (local < len) atomicAdd(&acc[local], val);
-        else atomicOr(err, kErrBounds);
-    }
-}
-
 template <bool kFused>
 __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const GatherArgs a) {
     if (a.st->stop) return;
@@ -384,7 +370,8 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
     float* acc = reinterpret_cast<float*>(smraw + kAccOffset);
 
     const uint32_t S = cluster_size(), rank = cluster_rank();
-    const uint32_t pd = a.bin_order[blockIdx.x / S];
+    const uint4 unit = a.units[a.order[blockIdx.x / S]];  // (bin, first chunk, end chunk, pieces of the bin)
+    const uint32_t pd = unit.x, npieces = unit.w;
     const uint32_t vbase = pd * a.q, len = min(a.q, a.n - vbase);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
@@ -397,9 +384,9 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
     const uint32_t h0 = a.hubs[2 * pd], h1 = a.hubs[2 * pd + 1];
     float hub0 = 0.0f, hub1 = 0.0f;
     const uint32_t E0 = a.bin_e[pd], E1 = a.bin_e[pd + 1];
-    if (E1 > E0) {
-        const uint32_t c_first = E0 / kChunk;
-        const uint32_t nch = (E1 - 1) / kChunk - c_first + 1;
+    if (unit.z > unit.y) {
+        const uint32_t c_first = unit.y;
+        const uint32_t nch = unit.z - unit.y;
         const uint32_t gw = rank * kGatherWarps + warp, GW = S * kGatherWarps;
         const uint32_t wc0 = c_first + (uint32_t)((uint64_t)nch * gw / GW);
         const uint32_t nmine = c_first + (uint32_t)((uint64_t)nch * (gw + 1) / GW) - wc0;
@@ -456,22 +443,65 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
             uint32_t fbase = wmeta[2 * slot];
             const uint32_t us = wmeta[2 * slot + 1];
             const uint32_t cstart = (wc0 + j) * kChunk;
+            // Only a bin's first and last chunk hold IDs of other bins.
+            const bool interior = cstart >= E0 && cstart + kChunk <= E1;
+            // All loads of the chunk first (IDs, then update values), then the
+            // adds, so each lane has eight independent shared-memory operations
+            // in flight instead of a chain per ID.
+            constexpr int kPer = kChunk / 32;  // IDs per lane
+            uint32_t id[kPer], uo[kPer];
 #pragma unroll
-            for (int h = 0; h < (int)(kChunk / 128); ++h) {
-                const uint4 ids = *reinterpret_cast<const uint4*>(ids_s + h * 128 + lane * 4);
-                const uint32_t f0 = ids.x >> 31, f1 = ids.y >> 31, f2 = ids.z >> 31, f3 = ids.w >> 31;
-                const uint32_t b0 = __ballot_sync(kFull, f0), b1 = __ballot_sync(kFull, f1);
-                const uint32_t b2 = __ballot_sync(kFull, f2), b3 = __ballot_sync(kFull, f3);
-                const uint32_t before = __popc(b0 & lt) + __popc(b1 & lt) + __popc(b2 & lt) + __popc(b3 & lt);
-                // update index (relative to the slot) of each ID: inclusive flag count - 1
-                const uint32_t u0 = fbase + before + f0 - 1 - us;
-                const uint32_t u1 = u0 + f1, u2 = u1 + f2, u3 = u2 + f3;
-                const uint32_t pos = cstart + h * 128 + lane * 4;
-                gather_one(ids.x, u0, pos, E0, E1, vbase, len, ups, acc, h0, h1, hub0, hub1, a.err);
-                gather_one(ids.y, u1, pos + 1, E0, E1, vbase, len, ups, acc, h0, h1, hub0, hub1, a.err);
-                gather_one(ids.z, u2, pos + 2, E0, E1, vbase, len, ups, acc, h0, h1, hub0, hub1, a.err);
-                gather_one(ids.w, u3, pos + 3, E0, E1, vbase, len, ups, acc, h0, h1, hub0, hub1, a.err);
-                fbase += __popc(b0) + __popc(b1) + __popc(b2) + __popc(b3);
+            for (int h = 0; h < kPer / 4; ++h) {
+                const uint4 v4 = *reinterpret_cast<const uint4*>(ids_s + h * 128 + lane * 4);
+                id[4 * h] = v4.x;
+                id[4 * h + 1] = v4.y;
+                id[4 * h + 2] = v4.z;
+                id[4 * h + 3] = v4.w;
+            }
+#pragma unroll
+            for (int h = 0; h < kPer / 4; ++h) {
+                uint32_t f[4], b[4], before = 0, total = 0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    f[q] = id[4 * h + q] >> 31;
+                    b[q] = __ballot_sync(kFull, f[q]);
+                    before += __popc(b[q] & lt);
+                    total += __popc(b[q]);
+                }
+                // update index (relative to the slot): inclusive flag count - 1
+                uint32_t u = fbase + before - 1 - us;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    u += f[q];
+                    uo[4 * h + q] = u;
+                }
+                fbase += total;
+            }
+            uint32_t valid = (1u << kPer) - 1u;
+            if (!interior) {
+                valid = 0;
+#pragma unroll
+                for (int h = 0; h < kPer / 4; ++h)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const uint32_t pos = cstart + h * 128 + lane * 4 + q;
+                        valid |= (pos >= E0 && pos < E1) ? 1u << (4 * h + q) : 0u;
+                    }
+            }
+            float val[kPer];
+#pragma unroll
+            for (int j = 0; j < kPer; ++j) val[j] = ups[(valid >> j & 1u) ? uo[j] : 0u];
+#pragma unroll
+            for (int j = 0; j < kPer; ++j) {
+                const uint32_t loc = (id[j] & kIdMask) - vbase;
+                const bool ok_j = (valid >> j & 1u) != 0;
+                const bool is0 = ok_j && loc == h0, is1 = ok_j && loc == h1;
+                hub0 += is0 ? val[j] : 0.0f;
+                hub1 += is1 ? val[j] : 0.0f;
+                if (ok_j && !is0 && !is1) {
+                    if (loc < len) atomicAdd(&acc[loc], val[j]);
+                    else atomicOr(a.err, kErrBounds);
+                }
             }
             __syncwarp();
             if (issued < nmine) {
@@ -505,17 +535,46 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
     const double D = a.uniform_dangling ? a.st->dangling : 0.0;
     const float cst = (float)((1.0 - (double)a.d) / (double)a.n + (double)a.d * D / (double)a.n);
     double res = 0.0, dg = 0.0;
-    for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-        float s = 0.0f;
-        for (uint32_t r = 0; r < S; ++r) s += ld_cluster_f32(map_rank(acc + i, r));
-        const uint32_t v = vbase + i;
-        const float x = fmaf(a.d, s, cst);
-        const float old = a.pr_in[v];
-        const float inv = a.inv_deg[v];
-        a.pr_out[v] = x;
-        if (kFused) acc[i] = x * inv;
-        res += fabs((double)x - (double)old);
-        if (inv == 0.0f) dg += (double)x;
+    if (npieces == 1) {
+        for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+            float s = 0.0f;
+            for (uint32_t r = 0; r < S; ++r) s += ld_cluster_f32(map_rank(acc + i, r));
+            const uint32_t v = vbase + i;
+            const float x = fmaf(a.d, s, cst);
+            const float old = a.pr_in[v];
+            const float inv = a.inv_deg[v];
+            a.pr_out[v] = x;
+            if (kFused) acc[i] = x * inv;
+            res += fabs((double)x - (double)old);
+            if (inv == 0.0f) dg += (double)x;
+        }
+    } else {
+        // The bin is cut into several units: add this unit's sums to the
+        // global partial sums; the last CTA to arrive applies the partition.
+        uint32_t& last = sh32[0];
+        for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+            float s = 0.0f;
+            for (uint32_t r = 0; r < S; ++r) s += ld_cluster_f32(map_rank(acc + i, r));
+            if (s != 0.0f) atomicAdd(&a.gacc[vbase + i], s);
+        }
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) last = atomicAdd(&a.bin_done[pd], 1u) == npieces * S - 1 ? 1u : 0u;
+        __syncthreads();
+        if (last) {
+            __threadfence();
+            for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) {
+                const uint32_t v = vbase + i;
+                const float x = fmaf(a.d, __ldcg(&a.gacc[v]), cst);
+                a.gacc[v] = 0.0f;
+                const float old = a.pr_in[v];
+                const float inv = a.inv_deg[v];
+                a.pr_out[v] = x;
+                res += fabs((double)x - (double)old);
+                if (inv == 0.0f) dg += (double)x;
+            }
+            if (threadIdx.x == 0) a.bin_done[pd] = 0;
+        }
     }
     block_sum2<kGatherWarps * 32>(res, dg);
     if (threadIdx.x == 0) {
@@ -525,6 +584,10 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
     cluster_sync();
 
     if constexpr (kFused) {
+        if (npieces != 1) {  // the host runs cut bins in two-phase form only
+            if (threadIdx.x == 0) atomicOr(a.err, kErrBounds);
+            return;
+        }
         // Fused scatter of the next iteration: gather SPR' of the whole
         // partition into this CTA's shared memory, then write 1/S of its
         // update segments.
@@ -581,7 +644,7 @@ size_t scatter_smem_bytes(uint32_t q, uint32_t k) {
 }  // namespace
 
 size_t partial_slots(const pcpm_png* g) {
-    return std::max<size_t>((size_t)g->k * kMaxCluster, (size_t)kInitBlocks);
+    return std::max<size_t>((size_t)g->ngunits * kMaxCluster, (size_t)kInitBlocks);
 }
 
 // Picks the cluster size for the gather and sets shared-memory limits.
@@ -591,15 +654,10 @@ int configure_kernels(pcpm_png* g) {
         cudaFuncSetAttribute(gather_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gs) != cudaSuccess ||
         cudaFuncSetAttribute(scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss) != cudaSuccess)
         return PCPM_ECUDA;
-    // Enough CTAs to give every SM about four of them, at least two per bin, at
-    // most kMaxCluster; a PCPM_GATHER_CLUSTER environment variable (1, 2, 4 or
-    // 8) overrides the choice.
-    int want = 2;
-    while (want < kMaxCluster && (uint64_t)g->k * want < (uint64_t)g->sms * 4) want *= 2;
-    if (const char* env = getenv("PCPM_GATHER_CLUSTER")) {
-        const int v = atoi(env);
-        if (v == 1 || v == 2 || v == 4 || v == 8) want = v;
-    }
+    // Two CTAs per gather unit unless the build options ask otherwise (two
+    // measured best at k = 512 against one and four); smaller if the device
+    // cannot co-schedule that many.
+    const int want = g->cluster ? g->cluster : 2;
     for (int S = want; S >= 1; S /= 2) {
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute attr[1];
@@ -607,7 +665,7 @@ int configure_kernels(pcpm_png* g) {
         attr[0].val.clusterDim.x = S;
         attr[0].val.clusterDim.y = 1;
         attr[0].val.clusterDim.z = 1;
-        cfg.gridDim = dim3(g->k * S);
+        cfg.gridDim = dim3(g->ngunits * S);
         cfg.blockDim = dim3(kGatherWarps * 32);
         cfg.dynamicSmemBytes = gs;
         cfg.attrs = attr;
@@ -636,9 +694,9 @@ int launch_spr(pcpm_png* g, float* spr, cudaStream_t s) {
 }
 
 int launch_scatter(pcpm_png* g, cudaStream_t s) {
-    scatter_kernel<<<g->k, kScatterThreads, scatter_smem_bytes(g->q, g->k), s>>>(
-        g->n, g->q, g->k, g->pr[g->cur], g->inv_deg, g->src, g->seg_u, g->cnt_u, g->src_order, g->upd[g->ucur],
-        g->state, &g->state->err);
+    scatter_kernel<<<g->nsunits, kScatterThreads, scatter_smem_bytes(g->q, g->k), s>>>(
+        g->n, g->q, g->k, g->pr[g->cur], g->inv_deg, g->src, g->seg_u, g->cnt_u, g->sunits, g->sorder,
+        g->upd[g->ucur], g->state, &g->state->err);
     return cudaGetLastError() == cudaSuccess ? PCPM_OK : PCPM_ECUDA;
 }
 
@@ -650,8 +708,11 @@ int launch_gather(pcpm_png* g, float d, uint32_t flags, bool fused, cudaStream_t
     a.dest = g->dest;
     a.bin_e = g->bin_e;
     a.chunk_base = g->chunk_base;
-    a.bin_order = g->bin_order;
+    a.units = g->gunits;
+    a.order = g->gorder;
     a.hubs = g->hubs;
+    a.gacc = g->gacc;
+    a.bin_done = g->bin_done;
     a.upd_in = g->upd[g->ucur];
     a.pr_in = g->pr[g->cur];
     a.inv_deg = g->inv_deg;
@@ -672,7 +733,7 @@ int launch_gather(pcpm_png* g, float d, uint32_t flags, bool fused, cudaStream_t
     attr[0].val.clusterDim.x = g->cluster;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(g->k * g->cluster);
+    cfg.gridDim = dim3(g->ngunits * g->cluster);
     cfg.blockDim = dim3(kGatherWarps * 32);
     cfg.dynamicSmemBytes = gather_smem_bytes(g->q);
     cfg.stream = s;
@@ -680,7 +741,7 @@ int launch_gather(pcpm_png* g, float d, uint32_t flags, bool fused, cudaStream_t
     cfg.numAttrs = 1;
     const cudaError_t e = fused ? cudaLaunchKernelEx(&cfg, gather_kernel<true>, a)
                                 : cudaLaunchKernelEx(&cfg, gather_kernel<false>, a);
-    g->partial_count = (int)(g->k * g->cluster);
+    g->partial_count = (int)(g->ngunits * g->cluster);
     return e == cudaSuccess ? PCPM_OK : PCPM_ECUDA;
 }
 

@@ -387,13 +387,7 @@ __global__ void __launch_bounds__(1024) hubs_kernel(const uint32_t* __restrict__
     }
 }
 
-// size[p] for ordering: entries of destination bin p, or 4-entry groups the
-// scatter of source partition p writes.
-__global__ void bin_sizes_kernel(const uint32_t* __restrict__ bin_e, uint32_t k, uint32_t* __restrict__ size) {
-    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < k; p += gridDim.x * blockDim.x)
-        size[p] = bin_e[p + 1] - bin_e[p];
-}
-
+// groups[p] = 4-entry groups the scatter of source partition p writes.
 __global__ void src_groups_kernel(const uint32_t* __restrict__ seg_u, const uint32_t* __restrict__ cnt_u, uint32_t k,
                                   uint32_t* __restrict__ size) {
     const uint32_t p = blockIdx.x;
@@ -424,6 +418,51 @@ __global__ void order_kernel(const uint32_t* __restrict__ size, uint32_t k, uint
             rank += (sj > si) || (sj == si && j < i);
         }
         order[rank] = i;
+    }
+}
+
+// ------------------------------------------------------------ work units
+// pieces[p] = units of bin p: its chunks cut into runs of at most `per`
+// (an empty bin still gets one unit for its apply).
+__global__ void gather_pieces_kernel(const uint32_t* __restrict__ bin_e, uint32_t k, uint32_t per,
+                                     uint32_t* __restrict__ pieces) {
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < k; p += gridDim.x * blockDim.x) {
+        const uint32_t e0 = bin_e[p], e1 = bin_e[p + 1];
+        const uint32_t nch = e1 > e0 ? (e1 - 1) / kChunk - e0 / kChunk + 1 : 0;
+        pieces[p] = nch ? (nch + per - 1) / per : 1;
+    }
+}
+
+__global__ void gather_units_kernel(const uint32_t* __restrict__ bin_e, const uint32_t* __restrict__ start,
+                                    uint32_t k, uint32_t per, uint32_t nunits, uint4* __restrict__ units,
+                                    uint32_t* __restrict__ sizes) {
+    for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < nunits; u += gridDim.x * blockDim.x) {
+        const uint32_t p = upper_bound_u32(start, 0, k + 1, u) - 1;
+        const uint32_t e0 = bin_e[p], e1 = bin_e[p + 1];
+        const uint32_t c0 = e0 / kChunk;
+        const uint32_t nch = e1 > e0 ? (e1 - 1) / kChunk - c0 + 1 : 0;
+        const uint32_t idx = u - start[p];
+        const uint32_t lo = c0 + min(nch, idx * per), hi = c0 + min(nch, (idx + 1) * per);
+        units[u] = make_uint4(p, lo, hi, start[p + 1] - start[p]);
+        sizes[u] = hi - lo;
+    }
+}
+
+__global__ void scatter_pieces_kernel(const uint32_t* __restrict__ groups, uint32_t k, uint32_t per,
+                                      uint32_t* __restrict__ pieces) {
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < k; p += gridDim.x * blockDim.x)
+        pieces[p] = groups[p] ? (groups[p] + per - 1) / per : 1;
+}
+
+__global__ void scatter_units_kernel(const uint32_t* __restrict__ groups, const uint32_t* __restrict__ start,
+                                     uint32_t k, uint32_t per, uint32_t nunits, uint4* __restrict__ units,
+                                     uint32_t* __restrict__ sizes) {
+    for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < nunits; u += gridDim.x * blockDim.x) {
+        const uint32_t p = upper_bound_u32(start, 0, k + 1, u) - 1;
+        const uint32_t idx = u - start[p];
+        const uint32_t lo = min(groups[p], idx * per), hi = min(groups[p], (idx + 1) * per);
+        units[u] = make_uint4(p, lo, hi, start[p + 1] - start[p]);
+        sizes[u] = hi - lo;
     }
 }
 
@@ -492,7 +531,8 @@ int read_err(int* d_err, cudaStream_t s, int* h_err) {
 
 }  // namespace
 
-int build_png(pcpm_png* g, const uint32_t* row_ptr, const uint32_t* col, cudaStream_t s) {
+int build_png(pcpm_png* g, const uint32_t* row_ptr, const uint32_t* col, const pcpm_build_options& opt,
+              cudaStream_t s) {
     const uint32_t n = g->n, q = g->q, k = g->k;
     const uint64_t m = g->m;
     TempBufs tmp;
@@ -593,20 +633,59 @@ int build_png(pcpm_png* g, const uint32_t* row_ptr, const uint32_t* col, cudaStr
         BCK(cudaMemsetAsync(g->chunk_base, 0, sizeof(uint32_t), s));
     }
 
-    // Hubs per bin and launch orders.
-    uint32_t *indeg = nullptr, *sizes = nullptr;
+    // Hubs per bin.
+    uint32_t* indeg = nullptr;
     BCK(tmp.alloc(&indeg, n));
-    BCK(tmp.alloc(&sizes, k));
     BCK(cudaMemsetAsync(indeg, 0, (size_t)n * sizeof(uint32_t), s));
     if (m) indegree_kernel<<<grid_for(m, 256, sms * 32), 256, 0, s>>>(col, m, indeg);
     BCK(dev_alloc(g, (void**)&g->hubs, 2 * (size_t)k * sizeof(uint32_t)));
     hubs_kernel<<<k, 1024, 0, s>>>(indeg, n, q, g->hubs);
-    BCK(dev_alloc(g, (void**)&g->bin_order, (size_t)k * sizeof(uint32_t)));
-    BCK(dev_alloc(g, (void**)&g->src_order, (size_t)k * sizeof(uint32_t)));
-    bin_sizes_kernel<<<grid_for(k, 256, 64), 256, 0, s>>>(g->bin_e, k, sizes);
-    order_kernel<<<grid_for(k, 128, 1024), 128, 0, s>>>(sizes, k, g->bin_order);
-    src_groups_kernel<<<k, 256, 0, s>>>(g->seg_u, g->cnt_u, k, sizes);
-    order_kernel<<<grid_for(k, 128, 1024), 128, 0, s>>>(sizes, k, g->src_order);
+    BCK(cudaGetLastError());
+
+    // Work units, largest first. Gather: runs of at most `gper` chunks, at
+    // least q/64 chunks (so a unit's flush of q partial sums stays small next
+    // to its work) and about nchunks/(2*SMs). Scatter: runs of at most `sper`
+    // groups, at least q (a unit stages the partition's q values once).
+    uint32_t *pieces = nullptr, *start = nullptr, *sizes = nullptr, *groups = nullptr, *gstart = nullptr;
+    BCK(tmp.alloc(&pieces, k));
+    BCK(tmp.alloc(&start, k + 1));
+    BCK(tmp.alloc(&groups, k));
+    BCK(tmp.alloc(&gstart, k + 1));
+    const uint32_t gper = opt.gather_unit_chunks ? opt.gather_unit_chunks
+                                                 : (uint32_t)std::max<uint64_t>((q + 63) / 64,
+                                                                                (g->nchunks + 2 * sms - 1) / (2 * sms));
+    gather_pieces_kernel<<<grid_for(k, 256, 64), 256, 0, s>>>(g->bin_e, k, gper, pieces);
+    if ((rc = scan_exclusive(pieces, start, k, tmp, s)) != PCPM_OK) return rc;
+    src_groups_kernel<<<k, 256, 0, s>>>(g->seg_u, g->cnt_u, k, groups);
+    if ((rc = scan_exclusive(groups, gstart, k, tmp, s)) != PCPM_OK) return rc;
+    uint32_t totals[2] = {0, 0};
+    BCK(cudaMemcpyAsync(&totals[0], start + k, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    BCK(cudaMemcpyAsync(&totals[1], gstart + k, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    BCK(cudaStreamSynchronize(s));
+    g->ngunits = totals[0];
+    g->fused_ok = g->ngunits == k;
+    BCK(tmp.alloc(&sizes, std::max<uint32_t>(g->ngunits, k) + 1));
+    BCK(dev_alloc(g, (void**)&g->gunits, (size_t)g->ngunits * sizeof(uint4)));
+    BCK(dev_alloc(g, (void**)&g->gorder, (size_t)g->ngunits * sizeof(uint32_t)));
+    gather_units_kernel<<<grid_for(g->ngunits, 256, 1024), 256, 0, s>>>(g->bin_e, start, k, gper, g->ngunits,
+                                                                        g->gunits, sizes);
+    order_kernel<<<grid_for(g->ngunits, 128, 1024), 128, 0, s>>>(sizes, g->ngunits, g->gorder);
+    BCK(cudaGetLastError());
+    const uint32_t sper = opt.scatter_unit_groups
+                              ? opt.scatter_unit_groups
+                              : (uint32_t)std::max<uint64_t>(q, ((uint64_t)totals[1] + 2 * sms - 1) / (2 * sms));
+    scatter_pieces_kernel<<<grid_for(k, 256, 64), 256, 0, s>>>(groups, k, sper, pieces);
+    if ((rc = scan_exclusive(pieces, start, k, tmp, s)) != PCPM_OK) return rc;
+    BCK(cudaMemcpyAsync(&totals[0], start + k, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    BCK(cudaStreamSynchronize(s));
+    g->nsunits = totals[0];
+    uint32_t* ssizes = nullptr;
+    BCK(tmp.alloc(&ssizes, g->nsunits + 1));
+    BCK(dev_alloc(g, (void**)&g->sunits, (size_t)g->nsunits * sizeof(uint4)));
+    BCK(dev_alloc(g, (void**)&g->sorder, (size_t)g->nsunits * sizeof(uint32_t)));
+    scatter_units_kernel<<<grid_for(g->nsunits, 256, 1024), 256, 0, s>>>(groups, start, k, sper, g->nsunits,
+                                                                         g->sunits, ssizes);
+    order_kernel<<<grid_for(g->nsunits, 128, 1024), 128, 0, s>>>(ssizes, g->nsunits, g->sorder);
     BCK(cudaGetLastError());
 
     BCK(dev_alloc(g, (void**)&g->inv_deg, (size_t)n * sizeof(float)));

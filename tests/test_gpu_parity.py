@@ -159,7 +159,8 @@ def test_fused_scatter_writes_next_bins_bit_exact():
     # at every PNG position (the fused kernel's scatter half).
     (rp, col), q = GRAPHS["rmat14_q_not_multiple"]()
     ref = oracle.png(rp, col, q)
-    with pcpm.PNG.from_host(rp, col, q) as g:
+    with pcpm.PNG.from_host(rp, col, q, gather_unit_chunks=1 << 30) as g:
+        assert g.info["fused_ok"] == 1
         g.reset()
         g.iterate(0.85, 3)
         st = g.export_state()
@@ -249,3 +250,60 @@ def test_errors_from_bad_inputs():
             g.iterate(1.0, 1)
         with pytest.raises(ValueError):
             g.iterate(0.85, 1, dangling="bogus")
+
+
+DECOMPOSITIONS = [
+    dict(),                                             # automatic
+    dict(gather_unit_chunks=1 << 30),                   # one unit per bin: fused path
+    dict(gather_unit_chunks=1, gather_cluster=1),       # every chunk its own unit
+    dict(gather_unit_chunks=3, gather_cluster=4),
+    dict(gather_unit_chunks=1 << 30, gather_cluster=8),
+    dict(scatter_unit_groups=1),                        # every 4-update group its own unit
+    dict(scatter_unit_groups=7, gather_unit_chunks=5, gather_cluster=2),
+]
+
+
+@pytest.mark.parametrize("opts", DECOMPOSITIONS, ids=lambda o: ",".join(f"{k}={v}" for k, v in o.items()) or "auto")
+@pytest.mark.parametrize("name", ["rmat12_bfs_q512", "rmat14_q_not_multiple", "random1000_q7", "single_partition"])
+@pytest.mark.parametrize("mode", ["fused", "two_phase"])
+def test_work_decompositions_match_oracle(name, opts, mode):
+    # How bins and source partitions are cut into work units, and how many
+    # CTAs share a unit, changes scheduling only: the bins stay bit-exact and
+    # the ranks follow the oracle on every iteration.
+    (rp, col), q = GRAPHS[name]()
+    ref = oracle.pagerank(rp, col, 0.85, iters=6, history=True)["hist"]
+    with pcpm.PNG.from_host(rp, col, q, **opts) as g:
+        info = g.info
+        k = info["num_partitions"]
+        assert info["gather_units"] >= k and info["scatter_units"] >= k
+        assert info["fused_ok"] == (info["gather_units"] == k)
+        if opts.get("gather_unit_chunks") == 1 << 30:
+            assert info["gather_units"] == k
+        g.reset()
+        for i in range(1, 7):
+            g.iterate(0.85, 1, mode=mode)
+            assert l1(g.ranks().cpu().numpy(), ref[i]) <= L1_TOL, i
+    if opts == DECOMPOSITIONS[2]:
+        with pcpm.PNG.from_host(rp, col, q, **opts) as g:
+            assert_png_matches(g.export(), oracle.png(rp, col, q))
+
+
+def test_skewed_bins_are_cut_into_units():
+    # BFS labels put most in-edges into the first partitions (a few bins hold
+    # most of the graph): the automatic decomposition cuts them into several
+    # gather units, and the result still follows the oracle.
+    rp, col = graphgen.rmat(16, 16, seed=1710, relabel="bfs")
+    q = 4096
+    ref = oracle.pagerank(rp, col, 0.85, iters=5)["x"]
+    with pcpm.PNG.from_host(rp, col, q) as g:
+        info = g.info
+        assert info["gather_units"] > info["num_partitions"]
+        pr, iters, _ = g.pagerank(0.85, max_iters=5)
+        assert l1(pr.cpu().numpy(), ref) <= L1_TOL
+
+
+def test_bad_cluster_option_rejected():
+    (rp, col), q = GRAPHS["random300_q1"]()
+    with pytest.raises(pcpm.PcpmError) as e:
+        pcpm.PNG.from_host(rp, col, q, gather_cluster=3)
+    assert e.value.code == -1
