@@ -49,6 +49,7 @@ extern "C" {
 #define PCPM_ETIMEOUT (-4)     /* a bounded device-side wait gave up */
 #define PCPM_EDEVICE (-5)      /* a device-side consistency check failed */
 #define PCPM_EBADGRAPH (-6)    /* CSR invalid: column >= n or a row not sorted */
+#define PCPM_ESCRATCH (-7)     /* input larger than the fixed no-allocation scratch */
 
 /* ------------------------------------------------------------------ limits */
 /* Node IDs keep their most significant bit free for the message flag
@@ -217,6 +218,34 @@ int pcpm_pagerank_host(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_
  * current update bins, bin order) and the dangling mass of pr. Synchronises. */
 int pcpm_scatter_only(pcpm_png* png, void* stream);
 int pcpm_export_state(const pcpm_png* png, float* pr, float* spr, float* updates, double* dangling);
+
+/* Allocation-free rank statistics. There is no counterpart in the paper: this
+ * entry point exists for callers that cannot call cudaMalloc, such as code
+ * running inside a custom memory pool or allocator callback that must not
+ * re-enter the allocator, or a process whose device memory is fully reserved
+ * before it starts. It allocates nothing: its scratch is a fixed array
+ * compiled into the library (PCPM_NOALLOC_MAX_BLOCKS * 16 bytes = 1 MiB,
+ * held on every GPU that loads the library until the process exits).
+ *
+ * Computes, in FP64, out[0] = sum_v |x(v) - y(v)| (the L1 change the solver
+ * reports per iteration) and out[1] = sum of x(v) over nodes v without
+ * out-edges (row_ptr[v+1] == row_ptr[v]; the dangling mass), summed in a
+ * fixed order.
+ *   x, y     device, float[n], caller-owned, read only.
+ *   row_ptr  device, uint32[n+1] (the CSR row offsets of pcpm_build).
+ *   out      device, double[2], caller-owned, written.
+ *   n        1 <= n <= PCPM_NOALLOC_MAX_NODES; larger inputs return
+ *            PCPM_ESCRATCH before anything is launched.
+ * Enqueued on `stream`; does not synchronise. The first call on each device
+ * looks up the scratch array's device address (with that device current) and
+ * so should come before any stream capture. Every call on a device shares the
+ * one scratch array: calls that may overlap on the GPU (different streams
+ * without ordering) race and must be serialised by the caller. Each call
+ * writes every scratch slot it reads, so nothing carries over between calls. */
+#define PCPM_NOALLOC_MAX_BLOCKS 65536u
+#define PCPM_NOALLOC_MAX_NODES (PCPM_NOALLOC_MAX_BLOCKS * 4096u)
+int pcpm_rank_stats_noalloc(const float* x, const float* y, const uint32_t* row_ptr, uint32_t n,
+                            double* out, void* stream);
 
 /* Message for a status code (static string). */
 const char* pcpm_strerror(int code);

@@ -83,6 +83,7 @@ def lib(path: str | None = None):
                 "pcpm_pagerank_host": (i32, [vp, vp, u32, u64, u32, f32, i32, f64, u32, vp, pi, pd]),
                 "pcpm_scatter_only": (i32, [vp, vp]),
                 "pcpm_export_state": (i32, [vp, vp, vp, vp, pd]),
+                "pcpm_rank_stats_noalloc": (i32, [vp, vp, vp, u32, vp, vp]),
                 "pcpm_strerror": (ctypes.c_char_p, [i32]),
             }
             for name, (res, args) in sig.items():
@@ -285,3 +286,19 @@ def pagerank_host(row_ptr: np.ndarray, col: np.ndarray, part_size: int, d: float
                                     out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(it), ctypes.byref(res))
     _check(code, "pcpm_pagerank_host", allow=(PCPM_OK, PCPM_NOT_CONVERGED))
     return out, it.value, res.value
+
+
+def rank_stats_noalloc(x, y, row_ptr, out=None, stream=None):
+    """(L1 change between x and y, dangling mass of x) in FP64 through the
+    allocation-free entry point. x, y: CUDA float32 [n]; row_ptr: CUDA 32-bit
+    integer [n+1]; out: CUDA float64 [2] (allocated here by torch if None)."""
+    import torch
+    n = row_ptr.numel() - 1
+    _f32_dev(x, n)
+    _f32_dev(y, n)
+    if out is None:
+        out = torch.empty(2, dtype=torch.float64, device="cuda")
+    _check(lib().pcpm_rank_stats_noalloc(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                         _dev_u32(row_ptr), n, ctypes.c_void_p(out.data_ptr()), _stream(stream)),
+           "pcpm_rank_stats_noalloc")
+    return out

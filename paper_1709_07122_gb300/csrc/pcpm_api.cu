@@ -467,6 +467,7 @@ const char* pcpm_strerror(int code) {
         case PCPM_ETIMEOUT: return "bounded device wait timed out";
         case PCPM_EDEVICE: return "device-side consistency check failed";
         case PCPM_EBADGRAPH: return "invalid CSR: column out of range or row not sorted";
+        case PCPM_ESCRATCH: return "input larger than the fixed no-allocation scratch (PCPM_NOALLOC_MAX_NODES)";
         default: return "unknown status code";
     }
 }
