@@ -36,6 +36,8 @@ namespace pcpm {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+// Nodes per thread in flight in the apply loop.
+constexpr int kApplyIlp = 8;
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t r;
@@ -130,6 +132,26 @@ __device__ __forceinline__ float4 ld_cluster_f32x4(uint32_t addr) {
     return v;
 }
 
+__device__ __forceinline__ void st_cluster_f32(uint32_t addr, float v) {
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+
+__device__ __forceinline__ void st_cluster_f32x4(uint32_t addr, float4 v) {
+    asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(v.x), "f"(v.y), "f"(v.z),
+                 "f"(v.w)
+                 : "memory");
+}
+
+// Copies cnt floats from this CTA's src to dst in the shared memory of CTA
+// `target` (both 16-byte aligned): distributed-shared-memory stores, which
+// need no round trip, where a remote load would wait for one.
+__device__ __forceinline__ void push_range(const float* src, float* dst, uint32_t cnt, uint32_t target) {
+    const uint32_t c4 = cnt >> 2;
+    for (uint32_t i = threadIdx.x; i < c4; i += blockDim.x)
+        st_cluster_f32x4(map_rank(dst + 4 * i, target), reinterpret_cast<const float4*>(src)[i]);
+    for (uint32_t i = (c4 << 2) + threadIdx.x; i < cnt; i += blockDim.x) st_cluster_f32(map_rank(dst + i, target), src[i]);
+}
+
 // ------------------------------------------------------------ global memory
 __device__ __forceinline__ uint4 ld_stream_u4(const uint32_t* p) {
     uint4 r;
@@ -211,31 +233,51 @@ __device__ void segment_groups_prefix(const uint32_t* __restrict__ segrow, const
     __syncthreads();
 }
 
+// Last segment j >= from with gpre[j] <= f (gpre non-decreasing, gpre[from]
+// <= f < gpre[k]): galloping forward, then bisection, O(log distance).
+__device__ __forceinline__ uint32_t segment_at(const uint32_t* gpre, uint32_t k, uint32_t from, uint32_t f) {
+    uint32_t lo = from, step = 1;
+    while (lo + step < k && gpre[lo + step] <= f) {
+        lo += step;
+        step <<= 1;
+    }
+    uint32_t hi = lo + step < k ? lo + step : k;
+    while (lo + 1 < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (gpre[mid] <= f) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
 // update[t] = sspr[src[t] - base] for the groups [f_lo, f_hi) of the
-// partition's flattened segment list (Algorithm 3).
+// partition's flattened segment list (Algorithm 3). Each warp takes a
+// contiguous run of groups, 32 * kScatterUnroll at a time, so the groups of
+// one step span only a few segments: the warp tracks the segment of its
+// current position and each lane walks forward from it.
 __device__ __forceinline__ void scatter_groups(const float* sspr, uint32_t base, uint32_t len,
                                                const uint32_t* gpre, uint32_t k,
                                                const uint32_t* __restrict__ segrow,
                                                const uint32_t* __restrict__ cntrow,
                                                const uint32_t* __restrict__ src, float* __restrict__ upd,
                                                uint32_t f_lo, uint32_t f_hi, int* err) {
-    uint32_t pd = 0;
-    for (uint32_t f0 = f_lo + threadIdx.x; f0 < f_hi; f0 += kScatterUnroll * blockDim.x) {
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t span = f_hi - f_lo;
+    const uint32_t w_lo = f_lo + (uint32_t)((uint64_t)span * warp / nw);
+    const uint32_t w_hi = f_lo + (uint32_t)((uint64_t)span * (warp + 1) / nw);
+    uint32_t wpd = 0;  // segment of the warp's current position
+    for (uint32_t f0 = w_lo; f0 < w_hi; f0 += 32 * kScatterUnroll) {
+        wpd = segment_at(gpre, k, wpd, f0);  // warp-uniform
         uint32_t e0[kScatterUnroll], s0[kScatterUnroll], c0[kScatterUnroll];
         uint4 ids[kScatterUnroll];
         bool live[kScatterUnroll], full[kScatterUnroll];
+        uint32_t pd = wpd;
 #pragma unroll
         for (int u = 0; u < kScatterUnroll; ++u) {
-            const uint32_t f = f0 + u * blockDim.x;
-            live[u] = f < f_hi;
+            const uint32_t f = f0 + u * 32 + lane;
+            live[u] = f < w_hi;
             full[u] = false;
             if (live[u]) {
-                uint32_t a = pd, b = k;  // last segment whose prefix is <= f
-                while (a + 1 < b) {
-                    const uint32_t mid = (a + b) >> 1;
-                    if (gpre[mid] <= f) a = mid; else b = mid;
-                }
-                pd = a;
+                pd = segment_at(gpre, k, pd, f);
                 s0[u] = segrow[pd];
                 c0[u] = cntrow[pd];
                 e0[u] = ((s0[u] >> 2) + (f - gpre[pd])) << 2;
@@ -306,13 +348,29 @@ __global__ void __launch_bounds__(kScatterThreads, 1) scatter_kernel(
     const uint32_t base = p * q, len = min(q, n - base);
     const uint32_t* segrow = seg_u + (size_t)p * k;
     const uint32_t* cntrow = cnt_u + (size_t)p * k;
-    // SPR of the partition, staged in shared memory.
+    // SPR of the partition, staged in shared memory (four independent 16-byte
+    // loads of each array in flight per thread).
     if ((base & 3) == 0) {
         const uint32_t v4 = len >> 2;
-        for (uint32_t i = threadIdx.x; i < v4; i += blockDim.x) {
-            const float4 x = __ldg(reinterpret_cast<const float4*>(pr + base) + i);
-            const float4 w = __ldg(reinterpret_cast<const float4*>(inv_deg + base) + i);
-            reinterpret_cast<float4*>(sspr)[i] = make_float4(x.x * w.x, x.y * w.y, x.z * w.z, x.w * w.w);
+        const float4* pr4 = reinterpret_cast<const float4*>(pr + base);
+        const float4* in4 = reinterpret_cast<const float4*>(inv_deg + base);
+        for (uint32_t i0 = threadIdx.x; i0 < v4; i0 += 4 * blockDim.x) {
+            float4 x[4], w[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t i = i0 + j * blockDim.x;
+                if (i < v4) {
+                    x[j] = __ldg(pr4 + i);
+                    w[j] = __ldg(in4 + i);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t i = i0 + j * blockDim.x;
+                if (i < v4)
+                    reinterpret_cast<float4*>(sspr)[i] =
+                        make_float4(x[j].x * w[j].x, x[j].y * w[j].y, x[j].z * w[j].z, x[j].w * w[j].w);
+            }
         }
         for (uint32_t i = (v4 << 2) + threadIdx.x; i < len; i += blockDim.x) sspr[i] = pr[base + i] * inv_deg[base + i];
     } else {
@@ -527,34 +585,75 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
         if (h0 < len) atomicAdd(&acc[h0], hub0);
         if (h1 < len) atomicAdd(&acc[h1], hub1);
     }
-    cluster_sync();
+    cluster_sync();  // every CTA of the cluster has finished its accumulator
 
-    // Apply over this CTA's 1/S of the partition (multiples of 4 nodes).
+    // This CTA owns nodes [lo, hi) of the partition (multiples of 4). The
+    // other CTAs push their partial sums for that range into this CTA's ring
+    // memory, idle now, so the merge below reads local shared memory only.
     const uint32_t per = (((len + S - 1) / S) + 3) & ~3u;
     const uint32_t lo = min(len, rank * per), hi = min(len, lo + per);
+    float* stage = reinterpret_cast<float*>(ring);
+    const bool push = (size_t)(S - 1) * per * sizeof(float) <= kRingBytes;
+    if (push && S > 1) {
+        for (uint32_t t = 0; t < S; ++t) {
+            if (t == rank) continue;
+            const uint32_t tlo = min(len, t * per), thi = min(len, tlo + per);
+            push_range(acc + tlo, stage + (size_t)(rank < t ? rank : rank - 1) * per, thi - tlo, t);
+        }
+        cluster_sync();
+    }
+    // Sum of the S partial sums of node i in [lo, hi), in a fixed order.
+    auto merged = [&](uint32_t i) -> float {
+        float s = 0.0f;
+        if (push) {
+            s = acc[i];
+            for (uint32_t q = 0; q + 1 < S; ++q) s += stage[(size_t)q * per + (i - lo)];
+        } else {
+            for (uint32_t r = 0; r < S; ++r) s += ld_cluster_f32(map_rank(acc + i, r));
+        }
+        return s;
+    };
+
     const double D = a.uniform_dangling ? a.st->dangling : 0.0;
     const float cst = (float)((1.0 - (double)a.d) / (double)a.n + (double)a.d * D / (double)a.n);
-    double res = 0.0, dg = 0.0;
+    // Per-thread partial sums of at most len / blockDim terms in FP32 (FP64
+    // arithmetic is slow on this part); thread and block totals in FP64.
+    float res_f = 0.0f, dg_f = 0.0f;
     if (npieces == 1) {
-        for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-            float s = 0.0f;
-            for (uint32_t r = 0; r < S; ++r) s += ld_cluster_f32(map_rank(acc + i, r));
-            const uint32_t v = vbase + i;
-            const float x = fmaf(a.d, s, cst);
-            const float old = a.pr_in[v];
-            const float inv = a.inv_deg[v];
-            a.pr_out[v] = x;
-            if (kFused) acc[i] = x * inv;
-            res += fabs((double)x - (double)old);
-            if (inv == 0.0f) dg += (double)x;
+        // Apply: kApplyIlp independent nodes per thread per round, their loads
+        // in flight together.
+        for (uint32_t i0 = lo + threadIdx.x; i0 < hi; i0 += kApplyIlp * blockDim.x) {
+            float s[kApplyIlp], old[kApplyIlp], inv[kApplyIlp];
+#pragma unroll
+            for (int j = 0; j < kApplyIlp; ++j) {
+                const uint32_t i = i0 + j * blockDim.x;
+                s[j] = 0.0f;
+                old[j] = 0.0f;
+                inv[j] = 1.0f;
+                if (i < hi) {
+                    old[j] = a.pr_in[vbase + i];
+                    inv[j] = a.inv_deg[vbase + i];
+                    s[j] = merged(i);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < kApplyIlp; ++j) {
+                const uint32_t i = i0 + j * blockDim.x;
+                if (i < hi) {
+                    const float x = fmaf(a.d, s[j], cst);
+                    a.pr_out[vbase + i] = x;
+                    if (kFused) acc[i] = x * inv[j];
+                    res_f += fabsf(x - old[j]);
+                    if (inv[j] == 0.0f) dg_f += x;
+                }
+            }
         }
     } else {
         // The bin is cut into several units: add this unit's sums to the
         // global partial sums; the last CTA to arrive applies the partition.
         uint32_t& last = sh32[0];
         for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-            float s = 0.0f;
-            for (uint32_t r = 0; r < S; ++r) s += ld_cluster_f32(map_rank(acc + i, r));
+            const float s = merged(i);
             if (s != 0.0f) atomicAdd(&a.gacc[vbase + i], s);
         }
         __threadfence();
@@ -563,44 +662,69 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
         __syncthreads();
         if (last) {
             __threadfence();
-            for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) {
-                const uint32_t v = vbase + i;
-                const float x = fmaf(a.d, __ldcg(&a.gacc[v]), cst);
-                a.gacc[v] = 0.0f;
-                const float old = a.pr_in[v];
-                const float inv = a.inv_deg[v];
-                a.pr_out[v] = x;
-                res += fabs((double)x - (double)old);
-                if (inv == 0.0f) dg += (double)x;
+            for (uint32_t i0 = threadIdx.x; i0 < len; i0 += kApplyIlp * blockDim.x) {
+                float s[kApplyIlp], old[kApplyIlp], inv[kApplyIlp];
+#pragma unroll
+                for (int j = 0; j < kApplyIlp; ++j) {
+                    const uint32_t i = i0 + j * blockDim.x;
+                    s[j] = 0.0f;
+                    old[j] = 0.0f;
+                    inv[j] = 1.0f;
+                    if (i < len) {
+                        s[j] = __ldcg(&a.gacc[vbase + i]);
+                        old[j] = a.pr_in[vbase + i];
+                        inv[j] = a.inv_deg[vbase + i];
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < kApplyIlp; ++j) {
+                    const uint32_t i = i0 + j * blockDim.x;
+                    if (i < len) {
+                        const float x = fmaf(a.d, s[j], cst);
+                        a.gacc[vbase + i] = 0.0f;
+                        a.pr_out[vbase + i] = x;
+                        res_f += fabsf(x - old[j]);
+                        if (inv[j] == 0.0f) dg_f += x;
+                    }
+                }
             }
             if (threadIdx.x == 0) a.bin_done[pd] = 0;
         }
     }
+    double res = (double)res_f, dg = (double)dg_f;
     block_sum2<kGatherWarps * 32>(res, dg);
     if (threadIdx.x == 0) {
         a.partials[2 * blockIdx.x] = res;
         a.partials[2 * blockIdx.x + 1] = dg;
     }
-    cluster_sync();
 
     if constexpr (kFused) {
         if (npieces != 1) {  // the host runs cut bins in two-phase form only
             if (threadIdx.x == 0) atomicOr(a.err, kErrBounds);
+            cluster_sync();
             return;
         }
-        // Fused scatter of the next iteration: gather SPR' of the whole
-        // partition into this CTA's shared memory, then write 1/S of its
-        // update segments.
-        for (uint32_t r = 0; r < S; ++r) {
-            if (r == rank) continue;
-            const uint32_t rlo = min(len, r * per), rhi = min(len, rlo + per);
-            const uint32_t q4 = (rhi - rlo) >> 2;
-            for (uint32_t i = threadIdx.x; i < q4; i += blockDim.x)
-                reinterpret_cast<float4*>(acc + rlo)[i] = ld_cluster_f32x4(map_rank(acc + rlo + 4 * i, r));
-            for (uint32_t i = rlo + (q4 << 2) + threadIdx.x; i < rhi; i += blockDim.x)
-                acc[i] = ld_cluster_f32(map_rank(acc + i, r));
+        // Fused scatter of the next iteration: assemble SPR' of the whole
+        // partition in every CTA's shared memory (each pushes its range to
+        // the others), then write 1/S of the partition's update segments.
+        __syncthreads();
+        if (push) {
+            for (uint32_t t = 0; t < S; ++t)
+                if (t != rank) push_range(acc + lo, acc + lo, hi - lo, t);
+            cluster_sync();
+        } else {
+            cluster_sync();
+            for (uint32_t r = 0; r < S; ++r) {
+                if (r == rank) continue;
+                const uint32_t rlo = min(len, r * per), rhi = min(len, rlo + per);
+                const uint32_t q4 = (rhi - rlo) >> 2;
+                for (uint32_t i = threadIdx.x; i < q4; i += blockDim.x)
+                    reinterpret_cast<float4*>(acc + rlo)[i] = ld_cluster_f32x4(map_rank(acc + rlo + 4 * i, r));
+                for (uint32_t i = rlo + (q4 << 2) + threadIdx.x; i < rhi; i += blockDim.x)
+                    acc[i] = ld_cluster_f32(map_rank(acc + i, r));
+            }
+            cluster_sync();  // no CTA reads another's shared memory after this point
         }
-        cluster_sync();  // no CTA reads another's shared memory after this point
         uint32_t* gpre = reinterpret_cast<uint32_t*>(ring);
         const uint32_t* segrow = a.seg_u + (size_t)pd * a.k;
         const uint32_t* cntrow = a.cnt_u + (size_t)pd * a.k;
@@ -609,6 +733,8 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
         const uint32_t f_lo = (uint32_t)((uint64_t)G * rank / S);
         const uint32_t f_hi = (uint32_t)((uint64_t)G * (rank + 1) / S);
         scatter_groups(acc, vbase, len, gpre, a.k, segrow, cntrow, a.src, a.upd_out, f_lo, f_hi, a.err);
+    } else {
+        if (!push) cluster_sync();  // remote loads of this CTA's shared memory are done
     }
 }
 

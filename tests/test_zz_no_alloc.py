@@ -19,7 +19,10 @@ pytestmark = pytest.mark.gpu
 
 import paper_1709_07122_gb300 as pcpm  # noqa: E402
 
-RTOL = 1e-12  # two FP64 sums of the same float terms, in different orders
+# The solver sums |x - y| per thread in FP32 over at most 64 nodes before its
+# FP64 reduction, so its total is within gamma_64 = 64 * 2^-24 (relative) of the
+# FP64 sum this entry point computes; the dangling mass likewise.
+RTOL = 64 * 2.0 ** -24
 
 
 @pytest.fixture(scope="module", autouse=True)
