@@ -97,7 +97,7 @@ typedef struct pcpm_png_info {
     uint32_t scatter_units;   /* scatter work units (source partitions, large ones cut) */
     uint32_t gather_cluster;  /* CTAs (one thread-block cluster) per gather unit */
     uint32_t fused_ok;        /* 1 if iterations can run fused (no bin was cut) */
-    uint32_t reserved2;
+    uint32_t canonical_gather; /* 1 if the gather decodes the canonical bins */
 } pcpm_png_info;
 
 /* Tuning of the work decomposition; zero fields take the automatic choice.
@@ -106,7 +106,10 @@ typedef struct pcpm_build_options {
     uint32_t gather_unit_chunks;  /* most 256-ID chunks one gather unit takes from a bin */
     uint32_t scatter_unit_groups; /* most 4-update groups one scatter unit writes */
     uint32_t gather_cluster;      /* CTAs per gather unit: 1, 2, 4 or 8 */
-    uint32_t reserved;
+    uint32_t canonical_gather;    /* 1: gather straight from the canonical bins, decoding the
+                                     message flags (Algorithm 4); 0: also build a gather copy of
+                                     the destination IDs with explicit update offsets, ordered so
+                                     concurrent shared-memory adds hit distinct banks */
 } pcpm_build_options;
 
 /* Builds the Partition-Node Graph of Sec. 3.3 from a CSR out-adjacency:

@@ -46,7 +46,8 @@ bool is_device_ptr(const void* p) {
 void release(pcpm_png* g) {
     if (!g) return;
     void* ptrs[] = {g->dest, g->src, g->bin_u, g->bin_e, g->seg_u, g->cnt_u, g->seg_e, g->cnt_e,
-                    g->chunk_base, g->hubs, g->gunits, g->gorder, g->sunits, g->sorder, g->gacc,
+                    g->chunk_base, g->hubs, g->gdest, g->gslice_start, g->gslice_bytes, g->ichunk_start,
+                    g->gunits, g->gorder, g->sunits, g->sorder, g->gacc,
                     g->bin_done, g->inv_deg, g->pr[0], g->pr[1], g->upd[0], g->upd[1], g->partials,
                     g->hist, g->state};
     for (void* p : ptrs)
@@ -270,6 +271,7 @@ int pcpm_png_get_info(const pcpm_png* g, pcpm_png_info* info) {
     info->scatter_units = g->nsunits;
     info->gather_cluster = (uint32_t)g->cluster;
     info->fused_ok = (uint32_t)g->fused_ok;
+    info->canonical_gather = (uint32_t)g->canonical_gather;
     return PCPM_OK;
 }
 

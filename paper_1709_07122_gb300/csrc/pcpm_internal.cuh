@@ -76,6 +76,18 @@ struct pcpm_png {
     uint32_t* cnt_e;         // k*k edges p -> p'
     uint32_t* chunk_base;    // nchunks+1: flagged IDs before each chunk
     uint32_t* hubs;          // 2k: per bin, local IDs of its two largest in-degrees (or kNoHub)
+    // Bank-spread gather layout (unless the canonical bins are gathered
+    // directly): every bin padded to whole kChunk-ID chunks; each chunk's IDs
+    // permuted so that the IDs one warp adds at once fall in distinct
+    // shared-memory banks as far as possible, each word holding the local
+    // destination (15 bits), the offset of its update in the chunk's update
+    // slice (9 bits) and bit 31 for padding.
+    int canonical_gather;    // 1: the gather decodes the canonical bins (MSB flags)
+    uint32_t* gdest;         // nichunks * kChunk words
+    uint32_t* gslice_start;  // nichunks: first update of the chunk's slice (multiple of 4)
+    uint32_t* gslice_bytes;  // nichunks: bytes of the slice (multiple of 16)
+    uint32_t* ichunk_start;  // k+1: first chunk of each bin in gdest
+    uint64_t nichunks;
     // Work units. A gather unit is a run of chunks of one bin (uint4: bin,
     // first chunk, end chunk, pieces of that bin); a scatter unit is a range of
     // 4-entry groups of one source partition (partition, first group, end

@@ -386,6 +386,9 @@ struct GatherArgs {
     const uint32_t* dest;
     const uint32_t* bin_e;
     const uint32_t* chunk_base;
+    const uint32_t* gdest;
+    const uint32_t* slice_start;
+    const uint32_t* slice_bytes;
     const uint4* units;
     const uint32_t* order;
     const uint32_t* hubs;
@@ -417,7 +420,7 @@ constexpr size_t kAccOffset = kRingBytes + kBarBytes + kMetaBytes;
 static_assert(kStageBytes % 16 == 0, "ring slots must stay 16-byte aligned");
 static_assert(kAccOffset % 16 == 0, "accumulator must be 16-byte aligned");
 
-template <bool kFused>
+template <bool kFused, bool kCanon>
 __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const GatherArgs a) {
     if (a.st->stop) return;
     extern __shared__ __align__(128) unsigned char smraw[];
@@ -453,35 +456,57 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
         uint32_t* wmeta = meta + warp * kGatherStages * 2;
         const uint32_t lt = lanemask_lt();
 
-        // Chunk bases of this warp's run, 32 per register table, two tables ahead.
-        auto load_table = [&](uint32_t t) -> uint32_t {
+        // Per-chunk values of this warp's run, 32 per register table, loaded
+        // two tables ahead: the canonical layout's update bases (entry j+1
+        // bounds chunk j's slice), or the bank-spread layout's slice start and
+        // size.
+        auto load_a = [&](uint32_t t) -> uint32_t {
             const uint32_t j = 32 * t + lane;
-            return j <= nmine ? a.chunk_base[wc0 + j] : 0u;
+            if constexpr (kCanon) return j <= nmine ? a.chunk_base[wc0 + j] : 0u;
+            else return j < nmine ? a.slice_start[wc0 + j] : 0u;
         };
-        uint32_t tb = 0, t0 = load_table(0), t1 = load_table(1), t2 = load_table(2);
-        auto cb_of = [&](uint32_t j) -> uint32_t {  // warp-collective, j in [32 tb, 32 tb + 64)
-            const uint32_t x0 = __shfl_sync(kFull, t0, j & 31);
-            const uint32_t x1 = __shfl_sync(kFull, t1, j & 31);
-            return (j >> 5) == tb ? x0 : x1;
+        auto load_b = [&](uint32_t t) -> uint32_t {
+            const uint32_t j = 32 * t + lane;
+            if constexpr (kCanon) return 0u;
+            else return j < nmine ? a.slice_bytes[wc0 + j] : 0u;
+        };
+        uint32_t tb = 0, t0 = load_a(0), t1 = load_a(1), t2 = load_a(2);
+        uint32_t s0 = load_b(0), s1 = load_b(1), s2 = load_b(2);
+        auto pick = [&](uint32_t x0, uint32_t x1, uint32_t j) -> uint32_t {  // warp-collective
+            const uint32_t y0 = __shfl_sync(kFull, x0, j & 31);
+            const uint32_t y1 = __shfl_sync(kFull, x1, j & 31);
+            return (j >> 5) == tb ? y0 : y1;
         };
         auto issue = [&](uint32_t j) {  // warp-collective
             if (((j + 1) >> 5) > tb + 1) {
                 ++tb;
                 t0 = t1;
                 t1 = t2;
-                t2 = load_table(tb + 2);
+                t2 = load_a(tb + 2);
+                s0 = s1;
+                s1 = s2;
+                s2 = load_b(tb + 2);
             }
-            const uint32_t cb0 = cb_of(j), cb1 = cb_of(j + 1);
+            uint32_t us, ubytes, fb = 0;
+            if constexpr (kCanon) {
+                const uint32_t cb0 = pick(t0, t1, j), cb1 = pick(t0, t1, j + 1);
+                us = (cb0 > 0 ? cb0 - 1 : 0) & ~3u;
+                ubytes = (((cb1 + 3) & ~3u) - us) * (uint32_t)sizeof(float);
+                fb = cb0;
+            } else {
+                us = pick(t0, t1, j);
+                ubytes = pick(s0, s1, j);
+            }
             if (lane == 0) {
                 const uint32_t slot = j % kGatherStages;
-                const uint32_t us = (cb0 > 0 ? cb0 - 1 : 0) & ~3u;
-                const uint32_t ue = (cb1 + 3) & ~3u;
-                const uint32_t ubytes = (ue - us) * (uint32_t)sizeof(float);
-                wmeta[2 * slot] = cb0;
-                wmeta[2 * slot + 1] = us;
                 unsigned char* dst = wring + (size_t)slot * kStageBytes;
+                if constexpr (kCanon) {
+                    wmeta[2 * slot] = fb;
+                    wmeta[2 * slot + 1] = us;
+                }
+                const uint32_t* ids = (kCanon ? a.dest : a.gdest) + (size_t)(wc0 + j) * kChunk;
                 mbar_arrive_expect_tx(&wbar[slot], kIdSlotBytes + ubytes);
-                bulk_load(dst, a.dest + (size_t)(wc0 + j) * kChunk, kIdSlotBytes, &wbar[slot]);
+                bulk_load(dst, ids, kIdSlotBytes, &wbar[slot]);
                 if (ubytes) bulk_load(dst + kIdSlotBytes, a.upd_in + us, ubytes, &wbar[slot]);
             }
         };
@@ -498,16 +523,10 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
             const unsigned char* stage = wring + (size_t)slot * kStageBytes;
             const uint32_t* ids_s = reinterpret_cast<const uint32_t*>(stage);
             const float* ups = reinterpret_cast<const float*>(stage + kIdSlotBytes);
-            uint32_t fbase = wmeta[2 * slot];
-            const uint32_t us = wmeta[2 * slot + 1];
-            const uint32_t cstart = (wc0 + j) * kChunk;
-            // Only a bin's first and last chunk hold IDs of other bins.
-            const bool interior = cstart >= E0 && cstart + kChunk <= E1;
-            // All loads of the chunk first (IDs, then update values), then the
-            // adds, so each lane has eight independent shared-memory operations
-            // in flight instead of a chain per ID.
             constexpr int kPer = kChunk / 32;  // IDs per lane
-            uint32_t id[kPer], uo[kPer];
+            // All loads of the chunk first (IDs, then update values), then the
+            // adds: eight independent shared-memory operations per lane.
+            uint32_t id[kPer], uo[kPer], valid = 0;
 #pragma unroll
             for (int h = 0; h < kPer / 4; ++h) {
                 const uint4 v4 = *reinterpret_cast<const uint4*>(ids_s + h * 128 + lane * 4);
@@ -516,48 +535,65 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
                 id[4 * h + 2] = v4.z;
                 id[4 * h + 3] = v4.w;
             }
+            if constexpr (kCanon) {
+                // Algorithm 4's update pointer as warp arithmetic: the update
+                // of an ID is the inclusive count of flagged IDs up to it - 1.
+                uint32_t fbase = wmeta[2 * slot];
+                const uint32_t us = wmeta[2 * slot + 1];
+                const uint32_t cstart = (wc0 + j) * kChunk;
 #pragma unroll
-            for (int h = 0; h < kPer / 4; ++h) {
-                uint32_t f[4], b[4], before = 0, total = 0;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    f[q] = id[4 * h + q] >> 31;
-                    b[q] = __ballot_sync(kFull, f[q]);
-                    before += __popc(b[q] & lt);
-                    total += __popc(b[q]);
-                }
-                // update index (relative to the slot): inclusive flag count - 1
-                uint32_t u = fbase + before - 1 - us;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    u += f[q];
-                    uo[4 * h + q] = u;
-                }
-                fbase += total;
-            }
-            uint32_t valid = (1u << kPer) - 1u;
-            if (!interior) {
-                valid = 0;
-#pragma unroll
-                for (int h = 0; h < kPer / 4; ++h)
+                for (int h = 0; h < kPer / 4; ++h) {
+                    uint32_t f[4], b[4], before = 0, total = 0;
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const uint32_t pos = cstart + h * 128 + lane * 4 + q;
-                        valid |= (pos >= E0 && pos < E1) ? 1u << (4 * h + q) : 0u;
+                        f[q] = id[4 * h + q] >> 31;
+                        b[q] = __ballot_sync(kFull, f[q]);
+                        before += __popc(b[q] & lt);
+                        total += __popc(b[q]);
                     }
+                    uint32_t u = fbase + before - 1 - us;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        u += f[q];
+                        uo[4 * h + q] = u;
+                        id[4 * h + q] = (id[4 * h + q] & kIdMask) - vbase;
+                    }
+                    fbase += total;
+                }
+                // Only a bin's first and last chunk hold IDs of other bins.
+                if (cstart >= E0 && cstart + kChunk <= E1) {
+                    valid = (1u << kPer) - 1u;
+                } else {
+#pragma unroll
+                    for (int h = 0; h < kPer / 4; ++h)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const uint32_t pos = cstart + h * 128 + lane * 4 + q;
+                            valid |= (pos >= E0 && pos < E1) ? 1u << (4 * h + q) : 0u;
+                        }
+                }
+            } else {
+                // Bank-spread layout: local destination and update offset are
+                // stored in the word; bit 31 marks padding.
+#pragma unroll
+                for (int q = 0; q < kPer; ++q) {
+                    valid |= (id[q] >> 31) ? 0u : 1u << q;
+                    uo[q] = (id[q] >> 15) & 0x1FFu;
+                    id[q] &= 0x7FFFu;
+                }
             }
             float val[kPer];
 #pragma unroll
-            for (int j = 0; j < kPer; ++j) val[j] = ups[(valid >> j & 1u) ? uo[j] : 0u];
+            for (int q = 0; q < kPer; ++q) val[q] = ups[(valid >> q & 1u) ? uo[q] : 0u];
 #pragma unroll
-            for (int j = 0; j < kPer; ++j) {
-                const uint32_t loc = (id[j] & kIdMask) - vbase;
-                const bool ok_j = (valid >> j & 1u) != 0;
-                const bool is0 = ok_j && loc == h0, is1 = ok_j && loc == h1;
-                hub0 += is0 ? val[j] : 0.0f;
-                hub1 += is1 ? val[j] : 0.0f;
-                if (ok_j && !is0 && !is1) {
-                    if (loc < len) atomicAdd(&acc[loc], val[j]);
+            for (int q = 0; q < kPer; ++q) {
+                const uint32_t loc = id[q];
+                const bool ok_q = (valid >> q & 1u) != 0;
+                const bool is0 = ok_q && loc == h0, is1 = ok_q && loc == h1;
+                hub0 += is0 ? val[q] : 0.0f;
+                hub1 += is1 ? val[q] : 0.0f;
+                if (ok_q && !is0 && !is1) {
+                    if (loc < len) atomicAdd(&acc[loc], val[q]);
                     else atomicOr(a.err, kErrBounds);
                 }
             }
@@ -776,8 +812,14 @@ size_t partial_slots(const pcpm_png* g) {
 // Picks the cluster size for the gather and sets shared-memory limits.
 int configure_kernels(pcpm_png* g) {
     const size_t gs = gather_smem_bytes(g->q), ss = scatter_smem_bytes(g->q, g->k);
-    if (cudaFuncSetAttribute(gather_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gs) != cudaSuccess ||
-        cudaFuncSetAttribute(gather_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gs) != cudaSuccess ||
+    if (cudaFuncSetAttribute(gather_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gs) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(gather_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gs) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(gather_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gs) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(gather_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gs) !=
+            cudaSuccess ||
         cudaFuncSetAttribute(scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss) != cudaSuccess)
         return PCPM_ECUDA;
     // Two CTAs per gather unit unless the build options ask otherwise (two
@@ -797,7 +839,8 @@ int configure_kernels(pcpm_png* g) {
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int clusters = 0;
-        if (cudaOccupancyMaxActiveClusters(&clusters, gather_kernel<true>, &cfg) == cudaSuccess && clusters > 0) {
+        if (cudaOccupancyMaxActiveClusters(&clusters, gather_kernel<true, false>, &cfg) == cudaSuccess &&
+            clusters > 0) {
             g->cluster = S;
             return PCPM_OK;
         }
@@ -834,6 +877,9 @@ int launch_gather(pcpm_png* g, float d, uint32_t flags, bool fused, cudaStream_t
     a.dest = g->dest;
     a.bin_e = g->bin_e;
     a.chunk_base = g->chunk_base;
+    a.gdest = g->gdest;
+    a.slice_start = g->gslice_start;
+    a.slice_bytes = g->gslice_bytes;
     a.units = g->gunits;
     a.order = g->gorder;
     a.hubs = g->hubs;
@@ -865,8 +911,13 @@ int launch_gather(pcpm_png* g, float d, uint32_t flags, bool fused, cudaStream_t
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    const cudaError_t e = fused ? cudaLaunchKernelEx(&cfg, gather_kernel<true>, a)
-                                : cudaLaunchKernelEx(&cfg, gather_kernel<false>, a);
+    cudaError_t e;
+    if (g->canonical_gather)
+        e = fused ? cudaLaunchKernelEx(&cfg, gather_kernel<true, true>, a)
+                  : cudaLaunchKernelEx(&cfg, gather_kernel<false, true>, a);
+    else
+        e = fused ? cudaLaunchKernelEx(&cfg, gather_kernel<true, false>, a)
+                  : cudaLaunchKernelEx(&cfg, gather_kernel<false, false>, a);
     g->partial_count = (int)(g->ngunits * g->cluster);
     return e == cudaSuccess ? PCPM_OK : PCPM_ECUDA;
 }

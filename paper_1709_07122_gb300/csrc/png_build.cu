@@ -422,29 +422,141 @@ __global__ void order_kernel(const uint32_t* __restrict__ size, uint32_t k, uint
 }
 
 // ------------------------------------------------------------ work units
+// Chunks of bin p: [first, first + count). Canonical layout: the globally
+// aligned kChunk-entry chunks the bin overlaps; bank-spread layout: the bin's
+// own padded chunks.
+__device__ __forceinline__ void bin_chunks(const uint32_t* bin_e, const uint32_t* ichunk_start, uint32_t p,
+                                           uint32_t& first, uint32_t& count) {
+    if (ichunk_start) {
+        first = ichunk_start[p];
+        count = ichunk_start[p + 1] - first;
+    } else {
+        const uint32_t e0 = bin_e[p], e1 = bin_e[p + 1];
+        first = e0 / kChunk;
+        count = e1 > e0 ? (e1 - 1) / kChunk - first + 1 : 0;
+    }
+}
+
 // pieces[p] = units of bin p: its chunks cut into runs of at most `per`
 // (an empty bin still gets one unit for its apply).
-__global__ void gather_pieces_kernel(const uint32_t* __restrict__ bin_e, uint32_t k, uint32_t per,
-                                     uint32_t* __restrict__ pieces) {
+__global__ void gather_pieces_kernel(const uint32_t* __restrict__ bin_e, const uint32_t* __restrict__ ichunk_start,
+                                     uint32_t k, uint32_t per, uint32_t* __restrict__ pieces) {
     for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < k; p += gridDim.x * blockDim.x) {
-        const uint32_t e0 = bin_e[p], e1 = bin_e[p + 1];
-        const uint32_t nch = e1 > e0 ? (e1 - 1) / kChunk - e0 / kChunk + 1 : 0;
+        uint32_t first, nch;
+        bin_chunks(bin_e, ichunk_start, p, first, nch);
         pieces[p] = nch ? (nch + per - 1) / per : 1;
     }
 }
 
-__global__ void gather_units_kernel(const uint32_t* __restrict__ bin_e, const uint32_t* __restrict__ start,
-                                    uint32_t k, uint32_t per, uint32_t nunits, uint4* __restrict__ units,
-                                    uint32_t* __restrict__ sizes) {
+__global__ void gather_units_kernel(const uint32_t* __restrict__ bin_e, const uint32_t* __restrict__ ichunk_start,
+                                    const uint32_t* __restrict__ start, uint32_t k, uint32_t per, uint32_t nunits,
+                                    uint4* __restrict__ units, uint32_t* __restrict__ sizes) {
     for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < nunits; u += gridDim.x * blockDim.x) {
         const uint32_t p = upper_bound_u32(start, 0, k + 1, u) - 1;
-        const uint32_t e0 = bin_e[p], e1 = bin_e[p + 1];
-        const uint32_t c0 = e0 / kChunk;
-        const uint32_t nch = e1 > e0 ? (e1 - 1) / kChunk - c0 + 1 : 0;
+        uint32_t c0, nch;
+        bin_chunks(bin_e, ichunk_start, p, c0, nch);
         const uint32_t idx = u - start[p];
         const uint32_t lo = c0 + min(nch, idx * per), hi = c0 + min(nch, (idx + 1) * per);
         units[u] = make_uint4(p, lo, hi, start[p + 1] - start[p]);
         sizes[u] = hi - lo;
+    }
+}
+
+// ------------------------------------------------- bank-spread gather layout
+__global__ void bin_chunk_counts_kernel(const uint32_t* __restrict__ bin_e, uint32_t k, uint32_t* __restrict__ cnt) {
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < k; p += gridDim.x * blockDim.x)
+        cnt[p] = (bin_e[p + 1] - bin_e[p] + kChunk - 1) / kChunk;
+}
+
+constexpr int kLayoutWarps = 8;
+constexpr uint32_t kKeyHub = 32, kKeyPad = 33, kNumKeys = 34;
+
+// One warp per padded chunk: the update index of every ID (flags before the
+// chunk plus the inclusive count inside it, minus one), then a stable counting
+// sort of the chunk's IDs by shared-memory bank of their destination (hub
+// destinations, which the gather sums in registers, and padding sort last).
+// Sorted position s goes to round s % 8 and lane s / 8 of the gather's
+// 8-round, 32-lane pass over the chunk, so the 32 adds of a round come from 32
+// consecutive sorted IDs: distinct banks unless a bank holds more than eight
+// of the chunk's IDs.
+__global__ void __launch_bounds__(kLayoutWarps * 32) gather_layout_kernel(
+    const uint32_t* __restrict__ dest, const uint32_t* __restrict__ bin_e, const uint32_t* __restrict__ ichunk_start,
+    uint32_t k, const uint32_t* __restrict__ chunk_base, const uint32_t* __restrict__ hubs, uint32_t q,
+    uint64_t nichunks, uint32_t* __restrict__ gdest, uint32_t* __restrict__ slice_start,
+    uint32_t* __restrict__ slice_bytes) {
+    __shared__ uint32_t keycnt[kLayoutWarps][kNumKeys + 2];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = lanemask_lt();
+    uint32_t* cnt = keycnt[warp];
+    for (uint64_t ic = blockIdx.x * (uint64_t)kLayoutWarps + warp; ic < nichunks;
+         ic += (uint64_t)gridDim.x * kLayoutWarps) {
+        const uint32_t p = upper_bound_u32(ichunk_start, 0, k + 1, (uint32_t)ic) - 1;
+        const uint32_t P = bin_e[p] + ((uint32_t)ic - ichunk_start[p]) * kChunk;
+        const uint32_t Pend = min(P + kChunk, bin_e[p + 1]);
+        const uint32_t vbase = p * q, h0 = hubs[2 * p], h1 = hubs[2 * p + 1];
+        // flagged IDs before P
+        const uint32_t cbase = P & ~(kChunk - 1);
+        uint32_t running = chunk_base[P / kChunk];
+        for (uint32_t x = cbase; x < P; x += 32) {
+            const uint32_t pos = x + lane;
+            running += __popc(__ballot_sync(0xffffffffu, pos < P && (dest[pos] >> 31)));
+        }
+        uint32_t idx[kChunk / 32], loc[kChunk / 32], key[kChunk / 32];
+#pragma unroll
+        for (int r = 0; r < (int)(kChunk / 32); ++r) {
+            const uint32_t pos = P + 32 * r + lane;
+            const bool valid = pos < Pend;
+            const uint32_t w = valid ? dest[pos] : 0u;
+            const uint32_t b = __ballot_sync(0xffffffffu, valid && (w >> 31));
+            idx[r] = running + __popc(b & (lt | (1u << lane))) - 1;
+            running += __popc(b);
+            loc[r] = (w & kIdMask) - vbase;
+            key[r] = !valid ? kKeyPad : (loc[r] == h0 || loc[r] == h1) ? kKeyHub : (loc[r] & 31u);
+        }
+        const uint32_t n = Pend - P;
+        const uint32_t u_first = __shfl_sync(0xffffffffu, idx[0], 0);
+        uint32_t u_last = 0;
+#pragma unroll
+        for (int r = 0; r < (int)(kChunk / 32); ++r) {
+            const uint32_t x = __shfl_sync(0xffffffffu, idx[r], (n - 1) & 31);
+            if ((uint32_t)r == (n - 1) / 32) u_last = x;
+        }
+        const uint32_t us = u_first & ~3u, ue = (u_last + 4) & ~3u;
+        // counting sort by key, stable in (round, lane) order
+        for (uint32_t j = lane; j < kNumKeys; j += 32) cnt[j] = 0;
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < (int)(kChunk / 32); ++r) {
+            const uint32_t peers = __match_any_sync(0xffffffffu, key[r]);
+            if (lane == (uint32_t)(__ffs(peers) - 1)) cnt[key[r]] += __popc(peers);
+            __syncwarp();
+        }
+        if (lane == 0) {
+            uint32_t run = 0;
+            for (uint32_t j = 0; j < kNumKeys; ++j) {
+                const uint32_t c = cnt[j];
+                cnt[j] = run;
+                run += c;
+            }
+        }
+        __syncwarp();
+        uint32_t* out = gdest + ic * kChunk;
+#pragma unroll
+        for (int r = 0; r < (int)(kChunk / 32); ++r) {
+            const uint32_t peers = __match_any_sync(0xffffffffu, key[r]);
+            const uint32_t s = cnt[key[r]] + __popc(peers & lt);
+            __syncwarp();
+            if (lane == (uint32_t)(__ffs(peers) - 1)) cnt[key[r]] += __popc(peers);
+            __syncwarp();
+            const uint32_t round = s & 7u, slot_lane = s >> 3;
+            const uint32_t word = 128 * (round >> 2) + 4 * slot_lane + (round & 3u);
+            out[word] = key[r] == kKeyPad ? 0x80000000u : (loc[r] | ((idx[r] - us) << 15));
+        }
+        if (lane == 0) {
+            slice_start[ic] = us;
+            slice_bytes[ic] = (ue - us) * (uint32_t)sizeof(float);
+        }
+        __syncwarp();
     }
 }
 
@@ -534,6 +646,7 @@ int read_err(int* d_err, cudaStream_t s, int* h_err) {
 int build_png(pcpm_png* g, const uint32_t* row_ptr, const uint32_t* col, const pcpm_build_options& opt,
               cudaStream_t s) {
     const uint32_t n = g->n, q = g->q, k = g->k;
+    g->canonical_gather = opt.canonical_gather ? 1 : 0;
     const uint64_t m = g->m;
     TempBufs tmp;
     int* d_err = nullptr;
@@ -651,10 +764,36 @@ int build_png(pcpm_png* g, const uint32_t* row_ptr, const uint32_t* col, const p
     BCK(tmp.alloc(&start, k + 1));
     BCK(tmp.alloc(&groups, k));
     BCK(tmp.alloc(&gstart, k + 1));
+    // Bank-spread gather layout.
+    const uint32_t* ichunks = nullptr;
+    uint64_t gchunks = g->nchunks;
+    if (!g->canonical_gather) {
+        uint32_t* cc = nullptr;
+        BCK(tmp.alloc(&cc, k));
+        BCK(dev_alloc(g, (void**)&g->ichunk_start, (k + 1) * sizeof(uint32_t)));
+        bin_chunk_counts_kernel<<<grid_for(k, 256, 64), 256, 0, s>>>(g->bin_e, k, cc);
+        if ((rc = scan_exclusive(cc, g->ichunk_start, k, tmp, s)) != PCPM_OK) return rc;
+        uint32_t nic = 0;
+        BCK(cudaMemcpyAsync(&nic, g->ichunk_start + k, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        BCK(cudaStreamSynchronize(s));
+        g->nichunks = nic;
+        BCK(dev_alloc(g, (void**)&g->gdest, std::max<uint64_t>(nic, 1) * kChunk * sizeof(uint32_t)));
+        BCK(dev_alloc(g, (void**)&g->gslice_start, std::max<uint64_t>(nic, 1) * sizeof(uint32_t)));
+        BCK(dev_alloc(g, (void**)&g->gslice_bytes, std::max<uint64_t>(nic, 1) * sizeof(uint32_t)));
+        if (nic) {
+            gather_layout_kernel<<<grid_for((uint64_t)nic * 32, kLayoutWarps * 32, sms * 8), kLayoutWarps * 32, 0, s>>>(
+                g->dest, g->bin_e, g->ichunk_start, k, g->chunk_base, g->hubs, q, nic, g->gdest, g->gslice_start,
+                g->gslice_bytes);
+            BCK(cudaGetLastError());
+        }
+        ichunks = g->ichunk_start;
+        gchunks = nic;
+    }
+
     const uint32_t gper = opt.gather_unit_chunks ? opt.gather_unit_chunks
                                                  : (uint32_t)std::max<uint64_t>((q + 63) / 64,
-                                                                                (g->nchunks + 2 * sms - 1) / (2 * sms));
-    gather_pieces_kernel<<<grid_for(k, 256, 64), 256, 0, s>>>(g->bin_e, k, gper, pieces);
+                                                                                (gchunks + 2 * sms - 1) / (2 * sms));
+    gather_pieces_kernel<<<grid_for(k, 256, 64), 256, 0, s>>>(g->bin_e, ichunks, k, gper, pieces);
     if ((rc = scan_exclusive(pieces, start, k, tmp, s)) != PCPM_OK) return rc;
     src_groups_kernel<<<k, 256, 0, s>>>(g->seg_u, g->cnt_u, k, groups);
     if ((rc = scan_exclusive(groups, gstart, k, tmp, s)) != PCPM_OK) return rc;
@@ -667,8 +806,8 @@ int build_png(pcpm_png* g, const uint32_t* row_ptr, const uint32_t* col, const p
     BCK(tmp.alloc(&sizes, std::max<uint32_t>(g->ngunits, k) + 1));
     BCK(dev_alloc(g, (void**)&g->gunits, (size_t)g->ngunits * sizeof(uint4)));
     BCK(dev_alloc(g, (void**)&g->gorder, (size_t)g->ngunits * sizeof(uint32_t)));
-    gather_units_kernel<<<grid_for(g->ngunits, 256, 1024), 256, 0, s>>>(g->bin_e, start, k, gper, g->ngunits,
-                                                                        g->gunits, sizes);
+    gather_units_kernel<<<grid_for(g->ngunits, 256, 1024), 256, 0, s>>>(g->bin_e, ichunks, start, k, gper,
+                                                                        g->ngunits, g->gunits, sizes);
     order_kernel<<<grid_for(g->ngunits, 128, 1024), 128, 0, s>>>(sizes, g->ngunits, g->gorder);
     BCK(cudaGetLastError());
     const uint32_t sper = opt.scatter_unit_groups

@@ -107,17 +107,18 @@ def test_scatter_bit_exact(name):
         np.testing.assert_allclose(st["dangling"], x0.cpu().numpy().astype(np.float64)[deg == 0].sum(), rtol=1e-12)
 
 
+@pytest.mark.parametrize("canonical", [0, 1])
 @pytest.mark.parametrize("mode", ["fused", "two_phase"])
 @pytest.mark.parametrize("dangling", ["uniform", "leak"])
 @pytest.mark.parametrize("start", ["uniform", "random"])
-def test_iterations_rmat16_l1_every_iteration(dangling, start, mode):
+def test_iterations_rmat16_l1_every_iteration(dangling, start, mode, canonical):
     # RMAT scale 16, edge factor 16, q = 16384, d = 0.85, 20 iterations.
     (rp, col), q = GRAPHS["rmat16_q16384"]()
     n = rp.size - 1
     x0 = None if start == "uniform" else graphgen.random_rank_vector(n, seed=33)
     ref = oracle.pagerank(rp, col, 0.85, iters=20, x0=x0, dangling=dangling, history=True)
     x0_t = None if x0 is None else torch.from_numpy(x0.astype(np.float32)).cuda()
-    with pcpm.PNG.from_host(rp, col, q) as g:
+    with pcpm.PNG.from_host(rp, col, q, canonical_gather=canonical) as g:
         g.reset(x0_t)
         errs = []
         for i in range(1, 21):
@@ -260,6 +261,9 @@ DECOMPOSITIONS = [
     dict(gather_unit_chunks=1 << 30, gather_cluster=8),
     dict(scatter_unit_groups=1),                        # every 4-update group its own unit
     dict(scatter_unit_groups=7, gather_unit_chunks=5, gather_cluster=2),
+    dict(canonical_gather=1),                           # decode the canonical bins' flags
+    dict(canonical_gather=1, gather_unit_chunks=1 << 30),
+    dict(canonical_gather=1, gather_unit_chunks=2, gather_cluster=1),
 ]
 
 
@@ -277,13 +281,14 @@ def test_work_decompositions_match_oracle(name, opts, mode):
         k = info["num_partitions"]
         assert info["gather_units"] >= k and info["scatter_units"] >= k
         assert info["fused_ok"] == (info["gather_units"] == k)
+        assert info["canonical_gather"] == opts.get("canonical_gather", 0)
         if opts.get("gather_unit_chunks") == 1 << 30:
             assert info["gather_units"] == k
         g.reset()
         for i in range(1, 7):
             g.iterate(0.85, 1, mode=mode)
             assert l1(g.ranks().cpu().numpy(), ref[i]) <= L1_TOL, i
-    if opts == DECOMPOSITIONS[2]:
+    if opts in (DECOMPOSITIONS[2], DECOMPOSITIONS[7]):
         with pcpm.PNG.from_host(rp, col, q, **opts) as g:
             assert_png_matches(g.export(), oracle.png(rp, col, q))
 
