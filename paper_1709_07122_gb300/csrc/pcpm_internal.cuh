@@ -27,8 +27,8 @@ constexpr uint32_t kChunk = 256;
 // continue the previous message), widened to 16-byte boundaries.
 constexpr uint32_t kUpdSlot = kChunk + 8;
 // Gather: warps per CTA and pipeline depth of each warp's private ring.
-constexpr int kGatherWarps = 16;
-constexpr int kGatherStages = 3;
+constexpr int kGatherWarps = 24;
+constexpr int kGatherStages = 2;
 // Scatter: threads per CTA and 4-entry groups in flight per thread.
 constexpr int kScatterThreads = 1024;
 constexpr int kScatterUnroll = 4;

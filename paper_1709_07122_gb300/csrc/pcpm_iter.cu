@@ -72,6 +72,39 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
         : "memory");
 }
 
+// L2 eviction-priority policies for bulk copies.
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+// Bulk copy as above with an L2 eviction policy (streamed data: evict first).
+__device__ __forceinline__ void bulk_load_hint(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                               uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::
+            "r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(policy)
+        : "memory");
+}
+
+// Prefetch [p, p + n floats) into L2 (whole 16-byte blocks inside the range).
+__device__ __forceinline__ void prefetch_l2(const float* p, uint32_t n, uint64_t policy) {
+    const uintptr_t a = ((uintptr_t)p + 15) & ~(uintptr_t)15;
+    const uintptr_t e = (uintptr_t)(p + n) & ~(uintptr_t)15;
+    if (e > a)
+        asm volatile("cp.async.bulk.prefetch.L2.global.L2::cache_hint [%0], %1, %2;" ::"l"(a), "r"((uint32_t)(e - a)),
+                     "l"(policy)
+                     : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -442,6 +475,15 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
     fence_mbar_init();
     __syncthreads();
 
+    // The apply at the end of the unit reads PR_old and 1/outdeg of this CTA's
+    // share of the partition: have them in L2 by then.
+    if (threadIdx.x == 0 && npieces == 1) {
+        const uint32_t per0 = (((len + S - 1) / S) + 3) & ~3u;
+        const uint32_t lo0 = min(len, rank * per0), hi0 = min(len, lo0 + per0);
+        const uint64_t keep = policy_evict_last();
+        prefetch_l2(a.pr_in + vbase + lo0, hi0 - lo0, keep);
+        prefetch_l2(a.inv_deg + vbase + lo0, hi0 - lo0, keep);
+    }
     const uint32_t h0 = a.hubs[2 * pd], h1 = a.hubs[2 * pd + 1];
     float hub0 = 0.0f, hub1 = 0.0f;
     const uint32_t E0 = a.bin_e[pd], E1 = a.bin_e[pd + 1];
@@ -455,6 +497,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
         uint64_t* wbar = bars + warp * kGatherStages;
         uint32_t* wmeta = meta + warp * kGatherStages * 2;
         const uint32_t lt = lanemask_lt();
+        const uint64_t stream_policy = policy_evict_first();  // each chunk is read once
 
         // Per-chunk values of this warp's run, 32 per register table, loaded
         // two tables ahead: the canonical layout's update bases (entry j+1
@@ -506,8 +549,8 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
                 }
                 const uint32_t* ids = (kCanon ? a.dest : a.gdest) + (size_t)(wc0 + j) * kChunk;
                 mbar_arrive_expect_tx(&wbar[slot], kIdSlotBytes + ubytes);
-                bulk_load(dst, ids, kIdSlotBytes, &wbar[slot]);
-                if (ubytes) bulk_load(dst + kIdSlotBytes, a.upd_in + us, ubytes, &wbar[slot]);
+                bulk_load_hint(dst, ids, kIdSlotBytes, &wbar[slot], stream_policy);
+                if (ubytes) bulk_load_hint(dst + kIdSlotBytes, a.upd_in + us, ubytes, &wbar[slot], stream_policy);
             }
         };
 
