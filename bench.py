@@ -340,6 +340,8 @@ def run_ours(a):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": wl, "n": n, "m": m, "part_size": a.part_size, "k": info["num_partitions"],
                    "num_updates": info["num_updates"], "r": info["compression_ratio"], "d": a.d,
+                   "gather_units": info["gather_units"], "gather_cluster": info["gather_cluster"],
+                   "gather_runs": info["gather_runs"], "merged_adds": info["merged_adds"],
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "no flush: each iteration moves ~%.2f GB, > 129 MB L2" % (iter_bytes / 1e9)},
         "roofline": roofline,

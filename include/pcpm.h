@@ -98,6 +98,10 @@ typedef struct pcpm_png_info {
     uint32_t gather_cluster;  /* CTAs (one thread-block cluster) per gather unit */
     uint32_t fused_ok;        /* 1 if iterations can run fused (no bin was cut) */
     uint32_t canonical_gather; /* 1 if the gather decodes the canonical bins */
+    uint32_t gather_runs;     /* 1 if the gather sums runs of IDs with the same destination in a
+                                 register before one shared-memory add */
+    uint64_t merged_adds;     /* IDs of the bank-spread layout whose value joins the next ID's
+                                 (same destination, same lane): adds saved by gather_runs */
 } pcpm_png_info;
 
 /* Tuning of the work decomposition; zero fields take the automatic choice.
@@ -110,6 +114,9 @@ typedef struct pcpm_build_options {
                                      message flags (Algorithm 4); 0: also build a gather copy of
                                      the destination IDs with explicit update offsets, ordered so
                                      concurrent shared-memory adds hit distinct banks */
+    uint32_t gather_runs;         /* bank-spread layout only: 1 sums runs of equal destinations in a
+                                     register before one shared-memory add, 2 adds every ID, 0 picks
+                                     1 when at least m/16 IDs join a run */
 } pcpm_build_options;
 
 /* Builds the Partition-Node Graph of Sec. 3.3 from a CSR out-adjacency:
@@ -138,7 +145,7 @@ int pcpm_build(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t n, uin
                uint32_t part_size, void* stream, pcpm_png** out);
 
 /* pcpm_build with tuning options (host struct, nullable = all automatic).
- * PCPM_EINVAL if gather_cluster is not 0, 1, 2, 4 or 8. */
+ * PCPM_EINVAL if gather_cluster is not 0, 1, 2, 4 or 8, or gather_runs is above 2. */
 int pcpm_build_ex(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t n, uint64_t m,
                   uint32_t part_size, const pcpm_build_options* options, void* stream,
                   pcpm_png** out);

@@ -43,12 +43,14 @@ class _Info(ctypes.Structure):
                 ("compression_ratio", ctypes.c_double), ("device_bytes", ctypes.c_uint64),
                 ("iterations_done", ctypes.c_int32), ("gather_units", ctypes.c_uint32),
                 ("scatter_units", ctypes.c_uint32), ("gather_cluster", ctypes.c_uint32),
-                ("fused_ok", ctypes.c_uint32), ("canonical_gather", ctypes.c_uint32)]
+                ("fused_ok", ctypes.c_uint32), ("canonical_gather", ctypes.c_uint32),
+                ("gather_runs", ctypes.c_uint32), ("merged_adds", ctypes.c_uint64)]
 
 
 class _Options(ctypes.Structure):
     _fields_ = [("gather_unit_chunks", ctypes.c_uint32), ("scatter_unit_groups", ctypes.c_uint32),
-                ("gather_cluster", ctypes.c_uint32), ("canonical_gather", ctypes.c_uint32)]
+                ("gather_cluster", ctypes.c_uint32), ("canonical_gather", ctypes.c_uint32),
+                ("gather_runs", ctypes.c_uint32)]
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -141,7 +143,8 @@ class PNG:
     def __init__(self, row_ptr, col, part_size: int, stream=None, **options):
         """row_ptr, col: CUDA int32/uint32 tensors (CSR out-adjacency, rows sorted).
         options: gather_unit_chunks, scatter_unit_groups, gather_cluster (0 = automatic),
-        canonical_gather (1 = gather from the canonical bins)."""
+        canonical_gather (1 = gather from the canonical bins), gather_runs (1 = sum runs of
+        equal destinations in registers, 2 = never, 0 = automatic)."""
         L = lib()
         n = row_ptr.numel() - 1
         m = int(row_ptr[-1].item()) & 0xFFFFFFFF

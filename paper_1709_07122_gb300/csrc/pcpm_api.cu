@@ -206,6 +206,7 @@ int pcpm_build_ex(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t n, 
     if (opt.gather_cluster != 0 && opt.gather_cluster != 1 && opt.gather_cluster != 2 && opt.gather_cluster != 4 &&
         opt.gather_cluster != 8)
         return PCPM_EINVAL;
+    if (opt.gather_runs > 2) return PCPM_EINVAL;
     if (m > 0xFFFFFF00ull) return PCPM_EINVAL;
     const uint64_t k = ((uint64_t)n + part_size - 1) / part_size;
     if (k > PCPM_MAX_PARTITIONS) return PCPM_EINVAL;
@@ -272,6 +273,8 @@ int pcpm_png_get_info(const pcpm_png* g, pcpm_png_info* info) {
     info->gather_cluster = (uint32_t)g->cluster;
     info->fused_ok = (uint32_t)g->fused_ok;
     info->canonical_gather = (uint32_t)g->canonical_gather;
+    info->gather_runs = (uint32_t)g->gather_runs;
+    info->merged_adds = g->merged_adds;
     return PCPM_OK;
 }
 

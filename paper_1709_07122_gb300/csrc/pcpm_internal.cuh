@@ -81,8 +81,11 @@ struct pcpm_png {
     // permuted so that the IDs one warp adds at once fall in distinct
     // shared-memory banks as far as possible, each word holding the local
     // destination (15 bits), the offset of its update in the chunk's update
-    // slice (9 bits) and bit 31 for padding.
+    // slice (9 bits), bit 30 when the next ID of the same gather lane has the
+    // same destination, and bit 31 for padding.
     int canonical_gather;    // 1: the gather decodes the canonical bins (MSB flags)
+    int gather_runs;         // 1: the gather sums bit-30 runs in a register
+    uint64_t merged_adds;    // IDs with bit 30 set
     uint32_t* gdest;         // nichunks * kChunk words
     uint32_t* gslice_start;  // nichunks: first update of the chunk's slice (multiple of 4)
     uint32_t* gslice_bytes;  // nichunks: bytes of the slice (multiple of 16)

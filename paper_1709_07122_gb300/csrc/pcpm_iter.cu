@@ -63,15 +63,6 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
                  : "memory");
 }
 
-// Bulk copy global -> shared completing on an mbarrier. Both addresses 16-byte
-// aligned, bytes a multiple of 16.
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(bar))
-        : "memory");
-}
-
 // L2 eviction-priority policies for bulk copies.
 __device__ __forceinline__ uint64_t policy_evict_first() {
     uint64_t p;
@@ -85,7 +76,8 @@ __device__ __forceinline__ uint64_t policy_evict_last() {
     return p;
 }
 
-// Bulk copy as above with an L2 eviction policy (streamed data: evict first).
+// Bulk copy global -> shared completing on an mbarrier, with an L2 eviction
+// policy. Both addresses 16-byte aligned, bytes a multiple of 16.
 __device__ __forceinline__ void bulk_load_hint(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
                                                uint64_t policy) {
     asm volatile(
@@ -453,7 +445,9 @@ constexpr size_t kAccOffset = kRingBytes + kBarBytes + kMetaBytes;
 static_assert(kStageBytes % 16 == 0, "ring slots must stay 16-byte aligned");
 static_assert(kAccOffset % 16 == 0, "accumulator must be 16-byte aligned");
 
-template <bool kFused, bool kCanon>
+// kFused: also scatter the next iteration; kCanon: decode the canonical bins;
+// kRuns: sum bit-30 runs of the bank-spread layout in a register.
+template <bool kFused, bool kCanon, bool kRuns>
 __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const GatherArgs a) {
     if (a.st->stop) return;
     extern __shared__ __align__(128) unsigned char smraw[];
@@ -569,7 +563,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
             constexpr int kPer = kChunk / 32;  // IDs per lane
             // All loads of the chunk first (IDs, then update values), then the
             // adds: eight independent shared-memory operations per lane.
-            uint32_t id[kPer], uo[kPer], valid = 0;
+            uint32_t id[kPer], uo[kPer], valid = 0, cont = 0;
 #pragma unroll
             for (int h = 0; h < kPer / 4; ++h) {
                 const uint4 v4 = *reinterpret_cast<const uint4*>(ids_s + h * 128 + lane * 4);
@@ -617,10 +611,12 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
                 }
             } else {
                 // Bank-spread layout: local destination and update offset are
-                // stored in the word; bit 31 marks padding.
+                // stored in the word; bit 31 marks padding, bit 30 an ID whose
+                // successor in this lane has the same destination.
 #pragma unroll
                 for (int q = 0; q < kPer; ++q) {
                     valid |= (id[q] >> 31) ? 0u : 1u << q;
+                    if constexpr (kRuns) cont |= (id[q] >> 30 & 1u) << q;
                     uo[q] = (id[q] >> 15) & 0x1FFu;
                     id[q] &= 0x7FFFu;
                 }
@@ -628,6 +624,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
             float val[kPer];
 #pragma unroll
             for (int q = 0; q < kPer; ++q) val[q] = ups[(valid >> q & 1u) ? uo[q] : 0u];
+            [[maybe_unused]] float run = 0.0f;  // kRuns: sum of a run of equal destinations in this lane
 #pragma unroll
             for (int q = 0; q < kPer; ++q) {
                 const uint32_t loc = id[q];
@@ -636,8 +633,18 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
                 hub0 += is0 ? val[q] : 0.0f;
                 hub1 += is1 ? val[q] : 0.0f;
                 if (ok_q && !is0 && !is1) {
-                    if (loc < len) atomicAdd(&acc[loc], val[q]);
-                    else atomicOr(a.err, kErrBounds);
+                    if constexpr (kRuns) {
+                        // one shared-memory add per run of equal destinations
+                        run += val[q];
+                        if (!(cont >> q & 1u)) {
+                            if (loc < len) atomicAdd(&acc[loc], run);
+                            else atomicOr(a.err, kErrBounds);
+                            run = 0.0f;
+                        }
+                    } else {
+                        if (loc < len) atomicAdd(&acc[loc], val[q]);
+                        else atomicOr(a.err, kErrBounds);
+                    }
                 }
             }
             __syncwarp();
@@ -855,15 +862,16 @@ size_t partial_slots(const pcpm_png* g) {
 // Picks the cluster size for the gather and sets shared-memory limits.
 int configure_kernels(pcpm_png* g) {
     const size_t gs = gather_smem_bytes(g->q), ss = scatter_smem_bytes(g->q, g->k);
-    if (cudaFuncSetAttribute(gather_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gs) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(gather_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gs) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(gather_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gs) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(gather_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gs) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss) != cudaSuccess)
+    const void* gathers[] = {(const void*)gather_kernel<false, false, false>,
+                             (const void*)gather_kernel<true, false, false>,
+                             (const void*)gather_kernel<false, false, true>,
+                             (const void*)gather_kernel<true, false, true>,
+                             (const void*)gather_kernel<false, true, false>,
+                             (const void*)gather_kernel<true, true, false>};
+    for (const void* f : gathers)
+        if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gs) != cudaSuccess)
+            return PCPM_ECUDA;
+    if (cudaFuncSetAttribute(scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss) != cudaSuccess)
         return PCPM_ECUDA;
     // Two CTAs per gather unit unless the build options ask otherwise (two
     // measured best at k = 512 against one and four); smaller if the device
@@ -882,7 +890,7 @@ int configure_kernels(pcpm_png* g) {
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int clusters = 0;
-        if (cudaOccupancyMaxActiveClusters(&clusters, gather_kernel<true, false>, &cfg) == cudaSuccess &&
+        if (cudaOccupancyMaxActiveClusters(&clusters, gather_kernel<true, false, false>, &cfg) == cudaSuccess &&
             clusters > 0) {
             g->cluster = S;
             return PCPM_OK;
@@ -956,11 +964,14 @@ int launch_gather(pcpm_png* g, float d, uint32_t flags, bool fused, cudaStream_t
     cfg.numAttrs = 1;
     cudaError_t e;
     if (g->canonical_gather)
-        e = fused ? cudaLaunchKernelEx(&cfg, gather_kernel<true, true>, a)
-                  : cudaLaunchKernelEx(&cfg, gather_kernel<false, true>, a);
+        e = fused ? cudaLaunchKernelEx(&cfg, gather_kernel<true, true, false>, a)
+                  : cudaLaunchKernelEx(&cfg, gather_kernel<false, true, false>, a);
+    else if (g->gather_runs)
+        e = fused ? cudaLaunchKernelEx(&cfg, gather_kernel<true, false, true>, a)
+                  : cudaLaunchKernelEx(&cfg, gather_kernel<false, false, true>, a);
     else
-        e = fused ? cudaLaunchKernelEx(&cfg, gather_kernel<true, false>, a)
-                  : cudaLaunchKernelEx(&cfg, gather_kernel<false, false>, a);
+        e = fused ? cudaLaunchKernelEx(&cfg, gather_kernel<true, false, false>, a)
+                  : cudaLaunchKernelEx(&cfg, gather_kernel<false, false, false>, a);
     g->partial_count = (int)(g->ngunits * g->cluster);
     return e == cudaSuccess ? PCPM_OK : PCPM_ECUDA;
 }

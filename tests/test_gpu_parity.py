@@ -264,6 +264,10 @@ DECOMPOSITIONS = [
     dict(canonical_gather=1),                           # decode the canonical bins' flags
     dict(canonical_gather=1, gather_unit_chunks=1 << 30),
     dict(canonical_gather=1, gather_unit_chunks=2, gather_cluster=1),
+    dict(gather_runs=1),                                # register runs of equal destinations
+    dict(gather_runs=1, gather_unit_chunks=1 << 30),
+    dict(gather_runs=1, gather_unit_chunks=1, gather_cluster=1),
+    dict(gather_runs=2),                                # one shared-memory add per ID
 ]
 
 
@@ -282,6 +286,13 @@ def test_work_decompositions_match_oracle(name, opts, mode):
         assert info["gather_units"] >= k and info["scatter_units"] >= k
         assert info["fused_ok"] == (info["gather_units"] == k)
         assert info["canonical_gather"] == opts.get("canonical_gather", 0)
+        assert info["merged_adds"] <= int(rp[-1])
+        if info["canonical_gather"]:
+            assert info["gather_runs"] == 0 and info["merged_adds"] == 0
+        elif opts.get("gather_runs"):
+            assert info["gather_runs"] == (opts["gather_runs"] == 1)
+        else:
+            assert info["gather_runs"] == (info["merged_adds"] * 16 >= info["num_edges"])
         if opts.get("gather_unit_chunks") == 1 << 30:
             assert info["gather_units"] == k
         g.reset()
@@ -312,3 +323,28 @@ def test_bad_cluster_option_rejected():
     with pytest.raises(pcpm.PcpmError) as e:
         pcpm.PNG.from_host(rp, col, q, gather_cluster=3)
     assert e.value.code == -1
+    with pytest.raises(pcpm.PcpmError) as e:
+        pcpm.PNG.from_host(rp, col, q, gather_runs=3)
+    assert e.value.code == -1
+
+
+def test_hot_destinations_take_register_runs():
+    # Every source points at the same 40 nodes: inside a bank each of them
+    # repeats, so most IDs join a run and the automatic choice sums runs in
+    # registers; a uniform random graph with large partitions has few repeats
+    # per chunk and keeps one add per ID. Both follow the oracle.
+    rng = np.random.default_rng(77)
+    n = 6000
+    src = np.repeat(np.arange(n), 12)
+    dst = rng.integers(0, 40, size=src.size) * 7 % 97
+    rp, col = graphgen.csr_from_edges(n, src, dst)
+    ref = oracle.pagerank(rp, col, 0.85, iters=5)["x"]
+    with pcpm.PNG.from_host(rp, col, 1024) as g:
+        info = g.info
+        assert info["merged_adds"] * 4 >= int(rp[-1]), info
+        assert info["gather_runs"] == 1
+        pr, _, _ = g.pagerank(0.85, max_iters=5)
+        assert l1(pr.cpu().numpy(), ref) <= L1_TOL
+    rp, col = graphgen.random_graph(1 << 15, 1 << 18, seed=5)
+    with pcpm.PNG.from_host(rp, col, 1 << 15) as g:
+        assert g.info["gather_runs"] == 0, g.info
