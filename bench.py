@@ -81,6 +81,46 @@ def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+class Replicas:
+    """The N ranks of one node, each running an independent replica of the
+    whole job (the path has no exchange step, so no data-path collective):
+    a barrier around the timed region and the maximum of a per-rank time.
+    NCCL on GPUs; gloo with device "cpu" runs the same logic on host ranks."""
+
+    def __init__(self, backend: str = "nccl", device=None):
+        self.rank, self.world, self.local = dist_env()
+        self.device = device
+        self.dist = None
+        if self.world > 1:
+            import torch
+            import torch.distributed as dist
+            kw = {"device_id": torch.device(device)} if backend == "nccl" else {}
+            dist.init_process_group(backend, **kw)
+            self.dist = dist
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def max(self, x: float) -> float:
+        if self.dist is None:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def aggregate_gteps(self, edges_per_replica: int, slowest_seconds_per_step: float) -> float:
+        """Whole-job GTEPS: the edges all replicas processed in one step over
+        the slowest rank's step time (the value `max` returned)."""
+        return self.world * edges_per_replica / slowest_seconds_per_step / 1e9
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.destroy_process_group()
+            self.dist = None
+
+
 # ----------------------------------------------------------------- clocks
 class ClockSampler:
     """nvidia-smi clocks/throttle sampling in the background (read-only)."""
@@ -254,21 +294,8 @@ def run_ours(a):
     if a.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    def max_over_ranks(x: float) -> float:
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    ranks = Replicas("nccl", f"cuda:{local}")
+    barrier, max_over_ranks = ranks.barrier, ranks.max
 
     pcpm.build()
     pcpm.lib()
@@ -303,7 +330,7 @@ def run_ours(a):
     clocks = sampler.stop(t0, t1)
     bracket_ms = ev0.elapsed_time(ev1)
     iter_ms = max_over_ranks(kms["span"] / a.steps)
-    value = world * m / (iter_ms * 1e-3) / 1e9
+    value = ranks.aggregate_gteps(m, iter_ms * 1e-3)
 
     # roofline of the kernel with the largest share of the time
     ab = algorithmic_bytes(info, a.mode)
@@ -391,8 +418,7 @@ def run_ours(a):
         out["cpu_baseline"] = {"value": gt, "unit": "GTEPS", "cores": 1, "kind": "oracle",
                                "sample": "one full FP64 pull iteration (Eq. 1) of the same graph as 16 "
                                          "destination-range steps, %.1f s, single thread" % dt}
-    if dist is not None:
-        dist.destroy_process_group()
+    ranks.close()
     if rank == 0:
         print(json.dumps(out), flush=True)
     return 0
