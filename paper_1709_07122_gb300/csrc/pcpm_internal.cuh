@@ -26,9 +26,25 @@ constexpr uint32_t kChunk = 256;
 // Gather: a chunk needs the updates [base-1, next base) (the first ID may
 // continue the previous message), widened to 16-byte boundaries.
 constexpr uint32_t kUpdSlot = kChunk + 8;
+// Gather, bank-spread layout: one 32-bit word per destination ID holding an
+// accumulator slot (16 bits), the offset of its update in the chunk's update
+// slice (9 bits) and a run bit (the next ID of the same gather lane has the
+// same slot). Slots below q are the partition's nodes. Padding words name one
+// of kPadSlots spare slots after them (offset 0), which are never read. IDs
+// of the bin's two hub destinations name slot q + kPadSlots + {0, 1}, which
+// each warp moves to a private pair of slots, so hub adds from different
+// warps never meet on one address; the pairs are added to the hubs' real
+// slots once, after the warp's last chunk.
+constexpr uint32_t kGwLocMask = 0xFFFFu;
+constexpr uint32_t kGwUpdShift = 16;
+constexpr uint32_t kGwUpdMask = 0x1FFu;
+constexpr uint32_t kGwRunBit = 1u << 30;
+constexpr uint32_t kPadSlots = 32;
+static_assert(kUpdSlot <= kGwUpdMask + 1, "update offsets must fit their field");
 // Gather: warps per CTA and pipeline depth of each warp's private ring.
 constexpr int kGatherWarps = 24;
 constexpr int kGatherStages = 2;
+constexpr uint32_t kHubSlots = 2 * kGatherWarps;
 // Scatter: threads per CTA and 4-entry groups in flight per thread.
 constexpr int kScatterThreads = 1024;
 constexpr int kScatterUnroll = 4;
@@ -79,12 +95,9 @@ struct pcpm_png {
     // Bank-spread gather layout (unless the canonical bins are gathered
     // directly): every bin padded to whole kChunk-ID chunks; each chunk's IDs
     // permuted so that the IDs one warp adds at once fall in distinct
-    // shared-memory banks as far as possible, each word holding the local
-    // destination (15 bits), the offset of its update in the chunk's update
-    // slice (9 bits), bit 30 when the next ID of the same gather lane has the
-    // same destination, and bit 31 for padding.
+    // shared-memory banks as far as possible, in the word format of kGw*.
     int canonical_gather;    // 1: the gather decodes the canonical bins (MSB flags)
-    int gather_runs;         // 1: the gather sums bit-30 runs in a register
+    int gather_runs;         // 1: the gather sums run-bit runs in a register
     uint64_t merged_adds;    // IDs with bit 30 set
     uint32_t* gdest;         // nichunks * kChunk words
     uint32_t* gslice_start;  // nichunks: first update of the chunk's slice (multiple of 4)

@@ -191,10 +191,12 @@ __device__ __forceinline__ void st_stream_f4(float* p, float4 v) {
                  : "memory");
 }
 
-// Deterministic block sum of two doubles; result valid in thread 0.
+// Deterministic block sum of two doubles; result valid in thread 0. `scratch`
+// is 2 * kThreads / 32 doubles of shared memory.
 template <int kThreads>
-__device__ __forceinline__ void block_sum2(double& a, double& b) {
-    __shared__ double sa[kThreads / 32], sb[kThreads / 32];
+__device__ __forceinline__ void block_sum2(double& a, double& b, double* scratch) {
+    double* sa = scratch;
+    double* sb = scratch + kThreads / 32;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         a += __shfl_down_sync(kFull, a, o);
@@ -215,6 +217,12 @@ __device__ __forceinline__ void block_sum2(double& a, double& b) {
             b += __shfl_down_sync(kFull, b, o);
         }
     }
+}
+
+template <int kThreads>
+__device__ __forceinline__ void block_sum2(double& a, double& b) {
+    __shared__ double scratch[2 * kThreads / 32];
+    block_sum2<kThreads>(a, b, scratch);
 }
 
 // ------------------------------------------------------------ scatter body
@@ -442,6 +450,9 @@ constexpr size_t kRingBytes = (size_t)kGatherWarps * kGatherStages * kStageBytes
 constexpr size_t kBarBytes = (size_t)kGatherWarps * kGatherStages * sizeof(uint64_t);
 constexpr size_t kMetaBytes = (size_t)kGatherWarps * kGatherStages * 2 * sizeof(uint32_t);
 constexpr size_t kAccOffset = kRingBytes + kBarBytes + kMetaBytes;
+// The block sum after the apply borrows the ring's last bytes (idle by then;
+// pushed partial sums stay below them).
+constexpr size_t kSumScratchBytes = 2 * kGatherWarps * sizeof(double);
 static_assert(kStageBytes % 16 == 0, "ring slots must stay 16-byte aligned");
 static_assert(kAccOffset % 16 == 0, "accumulator must be 16-byte aligned");
 
@@ -465,6 +476,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
 
     for (uint32_t i = threadIdx.x; i < (len + 3) / 4; i += blockDim.x)
         reinterpret_cast<float4*>(acc)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (threadIdx.x < kHubSlots) acc[a.q + kPadSlots + threadIdx.x] = 0.0f;
     if (threadIdx.x < kGatherWarps * kGatherStages) mbar_init(&bars[threadIdx.x], 1);
     fence_mbar_init();
     __syncthreads();
@@ -479,7 +491,9 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
         prefetch_l2(a.inv_deg + vbase + lo0, hi0 - lo0, keep);
     }
     const uint32_t h0 = a.hubs[2 * pd], h1 = a.hubs[2 * pd + 1];
-    float hub0 = 0.0f, hub1 = 0.0f;
+    float hub0 = 0.0f, hub1 = 0.0f;  // canonical layout: hub sums in registers
+    // bank-spread layout: hub slot pair of the words, and this warp's pair
+    const uint32_t hub_slot = a.q + kPadSlots, hub_off = 2u * (uint32_t)warp;
     const uint32_t E0 = a.bin_e[pd], E1 = a.bin_e[pd + 1];
     if (unit.z > unit.y) {
         const uint32_t c_first = unit.y;
@@ -611,39 +625,44 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
                 }
             } else {
                 // Bank-spread layout: local destination and update offset are
-                // stored in the word; bit 31 marks padding, bit 30 an ID whose
-                // successor in this lane has the same destination.
+                // stored in the word, padding names a spare accumulator slot,
+                // and the build checked every word against the accumulator
+                // and the slice, so no ID needs a test here.
 #pragma unroll
                 for (int q = 0; q < kPer; ++q) {
-                    valid |= (id[q] >> 31) ? 0u : 1u << q;
-                    if constexpr (kRuns) cont |= (id[q] >> 30 & 1u) << q;
-                    uo[q] = (id[q] >> 15) & 0x1FFu;
-                    id[q] &= 0x7FFFu;
+                    if constexpr (kRuns) cont |= (id[q] & kGwRunBit) ? 1u << q : 0u;
+                    uo[q] = (id[q] >> kGwUpdShift) & kGwUpdMask;
+                    id[q] &= kGwLocMask;
                 }
             }
             float val[kPer];
 #pragma unroll
-            for (int q = 0; q < kPer; ++q) val[q] = ups[(valid >> q & 1u) ? uo[q] : 0u];
+            for (int q = 0; q < kPer; ++q) val[q] = ups[(!kCanon || (valid >> q & 1u)) ? uo[q] : 0u];
             [[maybe_unused]] float run = 0.0f;  // kRuns: sum of a run of equal destinations in this lane
 #pragma unroll
             for (int q = 0; q < kPer; ++q) {
                 const uint32_t loc = id[q];
-                const bool ok_q = (valid >> q & 1u) != 0;
-                const bool is0 = ok_q && loc == h0, is1 = ok_q && loc == h1;
-                hub0 += is0 ? val[q] : 0.0f;
-                hub1 += is1 ? val[q] : 0.0f;
-                if (ok_q && !is0 && !is1) {
+                if constexpr (kCanon) {
+                    const bool ok_q = (valid >> q & 1u) != 0;
+                    const bool is0 = ok_q && loc == h0, is1 = ok_q && loc == h1;
+                    hub0 += is0 ? val[q] : 0.0f;
+                    hub1 += is1 ? val[q] : 0.0f;
+                    if (ok_q && !is0 && !is1) {
+                        if (loc < len) atomicAdd(&acc[loc], val[q]);
+                        else atomicOr(a.err, kErrBounds);
+                    }
+                } else {
+                    // hub slots move to this warp's private pair
+                    const uint32_t slot = loc + (loc >= hub_slot ? hub_off : 0u);
                     if constexpr (kRuns) {
-                        // one shared-memory add per run of equal destinations
+                        // one shared-memory add per run of equal slots
                         run += val[q];
                         if (!(cont >> q & 1u)) {
-                            if (loc < len) atomicAdd(&acc[loc], run);
-                            else atomicOr(a.err, kErrBounds);
+                            atomicAdd(&acc[slot], run);
                             run = 0.0f;
                         }
                     } else {
-                        if (loc < len) atomicAdd(&acc[loc], val[q]);
-                        else atomicOr(a.err, kErrBounds);
+                        atomicAdd(&acc[slot], val[q]);
                     }
                 }
             }
@@ -661,11 +680,18 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
                 (void)mbar_wait_bounded(&wbar[jj % kGatherStages], (jj / kGatherStages) & 1u);
         }
     }
-    // Register sums of the two hubs.
+    // The two hubs' sums: registers (canonical layout) or this warp's slot
+    // pair (bank-spread layout, complete after the loop's last __syncwarp).
+    if constexpr (kCanon) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        hub0 += __shfl_xor_sync(kFull, hub0, o);
-        hub1 += __shfl_xor_sync(kFull, hub1, o);
+        for (int o = 16; o > 0; o >>= 1) {
+            hub0 += __shfl_xor_sync(kFull, hub0, o);
+            hub1 += __shfl_xor_sync(kFull, hub1, o);
+        }
+    } else {
+        __syncwarp();
+        hub0 = acc[hub_slot + hub_off];
+        hub1 = acc[hub_slot + hub_off + 1];
     }
     if (lane == 0) {
         if (h0 < len) atomicAdd(&acc[h0], hub0);
@@ -679,7 +705,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
     const uint32_t per = (((len + S - 1) / S) + 3) & ~3u;
     const uint32_t lo = min(len, rank * per), hi = min(len, lo + per);
     float* stage = reinterpret_cast<float*>(ring);
-    const bool push = (size_t)(S - 1) * per * sizeof(float) <= kRingBytes;
+    const bool push = (size_t)(S - 1) * per * sizeof(float) <= kRingBytes - kSumScratchBytes;
     if (push && S > 1) {
         for (uint32_t t = 0; t < S; ++t) {
             if (t == rank) continue;
@@ -778,7 +804,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
         }
     }
     double res = (double)res_f, dg = (double)dg_f;
-    block_sum2<kGatherWarps * 32>(res, dg);
+    block_sum2<kGatherWarps * 32>(res, dg, reinterpret_cast<double*>(ring + kRingBytes - kSumScratchBytes));
     if (threadIdx.x == 0) {
         a.partials[2 * blockIdx.x] = res;
         a.partials[2 * blockIdx.x + 1] = dg;
@@ -848,7 +874,11 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_kernel(const double* __
 
 constexpr int kInitBlocks = 1024;
 
-size_t gather_smem_bytes(uint32_t q) { return kAccOffset + (size_t)((q + 3) & ~3u) * sizeof(float); }
+// The accumulator holds q real slots, kPadSlots for the layout's padding and
+// kHubSlots (a pair per warp) for the hubs.
+size_t gather_smem_bytes(uint32_t q) {
+    return kAccOffset + (size_t)(((q + 3) & ~3u) + kPadSlots + kHubSlots) * sizeof(float);
+}
 size_t scatter_smem_bytes(uint32_t q, uint32_t k) {
     return (size_t)((q + 3) & ~3u) * sizeof(float) + (size_t)(k + 1) * sizeof(uint32_t);
 }

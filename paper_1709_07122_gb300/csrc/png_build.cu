@@ -474,8 +474,8 @@ constexpr uint32_t kKeyHub = 32, kKeyPad = 33, kNumKeys = 34;
 // One warp per padded chunk: the update index of every ID (flags before the
 // chunk plus the inclusive count inside it, minus one), then a stable counting
 // sort of the chunk's IDs by shared-memory bank of their destination (hub
-// destinations, which the gather sums in registers, and padding sort last).
-// Inside a bank, IDs are ordered by destination. Sorted position s goes to
+// destinations, which the gather sums in per-warp slots, and padding sort
+// last). Inside a group, IDs are ordered by slot. Sorted position s goes to
 // round s % 8 and lane s / 8 of the gather's 8-round, 32-lane pass over the
 // chunk: the 32 adds of a round come from every eighth sorted ID (distinct
 // banks unless a bank holds more than eight of the chunk's IDs), and each
@@ -485,13 +485,14 @@ __global__ void __launch_bounds__(kLayoutWarps * 32) gather_layout_kernel(
     const uint32_t* __restrict__ dest, const uint32_t* __restrict__ bin_e, const uint32_t* __restrict__ ichunk_start,
     uint32_t k, const uint32_t* __restrict__ chunk_base, const uint32_t* __restrict__ hubs, uint32_t q,
     uint64_t nichunks, uint32_t* __restrict__ gdest, uint32_t* __restrict__ slice_start,
-    uint32_t* __restrict__ slice_bytes, unsigned long long* __restrict__ merged) {
+    uint32_t* __restrict__ slice_bytes, unsigned long long* __restrict__ stats) {
     __shared__ uint32_t keycnt[kLayoutWarps][kNumKeys + 2];
     __shared__ uint32_t sortbuf[kLayoutWarps][kChunk];
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt = lanemask_lt();
     uint32_t* cnt = keycnt[warp];
     uint32_t nmerged = 0;
+    bool bad = false;
     for (uint64_t ic = blockIdx.x * (uint64_t)kLayoutWarps + warp; ic < nichunks;
          ic += (uint64_t)gridDim.x * kLayoutWarps) {
         const uint32_t p = upper_bound_u32(ichunk_start, 0, k + 1, (uint32_t)ic) - 1;
@@ -553,19 +554,23 @@ __global__ void __launch_bounds__(kLayoutWarps * 32) gather_layout_kernel(
             __syncwarp();
             if (lane == (uint32_t)(__ffs(peers) - 1)) cnt[key[r]] += __popc(peers);
             __syncwarp();
-            sorted[pos] = key[r] == kKeyPad ? 0x80000000u : (loc[r] | ((idx[r] - us) << 15));
+            // padding: the pad slot of the lane that will hold it (distinct
+            // banks within a round); hubs: the hub slot pair
+            const uint32_t slot = key[r] == kKeyHub ? q + kPadSlots + (loc[r] == h1 ? 1u : 0u) : loc[r];
+            sorted[pos] = key[r] == kKeyPad ? q + (pos >> 3) : (slot | ((idx[r] - us) << kGwUpdShift));
+            if (key[r] != kKeyPad && (loc[r] >= q || idx[r] - us >= kUpdSlot)) bad = true;
         }
         __syncwarp();
         // cnt[j] now holds the end of group j; group j starts at cnt[j - 1].
-        // Inside each bank group order IDs by destination, so equal
-        // destinations sit next to each other and the gather sums them in a
-        // register before one shared-memory add.
-        {
-            const uint32_t g_end = cnt[lane], g_beg = lane ? cnt[lane - 1] : 0;
+        // Inside each bank group, and in the hub group, order IDs by slot, so
+        // equal destinations sit next to each other and the gather sums them
+        // in a register before one shared-memory add.
+        for (uint32_t grp = lane; grp <= kKeyHub; grp += 32) {
+            const uint32_t g_end = cnt[grp], g_beg = grp ? cnt[grp - 1] : 0;
             for (uint32_t x = g_beg + 1; x < g_end; ++x) {
                 const uint32_t w = sorted[x];
                 uint32_t y = x;
-                while (y > g_beg && (sorted[y - 1] & 0x7FFFu) > (w & 0x7FFFu)) {
+                while (y > g_beg && (sorted[y - 1] & kGwLocMask) > (w & kGwLocMask)) {
                     sorted[y] = sorted[y - 1];
                     --y;
                 }
@@ -574,27 +579,31 @@ __global__ void __launch_bounds__(kLayoutWarps * 32) gather_layout_kernel(
         }
         __syncwarp();
         // Position s goes to round s % 8, lane s / 8 of the gather's pass.
-        // Bit 30 marks an ID whose successor in the same lane has the same
-        // (non-hub) destination: the gather adds it to a register run instead
-        // of shared memory.
+        // The run bit marks an ID whose successor in the same lane has the
+        // same slot (not a padding slot): the gather adds it to a register
+        // run instead of shared memory.
         uint32_t* out = gdest + ic * kChunk;
         for (uint32_t sp = lane; sp < kChunk; sp += 32) {
             const uint32_t round = sp & 7u, slot_lane = sp >> 3;
             uint32_t w = sorted[sp];
-            if (round != 7u && !(w >> 31)) {
-                const uint32_t nx = sorted[sp + 1], l = w & 0x7FFFu;
-                if (!(nx >> 31) && (nx & 0x7FFFu) == l && l != h0 && l != h1) w |= 1u << 30;
-            }
-            nmerged += __popc(__ballot_sync(0xffffffffu, (w >> 30) & 1u));
+            const uint32_t l = w & kGwLocMask;
+            const bool pad = l >= q && l < q + kPadSlots;
+            if (round != 7u && !pad && (sorted[sp + 1] & kGwLocMask) == l) w |= kGwRunBit;
+            nmerged += __popc(__ballot_sync(0xffffffffu, (w & kGwRunBit) != 0));
             out[128 * (round >> 2) + 4 * slot_lane + (round & 3u)] = w;
         }
         if (lane == 0) {
             slice_start[ic] = us;
             slice_bytes[ic] = (ue - us) * (uint32_t)sizeof(float);
+            if (ue - us > kUpdSlot) bad = true;
         }
         __syncwarp();
     }
-    if (lane == 0 && nmerged) atomicAdd(merged, (unsigned long long)nmerged);
+    // stats[0]: IDs with the run bit; stats[1]: nonzero if a word would
+    // address outside the accumulator or the chunk's update slice (the gather
+    // relies on this check instead of testing every ID).
+    if (lane == 0 && nmerged) atomicAdd(&stats[0], (unsigned long long)nmerged);
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicAdd(&stats[1], 1ull);
 }
 
 __global__ void scatter_pieces_kernel(const uint32_t* __restrict__ groups, uint32_t k, uint32_t per,
@@ -817,18 +826,20 @@ int build_png(pcpm_png* g, const uint32_t* row_ptr, const uint32_t* col, const p
         BCK(dev_alloc(g, (void**)&g->gdest, std::max<uint64_t>(nic, 1) * kChunk * sizeof(uint32_t)));
         BCK(dev_alloc(g, (void**)&g->gslice_start, std::max<uint64_t>(nic, 1) * sizeof(uint32_t)));
         BCK(dev_alloc(g, (void**)&g->gslice_bytes, std::max<uint64_t>(nic, 1) * sizeof(uint32_t)));
-        unsigned long long* merged = nullptr;
-        BCK(tmp.alloc(&merged, 1));
-        BCK(cudaMemsetAsync(merged, 0, sizeof(*merged), s));
+        unsigned long long* lstats = nullptr;
+        BCK(tmp.alloc(&lstats, 2));
+        BCK(cudaMemsetAsync(lstats, 0, 2 * sizeof(*lstats), s));
         if (nic) {
             gather_layout_kernel<<<grid_for((uint64_t)nic * 32, kLayoutWarps * 32, sms * 8), kLayoutWarps * 32, 0, s>>>(
                 g->dest, g->bin_e, g->ichunk_start, k, g->chunk_base, g->hubs, q, nic, g->gdest, g->gslice_start,
-                g->gslice_bytes, merged);
+                g->gslice_bytes, lstats);
             BCK(cudaGetLastError());
         }
-        unsigned long long nmerged = 0;
-        BCK(cudaMemcpyAsync(&nmerged, merged, sizeof(nmerged), cudaMemcpyDeviceToHost, s));
+        unsigned long long hstats[2] = {0, 0};
+        BCK(cudaMemcpyAsync(hstats, lstats, sizeof(hstats), cudaMemcpyDeviceToHost, s));
         BCK(cudaStreamSynchronize(s));
+        if (hstats[1]) return PCPM_EDEVICE;
+        const unsigned long long nmerged = hstats[0];
         g->merged_adds = nmerged;
         // Register runs cost a few instructions per ID; they pay once runs
         // are common (hot destinations), where they also remove same-address
