@@ -56,6 +56,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-converge", action="store_true", help="skip the time-to-residual run")
     ap.add_argument("--no-two-phase", action="store_true", help="skip the two-phase (per-phase) leg")
+    ap.add_argument("--no-update-dtypes", action="store_true", help="skip the 16-bit update-bin leg")
     ap.add_argument("--mode", choices=("fused", "two_phase"), default="two_phase",
                     help="iteration form timed for `value` (the other is reported in other_mode)")
     ap.add_argument("--ref-budget-s", type=float, default=120.0, help="reference arm: timed seconds target")
@@ -179,12 +180,14 @@ class ClockSampler:
 
 # --------------------------------------------------------------- roofline
 def algorithmic_bytes(info, mode="fused"):
-    """Bytes each kernel must move per launch (4-byte indices and values)."""
+    """Bytes each kernel must move per launch (4-byte indices and ranks;
+    updates of info["update_bytes"], 4 unless the bins are 16-bit)."""
     n, m, ne, k = info["n"], info["num_edges"], info["num_updates"], info["num_partitions"]
+    ub = info.get("update_bytes", 4)
     nchunks = -(-m // 256)
-    gather = 4 * m + 4 * ne + 4 * nchunks + 8 * (k + 1) + 8 * k  # destIDs, updates, chunk bases, bins, hubs
+    gather = 4 * m + ub * ne + 4 * nchunks + 8 * (k + 1) + 8 * k  # destIDs, updates, chunk bases, bins, hubs
     apply = 12 * n  # PR_old and 1/outdeg read, PR' written
-    scatter = 8 * ne + 8 * k * k  # srcIdx read + update write, segment starts/counts
+    scatter = (4 + ub) * ne + 8 * k * k  # srcIdx read + update write, segment starts/counts
     if mode == "fused":
         return {"scatter": 0, "gather_apply": gather + apply + scatter, "reduce": 16 * k}
     return {"scatter": scatter + 8 * n, "gather_apply": gather + apply, "reduce": 16 * k}
@@ -226,8 +229,8 @@ def recorded_traffic(kernel: str, workload: str):
 
 # ---------------------------------------------------------------- CPU side
 def cpu_oracle_iteration(rp, col, d, slices=16):
-    """One full FP64 oracle iteration on the host, as `slices` destination
-    ranges; returns (GTEPS, seconds, edges)."""
+    """One full FP64 oracle iteration on the host from the uniform start, as
+    `slices` destination ranges; returns (GTEPS, seconds, edges, result)."""
     import oracle
     pull = oracle.Pull(rp, col)
     n = pull.n
@@ -238,7 +241,7 @@ def cpu_oracle_iteration(rp, col, d, slices=16):
         pull.step(x, y, d, v_begin=n * i // slices, v_end=n * (i + 1) // slices)
     dt = time.perf_counter() - t0
     m = int(rp[-1])
-    return m / dt / 1e9, dt, m
+    return m / dt / 1e9, dt, m, y
 
 
 def run_reference(a):
@@ -413,11 +416,37 @@ def run_ours(a):
                       "call": "pcpm_pagerank_host: H2D CSR (pinned) + PNG build + %d iterations + D2H ranks"
                               % e2e_iters, "wall_ms_per_call": wall * 1e3}
 
+    # Reduced-precision update bins (not in the paper): speed, bytes per edge,
+    # and the first iteration's distance to the FP64 oracle's (below).
+    first_iter = {}
+    if not a.no_update_dtypes:
+        d_rp, d_col = pcpm.to_device_csr(rp, col)
+        dts = {}
+        for dt_name in ("f32", "f16", "bf16"):
+            gu = pcpm.PNG(d_rp, d_col, a.part_size, update_dtype=dt_name)
+            iu = gu.info
+            gu.reset()
+            gu.iterate(a.d, 1, mode=a.mode)
+            first_iter[dt_name] = gu.ranks().cpu().numpy()
+            gu.iterate(a.d, 3, sync=False, mode=a.mode)
+            ksteps = max(3, min(a.steps, 100))
+            tu = gu.iterate_timed(a.d, ksteps, mode=a.mode)
+            abu = algorithmic_bytes(iu, a.mode)
+            dts[dt_name] = {"gteps": m / (tu["span"] / ksteps * 1e-3) / 1e9, "ms_per_iter": tu["span"] / ksteps,
+                            "phase_ms": {p: tu[p] / ksteps for p in PHASES},
+                            "bytes_per_edge": sum(abu.values()) / m, "update_bytes": iu["update_bytes"]}
+            gu.close()
+        del d_rp, d_col
+        out["update_dtypes"] = dts
+
     if rank == 0 and not a.no_cpu_baseline:
-        gt, dt, _ = cpu_oracle_iteration(rp, col, a.d)
+        gt, dt, _, y_ref = cpu_oracle_iteration(rp, col, a.d)
         out["cpu_baseline"] = {"value": gt, "unit": "GTEPS", "cores": 1, "kind": "oracle",
                                "sample": "one full FP64 pull iteration (Eq. 1) of the same graph as 16 "
                                          "destination-range steps, %.1f s, single thread" % dt}
+        for dt_name, x1 in first_iter.items():
+            out["update_dtypes"][dt_name]["l1_first_iteration_vs_fp64_oracle"] = float(
+                np.abs(x1.astype(np.float64) - y_ref).sum())
     ranks.close()
     if rank == 0:
         print(json.dumps(out), flush=True)

@@ -81,6 +81,17 @@ extern "C" {
 #define PCPM_PHASE_REDUCE 2
 #define PCPM_NUM_PHASES 3
 
+/* Storage type of the update bins (build option update_dtype). The paper
+ * keeps one 4-byte value per update (Sec. 3.2, Eq. 5's d_v); 16-bit updates
+ * halve the bins' part of the traffic at the cost of rounding every SPR
+ * value once per iteration. Accumulation stays FP32 and the reductions FP64. */
+#define PCPM_UPDATE_F32 0u  /* SPR(u) as float */
+#define PCPM_UPDATE_F16 1u  /* IEEE binary16 of SPR(u) * 2^15, round to nearest even, saturating at 65504 */
+#define PCPM_UPDATE_BF16 2u /* bfloat16 of SPR(u), round to nearest even */
+/* log2 of the FP16 scale: SPR <= PR <= 1 while ranks sum to at most 1, so
+ * SPR * 2^15 stays below FP16's largest finite value. */
+#define PCPM_F16_SCALE_LOG2 15
+
 typedef struct pcpm_png pcpm_png; /* opaque, device-resident */
 
 typedef struct pcpm_png_info {
@@ -102,6 +113,8 @@ typedef struct pcpm_png_info {
                                  register before one shared-memory add */
     uint64_t merged_adds;     /* IDs of the bank-spread layout whose value joins the next ID's
                                  (same destination, same lane): adds saved by gather_runs */
+    uint32_t update_dtype;    /* PCPM_UPDATE_* of the update bins */
+    uint32_t update_bytes;    /* bytes per update: 4 or 2 */
 } pcpm_png_info;
 
 /* Tuning of the work decomposition; zero fields take the automatic choice.
@@ -117,6 +130,9 @@ typedef struct pcpm_build_options {
     uint32_t gather_runs;         /* bank-spread layout only: 1 sums runs of equal destinations in a
                                      register before one shared-memory add, 2 adds every ID, 0 picks
                                      1 when at least m/16 IDs join a run */
+    uint32_t update_dtype;        /* PCPM_UPDATE_F32 (0, default), PCPM_UPDATE_F16 or
+                                     PCPM_UPDATE_BF16; 16-bit types need the bank-spread layout
+                                     (canonical_gather = 0) */
 } pcpm_build_options;
 
 /* Builds the Partition-Node Graph of Sec. 3.3 from a CSR out-adjacency:
@@ -145,7 +161,8 @@ int pcpm_build(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t n, uin
                uint32_t part_size, void* stream, pcpm_png** out);
 
 /* pcpm_build with tuning options (host struct, nullable = all automatic).
- * PCPM_EINVAL if gather_cluster is not 0, 1, 2, 4 or 8, or gather_runs is above 2. */
+ * PCPM_EINVAL if gather_cluster is not 0, 1, 2, 4 or 8, gather_runs is above 2, update_dtype
+ * is not a PCPM_UPDATE_* value, or a 16-bit update_dtype comes with canonical_gather. */
 int pcpm_build_ex(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t n, uint64_t m,
                   uint32_t part_size, const pcpm_build_options* options, void* stream,
                   pcpm_png** out);
@@ -224,10 +241,11 @@ int pcpm_pagerank_host(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_
 /* Test hooks. pcpm_scatter_only runs one scatter (Algorithm 3) of the current
  * ranks into the current update bins without advancing the solve.
  * pcpm_export_state copies the current state to host buffers (nullable):
- * pr[n], spr[n] (= pr/outdeg, recomputed on the device), updates[|E'|] (the
- * current update bins, bin order) and the dangling mass of pr. Synchronises. */
+ * pr[n], spr[n] (= pr/outdeg, recomputed on the device), updates (the current
+ * update bins in bin order: |E'| values of the handle's update_dtype, so
+ * |E'| * update_bytes bytes) and the dangling mass of pr. Synchronises. */
 int pcpm_scatter_only(pcpm_png* png, void* stream);
-int pcpm_export_state(const pcpm_png* png, float* pr, float* spr, float* updates, double* dangling);
+int pcpm_export_state(const pcpm_png* png, float* pr, float* spr, void* updates, double* dangling);
 
 /* Allocation-free rank statistics. There is no counterpart in the paper: this
  * entry point exists for callers that cannot call cudaMalloc, such as code

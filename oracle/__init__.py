@@ -17,6 +17,10 @@ passages they follow:
   and the bins in canonical order (source partitions in ID order, nodes in ID
   order, destination IDs in adjacency order; MSB marks a message's first ID).
 * :func:`scatter_gather` - Algorithm 3 followed by Algorithm 4 in FP64.
+* :func:`store_updates` / :func:`load_updates` - the storage formats of
+  reduced-precision update bins. Not in the paper (it keeps 4-byte updates,
+  Sec. 3.2): IEEE 754 binary16 of SPR * 2^15 and bfloat16 (binary32's upper
+  16 bits), both rounded to nearest, ties to even.
 
 Parity of :func:`pagerank` is pinned by closed forms, a dense linear solve and
 invariants; :func:`png` by brute-force enumeration and the paper's offset
@@ -183,3 +187,40 @@ def scatter_gather(g: dict, spr) -> np.ndarray:
     lib.oracle_scatter_gather(g["n"], g["k"], g["bin_u"], g["bin_e"], np.ascontiguousarray(src),
                               np.ascontiguousarray(dst), spr, y)
     return y
+
+
+# ------------------------------------------------------------------ formats
+F16_SCALE_LOG2 = 15
+_F16_MAX = 65504.0
+
+
+def store_updates(values_f32, dtype: str) -> np.ndarray:
+    """Stored form of FP32 update values. f32: unchanged. f16: binary16 of
+    value * 2^15 (an exact power-of-two scaling), rounded to nearest even,
+    saturating at the largest finite half (numpy's float32 -> float16 cast
+    rounds to nearest even). bf16: the 16-bit pattern of binary32 rounded to
+    nearest even at bit 16, returned as uint16."""
+    v = np.ascontiguousarray(values_f32, dtype=np.float32)
+    if dtype == "f32":
+        return v.copy()
+    if dtype == "f16":
+        scaled = v * np.float32(2.0 ** F16_SCALE_LOG2)
+        return np.minimum(scaled, np.float32(_F16_MAX)).astype(np.float16)
+    if dtype == "bf16":
+        bits = v.view(np.uint32).astype(np.uint64)
+        # round to nearest, ties to even: add 0x7FFF plus the lowest kept bit
+        rounded = (bits + 0x7FFF + ((bits >> 16) & 1)) >> 16
+        return rounded.astype(np.uint16)
+    raise ValueError("dtype must be f32, f16 or bf16")
+
+
+def load_updates(stored, dtype: str) -> np.ndarray:
+    """FP64 values of stored updates (inverse of the format, scale removed)."""
+    if dtype == "f32":
+        return np.asarray(stored, dtype=np.float64)
+    if dtype == "f16":
+        return np.asarray(stored, dtype=np.float16).astype(np.float64) * 2.0 ** -F16_SCALE_LOG2
+    if dtype == "bf16":
+        bits = np.asarray(stored, dtype=np.uint16).astype(np.uint32) << 16
+        return bits.view(np.float32).astype(np.float64)
+    raise ValueError("dtype must be f32, f16 or bf16")

@@ -44,13 +44,18 @@ class _Info(ctypes.Structure):
                 ("iterations_done", ctypes.c_int32), ("gather_units", ctypes.c_uint32),
                 ("scatter_units", ctypes.c_uint32), ("gather_cluster", ctypes.c_uint32),
                 ("fused_ok", ctypes.c_uint32), ("canonical_gather", ctypes.c_uint32),
-                ("gather_runs", ctypes.c_uint32), ("merged_adds", ctypes.c_uint64)]
+                ("gather_runs", ctypes.c_uint32), ("merged_adds", ctypes.c_uint64),
+                ("update_dtype", ctypes.c_uint32), ("update_bytes", ctypes.c_uint32)]
 
 
 class _Options(ctypes.Structure):
     _fields_ = [("gather_unit_chunks", ctypes.c_uint32), ("scatter_unit_groups", ctypes.c_uint32),
                 ("gather_cluster", ctypes.c_uint32), ("canonical_gather", ctypes.c_uint32),
-                ("gather_runs", ctypes.c_uint32)]
+                ("gather_runs", ctypes.c_uint32), ("update_dtype", ctypes.c_uint32)]
+
+# Storage of the update bins (PCPM_UPDATE_* in pcpm.h).
+UPDATE_DTYPES = {"f32": 0, "f16": 1, "bf16": 2}
+F16_SCALE_LOG2 = 15
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -144,11 +149,14 @@ class PNG:
         """row_ptr, col: CUDA int32/uint32 tensors (CSR out-adjacency, rows sorted).
         options: gather_unit_chunks, scatter_unit_groups, gather_cluster (0 = automatic),
         canonical_gather (1 = gather from the canonical bins), gather_runs (1 = sum runs of
-        equal destinations in registers, 2 = never, 0 = automatic)."""
+        equal destinations in registers, 2 = never, 0 = automatic), update_dtype ("f32", "f16",
+        "bf16" or the PCPM_UPDATE_* value)."""
         L = lib()
         n = row_ptr.numel() - 1
         m = int(row_ptr[-1].item()) & 0xFFFFFFFF
         h = ctypes.c_void_p()
+        if isinstance(options.get("update_dtype"), str):
+            options = dict(options, update_dtype=UPDATE_DTYPES[options["update_dtype"]])
         opt = _Options(**{k: int(v) for k, v in options.items()})
         _check(L.pcpm_build_ex(_dev_u32(row_ptr), _dev_u32(col), n, m, int(part_size), ctypes.byref(opt),
                                _stream(stream), ctypes.byref(h)), "pcpm_build")
@@ -257,7 +265,9 @@ class PNG:
         inf = self.info
         pr = np.empty(self.n, np.float32)
         spr = np.empty(self.n, np.float32)
-        upd = np.empty(max(inf["num_updates"], 1), np.float32)
+        # raw update bins: float32, float16 (SPR * 2^15) or bfloat16 bits as uint16
+        utype = {0: np.float32, 1: np.float16, 2: np.uint16}[inf["update_dtype"]]
+        upd = np.empty(max(inf["num_updates"], 1), utype)
         dang = ctypes.c_double(0.0)
         _check(lib().pcpm_export_state(self._h, pr.ctypes.data_as(ctypes.c_void_p),
                                        spr.ctypes.data_as(ctypes.c_void_p), upd.ctypes.data_as(ctypes.c_void_p),

@@ -62,10 +62,12 @@ int alloc_state(pcpm_png* g) {
     CK(dev_alloc(g, (void**)&g->pr[1], (size_t)n * sizeof(float)));
     // Update bins: two buffers (the fused iteration gathers one and scatters
     // the next), padded so a chunk's update slice may round up past the end.
-    CK(dev_alloc(g, (void**)&g->upd[0], (g->ne + 8) * sizeof(float)));
-    CK(dev_alloc(g, (void**)&g->upd[1], (g->ne + 8) * sizeof(float)));
-    CK(cudaMemset(g->upd[0], 0, (g->ne + 8) * sizeof(float)));
-    CK(cudaMemset(g->upd[1], 0, (g->ne + 8) * sizeof(float)));
+    // 16 spare entries: 16-byte update groups and slices never leave the buffer.
+    const size_t ubytes = (g->ne + 16) * g->upd_bytes;
+    CK(dev_alloc(g, (void**)&g->upd[0], ubytes));
+    CK(dev_alloc(g, (void**)&g->upd[1], ubytes));
+    CK(cudaMemset(g->upd[0], 0, ubytes));
+    CK(cudaMemset(g->upd[1], 0, ubytes));
     CK(dev_alloc(g, (void**)&g->partials, 2 * partial_slots(g) * sizeof(double)));
     CK(dev_alloc(g, (void**)&g->gacc, (size_t)n * sizeof(float)));
     CK(dev_alloc(g, (void**)&g->bin_done, (size_t)g->k * sizeof(uint32_t)));
@@ -207,6 +209,8 @@ int pcpm_build_ex(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t n, 
         opt.gather_cluster != 8)
         return PCPM_EINVAL;
     if (opt.gather_runs > 2) return PCPM_EINVAL;
+    if (opt.update_dtype > PCPM_UPDATE_BF16) return PCPM_EINVAL;
+    if (opt.update_dtype != PCPM_UPDATE_F32 && opt.canonical_gather) return PCPM_EINVAL;
     if (m > 0xFFFFFF00ull) return PCPM_EINVAL;
     const uint64_t k = ((uint64_t)n + part_size - 1) / part_size;
     if (k > PCPM_MAX_PARTITIONS) return PCPM_EINVAL;
@@ -232,6 +236,8 @@ int pcpm_build_ex(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t n, 
     g->m = m;
     g->last_stream = s;
     g->cluster = (int)opt.gather_cluster;
+    g->upd_dtype = (int)opt.update_dtype;
+    g->upd_bytes = opt.update_dtype == PCPM_UPDATE_F32 ? 4u : 2u;
     int rc = PCPM_OK;
     if (cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess) rc = PCPM_ECUDA;
     if (rc == PCPM_OK) rc = build_png(g, row_ptr, col_idx ? col_idx : row_ptr, opt, s);
@@ -275,6 +281,8 @@ int pcpm_png_get_info(const pcpm_png* g, pcpm_png_info* info) {
     info->canonical_gather = (uint32_t)g->canonical_gather;
     info->gather_runs = (uint32_t)g->gather_runs;
     info->merged_adds = g->merged_adds;
+    info->update_dtype = (uint32_t)g->upd_dtype;
+    info->update_bytes = g->upd_bytes;
     return PCPM_OK;
 }
 
@@ -436,7 +444,7 @@ int pcpm_scatter_only(pcpm_png* g, void* stream) {
     return PCPM_OK;
 }
 
-int pcpm_export_state(const pcpm_png* g, float* pr, float* spr, float* updates, double* dangling) {
+int pcpm_export_state(const pcpm_png* g, float* pr, float* spr, void* updates, double* dangling) {
     if (!g) return PCPM_EINVAL;
     CK(cudaStreamSynchronize(g->last_stream));
     if (pr) CK(cudaMemcpy(pr, g->pr[g->cur], (size_t)g->n * sizeof(float), cudaMemcpyDeviceToHost));
@@ -451,7 +459,7 @@ int pcpm_export_state(const pcpm_png* g, float* pr, float* spr, float* updates, 
         if (rc != PCPM_OK) return rc;
         if (e != cudaSuccess) return PCPM_ECUDA;
     }
-    if (updates && g->ne) CK(cudaMemcpy(updates, g->upd[g->ucur], g->ne * sizeof(float), cudaMemcpyDeviceToHost));
+    if (updates && g->ne) CK(cudaMemcpy(updates, g->upd[g->ucur], g->ne * g->upd_bytes, cudaMemcpyDeviceToHost));
     if (dangling) {
         DevState st;
         CK(cudaMemcpy(&st, g->state, sizeof(DevState), cudaMemcpyDeviceToHost));

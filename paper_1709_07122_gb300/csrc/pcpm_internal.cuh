@@ -24,7 +24,8 @@ constexpr uint32_t kHubMinInDegree = 64;
 // (the number of flagged IDs before it), so any warp can decode any chunk.
 constexpr uint32_t kChunk = 256;
 // Gather: a chunk needs the updates [base-1, next base) (the first ID may
-// continue the previous message), widened to 16-byte boundaries.
+// continue the previous message), widened to 16-byte boundaries: at most
+// kUpdSlot 4-byte updates, or 2 * kUpdSlot 2-byte ones (kChunk + 16 needed).
 constexpr uint32_t kUpdSlot = kChunk + 8;
 // Gather, bank-spread layout: one 32-bit word per destination ID holding an
 // accumulator slot (16 bits), the offset of its update in the chunk's update
@@ -40,11 +41,14 @@ constexpr uint32_t kGwUpdShift = 16;
 constexpr uint32_t kGwUpdMask = 0x1FFu;
 constexpr uint32_t kGwRunBit = 1u << 30;
 constexpr uint32_t kPadSlots = 32;
-static_assert(kUpdSlot <= kGwUpdMask + 1, "update offsets must fit their field");
+static_assert(kUpdSlot <= kGwUpdMask + 1 && kChunk + 16 <= kGwUpdMask + 1, "update offsets must fit their field");
 // Gather: warps per CTA and pipeline depth of each warp's private ring.
 constexpr int kGatherWarps = 24;
 constexpr int kGatherStages = 2;
 constexpr uint32_t kHubSlots = 2 * kGatherWarps;
+// Update bin storage: PCPM_UPDATE_F32, _F16 (SPR * 2^15), _BF16.
+constexpr int kUpdF32 = (int)PCPM_UPDATE_F32, kUpdF16 = (int)PCPM_UPDATE_F16, kUpdBF16 = (int)PCPM_UPDATE_BF16;
+constexpr float kF16Scale = (float)(1 << PCPM_F16_SCALE_LOG2);
 // Scatter: threads per CTA and 4-entry groups in flight per thread.
 constexpr int kScatterThreads = 1024;
 constexpr int kScatterUnroll = 4;
@@ -98,6 +102,8 @@ struct pcpm_png {
     // shared-memory banks as far as possible, in the word format of kGw*.
     int canonical_gather;    // 1: the gather decodes the canonical bins (MSB flags)
     int gather_runs;         // 1: the gather sums run-bit runs in a register
+    int upd_dtype;           // kUpd*: storage of the update bins
+    uint32_t upd_bytes;      // 4 or 2
     uint64_t merged_adds;    // IDs with bit 30 set
     uint32_t* gdest;         // nichunks * kChunk words
     uint32_t* gslice_start;  // nichunks: first update of the chunk's slice (multiple of 4)
@@ -122,7 +128,7 @@ struct pcpm_png {
     // solver state
     float* pr[2];            // ranks ping-pong
     int cur;                 // pr[cur] holds PR_i
-    float* upd[2];           // update bins (padded); upd[ucur] is the current one
+    void* upd[2];            // update bins (padded, upd_dtype); upd[ucur] is the current one
     int ucur;
     int upd_valid;           // upd[ucur] holds the scatter of PR_i
     int cluster;             // CTAs per gather unit (a thread-block cluster)

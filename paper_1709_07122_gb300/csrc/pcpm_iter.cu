@@ -28,6 +28,9 @@
 // the whole partition in shared memory and scatters it into the other update
 // buffer for the next iteration: gather, apply and the next scatter of one
 // partition in one launch, without writing SPR to memory.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include <algorithm>
 
 #include "pcpm_internal.cuh"
@@ -191,6 +194,51 @@ __device__ __forceinline__ void st_stream_f4(float* p, float4 v) {
                  : "memory");
 }
 
+__device__ __forceinline__ void st_stream_u2(void* p, uint32_t a, uint32_t b) {
+    asm volatile("st.global.cs.v2.u32 [%0], {%1, %2};" ::"l"(p), "r"(a), "r"(b) : "memory");
+}
+
+// ------------------------------------------------------------ update bins
+// One update as stored (PCPM_UPDATE_*): the FP32 SPR value, IEEE binary16 of
+// SPR * 2^15 (saturating at the largest finite half) or bfloat16 of SPR, both
+// rounded to nearest even. The gather adds the stored values in FP32 and
+// multiplies the sum by acc_scale.
+template <int kUpd>
+struct Upd;
+template <>
+struct Upd<kUpdF32> {
+    using T = float;
+    static constexpr float acc_scale = 1.0f;
+    __device__ static float load(const T* p, uint32_t i) { return p[i]; }
+    __device__ static T from(float x) { return x; }
+    __device__ static void store4(T* p, uint32_t e, float a, float b, float c, float d) {
+        st_stream_f4(p + e, make_float4(a, b, c, d));
+    }
+};
+template <>
+struct Upd<kUpdF16> {
+    using T = __half;
+    static constexpr float acc_scale = 1.0f / kF16Scale;
+    __device__ static float load(const T* p, uint32_t i) { return __half2float(p[i]); }
+    __device__ static T from(float x) { return __float2half_rn(fminf(x * kF16Scale, 65504.0f)); }
+    __device__ static void store4(T* p, uint32_t e, float a, float b, float c, float d) {
+        st_stream_u2(p + e, (uint32_t)__half_as_ushort(from(a)) | ((uint32_t)__half_as_ushort(from(b)) << 16),
+                     (uint32_t)__half_as_ushort(from(c)) | ((uint32_t)__half_as_ushort(from(d)) << 16));
+    }
+};
+template <>
+struct Upd<kUpdBF16> {
+    using T = __nv_bfloat16;
+    static constexpr float acc_scale = 1.0f;
+    __device__ static float load(const T* p, uint32_t i) { return __bfloat162float(p[i]); }
+    __device__ static T from(float x) { return __float2bfloat16_rn(x); }
+    __device__ static void store4(T* p, uint32_t e, float a, float b, float c, float d) {
+        st_stream_u2(p + e,
+                     (uint32_t)__bfloat16_as_ushort(from(a)) | ((uint32_t)__bfloat16_as_ushort(from(b)) << 16),
+                     (uint32_t)__bfloat16_as_ushort(from(c)) | ((uint32_t)__bfloat16_as_ushort(from(d)) << 16));
+    }
+};
+
 // Deterministic block sum of two doubles; result valid in thread 0. `scratch`
 // is 2 * kThreads / 32 doubles of shared memory.
 template <int kThreads>
@@ -286,13 +334,17 @@ __device__ __forceinline__ uint32_t segment_at(const uint32_t* gpre, uint32_t k,
 // partition's flattened segment list (Algorithm 3). Each warp takes a
 // contiguous run of groups, 32 * kScatterUnroll at a time, so the groups of
 // one step span only a few segments: the warp tracks the segment of its
-// current position and each lane walks forward from it.
+// current position and each lane walks forward from it. Updates are stored as
+// Upd<kUpd>.
+template <int kUpd>
 __device__ __forceinline__ void scatter_groups(const float* sspr, uint32_t base, uint32_t len,
                                                const uint32_t* gpre, uint32_t k,
                                                const uint32_t* __restrict__ segrow,
                                                const uint32_t* __restrict__ cntrow,
-                                               const uint32_t* __restrict__ src, float* __restrict__ upd,
+                                               const uint32_t* __restrict__ src, void* __restrict__ upd_raw,
                                                uint32_t f_lo, uint32_t f_hi, int* err) {
+    using U = Upd<kUpd>;
+    typename U::T* upd = reinterpret_cast<typename U::T*>(upd_raw);
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const uint32_t span = f_hi - f_lo;
     const uint32_t w_lo = f_lo + (uint32_t)((uint64_t)span * warp / nw);
@@ -324,7 +376,7 @@ __device__ __forceinline__ void scatter_groups(const float* sspr, uint32_t base,
             if (full[u]) {
                 const uint32_t i0 = ids[u].x - base, i1 = ids[u].y - base, i2 = ids[u].z - base, i3 = ids[u].w - base;
                 if (i0 < len && i1 < len && i2 < len && i3 < len)
-                    st_stream_f4(upd + e0[u], make_float4(sspr[i0], sspr[i1], sspr[i2], sspr[i3]));
+                    U::store4(upd, e0[u], sspr[i0], sspr[i1], sspr[i2], sspr[i3]);
                 else
                     atomicOr(err, kErrBounds);
             } else {
@@ -333,7 +385,7 @@ __device__ __forceinline__ void scatter_groups(const float* sspr, uint32_t base,
                     const uint32_t e = e0[u] + j;
                     if (e >= s0[u] && e < s0[u] + c0[u]) {
                         const uint32_t i = src[e] - base;
-                        if (i < len) upd[e] = sspr[i]; else atomicOr(err, kErrBounds);
+                        if (i < len) upd[e] = U::from(sspr[i]); else atomicOr(err, kErrBounds);
                     }
                 }
             }
@@ -366,10 +418,11 @@ __global__ void spr_kernel(uint32_t n, const float* __restrict__ pr, const float
 }
 
 // --------------------------------------------------------------- scatter
+template <int kUpd>
 __global__ void __launch_bounds__(kScatterThreads, 1) scatter_kernel(
     uint32_t n, uint32_t q, uint32_t k, const float* __restrict__ pr, const float* __restrict__ inv_deg,
     const uint32_t* __restrict__ src, const uint32_t* __restrict__ seg_u, const uint32_t* __restrict__ cnt_u,
-    const uint4* __restrict__ units, const uint32_t* __restrict__ order, float* __restrict__ upd,
+    const uint4* __restrict__ units, const uint32_t* __restrict__ order, void* __restrict__ upd,
     const DevState* __restrict__ st, int* __restrict__ err) {
     if (st->stop) return;
     extern __shared__ __align__(128) unsigned char smraw[];
@@ -410,7 +463,7 @@ __global__ void __launch_bounds__(kScatterThreads, 1) scatter_kernel(
         for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) sspr[i] = pr[base + i] * inv_deg[base + i];
     }
     segment_groups_prefix(segrow, cntrow, k, gpre, sh32);
-    scatter_groups(sspr, base, len, gpre, k, segrow, cntrow, src, upd, unit.y, min(unit.z, gpre[k]), err);
+    scatter_groups<kUpd>(sspr, base, len, gpre, k, segrow, cntrow, src, upd, unit.y, min(unit.z, gpre[k]), err);
 }
 
 // ---------------------------------------------------------- gather+apply
@@ -427,7 +480,7 @@ struct GatherArgs {
     const uint32_t* hubs;
     float* gacc;
     uint32_t* bin_done;
-    const float* upd_in;
+    const void* upd_in;
     const float* pr_in;
     const float* inv_deg;
     float* pr_out;
@@ -440,7 +493,7 @@ struct GatherArgs {
     const uint32_t* src;
     const uint32_t* seg_u;
     const uint32_t* cnt_u;
-    float* upd_out;
+    void* upd_out;
 };
 
 constexpr uint32_t kIdSlotBytes = kChunk * sizeof(uint32_t);
@@ -457,9 +510,12 @@ static_assert(kStageBytes % 16 == 0, "ring slots must stay 16-byte aligned");
 static_assert(kAccOffset % 16 == 0, "accumulator must be 16-byte aligned");
 
 // kFused: also scatter the next iteration; kCanon: decode the canonical bins;
-// kRuns: sum bit-30 runs of the bank-spread layout in a register.
-template <bool kFused, bool kCanon, bool kRuns>
+// kRuns: sum run-bit runs of the bank-spread layout in a register; kUpd: the
+// update bins' storage (canonical bins: FP32 only).
+template <bool kFused, bool kCanon, bool kRuns, int kUpd>
 __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const GatherArgs a) {
+    using U = Upd<kUpd>;
+    static_assert(!kCanon || kUpd == kUpdF32, "the canonical gather reads FP32 updates");
     if (a.st->stop) return;
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ uint32_t sh32[32];
@@ -558,7 +614,9 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
                 const uint32_t* ids = (kCanon ? a.dest : a.gdest) + (size_t)(wc0 + j) * kChunk;
                 mbar_arrive_expect_tx(&wbar[slot], kIdSlotBytes + ubytes);
                 bulk_load_hint(dst, ids, kIdSlotBytes, &wbar[slot], stream_policy);
-                if (ubytes) bulk_load_hint(dst + kIdSlotBytes, a.upd_in + us, ubytes, &wbar[slot], stream_policy);
+                if (ubytes)
+                    bulk_load_hint(dst + kIdSlotBytes, static_cast<const typename U::T*>(a.upd_in) + us, ubytes,
+                                   &wbar[slot], stream_policy);
             }
         };
 
@@ -573,7 +631,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
             if (!ok) break;
             const unsigned char* stage = wring + (size_t)slot * kStageBytes;
             const uint32_t* ids_s = reinterpret_cast<const uint32_t*>(stage);
-            const float* ups = reinterpret_cast<const float*>(stage + kIdSlotBytes);
+            const typename U::T* ups = reinterpret_cast<const typename U::T*>(stage + kIdSlotBytes);
             constexpr int kPer = kChunk / 32;  // IDs per lane
             // All loads of the chunk first (IDs, then update values), then the
             // adds: eight independent shared-memory operations per lane.
@@ -637,7 +695,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
             }
             float val[kPer];
 #pragma unroll
-            for (int q = 0; q < kPer; ++q) val[q] = ups[(!kCanon || (valid >> q & 1u)) ? uo[q] : 0u];
+            for (int q = 0; q < kPer; ++q) val[q] = U::load(ups, (!kCanon || (valid >> q & 1u)) ? uo[q] : 0u);
             [[maybe_unused]] float run = 0.0f;  // kRuns: sum of a run of equal destinations in this lane
 #pragma unroll
             for (int q = 0; q < kPer; ++q) {
@@ -728,6 +786,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
 
     const double D = a.uniform_dangling ? a.st->dangling : 0.0;
     const float cst = (float)((1.0 - (double)a.d) / (double)a.n + (double)a.d * D / (double)a.n);
+    const float d_acc = a.d * U::acc_scale;  // exact: the scale is a power of two
     // Per-thread partial sums of at most len / blockDim terms in FP32 (FP64
     // arithmetic is slow on this part); thread and block totals in FP64.
     float res_f = 0.0f, dg_f = 0.0f;
@@ -752,7 +811,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
             for (int j = 0; j < kApplyIlp; ++j) {
                 const uint32_t i = i0 + j * blockDim.x;
                 if (i < hi) {
-                    const float x = fmaf(a.d, s[j], cst);
+                    const float x = fmaf(d_acc, s[j], cst);
                     a.pr_out[vbase + i] = x;
                     if (kFused) acc[i] = x * inv[j];
                     res_f += fabsf(x - old[j]);
@@ -792,7 +851,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
                 for (int j = 0; j < kApplyIlp; ++j) {
                     const uint32_t i = i0 + j * blockDim.x;
                     if (i < len) {
-                        const float x = fmaf(a.d, s[j], cst);
+                        const float x = fmaf(d_acc, s[j], cst);
                         a.gacc[vbase + i] = 0.0f;
                         a.pr_out[vbase + i] = x;
                         res_f += fabsf(x - old[j]);
@@ -844,7 +903,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
         const uint32_t G = gpre[a.k];
         const uint32_t f_lo = (uint32_t)((uint64_t)G * rank / S);
         const uint32_t f_hi = (uint32_t)((uint64_t)G * (rank + 1) / S);
-        scatter_groups(acc, vbase, len, gpre, a.k, segrow, cntrow, a.src, a.upd_out, f_lo, f_hi, a.err);
+        scatter_groups<kUpd>(acc, vbase, len, gpre, a.k, segrow, cntrow, a.src, a.upd_out, f_lo, f_hi, a.err);
     } else {
         if (!push) cluster_sync();  // remote loads of this CTA's shared memory are done
     }
@@ -874,6 +933,23 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_kernel(const double* __
 
 constexpr int kInitBlocks = 1024;
 
+using GatherFn = void (*)(const GatherArgs);
+
+// The gather instantiation for a layout and update type (the canonical bins
+// hold FP32 updates only).
+template <bool kFused>
+GatherFn pick_gather(bool canonical, bool runs, int upd) {
+    if (canonical) return gather_kernel<kFused, true, false, kUpdF32>;
+    switch (upd) {
+        case kUpdF16:
+            return runs ? gather_kernel<kFused, false, true, kUpdF16> : gather_kernel<kFused, false, false, kUpdF16>;
+        case kUpdBF16:
+            return runs ? gather_kernel<kFused, false, true, kUpdBF16> : gather_kernel<kFused, false, false, kUpdBF16>;
+        default:
+            return runs ? gather_kernel<kFused, false, true, kUpdF32> : gather_kernel<kFused, false, false, kUpdF32>;
+    }
+}
+
 // The accumulator holds q real slots, kPadSlots for the layout's padding and
 // kHubSlots (a pair per warp) for the hubs.
 size_t gather_smem_bytes(uint32_t q) {
@@ -892,17 +968,22 @@ size_t partial_slots(const pcpm_png* g) {
 // Picks the cluster size for the gather and sets shared-memory limits.
 int configure_kernels(pcpm_png* g) {
     const size_t gs = gather_smem_bytes(g->q), ss = scatter_smem_bytes(g->q, g->k);
-    const void* gathers[] = {(const void*)gather_kernel<false, false, false>,
-                             (const void*)gather_kernel<true, false, false>,
-                             (const void*)gather_kernel<false, false, true>,
-                             (const void*)gather_kernel<true, false, true>,
-                             (const void*)gather_kernel<false, true, false>,
-                             (const void*)gather_kernel<true, true, false>};
+    const void* gathers[] = {
+        (const void*)gather_kernel<false, true, false, kUpdF32>, (const void*)gather_kernel<true, true, false, kUpdF32>,
+        (const void*)pick_gather<false>(false, false, kUpdF32), (const void*)pick_gather<true>(false, false, kUpdF32),
+        (const void*)pick_gather<false>(false, true, kUpdF32),  (const void*)pick_gather<true>(false, true, kUpdF32),
+        (const void*)pick_gather<false>(false, false, kUpdF16), (const void*)pick_gather<true>(false, false, kUpdF16),
+        (const void*)pick_gather<false>(false, true, kUpdF16),  (const void*)pick_gather<true>(false, true, kUpdF16),
+        (const void*)pick_gather<false>(false, false, kUpdBF16), (const void*)pick_gather<true>(false, false, kUpdBF16),
+        (const void*)pick_gather<false>(false, true, kUpdBF16), (const void*)pick_gather<true>(false, true, kUpdBF16)};
     for (const void* f : gathers)
         if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gs) != cudaSuccess)
             return PCPM_ECUDA;
-    if (cudaFuncSetAttribute(scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss) != cudaSuccess)
-        return PCPM_ECUDA;
+    const void* scatters[] = {(const void*)scatter_kernel<kUpdF32>, (const void*)scatter_kernel<kUpdF16>,
+                              (const void*)scatter_kernel<kUpdBF16>};
+    for (const void* f : scatters)
+        if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss) != cudaSuccess)
+            return PCPM_ECUDA;
     // Two CTAs per gather unit unless the build options ask otherwise (two
     // measured best at k = 512 against one and four); smaller if the device
     // cannot co-schedule that many.
@@ -920,7 +1001,7 @@ int configure_kernels(pcpm_png* g) {
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int clusters = 0;
-        if (cudaOccupancyMaxActiveClusters(&clusters, gather_kernel<true, false, false>, &cfg) == cudaSuccess &&
+        if (cudaOccupancyMaxActiveClusters(&clusters, gather_kernel<true, false, false, kUpdF32>, &cfg) == cudaSuccess &&
             clusters > 0) {
             g->cluster = S;
             return PCPM_OK;
@@ -944,9 +1025,15 @@ int launch_spr(pcpm_png* g, float* spr, cudaStream_t s) {
 }
 
 int launch_scatter(pcpm_png* g, cudaStream_t s) {
-    scatter_kernel<<<g->nsunits, kScatterThreads, scatter_smem_bytes(g->q, g->k), s>>>(
-        g->n, g->q, g->k, g->pr[g->cur], g->inv_deg, g->src, g->seg_u, g->cnt_u, g->sunits, g->sorder,
-        g->upd[g->ucur], g->state, &g->state->err);
+    const size_t smem = scatter_smem_bytes(g->q, g->k);
+    void (*f)(uint32_t, uint32_t, uint32_t, const float*, const float*, const uint32_t*, const uint32_t*,
+              const uint32_t*, const uint4*, const uint32_t*, void*, const DevState*, int*) =
+        g->upd_dtype == kUpdF16 ? scatter_kernel<kUpdF16>
+        : g->upd_dtype == kUpdBF16 ? scatter_kernel<kUpdBF16>
+                                   : scatter_kernel<kUpdF32>;
+    f<<<g->nsunits, kScatterThreads, smem, s>>>(g->n, g->q, g->k, g->pr[g->cur], g->inv_deg, g->src, g->seg_u,
+                                               g->cnt_u, g->sunits, g->sorder, g->upd[g->ucur], g->state,
+                                               &g->state->err);
     return cudaGetLastError() == cudaSuccess ? PCPM_OK : PCPM_ECUDA;
 }
 
@@ -993,15 +1080,9 @@ int launch_gather(pcpm_png* g, float d, uint32_t flags, bool fused, cudaStream_t
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     cudaError_t e;
-    if (g->canonical_gather)
-        e = fused ? cudaLaunchKernelEx(&cfg, gather_kernel<true, true, false>, a)
-                  : cudaLaunchKernelEx(&cfg, gather_kernel<false, true, false>, a);
-    else if (g->gather_runs)
-        e = fused ? cudaLaunchKernelEx(&cfg, gather_kernel<true, false, true>, a)
-                  : cudaLaunchKernelEx(&cfg, gather_kernel<false, false, true>, a);
-    else
-        e = fused ? cudaLaunchKernelEx(&cfg, gather_kernel<true, false, false>, a)
-                  : cudaLaunchKernelEx(&cfg, gather_kernel<false, false, false>, a);
+    const GatherFn f = fused ? pick_gather<true>(g->canonical_gather != 0, g->gather_runs != 0, g->upd_dtype)
+                             : pick_gather<false>(g->canonical_gather != 0, g->gather_runs != 0, g->upd_dtype);
+    e = cudaLaunchKernelEx(&cfg, f, a);
     g->partial_count = (int)(g->ngunits * g->cluster);
     return e == cudaSuccess ? PCPM_OK : PCPM_ECUDA;
 }

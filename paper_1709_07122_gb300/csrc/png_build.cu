@@ -485,7 +485,7 @@ __global__ void __launch_bounds__(kLayoutWarps * 32) gather_layout_kernel(
     const uint32_t* __restrict__ dest, const uint32_t* __restrict__ bin_e, const uint32_t* __restrict__ ichunk_start,
     uint32_t k, const uint32_t* __restrict__ chunk_base, const uint32_t* __restrict__ hubs, uint32_t q,
     uint64_t nichunks, uint32_t* __restrict__ gdest, uint32_t* __restrict__ slice_start,
-    uint32_t* __restrict__ slice_bytes, unsigned long long* __restrict__ stats) {
+    uint32_t* __restrict__ slice_bytes, uint32_t upd_bytes, unsigned long long* __restrict__ stats) {
     __shared__ uint32_t keycnt[kLayoutWarps][kNumKeys + 2];
     __shared__ uint32_t sortbuf[kLayoutWarps][kChunk];
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -526,7 +526,9 @@ __global__ void __launch_bounds__(kLayoutWarps * 32) gather_layout_kernel(
             const uint32_t x = __shfl_sync(0xffffffffu, idx[r], (n - 1) & 31);
             if ((uint32_t)r == (n - 1) / 32) u_last = x;
         }
-        const uint32_t us = u_first & ~3u, ue = (u_last + 4) & ~3u;
+        // the chunk's update slice, widened to 16-byte boundaries
+        const uint32_t align = 16u / upd_bytes, slot_max = min((kUpdSlot * 4u) / upd_bytes, kGwUpdMask + 1);
+        const uint32_t us = u_first & ~(align - 1), ue = (u_last + align) & ~(align - 1);
         // counting sort by key, stable in (round, lane) order
         for (uint32_t j = lane; j < kNumKeys; j += 32) cnt[j] = 0;
         __syncwarp();
@@ -558,7 +560,7 @@ __global__ void __launch_bounds__(kLayoutWarps * 32) gather_layout_kernel(
             // banks within a round); hubs: the hub slot pair
             const uint32_t slot = key[r] == kKeyHub ? q + kPadSlots + (loc[r] == h1 ? 1u : 0u) : loc[r];
             sorted[pos] = key[r] == kKeyPad ? q + (pos >> 3) : (slot | ((idx[r] - us) << kGwUpdShift));
-            if (key[r] != kKeyPad && (loc[r] >= q || idx[r] - us >= kUpdSlot)) bad = true;
+            if (key[r] != kKeyPad && (loc[r] >= q || idx[r] - us >= slot_max)) bad = true;
         }
         __syncwarp();
         // cnt[j] now holds the end of group j; group j starts at cnt[j - 1].
@@ -594,8 +596,8 @@ __global__ void __launch_bounds__(kLayoutWarps * 32) gather_layout_kernel(
         }
         if (lane == 0) {
             slice_start[ic] = us;
-            slice_bytes[ic] = (ue - us) * (uint32_t)sizeof(float);
-            if (ue - us > kUpdSlot) bad = true;
+            slice_bytes[ic] = (ue - us) * upd_bytes;
+            if (ue - us > slot_max) bad = true;
         }
         __syncwarp();
     }
@@ -832,7 +834,7 @@ int build_png(pcpm_png* g, const uint32_t* row_ptr, const uint32_t* col, const p
         if (nic) {
             gather_layout_kernel<<<grid_for((uint64_t)nic * 32, kLayoutWarps * 32, sms * 8), kLayoutWarps * 32, 0, s>>>(
                 g->dest, g->bin_e, g->ichunk_start, k, g->chunk_base, g->hubs, q, nic, g->gdest, g->gslice_start,
-                g->gslice_bytes, lstats);
+                g->gslice_bytes, g->upd_bytes, lstats);
             BCK(cudaGetLastError());
         }
         unsigned long long hstats[2] = {0, 0};
