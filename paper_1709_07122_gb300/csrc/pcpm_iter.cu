@@ -41,6 +41,8 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 // Nodes per thread in flight in the apply loop.
 constexpr int kApplyIlp = 8;
+// Groups of four nodes per thread in flight in the vectorised apply.
+constexpr int kApplyVec = 4;
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t r;
@@ -790,10 +792,57 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
     // Per-thread partial sums of at most len / blockDim terms in FP32 (FP64
     // arithmetic is slow on this part); thread and block totals in FP64.
     float res_f = 0.0f, dg_f = 0.0f;
+    // Apply to one node: PR', residual and dangling terms, SPR' for the fused scatter.
+    auto apply1 = [&](uint32_t i, float s, float old, float inv) -> float {
+        const float x = fmaf(d_acc, s, cst);
+        if (kFused) acc[i] = x * inv;
+        res_f += fabsf(x - old);
+        if (inv == 0.0f) dg_f += x;
+        return x;
+    };
+    // Nodes [lo, vec_end) go four at a time with 16-byte loads and stores
+    // (the partition starts on a 16-byte boundary), kApplyVec groups of
+    // four in flight per thread; the rest one at a time.
+    const uint32_t vec_end = (npieces == 1 && (vbase & 3u) == 0) ? lo + ((hi - lo) & ~3u) : lo;
+    for (uint32_t i0 = lo + 4 * threadIdx.x; i0 < vec_end; i0 += 4 * kApplyVec * blockDim.x) {
+        float4 o[kApplyVec], w[kApplyVec], s[kApplyVec];
+#pragma unroll
+        for (int j = 0; j < kApplyVec; ++j) {
+            const uint32_t i = i0 + 4 * j * blockDim.x;
+            if (i < vec_end) {
+                o[j] = __ldg(reinterpret_cast<const float4*>(a.pr_in + vbase + i));
+                w[j] = __ldg(reinterpret_cast<const float4*>(a.inv_deg + vbase + i));
+                if (push) {
+                    s[j] = *reinterpret_cast<const float4*>(acc + i);
+                    for (uint32_t q = 0; q + 1 < S; ++q) {
+                        const float4 t = *reinterpret_cast<const float4*>(stage + (size_t)q * per + (i - lo));
+                        s[j].x += t.x;
+                        s[j].y += t.y;
+                        s[j].z += t.z;
+                        s[j].w += t.w;
+                    }
+                } else {
+                    s[j] = make_float4(merged(i), merged(i + 1), merged(i + 2), merged(i + 3));
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kApplyVec; ++j) {
+            const uint32_t i = i0 + 4 * j * blockDim.x;
+            if (i < vec_end) {
+                float4 x;
+                x.x = apply1(i, s[j].x, o[j].x, w[j].x);
+                x.y = apply1(i + 1, s[j].y, o[j].y, w[j].y);
+                x.z = apply1(i + 2, s[j].z, o[j].z, w[j].z);
+                x.w = apply1(i + 3, s[j].w, o[j].w, w[j].w);
+                *reinterpret_cast<float4*>(a.pr_out + vbase + i) = x;
+            }
+        }
+    }
     if (npieces == 1) {
-        // Apply: kApplyIlp independent nodes per thread per round, their loads
-        // in flight together.
-        for (uint32_t i0 = lo + threadIdx.x; i0 < hi; i0 += kApplyIlp * blockDim.x) {
+        // The remaining nodes: kApplyIlp independent nodes per thread per
+        // round, their loads in flight together.
+        for (uint32_t i0 = vec_end + threadIdx.x; i0 < hi; i0 += kApplyIlp * blockDim.x) {
             float s[kApplyIlp], old[kApplyIlp], inv[kApplyIlp];
 #pragma unroll
             for (int j = 0; j < kApplyIlp; ++j) {
@@ -810,13 +859,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
 #pragma unroll
             for (int j = 0; j < kApplyIlp; ++j) {
                 const uint32_t i = i0 + j * blockDim.x;
-                if (i < hi) {
-                    const float x = fmaf(d_acc, s[j], cst);
-                    a.pr_out[vbase + i] = x;
-                    if (kFused) acc[i] = x * inv[j];
-                    res_f += fabsf(x - old[j]);
-                    if (inv[j] == 0.0f) dg_f += x;
-                }
+                if (i < hi) a.pr_out[vbase + i] = apply1(i, s[j], old[j], inv[j]);
             }
         }
     } else {
