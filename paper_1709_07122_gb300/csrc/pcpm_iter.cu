@@ -41,8 +41,10 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 // Nodes per thread in flight in the apply loop.
 constexpr int kApplyIlp = 8;
-// Groups of four nodes per thread in flight in the vectorised apply.
+// Groups of four nodes per thread in flight in the vectorised apply (and in
+// the apply of a bin cut into several units, done by one CTA).
 constexpr int kApplyVec = 4;
+constexpr int kApplyVecCut = 2;
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t r;
@@ -193,6 +195,12 @@ __device__ __forceinline__ uint4 ld_stream_u4(const uint32_t* p) {
 
 __device__ __forceinline__ void st_stream_f4(float* p, float4 v) {
     asm volatile("st.global.cs.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+
+// Vector FP32 reduction into global memory (p 16-byte aligned).
+__device__ __forceinline__ void red_add_v4(float* p, float4 v) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
                  : "memory");
 }
 
@@ -785,6 +793,19 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
         }
         return s;
     };
+    // The same for nodes i .. i+3 (i - lo a multiple of 4).
+    auto merged4 = [&](uint32_t i) -> float4 {
+        if (!push) return make_float4(merged(i), merged(i + 1), merged(i + 2), merged(i + 3));
+        float4 s = *reinterpret_cast<const float4*>(acc + i);
+        for (uint32_t q = 0; q + 1 < S; ++q) {
+            const float4 t = *reinterpret_cast<const float4*>(stage + (size_t)q * per + (i - lo));
+            s.x += t.x;
+            s.y += t.y;
+            s.z += t.z;
+            s.w += t.w;
+        }
+        return s;
+    };
 
     const double D = a.uniform_dangling ? a.st->dangling : 0.0;
     const float cst = (float)((1.0 - (double)a.d) / (double)a.n + (double)a.d * D / (double)a.n);
@@ -812,18 +833,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
             if (i < vec_end) {
                 o[j] = __ldg(reinterpret_cast<const float4*>(a.pr_in + vbase + i));
                 w[j] = __ldg(reinterpret_cast<const float4*>(a.inv_deg + vbase + i));
-                if (push) {
-                    s[j] = *reinterpret_cast<const float4*>(acc + i);
-                    for (uint32_t q = 0; q + 1 < S; ++q) {
-                        const float4 t = *reinterpret_cast<const float4*>(stage + (size_t)q * per + (i - lo));
-                        s[j].x += t.x;
-                        s[j].y += t.y;
-                        s[j].z += t.z;
-                        s[j].w += t.w;
-                    }
-                } else {
-                    s[j] = make_float4(merged(i), merged(i + 1), merged(i + 2), merged(i + 3));
-                }
+                s[j] = merged4(i);
             }
         }
 #pragma unroll
@@ -866,7 +876,13 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
         // The bin is cut into several units: add this unit's sums to the
         // global partial sums; the last CTA to arrive applies the partition.
         uint32_t& last = sh32[0];
-        for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const bool aligned = (vbase & 3u) == 0;
+        const uint32_t gv_end = aligned ? lo + ((hi - lo) & ~3u) : lo;
+        for (uint32_t i = lo + 4 * threadIdx.x; i < gv_end; i += 4 * blockDim.x) {
+            const float4 s = merged4(i);
+            if (s.x != 0.0f || s.y != 0.0f || s.z != 0.0f || s.w != 0.0f) red_add_v4(a.gacc + vbase + i, s);
+        }
+        for (uint32_t i = gv_end + threadIdx.x; i < hi; i += blockDim.x) {
             const float s = merged(i);
             if (s != 0.0f) atomicAdd(&a.gacc[vbase + i], s);
         }
@@ -876,7 +892,35 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
         __syncthreads();
         if (last) {
             __threadfence();
-            for (uint32_t i0 = threadIdx.x; i0 < len; i0 += kApplyIlp * blockDim.x) {
+            // The whole partition from the global sums: four nodes at a time
+            // where the partition starts on a 16-byte boundary, then the rest.
+            const uint32_t av_end = aligned ? (len & ~3u) : 0;
+            for (uint32_t i0 = 4 * threadIdx.x; i0 < av_end; i0 += 4 * kApplyVecCut * blockDim.x) {
+                float4 o[kApplyVecCut], w[kApplyVecCut], s[kApplyVecCut];
+#pragma unroll
+                for (int j = 0; j < kApplyVecCut; ++j) {
+                    const uint32_t i = i0 + 4 * j * blockDim.x;
+                    if (i < av_end) {
+                        s[j] = __ldcg(reinterpret_cast<const float4*>(a.gacc + vbase + i));
+                        o[j] = __ldg(reinterpret_cast<const float4*>(a.pr_in + vbase + i));
+                        w[j] = __ldg(reinterpret_cast<const float4*>(a.inv_deg + vbase + i));
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < kApplyVecCut; ++j) {
+                    const uint32_t i = i0 + 4 * j * blockDim.x;
+                    if (i < av_end) {
+                        float4 x;
+                        x.x = apply1(i, s[j].x, o[j].x, w[j].x);
+                        x.y = apply1(i + 1, s[j].y, o[j].y, w[j].y);
+                        x.z = apply1(i + 2, s[j].z, o[j].z, w[j].z);
+                        x.w = apply1(i + 3, s[j].w, o[j].w, w[j].w);
+                        *reinterpret_cast<float4*>(a.gacc + vbase + i) = make_float4(0.f, 0.f, 0.f, 0.f);
+                        *reinterpret_cast<float4*>(a.pr_out + vbase + i) = x;
+                    }
+                }
+            }
+            for (uint32_t i0 = av_end + threadIdx.x; i0 < len; i0 += kApplyIlp * blockDim.x) {
                 float s[kApplyIlp], old[kApplyIlp], inv[kApplyIlp];
 #pragma unroll
                 for (int j = 0; j < kApplyIlp; ++j) {
