@@ -1,0 +1,84 @@
+/* pcpm_warmstart.h - learned warm start for PCPM PageRank (C ABI).
+ *
+ * Not in the paper. PageRank by power iteration (Eq. 1) normally starts from
+ * the uniform vector 1/n. A small per-node network predicts log(n * PR*(v))
+ * from cheap features of the graph, and the iteration starts from the
+ * softmax of the prediction (pcpm_pagerank's pr_init) instead; it converges to
+ * the same fixed point, and the plain uniform start stays the reference.
+ *
+ * Features of node v, PCPM_WS_FEATURES = 5, row-major float[n][5]:
+ *   0  log1p(indeg(v))
+ *   1  log1p(outdeg(v))
+ *   2  log1p(sum of indeg(u) over in-neighbours u)    (exact integer sum)
+ *   3  log1p(sum of outdeg(u) over in-neighbours u)   (exact integer sum)
+ *   4  log(n * PR_1(v)), PR_1 one Eq. 1 step from the uniform start on the
+ *      handle (d = 0.85, dangling mass spread uniformly)
+ * Network: standardise x^ = (x - mu) * inv_sigma; h1 = relu(W1 x^ + b1);
+ * h2 = relu(W2 h1 + b2); y = w3 . h2 + b3 (width PCPM_WS_HIDDEN = 64).
+ * Parameters: one float array of PCPM_WS_PARAMS entries, in this order:
+ *   mu[5], inv_sigma[5], W1[64][5], b1[64], W2[64][64], b2[64], w3[64], b3.
+ * mu and inv_sigma are set by the caller and not trained.
+ *
+ * All pointers are device memory unless stated; every call is enqueued on
+ * `stream` and returns PCPM_* status codes of pcpm.h.
+ */
+#ifndef PCPM_WARMSTART_H
+#define PCPM_WARMSTART_H
+
+#include <stdint.h>
+
+#include "pcpm.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PCPM_WS_FEATURES 5
+#define PCPM_WS_HIDDEN 64
+#define PCPM_WS_PARAMS (2 * 5 + 64 * 5 + 64 + 64 * 64 + 64 + 64 + 1)
+/* first trainable entry (W1) */
+#define PCPM_WS_TRAINABLE_OFFSET 10
+
+/* Features of every node of the graph the handle was built from.
+ *   row_ptr, col  the device CSR given to pcpm_build (uint32[n+1], uint32[m]).
+ *   features      float[n][5], written.
+ * Resets the handle's solver state and runs one iteration on it (PR_1).
+ * Allocates and frees device scratch (24 bytes per node). Synchronises. */
+int pcpm_ws_features(pcpm_png* png, const uint32_t* row_ptr, const uint32_t* col, float* features,
+                     void* stream);
+
+/* Training targets: target(v) = log(n * pr(v)) computed in FP64 and rounded
+ * to float, for ranks pr (float[n], positive) of a graph of n nodes. */
+int pcpm_ws_targets(const float* pr, uint32_t n, float* target, void* stream);
+
+/* Network output for n feature rows, with W1, b1, W2, b2, w3, b3 rounded to
+ * bfloat16 (nearest even) and FP32 accumulation.
+ *   params float[PCPM_WS_PARAMS]; features float[n][5]; out float[n]. */
+int pcpm_ws_predict(const float* params, const float* features, uint32_t n, float* out, void* stream);
+
+/* Mean-squared-error loss L = sum_v (y(v) - target(v))^2 / n over n rows, with
+ * FP32 weights, and its gradient.
+ *   grad  float[PCPM_WS_PARAMS]: zeroed by the call, then dL/dparams (0 for
+ *         mu and inv_sigma).
+ *   loss  double[1]: written.
+ * FP32 arithmetic; per-tile sums of the gradient are added with atomics, so
+ * the last bits depend on the order. */
+int pcpm_ws_loss_grad(const float* params, const float* features, const float* target, uint32_t n,
+                      float* grad, double* loss, void* stream);
+
+/* One Adam step (Kingma and Ba, 2015) on the trainable entries, step >= 1.
+ *   m, v  float[PCPM_WS_PARAMS] first and second moments, updated in place. */
+int pcpm_ws_adam(float* params, const float* grad, float* m, float* v, int step, float lr, float beta1,
+                 float beta2, float eps, void* stream);
+
+/* Initial ranks from predictions: pr(v) = exp(p(v)) / sum_u exp(p(u)) with
+ * p = pred clamped to [-80, 80] (so no term overflows FP32), the sum in FP64.
+ * pred: float[n]; pr: float[n]. Allocates 8 bytes of device scratch.
+ * Synchronises. */
+int pcpm_ws_init_ranks(const float* pred, uint32_t n, float* pr, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PCPM_WARMSTART_H */

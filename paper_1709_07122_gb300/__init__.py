@@ -92,6 +92,12 @@ def lib(path: str | None = None):
                 "pcpm_export_state": (i32, [vp, vp, vp, vp, pd]),
                 "pcpm_rank_stats_noalloc": (i32, [vp, vp, vp, u32, vp, vp]),
                 "pcpm_strerror": (ctypes.c_char_p, [i32]),
+                "pcpm_ws_features": (i32, [vp, vp, vp, vp, vp]),
+                "pcpm_ws_predict": (i32, [vp, vp, u32, vp, vp]),
+                "pcpm_ws_targets": (i32, [vp, u32, vp, vp]),
+                "pcpm_ws_loss_grad": (i32, [vp, vp, vp, u32, vp, vp, vp]),
+                "pcpm_ws_adam": (i32, [vp, vp, vp, vp, i32, f32, f32, f32, f32, vp]),
+                "pcpm_ws_init_ranks": (i32, [vp, u32, vp, vp]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -315,4 +321,79 @@ def rank_stats_noalloc(x, y, row_ptr, out=None, stream=None):
     _check(lib().pcpm_rank_stats_noalloc(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
                                          _dev_u32(row_ptr), n, ctypes.c_void_p(out.data_ptr()), _stream(stream)),
            "pcpm_rank_stats_noalloc")
+    return out
+
+
+# ----------------------------------------------------------- warm start
+# Learned warm start (pcpm_warmstart.h): features, network inference and
+# training steps, and the initial rank vector. Shapes: features [n, 5],
+# params [WS_PARAMS] (mu, inv_sigma, W1, b1, W2, b2, w3, b3), all float32 CUDA.
+WS_FEATURES, WS_HIDDEN, WS_TRAINABLE = 5, 64, 10
+WS_PARAMS = 2 * 5 + 64 * 5 + 64 + 64 * 64 + 64 + 64 + 1
+
+
+def _f32(t, numel=None, name="tensor"):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise TypeError(f"{name}: expected a contiguous CUDA float32 tensor")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name}: expected {numel} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def ws_features(png: "PNG", row_ptr, col, out=None, stream=None):
+    """Features of every node (pcpm_ws_features); resets the handle's state."""
+    import torch
+    out = torch.empty((png.n, WS_FEATURES), dtype=torch.float32, device="cuda") if out is None else out
+    _check(lib().pcpm_ws_features(png._h, _dev_u32(row_ptr), _dev_u32(col),
+                                  _f32(out, png.n * WS_FEATURES, "features"), _stream(stream)), "pcpm_ws_features")
+    return out
+
+
+def ws_targets(pr, out=None, stream=None):
+    """Training targets log(n * pr) (pcpm_ws_targets)."""
+    import torch
+    n = pr.numel()
+    out = torch.empty(n, dtype=torch.float32, device="cuda") if out is None else out
+    _check(lib().pcpm_ws_targets(_f32(pr, n, "pr"), n, _f32(out, n, "out"), _stream(stream)), "pcpm_ws_targets")
+    return out
+
+
+def ws_predict(params, features, out=None, stream=None):
+    """Network output per row, BF16-rounded weights (pcpm_ws_predict)."""
+    import torch
+    n = features.shape[0]
+    out = torch.empty(n, dtype=torch.float32, device="cuda") if out is None else out
+    _check(lib().pcpm_ws_predict(_f32(params, WS_PARAMS, "params"), _f32(features, n * WS_FEATURES, "features"), n,
+                                 _f32(out, n, "out"), _stream(stream)), "pcpm_ws_predict")
+    return out
+
+
+def ws_loss_grad(params, features, target, grad, loss, stream=None):
+    """Mean squared error and its gradient into grad [WS_PARAMS] and loss
+    (float64 [1]) on the device (pcpm_ws_loss_grad); does not synchronise."""
+    import torch
+    n = features.shape[0]
+    if not (isinstance(loss, torch.Tensor) and loss.is_cuda and loss.dtype == torch.float64 and loss.numel() == 1):
+        raise TypeError("loss: expected a CUDA float64 tensor of one element")
+    _check(lib().pcpm_ws_loss_grad(_f32(params, WS_PARAMS, "params"), _f32(features, n * WS_FEATURES, "features"),
+                                   _f32(target, n, "target"), n, _f32(grad, WS_PARAMS, "grad"),
+                                   ctypes.c_void_p(loss.data_ptr()), _stream(stream)), "pcpm_ws_loss_grad")
+
+
+def ws_adam(params, grad, m, v, step: int, lr: float, beta1: float = 0.9, beta2: float = 0.999,
+            eps: float = 1e-8, stream=None):
+    """One Adam step on the trainable parameters (pcpm_ws_adam)."""
+    _check(lib().pcpm_ws_adam(_f32(params, WS_PARAMS, "params"), _f32(grad, WS_PARAMS, "grad"),
+                              _f32(m, WS_PARAMS, "m"), _f32(v, WS_PARAMS, "v"), int(step), float(lr), float(beta1),
+                              float(beta2), float(eps), _stream(stream)), "pcpm_ws_adam")
+
+
+def ws_init_ranks(pred, out=None, stream=None):
+    """Initial ranks softmax(pred) (pcpm_ws_init_ranks)."""
+    import torch
+    n = pred.numel()
+    out = torch.empty(n, dtype=torch.float32, device="cuda") if out is None else out
+    _check(lib().pcpm_ws_init_ranks(_f32(pred, n, "pred"), n, _f32(out, n, "out"), _stream(stream)),
+           "pcpm_ws_init_ranks")
     return out
