@@ -9,8 +9,11 @@
  * Features of node v, PCPM_WS_FEATURES = 5, row-major float[n][5]:
  *   0  log1p(indeg(v))
  *   1  log1p(outdeg(v))
- *   2  log1p(sum of indeg(u) over in-neighbours u)    (exact integer sum)
- *   3  log1p(sum of outdeg(u) over in-neighbours u)   (exact integer sum)
+ *   2  log1p(sum of indeg(u) over in-neighbours u)
+ *   3  log1p(sum of outdeg(u) over in-neighbours u)
+ * The in-degree and both sums are in-edge sums that the library computes as
+ * PCPM passes over the handle (FP32; counts below 2^24 come out exact up to
+ * the rounding of 1/outdeg), the logarithms in FP32.
  *   4  log(n * PR_1(v)), PR_1 one Eq. 1 step from the uniform start on the
  *      handle (d = 0.85, dangling mass spread uniformly)
  * Network: standardise x^ = (x - mu) * inv_sigma; h1 = relu(W1 x^ + b1);
@@ -42,8 +45,9 @@ extern "C" {
 /* Features of every node of the graph the handle was built from.
  *   row_ptr, col  the device CSR given to pcpm_build (uint32[n+1], uint32[m]).
  *   features      float[n][5], written.
- * Resets the handle's solver state and runs one iteration on it (PR_1).
- * Allocates and frees device scratch (24 bytes per node). Synchronises. */
+ * Uses the handle for four passes (three sums, then PR_1) and leaves its
+ * solver state after PR_1. Allocates 20 bytes per node of stream-ordered
+ * device scratch and frees it. Synchronises. */
 int pcpm_ws_features(pcpm_png* png, const uint32_t* row_ptr, const uint32_t* col, float* features,
                      void* stream);
 

@@ -188,6 +188,26 @@ bool bad_damping(float d) { return !(d >= 0.0f && d < 1.0f); }
 constexpr uint32_t kAllFlags = PCPM_DANGLING_LEAK | PCPM_TWO_PHASE;
 
 }  // namespace
+
+// out(v) = sum over in-edges u -> v of pr_like(u) / outdeg(u): one PCPM pass,
+// the scatter of pr_like * (1/outdeg) and a gather applied with d = 1 and no
+// dangling term, so the apply returns the bare sum. Leaves the handle after
+// that pass (callers reset before solving).
+int pull_sum(pcpm_png* g, const float* pr_like, float* out, cudaStream_t s) {
+    g->last_stream = s;
+    CK(cudaMemsetAsync(g->state, 0, sizeof(DevState), s));
+    CK(cudaMemsetAsync(g->gacc, 0, (size_t)g->n * sizeof(float), s));
+    CK(cudaMemsetAsync(g->bin_done, 0, (size_t)g->k * sizeof(uint32_t), s));
+    g->cur = 0;
+    g->iters_done = 0;
+    g->upd_valid = 0;
+    RC(launch_init(g, pr_like, s));
+    RC(run_iterations(g, 1.0f, 1, 0.0, PCPM_TWO_PHASE | PCPM_DANGLING_LEAK, s, nullptr));
+    g->iters_done = 1;
+    CK(cudaMemcpyAsync(out, g->pr[g->cur], (size_t)g->n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    return PCPM_OK;
+}
+
 }  // namespace pcpm
 
 using namespace pcpm;

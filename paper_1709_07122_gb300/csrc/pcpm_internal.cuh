@@ -152,6 +152,7 @@ int build_png(pcpm_png* g, const uint32_t* row_ptr, const uint32_t* col, const p
 
 // Iteration kernels (pcpm_iter.cu).
 int configure_kernels(pcpm_png* g);
+int pull_sum(pcpm_png* g, const float* pr_like, float* out, cudaStream_t s);
 int launch_init(pcpm_png* g, const float* pr_init, cudaStream_t s);
 int launch_scatter(pcpm_png* g, cudaStream_t s);
 int launch_gather(pcpm_png* g, float d, uint32_t flags, bool fused, cudaStream_t s);

@@ -1,5 +1,7 @@
 // warmstart.cu - learned warm start: node features, a 5-64-64-1 network's
-// inference and training kernels, Adam, and the initial rank vector.
+// inference and training kernels, Adam, and the initial rank vector. The
+// degree features are in-edge sums computed as PCPM passes over the handle
+// (scatter and gather of Algorithms 3 and 4, applied with d = 1).
 //
 // Not in the paper: power iteration (Eq. 1) starts from 1/n there. Here a
 // per-node network predicts log(n * PR*(v)) and the iteration may start from
@@ -29,45 +31,29 @@ static_assert(OFF_W1 == PCPM_WS_TRAINABLE_OFFSET, "parameter layout");
 constexpr int kPredictThreads = 256;
 constexpr int kTile = 256;     // nodes per training CTA (one per thread)
 constexpr int kRow = H + 1;    // padded shared-memory row
-constexpr int kEdgeWarps = 8;  // warps per CTA of the per-row edge kernels
 
 // ------------------------------------------------------------- features
-__global__ void indegree_count_kernel(const uint32_t* __restrict__ col, uint64_t m, uint32_t* __restrict__ indeg) {
-    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < m; e += (uint64_t)gridDim.x * blockDim.x)
-        atomicAdd(&indeg[col[e]], 1u);
-}
-
-// One warp per row u: every out-edge (u, v) adds indeg(u) and outdeg(u) to
-// v's two sums (64-bit integer atomics: exact and order-independent).
-__global__ void __launch_bounds__(kEdgeWarps * 32) two_hop_kernel(const uint32_t* __restrict__ row_ptr,
-                                                                  const uint32_t* __restrict__ col, uint32_t n,
-                                                                  const uint32_t* __restrict__ indeg,
-                                                                  unsigned long long* __restrict__ s_in,
-                                                                  unsigned long long* __restrict__ s_out) {
-    const uint32_t lane = threadIdx.x & 31;
-    for (uint64_t u = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; u < n;
-         u += ((uint64_t)gridDim.x * blockDim.x) >> 5) {
-        const uint32_t b = row_ptr[u], e = row_ptr[u + 1];
-        const unsigned long long di = indeg[u], dout = e - b;
-        for (uint32_t i = b + lane; i < e; i += 32) {
-            const uint32_t v = col[i];
-            atomicAdd(&s_in[v], di);
-            atomicAdd(&s_out[v], dout);
-        }
+// The vectors whose in-edge sums give the degree features: the PCPM pass of
+// pull_sum divides by outdeg(u), so x(u) * outdeg(u) yields sum_u x(u) over
+// in-edges: x = 1 (in-degree), x = indeg(u), x = outdeg(u).
+__global__ void degree_vector_kernel(const uint32_t* __restrict__ row_ptr, uint32_t n, const float* __restrict__ x,
+                                     int power, float* __restrict__ out) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const float dout = (float)(row_ptr[v + 1] - row_ptr[v]);
+        out[v] = x ? x[v] * dout : (power == 2 ? dout * dout : dout);
     }
 }
 
-__global__ void features_kernel(const uint32_t* __restrict__ row_ptr, uint32_t n,
-                                const uint32_t* __restrict__ indeg, const unsigned long long* __restrict__ s_in,
-                                const unsigned long long* __restrict__ s_out, const float* __restrict__ pr1,
-                                float* __restrict__ feat) {
+__global__ void features_kernel(const uint32_t* __restrict__ row_ptr, uint32_t n, const float* __restrict__ indeg,
+                                const float* __restrict__ s_in, const float* __restrict__ s_out,
+                                const float* __restrict__ pr1, float* __restrict__ feat) {
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         float* f = feat + (size_t)v * F;
-        f[0] = (float)log1p((double)indeg[v]);
-        f[1] = (float)log1p((double)(row_ptr[v + 1] - row_ptr[v]));
-        f[2] = (float)log1p((double)s_in[v]);
-        f[3] = (float)log1p((double)s_out[v]);
-        f[4] = (float)log((double)n * (double)pr1[v]);
+        f[0] = log1pf(indeg[v]);
+        f[1] = log1pf((float)(row_ptr[v + 1] - row_ptr[v]));
+        f[2] = log1pf(s_in[v]);
+        f[3] = log1pf(s_out[v]);
+        f[4] = logf((float)n * pr1[v]);
     }
 }
 
@@ -103,28 +89,61 @@ __device__ __forceinline__ void layer1(const float* w, const float* xh, float* h
     }
 }
 
+// Inference keeps W2 at a 16-byte-aligned shared offset (the flat layout puts
+// it at float 394): entries from W2 on move up by kShift floats.
+constexpr int kShift = 2;
+static_assert((OFF_W2 + kShift) % 4 == 0, "W2 rows must start on 16-byte boundaries");
+
 __global__ void __launch_bounds__(kPredictThreads) predict_kernel(const float* __restrict__ params,
                                                                   const float* __restrict__ feat, uint32_t n,
                                                                   float* __restrict__ out) {
-    __shared__ float w[P];
-    load_params<true>(params, w);
+    __shared__ __align__(16) float w[P + kShift];
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const float x = params[i];
+        w[i < OFF_W2 ? i : i + kShift] = i >= OFF_W1 ? __bfloat162float(__float2bfloat16_rn(x)) : x;
+    }
+    __syncthreads();
+    const float* w2 = w + OFF_W2 + kShift;
+    const float* b2 = w2 + H * H;
+    const float* w3 = b2 + H;
+    const float b3 = w3[H];
+    // two nodes per thread: every 16-byte weight load feeds eight FMAs
+    const uint64_t stride = 2ull * gridDim.x * blockDim.x;
 #pragma unroll 1
-    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        // Re-read the weights from shared memory for every node instead of
-        // holding all of them in registers across nodes.
-        asm volatile("" ::: "memory");
-        float xh[F], h1[H];
-        standardise(feat, v, w, xh);
-        layer1(w, xh, h1);
-        float y = w[OFF_B3];
+    for (uint64_t v0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) * 2; v0 < n; v0 += stride) {
+        asm volatile("" ::: "memory");  // weights stay in shared memory, not in registers across nodes
+        const bool two = v0 + 1 < n;
+        float xa[F], xb[F], ha[H], hb[H];
+        standardise(feat, v0, w, xa);
+        if (two) standardise(feat, v0 + 1, w, xb);
+        else {
+#pragma unroll
+            for (int f = 0; f < F; ++f) xb[f] = 0.0f;
+        }
+        layer1(w, xa, ha);
+        layer1(w, xb, hb);
+        float ya = b3, yb = b3;
 #pragma unroll 1
         for (int j = 0; j < H; ++j) {
-            float s = w[OFF_B2 + j];
+            float sa = b2[j], sb = sa;
+            const float4* row = reinterpret_cast<const float4*>(w2 + j * H);
 #pragma unroll
-            for (int i = 0; i < H; ++i) s = fmaf(w[OFF_W2 + j * H + i], h1[i], s);
-            y = fmaf(w[OFF_W3 + j], fmaxf(s, 0.0f), y);
+            for (int i4 = 0; i4 < H / 4; ++i4) {
+                const float4 q = row[i4];
+                sa = fmaf(q.x, ha[4 * i4], sa);
+                sa = fmaf(q.y, ha[4 * i4 + 1], sa);
+                sa = fmaf(q.z, ha[4 * i4 + 2], sa);
+                sa = fmaf(q.w, ha[4 * i4 + 3], sa);
+                sb = fmaf(q.x, hb[4 * i4], sb);
+                sb = fmaf(q.y, hb[4 * i4 + 1], sb);
+                sb = fmaf(q.z, hb[4 * i4 + 2], sb);
+                sb = fmaf(q.w, hb[4 * i4 + 3], sb);
+            }
+            ya = fmaf(w3[j], fmaxf(sa, 0.0f), ya);
+            yb = fmaf(w3[j], fmaxf(sb, 0.0f), yb);
         }
-        out[v] = y;
+        out[v0] = ya;
+        if (two) out[v0 + 1] = yb;
     }
 }
 
@@ -263,7 +282,7 @@ __global__ void adam_kernel(float* __restrict__ params, const float* __restrict_
 __global__ void exp_sum_kernel(const float* __restrict__ pred, uint32_t n, double* __restrict__ sum) {
     double s = 0.0;
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
-        s += exp((double)fminf(fmaxf(pred[v], -80.0f), 80.0f));
+        s += (double)expf(fminf(fmaxf(pred[v], -80.0f), 80.0f));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0) atomicAdd(sum, s);
@@ -273,7 +292,7 @@ __global__ void normalise_kernel(const float* __restrict__ pred, uint32_t n, con
                                  float* __restrict__ pr) {
     const double inv = 1.0 / *sum;
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
-        pr[v] = (float)(exp((double)fminf(fmaxf(pred[v], -80.0f), 80.0f)) * inv);
+        pr[v] = (float)((double)expf(fminf(fmaxf(pred[v], -80.0f), 80.0f)) * inv);
 }
 
 int grid_for_n(uint64_t work, int threads) {
@@ -302,35 +321,36 @@ extern "C" int pcpm_ws_features(pcpm_png* png, const uint32_t* row_ptr, const ui
     if (!png || pcpm_png_get_info(png, &info) != PCPM_OK) return PCPM_EINVAL;
     if (!is_dev(row_ptr) || !is_dev(features) || (info.num_edges > 0 && !is_dev(col))) return PCPM_EINVAL;
     const uint32_t n = info.n;
-    const uint64_t m = info.num_edges;
     cudaStream_t s = (cudaStream_t)stream;
-    uint32_t* indeg = nullptr;
-    unsigned long long* sums = nullptr;
-    float* pr1 = nullptr;
-    int rc = PCPM_OK;
-    if (cudaMalloc((void**)&indeg, (size_t)n * sizeof(uint32_t)) != cudaSuccess ||
-        cudaMalloc((void**)&sums, (size_t)2 * n * sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMalloc((void**)&pr1, (size_t)n * sizeof(float)) != cudaSuccess)
-        rc = PCPM_ENOMEM;
-    if (rc == PCPM_OK) {
-        cudaMemsetAsync(indeg, 0, (size_t)n * sizeof(uint32_t), s);
-        cudaMemsetAsync(sums, 0, (size_t)2 * n * sizeof(unsigned long long), s);
-        if (m) indegree_count_kernel<<<grid_for_n(m, 256), 256, 0, s>>>(col, m, indeg);
-        two_hop_kernel<<<grid_for_n((uint64_t)n * 32, kEdgeWarps * 32), kEdgeWarps * 32, 0, s>>>(
-            row_ptr, col, n, indeg, sums, sums + n);
-        if (cudaGetLastError() != cudaSuccess) rc = PCPM_ECUDA;
+    // scratch: a staging vector and four sums (in-degree, the two 2-hop sums, PR_1)
+    float* buf = nullptr;
+    if (cudaMallocAsync((void**)&buf, (size_t)5 * n * sizeof(float), s) != cudaSuccess) {
+        cudaGetLastError();
+        return PCPM_ENOMEM;
     }
-    // PR_1: one Eq. 1 step from the uniform start on the handle
+    float *x = buf, *indeg = buf + (size_t)n, *s_in = buf + 2 * (size_t)n, *s_out = buf + 3 * (size_t)n,
+          *pr1 = buf + 4 * (size_t)n;
+    const int grid = grid_for_n(n, 256);
+    int rc = PCPM_OK;
+    // in-degree: sum of 1 over in-edges
+    degree_vector_kernel<<<grid, 256, 0, s>>>(row_ptr, n, nullptr, 1, x);
+    if (rc == PCPM_OK) rc = pull_sum(png, x, indeg, s);
+    // sum of indeg(u) over in-edges
+    if (rc == PCPM_OK) degree_vector_kernel<<<grid, 256, 0, s>>>(row_ptr, n, indeg, 1, x);
+    if (rc == PCPM_OK) rc = pull_sum(png, x, s_in, s);
+    // sum of outdeg(u) over in-edges
+    if (rc == PCPM_OK) degree_vector_kernel<<<grid, 256, 0, s>>>(row_ptr, n, nullptr, 2, x);
+    if (rc == PCPM_OK) rc = pull_sum(png, x, s_out, s);
+    // PR_1: one Eq. 1 step from the uniform start
     if (rc == PCPM_OK) rc = pcpm_reset(png, nullptr, stream);
     if (rc == PCPM_OK) rc = pcpm_iterate(png, 0.85f, 1, 0.0, PCPM_TWO_PHASE, nullptr, nullptr, stream);
     if (rc == PCPM_OK) rc = pcpm_ranks(png, pr1, stream);
     if (rc == PCPM_OK) {
-        features_kernel<<<grid_for_n(n, 256), 256, 0, s>>>(row_ptr, n, indeg, sums, sums + n, pr1, features);
-        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) rc = PCPM_ECUDA;
+        features_kernel<<<grid, 256, 0, s>>>(row_ptr, n, indeg, s_in, s_out, pr1, features);
+        if (cudaGetLastError() != cudaSuccess) rc = PCPM_ECUDA;
     }
-    cudaFree(indeg);
-    cudaFree(sums);
-    cudaFree(pr1);
+    cudaFreeAsync(buf, s);
+    if (rc == PCPM_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = PCPM_ECUDA;
     return rc;
 }
 
@@ -381,14 +401,18 @@ extern "C" int pcpm_ws_init_ranks(const float* pred, uint32_t n, float* pr, void
     if (!pred || !pr || n == 0) return PCPM_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     double* sum = nullptr;
-    if (cudaMalloc((void**)&sum, sizeof(double)) != cudaSuccess) return PCPM_ENOMEM;
+    if (cudaMallocAsync((void**)&sum, sizeof(double), s) != cudaSuccess) {
+        cudaGetLastError();
+        return PCPM_ENOMEM;
+    }
     int rc = PCPM_OK;
     if (cudaMemsetAsync(sum, 0, sizeof(double), s) != cudaSuccess) rc = PCPM_ECUDA;
     if (rc == PCPM_OK) {
         exp_sum_kernel<<<grid_for_n(n, 256), 256, 0, s>>>(pred, n, sum);
         normalise_kernel<<<grid_for_n(n, 256), 256, 0, s>>>(pred, n, sum, pr);
-        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) rc = PCPM_ECUDA;
+        if (cudaGetLastError() != cudaSuccess) rc = PCPM_ECUDA;
     }
-    cudaFree(sum);
+    cudaFreeAsync(sum, s);
+    if (rc == PCPM_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = PCPM_ECUDA;
     return rc;
 }

@@ -1,8 +1,7 @@
 """Learned warm start on the GPU against the FP64 reference (oracle/warmstart.py).
 
-Features: degrees and 2-hop sums are exact integers (then log1p, compared
-within one FP32 rounding); the one-iteration feature follows the FP32 path's
-1e-6 bar. Inference with BF16-rounded weights is compared with the FP64
+Features: the degree sums are FP32 PCPM passes (compared within the FP32
+summation bound); the one-iteration feature follows the FP32 path's 1e-6 bar. Inference with BF16-rounded weights is compared with the FP64
 network on the same rounded weights. The loss gradient (FP32 sums over a
 batch) is compared norm-wise, Adam per entry, and the initial ranks with the
 FP64 softmax. End to end, a network trained on small RMAT graphs starts an
@@ -48,7 +47,13 @@ def test_features_match_reference(name, gen, q):
     rp, col = gen()
     got = gpu_features(rp, col, q).astype(np.float64)
     want = ows.features(rp, col)
-    np.testing.assert_allclose(got[:, :4], want[:, :4], rtol=2 * FP32, atol=0)
+    # The degree sums are FP32 PCPM passes: each term x(u) * outdeg(u) *
+    # fl(1/outdeg(u)) is within 2^-23 of x(u), and a k-term FP32 sum within
+    # about k * 2^-24 of exact (k <= the largest in-degree); log1pf adds a few
+    # FP32 roundings.
+    kmax = int(np.bincount(col, minlength=rp.size - 1).max())
+    tol = (kmax + 8) * FP32 + 4 * FP32
+    np.testing.assert_allclose(got[:, :4], want[:, :4], rtol=tol, atol=tol)
     # log(n * PR_1): PR_1 from the FP32 path (L1 <= 1e-6 against FP64), so
     # |d log| <= |d PR| / PR per node; the sum of |n PR1 - n PR1*| is what the
     # 1e-6 bar controls
