@@ -17,6 +17,9 @@ passages they follow:
   and the bins in canonical order (source partitions in ID order, nodes in ID
   order, destination IDs in adjacency order; MSB marks a message's first ID).
 * :func:`scatter_gather` - Algorithm 3 followed by Algorithm 4 in FP64.
+* :func:`bin_weights`, :func:`spmv`, :func:`weighted_scatter_gather` -
+  weighted graphs and SpMV (Sec. 3.5): weights stored beside the destination
+  IDs in bin order; y = A^T_w x by its definition and through the bins.
 * :func:`store_updates` / :func:`load_updates` - the storage formats of
   reduced-precision update bins. Not in the paper (it keeps 4-byte updates,
   Sec. 3.2): IEEE 754 binary16 of SPR * 2^15 and bfloat16 (binary32's upper
@@ -75,6 +78,14 @@ def _load():
             lib.oracle_png_fill.argtypes = [ctypes.c_uint32, _u32p, _u32p, ctypes.c_uint32, _u32p, _u32p,
                                             _u32p, _u32p, _u32p, _u32p, _u32p, _u32p]
             lib.oracle_png_fill.restype = None
+            lib.oracle_png_fill_weights.argtypes = [ctypes.c_uint32, _u32p, _u32p, ctypes.c_uint32, _u32p, _u32p,
+                                                    _f64p, _f64p]
+            lib.oracle_png_fill_weights.restype = None
+            lib.oracle_spmv.argtypes = [ctypes.c_uint32, _u32p, _u32p, _f64p, _f64p, _f64p]
+            lib.oracle_spmv.restype = None
+            lib.oracle_weighted_gather.argtypes = [ctypes.c_uint32, ctypes.c_uint32, _u32p, _u32p, _u32p, _u32p,
+                                                   _f64p, _f64p, _f64p]
+            lib.oracle_weighted_gather.restype = None
             lib.oracle_scatter_gather.argtypes = [ctypes.c_uint32, ctypes.c_uint32, _u32p, _u32p, _u32p, _u32p,
                                                   _f64p, _f64p]
             lib.oracle_scatter_gather.restype = None
@@ -224,3 +235,41 @@ def load_updates(stored, dtype: str) -> np.ndarray:
         bits = np.asarray(stored, dtype=np.uint16).astype(np.uint32) << 16
         return bits.view(np.float32).astype(np.float64)
     raise ValueError("dtype must be f32, f16 or bf16")
+
+
+def bin_weights(row_ptr, col, q: int, weights, g: dict | None = None) -> np.ndarray:
+    """Edge weights (CSR order) placed beside their destination IDs in bin
+    order (Sec. 3.5)."""
+    lib = _load()
+    row_ptr, col = _csr(row_ptr, col)
+    g = png(row_ptr, col, q) if g is None else g
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    out = np.empty(max(g["m"], 1), dtype=np.float64)
+    off_e = np.ascontiguousarray(g["off_e"].ravel())
+    lib.oracle_png_fill_weights(g["n"], row_ptr, col, int(q), off_e, g["bin_e"], w if w.size else np.zeros(1), out)
+    return out[:g["m"]]
+
+
+def spmv(row_ptr, col, weights, x) -> np.ndarray:
+    """y(v) = sum over edges (u, v) of w(u, v) * x(u), FP64."""
+    lib = _load()
+    row_ptr, col = _csr(row_ptr, col)
+    n = row_ptr.size - 1
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    y = np.empty(n, dtype=np.float64)
+    lib.oracle_spmv(n, row_ptr, col if col.size else np.zeros(1, np.uint32), w if w.size else np.zeros(1),
+                    np.ascontiguousarray(x, dtype=np.float64), y)
+    return y
+
+
+def weighted_scatter_gather(g: dict, wbin, x) -> np.ndarray:
+    """Algorithm 3 + Algorithm 4 over the bins of :func:`png` with the weights
+    applied in the gather (Sec. 3.5), FP64."""
+    lib = _load()
+    y = np.empty(g["n"], dtype=np.float64)
+    src = g["src_idx"] if g["ne"] else np.zeros(1, dtype=np.uint32)
+    dst = g["dest_ids"] if g["m"] else np.zeros(1, dtype=np.uint32)
+    wb = np.ascontiguousarray(wbin, dtype=np.float64) if g["m"] else np.zeros(1)
+    lib.oracle_weighted_gather(g["n"], g["k"], g["bin_u"], g["bin_e"], np.ascontiguousarray(src),
+                               np.ascontiguousarray(dst), wb, np.ascontiguousarray(x, dtype=np.float64), y)
+    return y

@@ -31,6 +31,13 @@
  *   oracle_scatter_gather  Algorithm 3 (scatter over the PNG) followed by the
  *                       branch-avoiding gather of Algorithm 4, in FP64, giving
  *                       the sum of SPR over in-neighbours for every node.
+ *   oracle_png_fill_weights  weighted graphs (Sec. 3.5): the edge weights
+ *                       stored beside the destination IDs, in bin order.
+ *   oracle_spmv         y(v) = sum over in-edges (u, v) of w(u, v) * x(u), the
+ *                       weighted product the extension computes, by its plain
+ *                       definition over the edges.
+ *   oracle_weighted_gather  Algorithm 3 then Algorithm 4 with the weights read
+ *                       in the gather and applied to each update (Sec. 3.5).
  *
  * Partitions are index ranges [i*q, (i+1)*q) (Sec. 3.1); the last one may be
  * shorter. Inputs are a CSR out-adjacency (row_ptr[n+1], col[m]) whose rows are
@@ -220,6 +227,51 @@ void oracle_scatter_gather(uint32_t n, uint32_t k, const uint32_t* bin_u, const 
             uint32_t id = dest_ids[j];
             update_ptr += id >> 31;
             y[id & ID_MASK] += update[update_ptr];
+        }
+    }
+    free(update);
+}
+
+/* Weighted graphs (Sec. 3.5): the weight of every edge goes to the position
+ * its destination ID takes in the bins (the second PNG scan, same cursors).
+ * weights[m] in CSR order; wbin[m] receives them in bin order. */
+void oracle_png_fill_weights(uint32_t n, const uint32_t* row_ptr, const uint32_t* col, uint32_t q,
+                             const uint32_t* off_e, const uint32_t* bin_e, const double* weights, double* wbin) {
+    uint32_t k = (n + q - 1) / q;
+    uint32_t* cur_e = (uint32_t*)malloc((size_t)(k ? k : 1) * sizeof(uint32_t));
+    for (uint32_t p = 0; p < k; ++p) {
+        for (uint32_t pd = 0; pd < k; ++pd) cur_e[pd] = bin_e[pd] + off_e[(size_t)p * k + pd];
+        uint32_t u_end = (p + 1) * (uint64_t)q < n ? (p + 1) * q : n;
+        for (uint32_t u = p * q; u < u_end; ++u)
+            for (uint32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) wbin[cur_e[col[e] / q]++] = weights[e];
+    }
+    free(cur_e);
+}
+
+/* y(v) = sum over edges (u, v) of w(u, v) * x(u), in FP64, by the definition:
+ * one pass over the out-adjacency. */
+void oracle_spmv(uint32_t n, const uint32_t* row_ptr, const uint32_t* col, const double* weights,
+                 const double* x, double* y) {
+    memset(y, 0, (size_t)n * sizeof(double));
+    for (uint32_t u = 0; u < n; ++u)
+        for (uint32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) y[col[e]] += weights[e] * x[u];
+}
+
+/* Sec. 3.5 with Algorithms 3 and 4: update[t] = x[src_idx[t]]; the gather
+ * walks each bin's IDs with the update pointer of Algorithm 4 and adds
+ * weight * update to the destination. */
+void oracle_weighted_gather(uint32_t n, uint32_t k, const uint32_t* bin_u, const uint32_t* bin_e,
+                            const uint32_t* src_idx, const uint32_t* dest_ids, const double* wbin,
+                            const double* x, double* y) {
+    uint32_t ne = bin_u[k];
+    double* update = (double*)malloc((size_t)(ne ? ne : 1) * sizeof(double));
+    for (uint32_t t = 0; t < ne; ++t) update[t] = x[src_idx[t]];
+    memset(y, 0, (size_t)n * sizeof(double));
+    for (uint32_t pd = 0; pd < k; ++pd) {
+        int64_t ptr = (int64_t)bin_u[pd] - 1;
+        for (uint32_t j = bin_e[pd]; j < bin_e[pd + 1]; ++j) {
+            ptr += dest_ids[j] >> 31;
+            y[dest_ids[j] & ID_MASK] += wbin[j] * update[ptr];
         }
     }
     free(update);
