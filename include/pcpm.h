@@ -57,6 +57,9 @@ extern "C" {
 #define PCPM_MAX_NODES 0x7FFFFFFFu
 /* One partition's FP32 accumulator lives in shared memory (<= 227 KB/CTA). */
 #define PCPM_MAX_PART_SIZE 32768u
+/* Weighted graphs stage each chunk's weights beside its IDs, which leaves
+ * room for half the accumulator. */
+#define PCPM_MAX_WEIGHTED_PART_SIZE 16384u
 /* Bounded by the builder's per-warp counting tables in shared memory. */
 #define PCPM_MAX_PARTITIONS 8192u
 
@@ -166,6 +169,33 @@ int pcpm_build(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t n, uin
 int pcpm_build_ex(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t n, uint64_t m,
                   uint32_t part_size, const pcpm_build_options* options, void* stream,
                   pcpm_png** out);
+
+/* Weighted graphs and SpMV (Sec. 3.5): pcpm_build with an edge weight per
+ * column index.
+ *   weights  device, float[m], in CSR order (weight of col_idx[e] at e); only
+ *            read during this call. Weights are stored beside the destination
+ *            IDs in bin order and applied in the gather of pcpm_spmv.
+ * Requires part_size <= PCPM_MAX_WEIGHTED_PART_SIZE, canonical_gather = 0 and
+ * FP32 updates (PCPM_EINVAL otherwise). PageRank iterations on the handle
+ * ignore the weights (PageRank of the unweighted graph). */
+int pcpm_build_weighted(const uint32_t* row_ptr, const uint32_t* col_idx, const float* weights, uint32_t n,
+                        uint64_t m, uint32_t part_size, const pcpm_build_options* options, void* stream,
+                        pcpm_png** out);
+
+/* Sparse matrix-vector product over the PNG (Sec. 3.5):
+ *   y(v) = sum over edges (u, v) of w(u, v) * x(u)      (y = A^T_w x)
+ * with w = 1 on an unweighted handle. One scatter of x (Algorithm 3, x
+ * itself rather than x/outdeg) and one gather with the weights applied
+ * (Algorithm 4), FP32 accumulation.
+ *   x  device float[n], read;  y  device float[n], written.
+ * Uses the handle's rank buffers: its solver state afterwards is undefined
+ * (pcpm_reset before solving). Enqueued on `stream`; does not synchronise. */
+int pcpm_spmv(pcpm_png* png, const float* x, float* y, void* stream);
+
+/* Test hook: the weights in canonical bin order, host float[m] (the position
+ * of each weight matches pcpm_png_export's dest_ids). Synchronises.
+ * PCPM_EINVAL for an unweighted handle. */
+int pcpm_export_weights(const pcpm_png* png, float* wbin);
 
 /* Releases the handle and all its device memory. NULL is a no-op. Waits for
  * work the library enqueued on the handle's last stream. */

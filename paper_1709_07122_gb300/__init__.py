@@ -92,6 +92,10 @@ def lib(path: str | None = None):
                 "pcpm_export_state": (i32, [vp, vp, vp, vp, pd]),
                 "pcpm_rank_stats_noalloc": (i32, [vp, vp, vp, u32, vp, vp]),
                 "pcpm_strerror": (ctypes.c_char_p, [i32]),
+                "pcpm_build_weighted": (i32, [vp, vp, vp, u32, u64, u32, ctypes.POINTER(_Options), vp,
+                                              ctypes.POINTER(vp)]),
+                "pcpm_spmv": (i32, [vp, vp, vp, vp]),
+                "pcpm_export_weights": (i32, [vp, vp]),
                 "pcpm_ws_features": (i32, [vp, vp, vp, vp, vp]),
                 "pcpm_ws_predict": (i32, [vp, vp, u32, vp, vp]),
                 "pcpm_ws_targets": (i32, [vp, u32, vp, vp]),
@@ -168,6 +172,41 @@ class PNG:
                                _stream(stream), ctypes.byref(h)), "pcpm_build")
         self._h = h
         self.n = n
+
+    @classmethod
+    def weighted(cls, row_ptr, col, weights, part_size: int, stream=None, **options):
+        """Weighted graph (Sec. 3.5): weights is a CUDA float32 tensor of one
+        value per column index (CSR order); see pcpm_build_weighted."""
+        if isinstance(options.get("update_dtype"), str):
+            options = dict(options, update_dtype=UPDATE_DTYPES[options["update_dtype"]])
+        L = lib()
+        n = row_ptr.numel() - 1
+        m = int(row_ptr[-1].item()) & 0xFFFFFFFF
+        opt = _Options(**{k: int(v) for k, v in options.items()})
+        h = ctypes.c_void_p()
+        w = ctypes.c_void_p(weights.data_ptr()) if m else ctypes.c_void_p(1)
+        if m:
+            _f32(weights, m, "weights")
+        _check(L.pcpm_build_weighted(_dev_u32(row_ptr), _dev_u32(col), w, n, m, int(part_size), ctypes.byref(opt),
+                                     _stream(stream), ctypes.byref(h)), "pcpm_build_weighted")
+        obj = cls.__new__(cls)
+        obj._h = h
+        obj.n = n
+        return obj
+
+    def spmv(self, x, out=None, stream=None):
+        """y = A^T_w x over the PNG (pcpm_spmv): y(v) = sum of w(u, v) x(u)."""
+        import torch
+        out = torch.empty(self.n, dtype=torch.float32, device="cuda") if out is None else out
+        _check(lib().pcpm_spmv(self._h, _f32(x, self.n, "x"), _f32(out, self.n, "out"), _stream(stream)), "pcpm_spmv")
+        return out
+
+    def export_weights(self) -> np.ndarray:
+        """Weights in canonical bin order (pcpm_export_weights)."""
+        m = self.info["num_edges"]
+        w = np.empty(max(m, 1), np.float32)
+        _check(lib().pcpm_export_weights(self._h, w.ctypes.data_as(ctypes.c_void_p)), "pcpm_export_weights")
+        return w[:m]
 
     @classmethod
     def from_host(cls, row_ptr: np.ndarray, col: np.ndarray, part_size: int, stream=None, **options):

@@ -49,7 +49,7 @@ void release(pcpm_png* g) {
                     g->chunk_base, g->hubs, g->gdest, g->gslice_start, g->gslice_bytes, g->ichunk_start,
                     g->gunits, g->gorder, g->sunits, g->sorder, g->gacc,
                     g->bin_done, g->inv_deg, g->pr[0], g->pr[1], g->upd[0], g->upd[1], g->partials,
-                    g->hist, g->state};
+                    g->hist, g->state, g->wdest, g->gweight};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (g->state_host) cudaFreeHost(g->state_host);
@@ -219,12 +219,18 @@ int pcpm_build(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t n, uin
     return pcpm_build_ex(row_ptr, col_idx, n, m, part_size, nullptr, stream, out);
 }
 
-int pcpm_build_ex(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t n, uint64_t m, uint32_t part_size,
-                  const pcpm_build_options* options, void* stream, pcpm_png** out) {
+namespace {
+int build_impl(const uint32_t* row_ptr, const uint32_t* col_idx, const float* weights, uint32_t n, uint64_t m,
+               uint32_t part_size, const pcpm_build_options* options, void* stream, pcpm_png** out) {
     if (!out || !row_ptr || n == 0 || n > PCPM_MAX_NODES || part_size == 0 || part_size > PCPM_MAX_PART_SIZE)
         return PCPM_EINVAL;
     pcpm_build_options opt = {};
     if (options) opt = *options;
+    if (weights) {
+        if (part_size > PCPM_MAX_WEIGHTED_PART_SIZE || opt.canonical_gather || opt.update_dtype != PCPM_UPDATE_F32)
+            return PCPM_EINVAL;
+        if (m > 0 && !is_device_ptr(weights)) return PCPM_EINVAL;
+    }
     if (opt.gather_cluster != 0 && opt.gather_cluster != 1 && opt.gather_cluster != 2 && opt.gather_cluster != 4 &&
         opt.gather_cluster != 8)
         return PCPM_EINVAL;
@@ -258,6 +264,8 @@ int pcpm_build_ex(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t n, 
     g->cluster = (int)opt.gather_cluster;
     g->upd_dtype = (int)opt.update_dtype;
     g->upd_bytes = opt.update_dtype == PCPM_UPDATE_F32 ? 4u : 2u;
+    g->weighted = weights ? 1 : 0;
+    g->weights_in = weights;
     int rc = PCPM_OK;
     if (cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess) rc = PCPM_ECUDA;
     if (rc == PCPM_OK) rc = build_png(g, row_ptr, col_idx ? col_idx : row_ptr, opt, s);
@@ -266,6 +274,7 @@ int pcpm_build_ex(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t n, 
     if (rc == PCPM_OK) {
         if (cudaStreamSynchronize(s) != cudaSuccess) rc = PCPM_ECUDA;
     }
+    g->weights_in = nullptr;  // read during the build only
     if (rc != PCPM_OK) {
         cudaStreamSynchronize(s);
         cudaGetLastError();
@@ -273,6 +282,43 @@ int pcpm_build_ex(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t n, 
         return rc;
     }
     *out = g;
+    return PCPM_OK;
+}
+}  // namespace
+
+int pcpm_build_ex(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t n, uint64_t m, uint32_t part_size,
+                  const pcpm_build_options* options, void* stream, pcpm_png** out) {
+    return build_impl(row_ptr, col_idx, nullptr, n, m, part_size, options, stream, out);
+}
+
+int pcpm_build_weighted(const uint32_t* row_ptr, const uint32_t* col_idx, const float* weights, uint32_t n,
+                        uint64_t m, uint32_t part_size, const pcpm_build_options* options, void* stream,
+                        pcpm_png** out) {
+    if (!weights) return PCPM_EINVAL;
+    return build_impl(row_ptr, col_idx, weights, n, m, part_size, options, stream, out);
+}
+
+int pcpm_spmv(pcpm_png* g, const float* x, float* y, void* stream) {
+    if (!g || !is_device_ptr(x) || !is_device_ptr(y)) return PCPM_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    g->last_stream = s;
+    CK(cudaMemsetAsync(g->state, 0, sizeof(DevState), s));
+    CK(cudaMemsetAsync(g->gacc, 0, (size_t)g->n * sizeof(float), s));
+    CK(cudaMemsetAsync(g->bin_done, 0, (size_t)g->k * sizeof(uint32_t), s));
+    g->cur = 0;
+    g->iters_done = 0;
+    g->upd_valid = 0;
+    RC(launch_init(g, x, s));                     // pr[0] = x
+    RC(launch_scatter(g, s, /*raw=*/true));       // update[t] = x[src[t]] (Algorithm 3 without 1/outdeg)
+    RC(launch_gather(g, 1.0f, PCPM_DANGLING_LEAK, /*fused=*/false, s, /*spmv=*/true));
+    CK(cudaMemcpyAsync(y, g->pr[1], (size_t)g->n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    return PCPM_OK;
+}
+
+int pcpm_export_weights(const pcpm_png* g, float* wbin) {
+    if (!g || !wbin || !g->weighted) return PCPM_EINVAL;
+    CK(cudaStreamSynchronize(g->last_stream));
+    if (g->m) CK(cudaMemcpy(wbin, g->wdest, g->m * sizeof(float), cudaMemcpyDeviceToHost));
     return PCPM_OK;
 }
 

@@ -103,6 +103,11 @@ struct pcpm_png {
     int canonical_gather;    // 1: the gather decodes the canonical bins (MSB flags)
     int gather_runs;         // 1: the gather sums run-bit runs in a register
     int upd_dtype;           // kUpd*: storage of the update bins
+    // Weighted graphs (Sec. 3.5): edge weights beside the destination IDs.
+    int weighted;
+    const float* weights_in; // caller's CSR-order weights, read during the build only
+    float* wdest;            // m (padded like dest): weights in canonical bin order
+    float* gweight;          // nichunks * kChunk: weights in the bank-spread layout's order
     uint32_t upd_bytes;      // 4 or 2
     uint64_t merged_adds;    // IDs with bit 30 set
     uint32_t* gdest;         // nichunks * kChunk words
@@ -154,8 +159,10 @@ int build_png(pcpm_png* g, const uint32_t* row_ptr, const uint32_t* col, const p
 int configure_kernels(pcpm_png* g);
 int pull_sum(pcpm_png* g, const float* pr_like, float* out, cudaStream_t s);
 int launch_init(pcpm_png* g, const float* pr_init, cudaStream_t s);
-int launch_scatter(pcpm_png* g, cudaStream_t s);
-int launch_gather(pcpm_png* g, float d, uint32_t flags, bool fused, cudaStream_t s);
+// raw: stage x itself (SpMV) instead of x * (1/outdeg).
+int launch_scatter(pcpm_png* g, cudaStream_t s, bool raw = false);
+// spmv: the weighted gather of a weighted handle (Sec. 3.5).
+int launch_gather(pcpm_png* g, float d, uint32_t flags, bool fused, cudaStream_t s, bool spmv = false);
 int launch_reduce(pcpm_png* g, double tol, int hist_slot, cudaStream_t s);
 int launch_spr(pcpm_png* g, float* spr, cudaStream_t s);
 size_t partial_slots(const pcpm_png* g);

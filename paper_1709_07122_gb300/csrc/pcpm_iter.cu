@@ -444,12 +444,13 @@ __global__ void __launch_bounds__(kScatterThreads, 1) scatter_kernel(
     const uint32_t base = p * q, len = min(q, n - base);
     const uint32_t* segrow = seg_u + (size_t)p * k;
     const uint32_t* cntrow = cnt_u + (size_t)p * k;
-    // SPR of the partition, staged in shared memory (four independent 16-byte
+    // SPR of the partition, staged in shared memory (x itself when inv_deg is
+    // null: the SpMV of weighted graphs scatters the vector unscaled) (four independent 16-byte
     // loads of each array in flight per thread).
     if ((base & 3) == 0) {
         const uint32_t v4 = len >> 2;
         const float4* pr4 = reinterpret_cast<const float4*>(pr + base);
-        const float4* in4 = reinterpret_cast<const float4*>(inv_deg + base);
+        const float4* in4 = reinterpret_cast<const float4*>(inv_deg ? inv_deg + base : pr + base);
         for (uint32_t i0 = threadIdx.x; i0 < v4; i0 += 4 * blockDim.x) {
             float4 x[4], w[4];
 #pragma unroll
@@ -457,7 +458,7 @@ __global__ void __launch_bounds__(kScatterThreads, 1) scatter_kernel(
                 const uint32_t i = i0 + j * blockDim.x;
                 if (i < v4) {
                     x[j] = __ldg(pr4 + i);
-                    w[j] = __ldg(in4 + i);
+                    w[j] = inv_deg ? __ldg(in4 + i) : make_float4(1.f, 1.f, 1.f, 1.f);
                 }
             }
 #pragma unroll
@@ -468,9 +469,11 @@ __global__ void __launch_bounds__(kScatterThreads, 1) scatter_kernel(
                         make_float4(x[j].x * w[j].x, x[j].y * w[j].y, x[j].z * w[j].z, x[j].w * w[j].w);
             }
         }
-        for (uint32_t i = (v4 << 2) + threadIdx.x; i < len; i += blockDim.x) sspr[i] = pr[base + i] * inv_deg[base + i];
+        for (uint32_t i = (v4 << 2) + threadIdx.x; i < len; i += blockDim.x)
+            sspr[i] = pr[base + i] * (inv_deg ? inv_deg[base + i] : 1.0f);
     } else {
-        for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) sspr[i] = pr[base + i] * inv_deg[base + i];
+        for (uint32_t i = threadIdx.x; i < len; i += blockDim.x)
+            sspr[i] = pr[base + i] * (inv_deg ? inv_deg[base + i] : 1.0f);
     }
     segment_groups_prefix(segrow, cntrow, k, gpre, sh32);
     scatter_groups<kUpd>(sspr, base, len, gpre, k, segrow, cntrow, src, upd, unit.y, min(unit.z, gpre[k]), err);
@@ -491,6 +494,7 @@ struct GatherArgs {
     float* gacc;
     uint32_t* bin_done;
     const void* upd_in;
+    const float* gweight;  // weighted gather (kW): weights in the layout's order
     const float* pr_in;
     const float* inv_deg;
     float* pr_out;
@@ -508,31 +512,42 @@ struct GatherArgs {
 
 constexpr uint32_t kIdSlotBytes = kChunk * sizeof(uint32_t);
 constexpr uint32_t kUpdSlotBytes = kUpdSlot * sizeof(float);
-constexpr uint32_t kStageBytes = kIdSlotBytes + kUpdSlotBytes;
-constexpr size_t kRingBytes = (size_t)kGatherWarps * kGatherStages * kStageBytes;
-constexpr size_t kBarBytes = (size_t)kGatherWarps * kGatherStages * sizeof(uint64_t);
-constexpr size_t kMetaBytes = (size_t)kGatherWarps * kGatherStages * 2 * sizeof(uint32_t);
-constexpr size_t kAccOffset = kRingBytes + kBarBytes + kMetaBytes;
+// Shared-memory layout of the gather: per warp kGatherStages ring slots of
+// [IDs | weights (weighted graphs) | update slice], then the mbarriers, the
+// per-slot metadata and the accumulator.
+template <bool kW>
+struct Ring {
+    static constexpr uint32_t kWOff = kIdSlotBytes;
+    static constexpr uint32_t kUpdOff = kIdSlotBytes + (kW ? kChunk * sizeof(float) : 0);
+    static constexpr uint32_t kStage = kUpdOff + kUpdSlotBytes;
+    static constexpr size_t kBytes = (size_t)kGatherWarps * kGatherStages * kStage;
+    static constexpr size_t kBar = (size_t)kGatherWarps * kGatherStages * sizeof(uint64_t);
+    static constexpr size_t kMeta = (size_t)kGatherWarps * kGatherStages * 2 * sizeof(uint32_t);
+    static constexpr size_t kAcc = kBytes + kBar + kMeta;
+    static_assert(kStage % 16 == 0, "ring slots must stay 16-byte aligned");
+    static_assert(kAcc % 16 == 0, "accumulator must be 16-byte aligned");
+};
 // The block sum after the apply borrows the ring's last bytes (idle by then;
 // pushed partial sums stay below them).
 constexpr size_t kSumScratchBytes = 2 * kGatherWarps * sizeof(double);
-static_assert(kStageBytes % 16 == 0, "ring slots must stay 16-byte aligned");
-static_assert(kAccOffset % 16 == 0, "accumulator must be 16-byte aligned");
 
 // kFused: also scatter the next iteration; kCanon: decode the canonical bins;
 // kRuns: sum run-bit runs of the bank-spread layout in a register; kUpd: the
-// update bins' storage (canonical bins: FP32 only).
-template <bool kFused, bool kCanon, bool kRuns, int kUpd>
+// update bins' storage (canonical bins: FP32 only); kW: multiply every update
+// by its edge's weight (weighted graphs, Sec. 3.5).
+template <bool kFused, bool kCanon, bool kRuns, int kUpd, bool kW = false>
 __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const GatherArgs a) {
     using U = Upd<kUpd>;
+    using R = Ring<kW>;
     static_assert(!kCanon || kUpd == kUpdF32, "the canonical gather reads FP32 updates");
+    static_assert(!kW || (!kCanon && !kFused), "the weighted gather is a two-phase, bank-spread gather");
     if (a.st->stop) return;
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ uint32_t sh32[32];
     unsigned char* ring = smraw;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smraw + kRingBytes);
-    uint32_t* meta = reinterpret_cast<uint32_t*>(smraw + kRingBytes + kBarBytes);
-    float* acc = reinterpret_cast<float*>(smraw + kAccOffset);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smraw + R::kBytes);
+    uint32_t* meta = reinterpret_cast<uint32_t*>(smraw + R::kBytes + R::kBar);
+    float* acc = reinterpret_cast<float*>(smraw + R::kAcc);
 
     const uint32_t S = cluster_size(), rank = cluster_rank();
     const uint4 unit = a.units[a.order[blockIdx.x / S]];  // (bin, first chunk, end chunk, pieces of the bin)
@@ -567,7 +582,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
         const uint32_t gw = rank * kGatherWarps + warp, GW = S * kGatherWarps;
         const uint32_t wc0 = c_first + (uint32_t)((uint64_t)nch * gw / GW);
         const uint32_t nmine = c_first + (uint32_t)((uint64_t)nch * (gw + 1) / GW) - wc0;
-        unsigned char* wring = ring + (size_t)warp * kGatherStages * kStageBytes;
+        unsigned char* wring = ring + (size_t)warp * kGatherStages * R::kStage;
         uint64_t* wbar = bars + warp * kGatherStages;
         uint32_t* wmeta = meta + warp * kGatherStages * 2;
         const uint32_t lt = lanemask_lt();
@@ -616,16 +631,19 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
             }
             if (lane == 0) {
                 const uint32_t slot = j % kGatherStages;
-                unsigned char* dst = wring + (size_t)slot * kStageBytes;
+                unsigned char* dst = wring + (size_t)slot * R::kStage;
                 if constexpr (kCanon) {
                     wmeta[2 * slot] = fb;
                     wmeta[2 * slot + 1] = us;
                 }
                 const uint32_t* ids = (kCanon ? a.dest : a.gdest) + (size_t)(wc0 + j) * kChunk;
-                mbar_arrive_expect_tx(&wbar[slot], kIdSlotBytes + ubytes);
+                mbar_arrive_expect_tx(&wbar[slot], kIdSlotBytes + (kW ? kChunk * 4u : 0u) + ubytes);
                 bulk_load_hint(dst, ids, kIdSlotBytes, &wbar[slot], stream_policy);
+                if constexpr (kW)
+                    bulk_load_hint(dst + R::kWOff, a.gweight + (size_t)(wc0 + j) * kChunk, kChunk * 4u, &wbar[slot],
+                                   stream_policy);
                 if (ubytes)
-                    bulk_load_hint(dst + kIdSlotBytes, static_cast<const typename U::T*>(a.upd_in) + us, ubytes,
+                    bulk_load_hint(dst + R::kUpdOff, static_cast<const typename U::T*>(a.upd_in) + us, ubytes,
                                    &wbar[slot], stream_policy);
             }
         };
@@ -639,9 +657,9 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
             const uint32_t slot = j % kGatherStages;
             ok = __all_sync(kFull, mbar_wait_bounded(&wbar[slot], (j / kGatherStages) & 1u));
             if (!ok) break;
-            const unsigned char* stage = wring + (size_t)slot * kStageBytes;
+            const unsigned char* stage = wring + (size_t)slot * R::kStage;
             const uint32_t* ids_s = reinterpret_cast<const uint32_t*>(stage);
-            const typename U::T* ups = reinterpret_cast<const typename U::T*>(stage + kIdSlotBytes);
+            const typename U::T* ups = reinterpret_cast<const typename U::T*>(stage + R::kUpdOff);
             constexpr int kPer = kChunk / 32;  // IDs per lane
             // All loads of the chunk first (IDs, then update values), then the
             // adds: eight independent shared-memory operations per lane.
@@ -706,6 +724,18 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
             float val[kPer];
 #pragma unroll
             for (int q = 0; q < kPer; ++q) val[q] = U::load(ups, (!kCanon || (valid >> q & 1u)) ? uo[q] : 0u);
+            if constexpr (kW) {
+                // the weight of each ID sits at the ID's position (Sec. 3.5)
+                const float* wts = reinterpret_cast<const float*>(stage + R::kWOff);
+#pragma unroll
+                for (int h = 0; h < kPer / 4; ++h) {
+                    const float4 w4 = *reinterpret_cast<const float4*>(wts + h * 128 + lane * 4);
+                    val[4 * h] *= w4.x;
+                    val[4 * h + 1] *= w4.y;
+                    val[4 * h + 2] *= w4.z;
+                    val[4 * h + 3] *= w4.w;
+                }
+            }
             [[maybe_unused]] float run = 0.0f;  // kRuns: sum of a run of equal destinations in this lane
 #pragma unroll
             for (int q = 0; q < kPer; ++q) {
@@ -773,7 +803,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
     const uint32_t per = (((len + S - 1) / S) + 3) & ~3u;
     const uint32_t lo = min(len, rank * per), hi = min(len, lo + per);
     float* stage = reinterpret_cast<float*>(ring);
-    const bool push = (size_t)(S - 1) * per * sizeof(float) <= kRingBytes - kSumScratchBytes;
+    const bool push = (size_t)(S - 1) * per * sizeof(float) <= R::kBytes - kSumScratchBytes;
     if (push && S > 1) {
         for (uint32_t t = 0; t < S; ++t) {
             if (t == rank) continue;
@@ -950,7 +980,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
         }
     }
     double res = (double)res_f, dg = (double)dg_f;
-    block_sum2<kGatherWarps * 32>(res, dg, reinterpret_cast<double*>(ring + kRingBytes - kSumScratchBytes));
+    block_sum2<kGatherWarps * 32>(res, dg, reinterpret_cast<double*>(ring + R::kBytes - kSumScratchBytes));
     if (threadIdx.x == 0) {
         a.partials[2 * blockIdx.x] = res;
         a.partials[2 * blockIdx.x + 1] = dg;
@@ -1039,8 +1069,9 @@ GatherFn pick_gather(bool canonical, bool runs, int upd) {
 
 // The accumulator holds q real slots, kPadSlots for the layout's padding and
 // kHubSlots (a pair per warp) for the hubs.
+template <bool kW = false>
 size_t gather_smem_bytes(uint32_t q) {
-    return kAccOffset + (size_t)(((q + 3) & ~3u) + kPadSlots + kHubSlots) * sizeof(float);
+    return Ring<kW>::kAcc + (size_t)(((q + 3) & ~3u) + kPadSlots + kHubSlots) * sizeof(float);
 }
 size_t scatter_smem_bytes(uint32_t q, uint32_t k) {
     return (size_t)((q + 3) & ~3u) * sizeof(float) + (size_t)(k + 1) * sizeof(uint32_t);
@@ -1066,6 +1097,14 @@ int configure_kernels(pcpm_png* g) {
     for (const void* f : gathers)
         if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gs) != cudaSuccess)
             return PCPM_ECUDA;
+    if (g->weighted) {  // weighted handles have q <= PCPM_MAX_WEIGHTED_PART_SIZE
+        const size_t gw = gather_smem_bytes<true>(g->q);
+        const void* wg[] = {(const void*)gather_kernel<false, false, false, kUpdF32, true>,
+                            (const void*)gather_kernel<false, false, true, kUpdF32, true>};
+        for (const void* f : wg)
+            if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gw) != cudaSuccess)
+                return PCPM_ECUDA;
+    }
     const void* scatters[] = {(const void*)scatter_kernel<kUpdF32>, (const void*)scatter_kernel<kUpdF16>,
                               (const void*)scatter_kernel<kUpdBF16>};
     for (const void* f : scatters)
@@ -1111,21 +1150,24 @@ int launch_spr(pcpm_png* g, float* spr, cudaStream_t s) {
     return cudaGetLastError() == cudaSuccess ? PCPM_OK : PCPM_ECUDA;
 }
 
-int launch_scatter(pcpm_png* g, cudaStream_t s) {
+int launch_scatter(pcpm_png* g, cudaStream_t s, bool raw) {
     const size_t smem = scatter_smem_bytes(g->q, g->k);
     void (*f)(uint32_t, uint32_t, uint32_t, const float*, const float*, const uint32_t*, const uint32_t*,
               const uint32_t*, const uint4*, const uint32_t*, void*, const DevState*, int*) =
         g->upd_dtype == kUpdF16 ? scatter_kernel<kUpdF16>
         : g->upd_dtype == kUpdBF16 ? scatter_kernel<kUpdBF16>
                                    : scatter_kernel<kUpdF32>;
-    f<<<g->nsunits, kScatterThreads, smem, s>>>(g->n, g->q, g->k, g->pr[g->cur], g->inv_deg, g->src, g->seg_u,
+    f<<<g->nsunits, kScatterThreads, smem, s>>>(g->n, g->q, g->k, g->pr[g->cur], raw ? nullptr : g->inv_deg, g->src,
+                                               g->seg_u,
                                                g->cnt_u, g->sunits, g->sorder, g->upd[g->ucur], g->state,
                                                &g->state->err);
     return cudaGetLastError() == cudaSuccess ? PCPM_OK : PCPM_ECUDA;
 }
 
-int launch_gather(pcpm_png* g, float d, uint32_t flags, bool fused, cudaStream_t s) {
+int launch_gather(pcpm_png* g, float d, uint32_t flags, bool fused, cudaStream_t s, bool spmv) {
+    const bool weighted = spmv && g->weighted;  // only SpMV applies the weights
     GatherArgs a;
+    a.gweight = g->gweight;
     a.n = g->n;
     a.q = g->q;
     a.k = g->k;
@@ -1162,13 +1204,15 @@ int launch_gather(pcpm_png* g, float d, uint32_t flags, bool fused, cudaStream_t
     attr[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(g->ngunits * g->cluster);
     cfg.blockDim = dim3(kGatherWarps * 32);
-    cfg.dynamicSmemBytes = gather_smem_bytes(g->q);
+    cfg.dynamicSmemBytes = weighted ? gather_smem_bytes<true>(g->q) : gather_smem_bytes(g->q);
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     cudaError_t e;
-    const GatherFn f = fused ? pick_gather<true>(g->canonical_gather != 0, g->gather_runs != 0, g->upd_dtype)
-                             : pick_gather<false>(g->canonical_gather != 0, g->gather_runs != 0, g->upd_dtype);
+    const GatherFn f = weighted ? (g->gather_runs ? gather_kernel<false, false, true, kUpdF32, true>
+                                                  : gather_kernel<false, false, false, kUpdF32, true>)
+                       : fused  ? pick_gather<true>(g->canonical_gather != 0, g->gather_runs != 0, g->upd_dtype)
+                                : pick_gather<false>(g->canonical_gather != 0, g->gather_runs != 0, g->upd_dtype);
     e = cudaLaunchKernelEx(&cfg, f, a);
     g->partial_count = (int)(g->ngunits * g->cluster);
     return e == cudaSuccess ? PCPM_OK : PCPM_ECUDA;

@@ -162,7 +162,8 @@ __global__ void tile_kernel(const uint32_t* __restrict__ row_ptr, const uint32_t
                             uint32_t q, uint32_t k, const uint32_t* __restrict__ tile_start, uint32_t ntiles,
                             uint32_t* __restrict__ tab_e, uint32_t* __restrict__ tab_u,
                             const uint32_t* __restrict__ bin_e, const uint32_t* __restrict__ bin_u,
-                            uint32_t* __restrict__ dest, uint32_t* __restrict__ src, int* __restrict__ err) {
+                            uint32_t* __restrict__ dest, uint32_t* __restrict__ src, int* __restrict__ err,
+                            const float* __restrict__ weights = nullptr, float* __restrict__ wdest = nullptr) {
     extern __shared__ uint32_t sh[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
     uint32_t* ce = sh + (size_t)warp * 2 * k;  // edges (count) / ID cursor (fill)
@@ -218,6 +219,7 @@ __global__ void tile_kernel(const uint32_t* __restrict__ row_ptr, const uint32_t
             if (kFill && valid) {
                 const uint32_t pos_e = ce[key] + __popc(peers & lt);
                 dest[pos_e] = start ? (v | kMsb) : v;
+                if (wdest) wdest[pos_e] = weights[e];  // Sec. 3.5: the weight beside its ID
                 if (start) src[cu[key] + __popc(peers & smask & lt)] = u;
             }
             __syncwarp();
@@ -485,9 +487,11 @@ __global__ void __launch_bounds__(kLayoutWarps * 32) gather_layout_kernel(
     const uint32_t* __restrict__ dest, const uint32_t* __restrict__ bin_e, const uint32_t* __restrict__ ichunk_start,
     uint32_t k, const uint32_t* __restrict__ chunk_base, const uint32_t* __restrict__ hubs, uint32_t q,
     uint64_t nichunks, uint32_t* __restrict__ gdest, uint32_t* __restrict__ slice_start,
-    uint32_t* __restrict__ slice_bytes, uint32_t upd_bytes, unsigned long long* __restrict__ stats) {
+    uint32_t* __restrict__ slice_bytes, uint32_t upd_bytes, unsigned long long* __restrict__ stats,
+    const float* __restrict__ wdest = nullptr, float* __restrict__ gweight = nullptr) {
     __shared__ uint32_t keycnt[kLayoutWarps][kNumKeys + 2];
     __shared__ uint32_t sortbuf[kLayoutWarps][kChunk];
+    __shared__ float sortw[kLayoutWarps][kChunk];  // weighted graphs: weights follow their IDs
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt = lanemask_lt();
     uint32_t* cnt = keycnt[warp];
@@ -560,6 +564,7 @@ __global__ void __launch_bounds__(kLayoutWarps * 32) gather_layout_kernel(
             // banks within a round); hubs: the hub slot pair
             const uint32_t slot = key[r] == kKeyHub ? q + kPadSlots + (loc[r] == h1 ? 1u : 0u) : loc[r];
             sorted[pos] = key[r] == kKeyPad ? q + (pos >> 3) : (slot | ((idx[r] - us) << kGwUpdShift));
+            if (gweight) sortw[warp][pos] = key[r] == kKeyPad ? 0.0f : wdest[P + 32 * r + lane];
             if (key[r] != kKeyPad && (loc[r] >= q || idx[r] - us >= slot_max)) bad = true;
         }
         __syncwarp();
@@ -571,12 +576,15 @@ __global__ void __launch_bounds__(kLayoutWarps * 32) gather_layout_kernel(
             const uint32_t g_end = cnt[grp], g_beg = grp ? cnt[grp - 1] : 0;
             for (uint32_t x = g_beg + 1; x < g_end; ++x) {
                 const uint32_t w = sorted[x];
+                const float wt = gweight ? sortw[warp][x] : 0.0f;
                 uint32_t y = x;
                 while (y > g_beg && (sorted[y - 1] & kGwLocMask) > (w & kGwLocMask)) {
                     sorted[y] = sorted[y - 1];
+                    if (gweight) sortw[warp][y] = sortw[warp][y - 1];
                     --y;
                 }
                 sorted[y] = w;
+                if (gweight) sortw[warp][y] = wt;
             }
         }
         __syncwarp();
@@ -592,7 +600,9 @@ __global__ void __launch_bounds__(kLayoutWarps * 32) gather_layout_kernel(
             const bool pad = l >= q && l < q + kPadSlots;
             if (round != 7u && !pad && (sorted[sp + 1] & kGwLocMask) == l) w |= kGwRunBit;
             nmerged += __popc(__ballot_sync(0xffffffffu, (w & kGwRunBit) != 0));
-            out[128 * (round >> 2) + 4 * slot_lane + (round & 3u)] = w;
+            const uint32_t o = 128 * (round >> 2) + 4 * slot_lane + (round & 3u);
+            out[o] = w;
+            if (gweight) gweight[ic * kChunk + o] = sortw[warp][sp];
         }
         if (lane == 0) {
             slice_start[ic] = us;
@@ -767,8 +777,10 @@ int build_png(pcpm_png* g, const uint32_t* row_ptr, const uint32_t* col, const p
     BCK(cudaMemsetAsync(g->dest, 0, dest_len * sizeof(uint32_t), s));
     BCK(dev_alloc(g, (void**)&g->src, (g->ne + 4) * sizeof(uint32_t)));
     if (ntiles) {
+        if (g->weighted) BCK(dev_alloc(g, (void**)&g->wdest, dest_len * sizeof(float)));
         tile_kernel<true><<<tile_grid, wpc * 32, tile_smem, s>>>(row_ptr, col, n, q, k, tile_start, ntiles, tab_e,
-                                                                tab_u, g->bin_e, g->bin_u, g->dest, g->src, d_err);
+                                                                tab_u, g->bin_e, g->bin_u, g->dest, g->src, d_err,
+                                                                g->weights_in, g->wdest);
         BCK(cudaGetLastError());
     }
 
@@ -832,9 +844,10 @@ int build_png(pcpm_png* g, const uint32_t* row_ptr, const uint32_t* col, const p
         BCK(tmp.alloc(&lstats, 2));
         BCK(cudaMemsetAsync(lstats, 0, 2 * sizeof(*lstats), s));
         if (nic) {
+            if (g->weighted) BCK(dev_alloc(g, (void**)&g->gweight, (size_t)nic * kChunk * sizeof(float)));
             gather_layout_kernel<<<grid_for((uint64_t)nic * 32, kLayoutWarps * 32, sms * 8), kLayoutWarps * 32, 0, s>>>(
                 g->dest, g->bin_e, g->ichunk_start, k, g->chunk_base, g->hubs, q, nic, g->gdest, g->gslice_start,
-                g->gslice_bytes, g->upd_bytes, lstats);
+                g->gslice_bytes, g->upd_bytes, lstats, g->wdest, g->gweight);
             BCK(cudaGetLastError());
         }
         unsigned long long hstats[2] = {0, 0};
