@@ -61,6 +61,7 @@ def parse_args():
                     help="also train the learned warm start on 64 RMAT graphs (scales 18-22, a in [0.45, 0.65]) "
                          "and compare iterations and time to residual 1e-7 with the uniform start (minutes)")
     ap.add_argument("--ws-graphs", type=int, default=64, help="training graphs of the warm-start leg")
+    ap.add_argument("--no-spmv", action="store_true", help="skip the weighted SpMV leg")
     ap.add_argument("--mode", choices=("fused", "two_phase"), default="two_phase",
                     help="iteration form timed for `value` (the other is reported in other_mode)")
     ap.add_argument("--ref-budget-s", type=float, default=120.0, help="reference arm: timed seconds target")
@@ -293,6 +294,40 @@ def run_reference(a):
 
 
 # ---------------------------------------------------------------- GPU side
+def spmv_leg(a, rp, col, m):
+    """Weighted SpMV y = A^T_w x over the PNG (Sec. 3.5) on the same graph:
+    random weights, q = 16384 (the weighted gather's limit), GTEPS of the
+    product (scatter of x + weighted gather) from CUDA events."""
+    import torch
+    import paper_1709_07122_gb300 as pcpm
+    q = min(a.part_size, 16384)
+    rng = np.random.default_rng(a.seed + 11)
+    w = torch.from_numpy(rng.random(m, dtype=np.float32)).cuda()
+    x = torch.from_numpy(rng.random(rp.size - 1, dtype=np.float32)).cuda()
+    d_rp, d_col = pcpm.to_device_csr(rp, col)
+    res = {}
+    with pcpm.PNG.weighted(d_rp, d_col, w, q) as gw, pcpm.PNG(d_rp, d_col, q) as gu:
+        for name, g in (("weighted", gw), ("unit_weights", gu)):
+            y = torch.empty_like(x)
+            for _ in range(3):
+                g.spmv(x, y)
+            reps = 20
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(reps):
+                g.spmv(x, y)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            res[name] = {"ms": ms, "gteps": m / (ms * 1e-3) / 1e9}
+    del d_rp, d_col, w, x
+    torch.cuda.empty_cache()
+    res["part_size"] = q
+    res["note"] = "one scatter of x (no 1/outdeg) + one gather; weighted stages 4 extra bytes per edge"
+    return res
+
+
 def warm_start_leg(a, rp, col):
     """Learned warm start (not in the paper): train on RMAT graphs of scales
     18-22 with a drawn from [0.45, 0.65], then solve the benchmark graph (not
@@ -479,6 +514,9 @@ def run_ours(a):
             gu.close()
         del d_rp, d_col
         out["update_dtypes"] = dts
+
+    if not a.no_spmv:
+        out["spmv"] = spmv_leg(a, rp, col, m)
 
     if a.warm_start:
         out["warm_start"] = warm_start_leg(a, rp, col)
