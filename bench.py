@@ -62,6 +62,8 @@ def parse_args():
                          "and compare iterations and time to residual 1e-7 with the uniform start (minutes)")
     ap.add_argument("--ws-graphs", type=int, default=64, help="training graphs of the warm-start leg")
     ap.add_argument("--no-spmv", action="store_true", help="skip the weighted SpMV leg")
+    ap.add_argument("--batched", action="store_true",
+                    help="also solve 256 RMAT graphs of scales 10-18 with one captured CUDA graph launch")
     ap.add_argument("--mode", choices=("fused", "two_phase"), default="two_phase",
                     help="iteration form timed for `value` (the other is reported in other_mode)")
     ap.add_argument("--ref-budget-s", type=float, default=120.0, help="reference arm: timed seconds target")
@@ -328,6 +330,68 @@ def spmv_leg(a, rp, col, m):
     return res
 
 
+def batched_leg(a, graphs: int = 256, iters: int = 20):
+    """Many small independent graphs (RMAT, scales drawn from 10-18, random
+    labels) solved for `iters` iterations each by one captured CUDA graph
+    launch, against the same solves issued call by call on one stream. The
+    partition size is picked per scale from {2048, 8192, 32768} by timing
+    five iterations on the first graph of that scale."""
+    import torch
+    import paper_1709_07122_gb300 as pcpm
+    import graphgen
+    rng = np.random.default_rng(a.seed + 21)
+    scales = [int(s) for s in rng.integers(10, 19, size=graphs)]
+    t0 = time.perf_counter()
+    data = [graphgen.rmat(s, a.edge_factor, seed=a.seed + 3000 + i, relabel="random") for i, s in enumerate(scales)]
+    gen_s = time.perf_counter() - t0
+    dev = [pcpm.to_device_csr(rp, col) for rp, col in data]
+    edges = sum(int(rp[-1]) for rp, _ in data)
+    # partition size per scale
+    best_q = {}
+    for s in sorted(set(scales)):
+        i = scales.index(s)
+        times = {}
+        for q in (2048, 8192, 32768):
+            with pcpm.PNG(*dev[i], q) as g:
+                g.reset()
+                g.iterate(a.d, 2, mode="two_phase")
+                times[q] = g.iterate_timed(a.d, 5, mode="two_phase")["span"]
+        best_q[s] = min(times, key=times.get)
+    handles = [pcpm.PNG(*dev[i], best_q[s]) for i, s in enumerate(scales)]
+    del dev
+    t1 = time.perf_counter()
+    batch = pcpm.Batch(handles, a.d, iters, mode="two_phase")
+    capture_s = time.perf_counter() - t1
+    batch.launch()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        batch.launch()
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    graph_ms = statistics.median(ms)
+    # the same work, one call after another
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for h in handles:
+        h.reset()
+        h.iterate(a.d, iters, sync=False, mode="two_phase")
+    e1.record()
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1)
+    batch.close()
+    for h in handles:
+        h.close()
+    return {"graphs": graphs, "scales": "10-18", "iterations_each": iters, "edges_total": edges,
+            "partition_size_per_scale": {str(k): v for k, v in sorted(best_q.items())},
+            "one_graph_launch_ms": graph_ms, "gteps": edges * iters / (graph_ms * 1e-3) / 1e9,
+            "call_by_call_ms": seq_ms, "call_by_call_gteps": edges * iters / (seq_ms * 1e-3) / 1e9,
+            "capture_ms": capture_s * 1e3, "generate_s": gen_s}
+
+
 def warm_start_leg(a, rp, col):
     """Learned warm start (not in the paper): train on RMAT graphs of scales
     18-22 with a drawn from [0.45, 0.65], then solve the benchmark graph (not
@@ -520,6 +584,9 @@ def run_ours(a):
 
     if a.warm_start:
         out["warm_start"] = warm_start_leg(a, rp, col)
+
+    if a.batched:
+        out["batched"] = batched_leg(a)
 
     if rank == 0 and not a.no_cpu_baseline:
         gt, dt, _, y_ref = cpu_oracle_iteration(rp, col, a.d)

@@ -170,6 +170,25 @@ int pcpm_build_ex(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t n, 
                   uint32_t part_size, const pcpm_build_options* options, void* stream,
                   pcpm_png** out);
 
+/* Batched solves (not in the paper): many independent graphs, each with its
+ * own handle, solved by one CUDA graph launch. pcpm_batch_create captures,
+ * for every handle, pcpm_reset to the uniform start followed by `iters`
+ * iterations (d, flags as in pcpm_iterate, no tolerance), each handle on one
+ * of up to 32 graph branches so that small graphs run side by side; it
+ * instantiates the graph once. pcpm_batch_launch runs the whole batch with
+ * one cudaGraphLaunch on `stream` and leaves every handle as if that work had
+ * been enqueued through pcpm_reset and pcpm_iterate (pcpm_ranks and
+ * pcpm_residual_history then read the results).
+ *   handles  host array of `count` distinct handles (PCPM_EINVAL otherwise),
+ *            which must outlive the batch.
+ * pcpm_batch_create synchronises the default stream if a handle's residual
+ * history has to grow (it captures on private streams). */
+typedef struct pcpm_batch pcpm_batch;
+int pcpm_batch_create(pcpm_png* const* handles, int count, float d, int iters, uint32_t flags,
+                      pcpm_batch** out);
+int pcpm_batch_launch(pcpm_batch* batch, void* stream);
+void pcpm_batch_free(pcpm_batch* batch); /* NULL is a no-op */
+
 /* Weighted graphs and SpMV (Sec. 3.5): pcpm_build with an edge weight per
  * column index.
  *   weights  device, float[m], in CSR order (weight of col_idx[e] at e); only
@@ -307,6 +326,10 @@ int pcpm_rank_stats_noalloc(const float* x, const float* y, const uint32_t* row_
 
 /* Message for a status code (static string). */
 const char* pcpm_strerror(int code);
+/* Name of the CUDA runtime error behind the calling thread's last PCPM_ECUDA
+ * (or PCPM_ENOMEM from an allocation), e.g. "cudaErrorInvalidValue";
+ * "cudaSuccess" if none was recorded. */
+const char* pcpm_last_cuda_error(void);
 
 #ifdef __cplusplus
 }

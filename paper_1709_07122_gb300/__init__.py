@@ -34,6 +34,8 @@ class PcpmError(RuntimeError):
     def __init__(self, code: int, where: str):
         self.code = code
         msg = lib().pcpm_strerror(code).decode() if _lib is not None else str(code)
+        if code == -2 and _lib is not None:  # PCPM_ECUDA: name the CUDA error
+            msg += " [" + lib().pcpm_last_cuda_error().decode() + "]"
         super().__init__(f"{where} failed: {msg} (status {code})")
 
 
@@ -92,9 +94,13 @@ def lib(path: str | None = None):
                 "pcpm_export_state": (i32, [vp, vp, vp, vp, pd]),
                 "pcpm_rank_stats_noalloc": (i32, [vp, vp, vp, u32, vp, vp]),
                 "pcpm_strerror": (ctypes.c_char_p, [i32]),
+                "pcpm_last_cuda_error": (ctypes.c_char_p, []),
                 "pcpm_build_weighted": (i32, [vp, vp, vp, u32, u64, u32, ctypes.POINTER(_Options), vp,
                                               ctypes.POINTER(vp)]),
                 "pcpm_spmv": (i32, [vp, vp, vp, vp]),
+                "pcpm_batch_create": (i32, [vp, i32, f32, i32, u32, ctypes.POINTER(vp)]),
+                "pcpm_batch_launch": (i32, [vp, vp]),
+                "pcpm_batch_free": (None, [vp]),
                 "pcpm_export_weights": (i32, [vp, vp]),
                 "pcpm_ws_features": (i32, [vp, vp, vp, vp, vp]),
                 "pcpm_ws_predict": (i32, [vp, vp, u32, vp, vp]),
@@ -436,3 +442,37 @@ def ws_init_ranks(pred, out=None, stream=None):
     _check(lib().pcpm_ws_init_ranks(_f32(pred, n, "pred"), n, _f32(out, n, "out"), _stream(stream)),
            "pcpm_ws_init_ranks")
     return out
+
+
+class Batch:
+    """Independent graphs solved by one CUDA graph launch (pcpm_batch_*):
+    every handle is reset to the uniform start and iterated `iters` times."""
+
+    def __init__(self, handles, d: float = 0.85, iters: int = 20, dangling: str = "uniform",
+                 mode: str = "two_phase"):
+        self.handles = list(handles)  # the handles must outlive the batch
+        arr = (ctypes.c_void_p * len(self.handles))(*[h._h.value for h in self.handles])
+        b = ctypes.c_void_p()
+        _check(lib().pcpm_batch_create(arr, len(self.handles), float(d), int(iters), _flags(dangling, mode),
+                                       ctypes.byref(b)), "pcpm_batch_create")
+        self._b = b
+
+    def launch(self, stream=None):
+        _check(lib().pcpm_batch_launch(self._b, _stream(stream)), "pcpm_batch_launch")
+
+    def close(self):
+        if getattr(self, "_b", None) is not None and self._b.value:
+            lib().pcpm_batch_free(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -5,6 +5,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <set>
 #include <vector>
 
 #include "pcpm_internal.cuh"
@@ -19,12 +20,26 @@ cudaError_t dev_alloc(pcpm_png* g, void** p, size_t bytes) {
     return e;
 }
 
+thread_local cudaError_t g_last_cuda_error = cudaSuccess;
+
+void note_cuda_error(cudaError_t e) { g_last_cuda_error = e; }
+
+int launch_status() {
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) return PCPM_OK;
+    note_cuda_error(e);
+    return PCPM_ECUDA;
+}
+
 namespace {
 
-#define CK(call)                                                                                  \
-    do {                                                                                          \
-        cudaError_t e_ = (call);                                                                  \
-        if (e_ != cudaSuccess) return e_ == cudaErrorMemoryAllocation ? PCPM_ENOMEM : PCPM_ECUDA; \
+#define CK(call)                                                                  \
+    do {                                                                          \
+        cudaError_t e_ = (call);                                                  \
+        if (e_ != cudaSuccess) {                                                  \
+            note_cuda_error(e_);                                                  \
+            return e_ == cudaErrorMemoryAllocation ? PCPM_ENOMEM : PCPM_ECUDA;    \
+        }                                                                         \
     } while (0)
 
 #define RC(call)                          \
@@ -315,6 +330,124 @@ int pcpm_spmv(pcpm_png* g, const float* x, float* y, void* stream) {
     return PCPM_OK;
 }
 
+// ------------------------------------------------------------------ batches
+struct pcpm_batch {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    // each handle's host-side solver state right after the captured work
+    struct After {
+        pcpm_png* g;
+        int cur, ucur, upd_valid, iters_done;
+    };
+    std::vector<After> after;
+};
+
+int pcpm_batch_create(pcpm_png* const* handles, int count, float d, int iters, uint32_t flags, pcpm_batch** out) {
+    if (!handles || count < 1 || iters < 1 || bad_damping(d) || (flags & ~kAllFlags) || !out) return PCPM_EINVAL;
+    std::set<const pcpm_png*> seen;
+    for (int i = 0; i < count; ++i)
+        if (!handles[i] || !seen.insert(handles[i]).second) return PCPM_EINVAL;  // no handle twice
+    // history room for the captured iterations (grows outside the capture)
+    for (int i = 0; i < count; ++i) RC(ensure_hist(handles[i], iters, (cudaStream_t)0));
+    pcpm_batch* b = new (std::nothrow) pcpm_batch;
+    if (!b) return PCPM_ENOMEM;
+    const int nb = std::min(count, kBatchStreams);
+    std::vector<cudaStream_t> streams(nb, nullptr);
+    std::vector<cudaEvent_t> joins(nb, nullptr);
+    cudaStream_t origin = nullptr;
+    cudaEvent_t fork = nullptr;
+    int rc = PCPM_OK;
+    bool capturing = false;
+    if (cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess)
+        rc = PCPM_ECUDA;
+    for (int j = 0; j < nb && rc == PCPM_OK; ++j)
+        if (cudaStreamCreateWithFlags(&streams[j], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&joins[j], cudaEventDisableTiming) != cudaSuccess)
+            rc = PCPM_ECUDA;
+    if (rc == PCPM_OK) {
+        const cudaError_t e = cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            note_cuda_error(e);
+            rc = PCPM_ECUDA;
+        }
+    }
+    capturing = rc == PCPM_OK;
+    auto ok = [&](cudaError_t e) {
+        if (e != cudaSuccess) {
+            note_cuda_error(e);
+            rc = PCPM_ECUDA;
+        }
+        return rc == PCPM_OK;
+    };
+    if (rc == PCPM_OK) ok(cudaEventRecord(fork, origin));
+    for (int j = 0; j < nb && rc == PCPM_OK; ++j) ok(cudaStreamWaitEvent(streams[j], fork, 0));
+    // handle i on branch i % nb: independent graphs run side by side
+    for (int i = 0; i < count && rc == PCPM_OK; ++i) {
+        pcpm_png* g = handles[i];
+        cudaStream_t s = streams[i % nb];
+        rc = pcpm_reset(g, nullptr, s);
+        if (rc == PCPM_OK) rc = run_iterations(g, d, iters, 0.0, flags, s, nullptr);
+        if (rc == PCPM_OK) {
+            g->iters_done = iters;
+            b->after.push_back({g, g->cur, g->ucur, g->upd_valid, g->iters_done});
+        }
+    }
+    for (int j = 0; j < nb && rc == PCPM_OK; ++j)
+        if (ok(cudaEventRecord(joins[j], streams[j]))) ok(cudaStreamWaitEvent(origin, joins[j], 0));
+    if (capturing) {
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(origin, &graph);
+        if (rc == PCPM_OK && e == cudaSuccess) {
+            b->graph = graph;
+            const cudaError_t ei = cudaGraphInstantiate(&b->exec, graph, 0);
+            if (ei != cudaSuccess) {
+                note_cuda_error(ei);
+                rc = PCPM_ECUDA;
+            }
+        } else {
+            if (e != cudaSuccess) note_cuda_error(e);
+            if (graph) cudaGraphDestroy(graph);
+            if (rc == PCPM_OK) rc = PCPM_ECUDA;
+        }
+    }
+    cudaGetLastError();
+    for (int j = 0; j < nb; ++j) {
+        if (joins[j]) cudaEventDestroy(joins[j]);
+        if (streams[j]) cudaStreamDestroy(streams[j]);
+    }
+    if (fork) cudaEventDestroy(fork);
+    if (origin) cudaStreamDestroy(origin);
+    for (int i = 0; i < count; ++i) handles[i]->last_stream = nullptr;
+    if (rc != PCPM_OK) {
+        pcpm_batch_free(b);
+        return rc;
+    }
+    *out = b;
+    return PCPM_OK;
+}
+
+int pcpm_batch_launch(pcpm_batch* b, void* stream) {
+    if (!b || !b->exec) return PCPM_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaGraphLaunch(b->exec, s));
+    for (const auto& a : b->after) {
+        a.g->cur = a.cur;
+        a.g->ucur = a.ucur;
+        a.g->upd_valid = a.upd_valid;
+        a.g->iters_done = a.iters_done;
+        a.g->last_stream = s;
+    }
+    return PCPM_OK;
+}
+
+void pcpm_batch_free(pcpm_batch* b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    delete b;
+}
+
 int pcpm_export_weights(const pcpm_png* g, float* wbin) {
     if (!g || !wbin || !g->weighted) return PCPM_EINVAL;
     CK(cudaStreamSynchronize(g->last_stream));
@@ -535,6 +668,8 @@ int pcpm_export_state(const pcpm_png* g, float* pr, float* spr, void* updates, d
     }
     return PCPM_OK;
 }
+
+const char* pcpm_last_cuda_error(void) { return cudaGetErrorName(g_last_cuda_error); }
 
 const char* pcpm_strerror(int code) {
     switch (code) {

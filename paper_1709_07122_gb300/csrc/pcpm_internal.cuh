@@ -56,6 +56,8 @@ constexpr int kScatterUnroll = 4;
 constexpr int kReduceThreads = 512;
 // Largest thread-block cluster used for one bin.
 constexpr int kMaxCluster = 8;
+// Streams (graph branches) a batch capture spreads its solves over.
+constexpr int kBatchStreams = 32;
 
 // Upper bound for a device-side wait on an mbarrier, in SM clock cycles
 // (about one second at 2 GHz). A wait that runs out sets kErrTimeout.
@@ -158,6 +160,11 @@ int build_png(pcpm_png* g, const uint32_t* row_ptr, const uint32_t* col, const p
 // Iteration kernels (pcpm_iter.cu).
 int configure_kernels(pcpm_png* g);
 int pull_sum(pcpm_png* g, const float* pr_like, float* out, cudaStream_t s);
+// Records a failed CUDA call for pcpm_last_cuda_error (per thread).
+void note_cuda_error(cudaError_t e);
+// PCPM_OK if the last kernel launch on this thread succeeded, else records the
+// error and returns PCPM_ECUDA.
+int launch_status();
 int launch_init(pcpm_png* g, const float* pr_init, cudaStream_t s);
 // raw: stage x itself (SpMV) instead of x * (1/outdeg).
 int launch_scatter(pcpm_png* g, cudaStream_t s, bool raw = false);

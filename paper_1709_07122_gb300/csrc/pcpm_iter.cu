@@ -32,6 +32,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "pcpm_internal.cuh"
 
@@ -1084,6 +1085,20 @@ size_t partial_slots(const pcpm_png* g) {
 }
 
 // Picks the cluster size for the gather and sets shared-memory limits.
+// The dynamic shared-memory limit is a property of the kernel, shared by every
+// handle: only ever raise it, so a handle built later with a smaller q does
+// not lower the limit an earlier handle's launches need.
+std::mutex g_smem_attr_mutex;
+
+cudaError_t raise_smem_limit(const void* f, size_t bytes) {
+    std::lock_guard<std::mutex> lock(g_smem_attr_mutex);
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, f);
+    if (e != cudaSuccess) return e;
+    if ((size_t)fa.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 int configure_kernels(pcpm_png* g) {
     const size_t gs = gather_smem_bytes(g->q), ss = scatter_smem_bytes(g->q, g->k);
     const void* gathers[] = {
@@ -1095,21 +1110,27 @@ int configure_kernels(pcpm_png* g) {
         (const void*)pick_gather<false>(false, false, kUpdBF16), (const void*)pick_gather<true>(false, false, kUpdBF16),
         (const void*)pick_gather<false>(false, true, kUpdBF16), (const void*)pick_gather<true>(false, true, kUpdBF16)};
     for (const void* f : gathers)
-        if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gs) != cudaSuccess)
+        if (const cudaError_t e = raise_smem_limit(f, gs); e != cudaSuccess) {
+            note_cuda_error(e);
             return PCPM_ECUDA;
+        }
     if (g->weighted) {  // weighted handles have q <= PCPM_MAX_WEIGHTED_PART_SIZE
         const size_t gw = gather_smem_bytes<true>(g->q);
         const void* wg[] = {(const void*)gather_kernel<false, false, false, kUpdF32, true>,
                             (const void*)gather_kernel<false, false, true, kUpdF32, true>};
         for (const void* f : wg)
-            if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gw) != cudaSuccess)
+            if (const cudaError_t e = raise_smem_limit(f, gw); e != cudaSuccess) {
+                note_cuda_error(e);
                 return PCPM_ECUDA;
+            }
     }
     const void* scatters[] = {(const void*)scatter_kernel<kUpdF32>, (const void*)scatter_kernel<kUpdF16>,
                               (const void*)scatter_kernel<kUpdBF16>};
     for (const void* f : scatters)
-        if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss) != cudaSuccess)
+        if (const cudaError_t e = raise_smem_limit(f, ss); e != cudaSuccess) {
+            note_cuda_error(e);
             return PCPM_ECUDA;
+        }
     // Two CTAs per gather unit unless the build options ask otherwise (two
     // measured best at k = 512 against one and four); smaller if the device
     // cannot co-schedule that many.
@@ -1141,13 +1162,13 @@ int launch_init(pcpm_png* g, const float* pr_init, cudaStream_t s) {
     const int blocks = (int)std::min<uint64_t>(kInitBlocks, (g->n + kReduceThreads - 1) / kReduceThreads);
     init_kernel<<<blocks, kReduceThreads, 0, s>>>(g->n, pr_init, g->inv_deg, g->pr[g->cur], g->partials);
     g->partial_count = blocks;
-    return cudaGetLastError() == cudaSuccess ? PCPM_OK : PCPM_ECUDA;
+    return launch_status();
 }
 
 int launch_spr(pcpm_png* g, float* spr, cudaStream_t s) {
     spr_kernel<<<(int)std::min<uint64_t>(4096, (g->n + 255) / 256), 256, 0, s>>>(g->n, g->pr[g->cur], g->inv_deg,
                                                                                   spr);
-    return cudaGetLastError() == cudaSuccess ? PCPM_OK : PCPM_ECUDA;
+    return launch_status();
 }
 
 int launch_scatter(pcpm_png* g, cudaStream_t s, bool raw) {
@@ -1161,7 +1182,7 @@ int launch_scatter(pcpm_png* g, cudaStream_t s, bool raw) {
                                                g->seg_u,
                                                g->cnt_u, g->sunits, g->sorder, g->upd[g->ucur], g->state,
                                                &g->state->err);
-    return cudaGetLastError() == cudaSuccess ? PCPM_OK : PCPM_ECUDA;
+    return launch_status();
 }
 
 int launch_gather(pcpm_png* g, float d, uint32_t flags, bool fused, cudaStream_t s, bool spmv) {
@@ -1215,12 +1236,13 @@ int launch_gather(pcpm_png* g, float d, uint32_t flags, bool fused, cudaStream_t
                                 : pick_gather<false>(g->canonical_gather != 0, g->gather_runs != 0, g->upd_dtype);
     e = cudaLaunchKernelEx(&cfg, f, a);
     g->partial_count = (int)(g->ngunits * g->cluster);
+    if (e != cudaSuccess) note_cuda_error(e);
     return e == cudaSuccess ? PCPM_OK : PCPM_ECUDA;
 }
 
 int launch_reduce(pcpm_png* g, double tol, int hist_slot, cudaStream_t s) {
     reduce_kernel<<<1, kReduceThreads, 0, s>>>(g->partials, g->partial_count, g->state, g->hist, hist_slot, tol);
-    return cudaGetLastError() == cudaSuccess ? PCPM_OK : PCPM_ECUDA;
+    return launch_status();
 }
 
 }  // namespace pcpm

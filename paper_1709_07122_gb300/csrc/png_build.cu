@@ -653,10 +653,13 @@ struct TempBufs {
     }
 };
 
-#define BCK(call)                                                                    \
-    do {                                                                             \
-        cudaError_t e_ = (call);                                                     \
-        if (e_ != cudaSuccess) return e_ == cudaErrorMemoryAllocation ? PCPM_ENOMEM : PCPM_ECUDA; \
+#define BCK(call)                                                              \
+    do {                                                                       \
+        cudaError_t e_ = (call);                                               \
+        if (e_ != cudaSuccess) {                                               \
+            note_cuda_error(e_);                                               \
+            return e_ == cudaErrorMemoryAllocation ? PCPM_ENOMEM : PCPM_ECUDA; \
+        }                                                                      \
     } while (0)
 
 int grid_for(uint64_t work, int threads, int cap) {
@@ -668,7 +671,7 @@ int grid_for(uint64_t work, int threads, int cap) {
 int scan_exclusive(const uint32_t* in, uint32_t* out, uint64_t N, TempBufs& tmp, cudaStream_t s) {
     if (N <= 1024ull * kSmallScanItems) {
         scan_small_kernel<<<1, 1024, 0, s>>>(in, out, (uint32_t)N);
-        return cudaGetLastError() == cudaSuccess ? PCPM_OK : PCPM_ECUDA;
+        return launch_status();
     }
     const uint64_t nb = (N + kScanBlockItems - 1) / kScanBlockItems;
     if (nb > 1024ull * kSmallScanItems) return PCPM_EINVAL;
@@ -679,7 +682,7 @@ int scan_exclusive(const uint32_t* in, uint32_t* out, uint64_t N, TempBufs& tmp,
     scan_small_kernel<<<1, 1024, 0, s>>>(sums, offs, (uint32_t)nb);
     scan_block_apply_kernel<<<(unsigned)nb, 1024, 0, s>>>(in, (uint32_t)N, offs, out);
     BCK(cudaMemcpyAsync(out + N, offs + nb, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
-    return cudaGetLastError() == cudaSuccess ? PCPM_OK : PCPM_ECUDA;
+    return launch_status();
 }
 
 int colscan(uint32_t* tab, uint32_t nrows, uint32_t k, uint32_t* totals, TempBufs& tmp, cudaStream_t s) {
@@ -690,7 +693,7 @@ int colscan(uint32_t* tab, uint32_t nrows, uint32_t k, uint32_t* totals, TempBuf
     colscan_sums_kernel<<<grd, blk, 0, s>>>(tab, nrows, k, bsum);
     colscan_blocks_kernel<<<(k + 255) / 256, 256, 0, s>>>(bsum, nb, k, tab, nrows, totals);
     colscan_apply_kernel<<<grd, blk, 0, s>>>(tab, nrows, k, bsum);
-    return cudaGetLastError() == cudaSuccess ? PCPM_OK : PCPM_ECUDA;
+    return launch_status();
 }
 
 int read_err(int* d_err, cudaStream_t s, int* h_err) {

@@ -348,3 +348,20 @@ def test_hot_destinations_take_register_runs():
     rp, col = graphgen.random_graph(1 << 15, 1 << 18, seed=5)
     with pcpm.PNG.from_host(rp, col, 1 << 15) as g:
         assert g.info["gather_runs"] == 0, g.info
+
+
+def test_handles_with_different_partition_sizes_coexist():
+    # Kernel limits (such as the dynamic shared memory a launch may use) are
+    # shared by all handles: building a small-q handle must not break a
+    # large-q handle built before it, and the other way round.
+    graphs = [(graphgen.rmat(10, 8, seed=91), 32768), (graphgen.rmat(11, 8, seed=92), 64),
+              (graphgen.rmat(9, 8, seed=93), 4096)]
+    handles = [pcpm.PNG.from_host(rp, col, q) for (rp, col), q in graphs]
+    refs = [oracle.pagerank(rp, col, 0.85, iters=4)["x"] for (rp, col), _ in graphs]
+    for order in ([0, 1, 2], [2, 0, 1]):
+        for i in order:
+            handles[i].reset()
+            handles[i].iterate(0.85, 4, mode="two_phase")
+            assert l1(handles[i].ranks().cpu().numpy(), refs[i]) <= L1_TOL
+    for h in handles:
+        h.close()
