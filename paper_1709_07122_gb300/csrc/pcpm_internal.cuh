@@ -49,9 +49,10 @@ constexpr uint32_t kHubSlots = 2 * kGatherWarps;
 // Update bin storage: PCPM_UPDATE_F32, _F16 (SPR * 2^15), _BF16.
 constexpr int kUpdF32 = (int)PCPM_UPDATE_F32, kUpdF16 = (int)PCPM_UPDATE_F16, kUpdBF16 = (int)PCPM_UPDATE_BF16;
 constexpr float kF16Scale = (float)(1 << PCPM_F16_SCALE_LOG2);
-// Scatter: threads per CTA and 4-entry groups in flight per thread.
+// Scatter: threads per CTA; bytes of each of a warp's two bulk-copy stages of
+// source indices.
 constexpr int kScatterThreads = 1024;
-constexpr int kScatterUnroll = 4;
+constexpr uint32_t kScatterStageBytes = 1488;
 // Apply / reduce threads.
 constexpr int kReduceThreads = 512;
 // Largest thread-block cluster used for one bin.

@@ -65,6 +65,11 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 __device__ __forceinline__ void fence_mbar_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
+// Orders this thread's earlier generic-proxy shared-memory accesses before
+// later bulk copies (async proxy) into the same memory.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
 
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
@@ -186,14 +191,6 @@ __device__ __forceinline__ void push_range(const float* src, float* dst, uint32_
 }
 
 // ------------------------------------------------------------ global memory
-__device__ __forceinline__ uint4 ld_stream_u4(const uint32_t* p) {
-    uint4 r;
-    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
-                 : "l"(p));
-    return r;
-}
-
 __device__ __forceinline__ void st_stream_f4(float* p, float4 v) {
     asm volatile("st.global.cs.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
                  : "memory");
@@ -290,9 +287,14 @@ __device__ __forceinline__ uint32_t seg_groups(uint32_t a, uint32_t c) {
     return c ? ((a + c + 3) >> 2) - (a >> 2) : 0;
 }
 
-// gpre[j] = groups of segments < j, gpre[k] = total (whole block).
+// gpre[j] = groups of segments < j, gpre[k] = total (whole block). With
+// dsh: dsh[j] = segrow[j] / 4 - gpre[j] (mod 2^32), so the flattened group f
+// of segment j starts at entry 4 * (f + dsh[j]) of the update array, and
+// emsk[j] = lo | hi << 2: the entries of the segment's first group start at
+// lo, those of its last group end before hi (1..4).
 __device__ void segment_groups_prefix(const uint32_t* __restrict__ segrow, const uint32_t* __restrict__ cntrow,
-                                      uint32_t k, uint32_t* gpre, uint32_t* sh32) {
+                                      uint32_t k, uint32_t* gpre, uint32_t* sh32, uint32_t* dsh = nullptr,
+                                      uint8_t* emsk = nullptr) {
     const uint32_t per = (k + blockDim.x - 1) / blockDim.x;
     const uint32_t lo = min(k, threadIdx.x * per), hi = min(k, lo + per);
     uint32_t s = 0;
@@ -318,8 +320,13 @@ __device__ void segment_groups_prefix(const uint32_t* __restrict__ segrow, const
     __syncthreads();
     uint32_t run = (warp ? sh32[warp - 1] : 0) + x - s;
     for (uint32_t j = lo; j < hi; ++j) {
+        const uint32_t a = segrow[j], c = cntrow[j];
         gpre[j] = run;
-        run += seg_groups(segrow[j], cntrow[j]);
+        if (dsh) {
+            dsh[j] = (a >> 2) - run;
+            emsk[j] = (uint8_t)((a & 3u) | ((((a + c - 1u) & 3u) + 1u) << 2));
+        }
+        run += seg_groups(a, c);
     }
     if (threadIdx.x == 0) gpre[k] = sh32[nw - 1];
     __syncthreads();
@@ -341,68 +348,6 @@ __device__ __forceinline__ uint32_t segment_at(const uint32_t* gpre, uint32_t k,
     return lo;
 }
 
-// update[t] = sspr[src[t] - base] for the groups [f_lo, f_hi) of the
-// partition's flattened segment list (Algorithm 3). Each warp takes a
-// contiguous run of groups, 32 * kScatterUnroll at a time, so the groups of
-// one step span only a few segments: the warp tracks the segment of its
-// current position and each lane walks forward from it. Updates are stored as
-// Upd<kUpd>.
-template <int kUpd>
-__device__ __forceinline__ void scatter_groups(const float* sspr, uint32_t base, uint32_t len,
-                                               const uint32_t* gpre, uint32_t k,
-                                               const uint32_t* __restrict__ segrow,
-                                               const uint32_t* __restrict__ cntrow,
-                                               const uint32_t* __restrict__ src, void* __restrict__ upd_raw,
-                                               uint32_t f_lo, uint32_t f_hi, int* err) {
-    using U = Upd<kUpd>;
-    typename U::T* upd = reinterpret_cast<typename U::T*>(upd_raw);
-    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const uint32_t span = f_hi - f_lo;
-    const uint32_t w_lo = f_lo + (uint32_t)((uint64_t)span * warp / nw);
-    const uint32_t w_hi = f_lo + (uint32_t)((uint64_t)span * (warp + 1) / nw);
-    uint32_t wpd = 0;  // segment of the warp's current position
-    for (uint32_t f0 = w_lo; f0 < w_hi; f0 += 32 * kScatterUnroll) {
-        wpd = segment_at(gpre, k, wpd, f0);  // warp-uniform
-        uint32_t e0[kScatterUnroll], s0[kScatterUnroll], c0[kScatterUnroll];
-        uint4 ids[kScatterUnroll];
-        bool live[kScatterUnroll], full[kScatterUnroll];
-        uint32_t pd = wpd;
-#pragma unroll
-        for (int u = 0; u < kScatterUnroll; ++u) {
-            const uint32_t f = f0 + u * 32 + lane;
-            live[u] = f < w_hi;
-            full[u] = false;
-            if (live[u]) {
-                pd = segment_at(gpre, k, pd, f);
-                s0[u] = segrow[pd];
-                c0[u] = cntrow[pd];
-                e0[u] = ((s0[u] >> 2) + (f - gpre[pd])) << 2;
-                full[u] = e0[u] >= s0[u] && e0[u] + 4 <= s0[u] + c0[u];
-                if (full[u]) ids[u] = ld_stream_u4(src + e0[u]);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < kScatterUnroll; ++u) {
-            if (!live[u]) continue;
-            if (full[u]) {
-                const uint32_t i0 = ids[u].x - base, i1 = ids[u].y - base, i2 = ids[u].z - base, i3 = ids[u].w - base;
-                if (i0 < len && i1 < len && i2 < len && i3 < len)
-                    U::store4(upd, e0[u], sspr[i0], sspr[i1], sspr[i2], sspr[i3]);
-                else
-                    atomicOr(err, kErrBounds);
-            } else {
-#pragma unroll
-                for (uint32_t j = 0; j < 4; ++j) {
-                    const uint32_t e = e0[u] + j;
-                    if (e >= s0[u] && e < s0[u] + c0[u]) {
-                        const uint32_t i = src[e] - base;
-                        if (i < len) upd[e] = U::from(sspr[i]); else atomicOr(err, kErrBounds);
-                    }
-                }
-            }
-        }
-    }
-}
 
 // ------------------------------------------------------------------ init
 __global__ void __launch_bounds__(kReduceThreads) init_kernel(uint32_t n, const float* __restrict__ pr_init,
@@ -428,7 +373,158 @@ __global__ void spr_kernel(uint32_t n, const float* __restrict__ pr, const float
         spr[v] = pr[v] * inv_deg[v];
 }
 
+// Algorithm 3 for the groups [f_lo, f_hi) of one source partition's
+// flattened segment list: update[t] = sspr[src[t] - base], stored as
+// Upd<kUpd>. The source indices are fed through bulk copies into shared
+// memory: each warp owns two stages of up to stage_bytes / 16 groups, so a
+// whole stage of loads is in flight while the warp works on the other,
+// without holding them in registers. A stage holds a contiguous range of the
+// flattened group index: whole segments while they fit (not contiguous in
+// src: one copy each), else a piece of one segment. The segment tables gpre,
+// dsh and emsk (see segment_groups_prefix) are in shared memory, so the loop
+// reads no other table. `prologue` runs (on every thread) once the first
+// stages are in flight and before any is read, followed by a block barrier:
+// the scatter kernel fills sspr there. The barriers `bars` (two per warp) must
+// be initialised and visible to the block.
+template <int kUpd, class Prologue>
+__device__ void scatter_groups_staged(const float* sspr, uint32_t base, uint32_t len, const uint32_t* gpre,
+                                      const uint32_t* dsh, const uint8_t* emsk, uint32_t k,
+                                      const uint32_t* __restrict__ src,
+                                      void* __restrict__ upd_raw, uint32_t f_lo, uint32_t f_hi, int* err,
+                                      unsigned char* stages, uint32_t stage_bytes, uint64_t* bars,
+                                      Prologue prologue) {
+    using U = Upd<kUpd>;
+    typename U::T* upd = reinterpret_cast<typename U::T*>(upd_raw);
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t span = f_hi - f_lo;
+    const uint32_t w_lo = f_lo + (uint32_t)((uint64_t)span * warp / nw);
+    const uint32_t w_hi = f_lo + (uint32_t)((uint64_t)span * (warp + 1) / nw);
+    const uint32_t cap = stage_bytes / 16;
+    unsigned char* wst = stages + (size_t)warp * 2 * stage_bytes;
+    uint64_t* wb = bars + 2 * warp;
+    const uint64_t policy = policy_evict_first();
+    // per slot (warp-uniform): groups, first flattened group, its segment
+    uint32_t n0 = 0, n1 = 0, fb0 = 0, fb1 = 0, sg0 = 0, sg1 = 0, ph0 = 0, ph1 = 0;
+    uint32_t pf = w_lo, ppd = 0;
+    auto issue = [&](int slot) -> bool {  // warp-collective
+        if (pf >= w_hi) return false;
+        ppd = segment_at(gpre, k, ppd, pf);  // gpre[ppd] <= pf < gpre[ppd + 1]
+        // The stage holds a piece of one segment that alone fills it (the
+        // common case: one copy), or else whole segments while they fit,
+        // found 32 at a time (one copy each: they are not contiguous in src).
+        const uint32_t lim = min(w_hi, pf + cap);
+        unsigned char* dst = wst + (size_t)slot * stage_bytes;
+        uint32_t f_end = lim;
+        if (gpre[ppd + 1] >= lim) {
+            if (lane == 0) {
+                mbar_arrive_expect_tx(&wb[slot], (lim - pf) * 16u);
+                bulk_load_hint(dst, src + ((pf + dsh[ppd]) << 2), (lim - pf) * 16u, &wb[slot], policy);
+            }
+        } else {
+            for (uint32_t j0 = ppd;; j0 += 32) {
+                const uint32_t j = j0 + lane;
+                const uint32_t c = __popc(__ballot_sync(kFull, j < k && gpre[j + 1] <= lim));  // a prefix
+                if (c) f_end = gpre[j0 + c];
+                if (c < 32) break;
+            }
+            if (lane == 0) mbar_arrive_expect_tx(&wb[slot], (f_end - pf) * 16u);
+            __syncwarp();
+            // the pieces [max(pf, gpre[j]), min(gpre[j+1], f_end)) tile [pf, f_end)
+            for (uint32_t j0 = ppd; j0 < k && gpre[j0] < f_end; j0 += 32) {
+                const uint32_t j = j0 + lane;
+                if (j < k) {
+                    const uint32_t fs = max(pf, gpre[j]), fe = min(gpre[j + 1], f_end);
+                    if (fs < fe)
+                        bulk_load_hint(dst + (size_t)(fs - pf) * 16u, src + ((fs + dsh[j]) << 2), (fe - fs) * 16u,
+                                       &wb[slot], policy);
+                }
+            }
+        }
+        if (slot) { n1 = f_end - pf; fb1 = pf; sg1 = ppd; } else { n0 = f_end - pf; fb0 = pf; sg0 = ppd; }
+        pf = f_end;
+        return true;
+    };
+    bool has0 = issue(0), has1 = issue(1), ok = true;
+    prologue();
+    __syncthreads();
+    auto consume = [&](int slot) -> bool {  // false: nothing left, or a wait timed out
+        const bool has = slot ? has1 : has0;
+        if (!has) return false;
+        ok = __all_sync(kFull, mbar_wait_bounded(&wb[slot], slot ? ph1 : ph0));
+        if (!ok) return false;
+        if (slot) ph1 ^= 1u; else ph0 ^= 1u;
+        const uint32_t n = slot ? n1 : n0, fb = slot ? fb1 : fb0;
+        uint32_t pd = slot ? sg1 : sg0;
+        const uint4* ids = reinterpret_cast<const uint4*>(wst + (size_t)slot * stage_bytes);
+        // one group: interior groups lie inside their segment; a segment's
+        // first or last group holds its entries [jlo, jhi) only
+        auto put = [&](uint32_t f, uint32_t g, uint32_t dd, uint32_t glo, uint32_t ghi, uint32_t em) {
+            const uint32_t e = (f + dd) << 2;
+            const uint4 id = ids[g];
+            if (f != glo && f + 1 != ghi) {
+                const uint32_t i0 = id.x - base, i1 = id.y - base, i2 = id.z - base, i3 = id.w - base;
+                if (i0 < len && i1 < len && i2 < len && i3 < len)
+                    U::store4(upd, e, sspr[i0], sspr[i1], sspr[i2], sspr[i3]);
+                else
+                    atomicOr(err, kErrBounds);
+            } else {
+                const uint32_t jlo = f == glo ? (em & 3u) : 0u, jhi = f + 1 == ghi ? (em >> 2) : 4u;
+                const uint32_t v[4] = {id.x, id.y, id.z, id.w};
+#pragma unroll
+                for (uint32_t jj = 0; jj < 4; ++jj) {
+                    if (jj >= jlo && jj < jhi) {
+                        const uint32_t i = v[jj] - base;
+                        if (i < len) upd[e + jj] = U::from(sspr[i]); else atomicOr(err, kErrBounds);
+                    }
+                }
+            }
+        };
+        if (fb + n <= gpre[pd + 1]) {  // inside one segment (the common case): no per-group search
+            const uint32_t glo = gpre[pd], ghi = gpre[pd + 1], dd = dsh[pd], em = emsk[pd];
+            for (uint32_t g = lane; g < n; g += 32) put(fb + g, g, dd, glo, ghi, em);
+        } else {
+            for (uint32_t g = lane; g < n; g += 32) {
+                const uint32_t f = fb + g;
+                pd = segment_at(gpre, k, pd, f);
+                put(f, g, dsh[pd], gpre[pd], gpre[pd + 1], emsk[pd]);
+            }
+        }
+        __syncwarp();  // every lane is done with the slot before it is refilled
+        if (slot) has1 = issue(1); else has0 = issue(0);
+        return true;
+    };
+    while (consume(0) && consume(1)) {
+    }
+    if (!ok) {
+        // a copy did not land in time: record it and wait (bounded) for the
+        // copies still in flight before the shared memory is released
+        if (lane == 0) atomicOr(err, kErrTimeout);
+        if (has0) (void)mbar_wait_bounded(&wb[0], ph0);
+        if (has1) (void)mbar_wait_bounded(&wb[1], ph1);
+    }
+}
+
 // --------------------------------------------------------------- scatter
+// Bytes of the staged scatter's segment tables in shared memory: gpre (k + 1
+// group starts), dsh (k offsets) and emsk (k bytes), each rounded to 128
+// bytes so the stages after them stay aligned.
+__host__ __device__ constexpr size_t scatter_gpre_bytes(uint32_t k) {
+    return (((size_t)k + 1) * sizeof(uint32_t) + 127) & ~(size_t)127;
+}
+__host__ __device__ constexpr size_t scatter_dsh_bytes(uint32_t k) {
+    return (((size_t)k) * sizeof(uint32_t) + 127) & ~(size_t)127;
+}
+__host__ __device__ constexpr size_t scatter_table_bytes(uint32_t k) {
+    return scatter_gpre_bytes(k) + scatter_dsh_bytes(k) + (((size_t)k + 127) & ~(size_t)127);
+}
+// The scatter kernel's stage bytes: kScatterStageBytes, smaller where the
+// partition and its tables leave less room in the CTA's shared memory.
+constexpr size_t kScatterSmemBudget = 232448 - 1024;
+__host__ __device__ constexpr uint32_t scatter_stage_bytes(uint32_t q, uint32_t k) {
+    const size_t fit = ((kScatterSmemBudget - (size_t)((q + 3) & ~3u) * sizeof(float) - scatter_table_bytes(k)) /
+                        (2 * (kScatterThreads / 32))) & ~(size_t)15;
+    return fit < kScatterStageBytes ? (uint32_t)fit : kScatterStageBytes;
+}
 template <int kUpd>
 __global__ void __launch_bounds__(kScatterThreads, 1) scatter_kernel(
     uint32_t n, uint32_t q, uint32_t k, const float* __restrict__ pr, const float* __restrict__ inv_deg,
@@ -438,46 +534,58 @@ __global__ void __launch_bounds__(kScatterThreads, 1) scatter_kernel(
     if (st->stop) return;
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ uint32_t sh32[32];
+    __shared__ __align__(8) uint64_t bars[2 * (kScatterThreads / 32)];
     float* sspr = reinterpret_cast<float*>(smraw);
-    uint32_t* gpre = reinterpret_cast<uint32_t*>(smraw + (size_t)((q + 3) & ~3u) * sizeof(float));
+    const size_t gpre_off = (size_t)((q + 3) & ~3u) * sizeof(float);
+    uint32_t* gpre = reinterpret_cast<uint32_t*>(smraw + gpre_off);
+    uint32_t* dsh = reinterpret_cast<uint32_t*>(smraw + gpre_off + scatter_gpre_bytes(k));
+    uint8_t* emsk = smraw + gpre_off + scatter_gpre_bytes(k) + scatter_dsh_bytes(k);
+    unsigned char* stages = smraw + gpre_off + scatter_table_bytes(k);
     const uint4 unit = units[order[blockIdx.x]];  // (partition, first group, end group, pieces)
     const uint32_t p = unit.x;
     const uint32_t base = p * q, len = min(q, n - base);
     const uint32_t* segrow = seg_u + (size_t)p * k;
     const uint32_t* cntrow = cnt_u + (size_t)p * k;
-    // SPR of the partition, staged in shared memory (x itself when inv_deg is
-    // null: the SpMV of weighted graphs scatters the vector unscaled) (four independent 16-byte
-    // loads of each array in flight per thread).
-    if ((base & 3) == 0) {
-        const uint32_t v4 = len >> 2;
-        const float4* pr4 = reinterpret_cast<const float4*>(pr + base);
-        const float4* in4 = reinterpret_cast<const float4*>(inv_deg ? inv_deg + base : pr + base);
-        for (uint32_t i0 = threadIdx.x; i0 < v4; i0 += 4 * blockDim.x) {
-            float4 x[4], w[4];
+    if (threadIdx.x < 2 * (kScatterThreads / 32)) mbar_init(&bars[threadIdx.x], 1);
+    fence_mbar_init();
+    segment_groups_prefix(segrow, cntrow, k, gpre, sh32, dsh, emsk);  // ends with __syncthreads
+    // While the first stages of source indices load: SPR of the partition,
+    // staged in shared memory (x itself when inv_deg is null: the SpMV of
+    // weighted graphs scatters the vector unscaled), two independent 16-byte
+    // loads of each array in flight per thread.
+    auto stage_spr = [&] {
+        constexpr int kIlp = 2;
+        if ((base & 3) == 0) {
+            const uint32_t v4 = len >> 2;
+            const float4* pr4 = reinterpret_cast<const float4*>(pr + base);
+            const float4* in4 = reinterpret_cast<const float4*>(inv_deg ? inv_deg + base : pr + base);
+            for (uint32_t i0 = threadIdx.x; i0 < v4; i0 += kIlp * blockDim.x) {
+                float4 x[kIlp], w[kIlp];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const uint32_t i = i0 + j * blockDim.x;
-                if (i < v4) {
-                    x[j] = __ldg(pr4 + i);
-                    w[j] = inv_deg ? __ldg(in4 + i) : make_float4(1.f, 1.f, 1.f, 1.f);
+                for (int j = 0; j < kIlp; ++j) {
+                    const uint32_t i = i0 + j * blockDim.x;
+                    if (i < v4) {
+                        x[j] = __ldg(pr4 + i);
+                        w[j] = inv_deg ? __ldg(in4 + i) : make_float4(1.f, 1.f, 1.f, 1.f);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < kIlp; ++j) {
+                    const uint32_t i = i0 + j * blockDim.x;
+                    if (i < v4)
+                        reinterpret_cast<float4*>(sspr)[i] =
+                            make_float4(x[j].x * w[j].x, x[j].y * w[j].y, x[j].z * w[j].z, x[j].w * w[j].w);
                 }
             }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const uint32_t i = i0 + j * blockDim.x;
-                if (i < v4)
-                    reinterpret_cast<float4*>(sspr)[i] =
-                        make_float4(x[j].x * w[j].x, x[j].y * w[j].y, x[j].z * w[j].z, x[j].w * w[j].w);
-            }
+            for (uint32_t i = (v4 << 2) + threadIdx.x; i < len; i += blockDim.x)
+                sspr[i] = pr[base + i] * (inv_deg ? inv_deg[base + i] : 1.0f);
+        } else {
+            for (uint32_t i = threadIdx.x; i < len; i += blockDim.x)
+                sspr[i] = pr[base + i] * (inv_deg ? inv_deg[base + i] : 1.0f);
         }
-        for (uint32_t i = (v4 << 2) + threadIdx.x; i < len; i += blockDim.x)
-            sspr[i] = pr[base + i] * (inv_deg ? inv_deg[base + i] : 1.0f);
-    } else {
-        for (uint32_t i = threadIdx.x; i < len; i += blockDim.x)
-            sspr[i] = pr[base + i] * (inv_deg ? inv_deg[base + i] : 1.0f);
-    }
-    segment_groups_prefix(segrow, cntrow, k, gpre, sh32);
-    scatter_groups<kUpd>(sspr, base, len, gpre, k, segrow, cntrow, src, upd, unit.y, min(unit.z, gpre[k]), err);
+    };
+    scatter_groups_staged<kUpd>(sspr, base, len, gpre, dsh, emsk, k, src, upd, unit.y, min(unit.z, gpre[k]), err,
+                                stages, scatter_stage_bytes(q, k), bars, stage_spr);
 }
 
 // ---------------------------------------------------------- gather+apply
@@ -1017,11 +1125,25 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
         uint32_t* gpre = reinterpret_cast<uint32_t*>(ring);
         const uint32_t* segrow = a.seg_u + (size_t)pd * a.k;
         const uint32_t* cntrow = a.cnt_u + (size_t)pd * a.k;
-        segment_groups_prefix(segrow, cntrow, a.k, gpre, sh32);
+        // the stage barriers take the per-slot metadata's place (unused now)
+        uint64_t* sbars = reinterpret_cast<uint64_t*>(meta);
+        static_assert(R::kMeta >= 2 * kGatherWarps * sizeof(uint64_t), "two stage barriers per warp");
+        static_assert(R::kBytes >= scatter_table_bytes(PCPM_MAX_PARTITIONS) + 2 * kGatherWarps * 32 * 16,
+                      "the stages must hold at least 32 groups beside the largest segment tables");
+        if (threadIdx.x < 2 * kGatherWarps) mbar_init(&sbars[threadIdx.x], 1);
+        fence_mbar_init();
+        fence_proxy_async_smem();  // the block sum's scratch becomes a bulk-copy target
+        uint32_t* dsh = reinterpret_cast<uint32_t*>(ring + scatter_gpre_bytes(a.k));
+        uint8_t* emsk = ring + scatter_gpre_bytes(a.k) + scatter_dsh_bytes(a.k);
+        segment_groups_prefix(segrow, cntrow, a.k, gpre, sh32, dsh, emsk);  // ends with __syncthreads
         const uint32_t G = gpre[a.k];
         const uint32_t f_lo = (uint32_t)((uint64_t)G * rank / S);
         const uint32_t f_hi = (uint32_t)((uint64_t)G * (rank + 1) / S);
-        scatter_groups<kUpd>(acc, vbase, len, gpre, a.k, segrow, cntrow, a.src, a.upd_out, f_lo, f_hi, a.err);
+        // stages: the ring after the segment table
+        const size_t st_off = scatter_table_bytes(a.k);
+        const uint32_t stage_bytes = (uint32_t)(((R::kBytes - st_off) / (2 * kGatherWarps)) & ~(size_t)15);
+        scatter_groups_staged<kUpd>(acc, vbase, len, gpre, dsh, emsk, a.k, a.src, a.upd_out, f_lo, f_hi, a.err,
+                                    ring + st_off, stage_bytes, sbars, [] {});
     } else {
         if (!push) cluster_sync();  // remote loads of this CTA's shared memory are done
     }
@@ -1074,8 +1196,11 @@ template <bool kW = false>
 size_t gather_smem_bytes(uint32_t q) {
     return Ring<kW>::kAcc + (size_t)(((q + 3) & ~3u) + kPadSlots + kHubSlots) * sizeof(float);
 }
+static_assert(scatter_stage_bytes(PCPM_MAX_PART_SIZE, PCPM_MAX_PARTITIONS) >= 16 * 16,
+              "the scatter's stages must hold at least 16 groups at the largest partition size and count");
 size_t scatter_smem_bytes(uint32_t q, uint32_t k) {
-    return (size_t)((q + 3) & ~3u) * sizeof(float) + (size_t)(k + 1) * sizeof(uint32_t);
+    return (size_t)((q + 3) & ~3u) * sizeof(float) + scatter_table_bytes(k) +
+           (size_t)2 * (kScatterThreads / 32) * scatter_stage_bytes(q, k);
 }
 
 }  // namespace
