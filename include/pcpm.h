@@ -217,8 +217,19 @@ int pcpm_spmv(pcpm_png* png, const float* x, float* y, void* stream);
 int pcpm_export_weights(const pcpm_png* png, float* wbin);
 
 /* Releases the handle and all its device memory. NULL is a no-op. Waits for
- * work the library enqueued on the handle's last stream. */
+ * all work on the device (as cudaFree does), then returns the memory to the
+ * library's device-memory pool.
+ *
+ * Memory: handles, build temporaries and pcpm_pagerank_host's copies come
+ * from one stream-ordered pool per device (cudaMemPool) that keeps freed
+ * memory for the next build instead of returning it to the driver, so
+ * repeated builds make no new driver allocations. */
 void pcpm_free(pcpm_png* png);
+
+/* Returns the memory that the library's pools hold but no live handle uses
+ * to the driver (cudaMemPoolTrimTo 0 on every device the library used).
+ * PCPM_ECUDA if a trim fails. */
+int pcpm_release_cached_memory(void);
 
 /* Sizes of the handle (host struct). */
 int pcpm_png_get_info(const pcpm_png* png, pcpm_png_info* info);

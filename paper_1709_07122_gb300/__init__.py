@@ -95,6 +95,7 @@ def lib(path: str | None = None):
                 "pcpm_rank_stats_noalloc": (i32, [vp, vp, vp, u32, vp, vp]),
                 "pcpm_strerror": (ctypes.c_char_p, [i32]),
                 "pcpm_last_cuda_error": (ctypes.c_char_p, []),
+                "pcpm_release_cached_memory": (i32, []),
                 "pcpm_build_weighted": (i32, [vp, vp, vp, u32, u64, u32, ctypes.POINTER(_Options), vp,
                                               ctypes.POINTER(vp)]),
                 "pcpm_spmv": (i32, [vp, vp, vp, vp]),
@@ -147,6 +148,12 @@ def _flags(dangling: str, mode: str = "fused") -> int:
     if mode not in ("fused", "two_phase"):
         raise ValueError("mode must be 'fused' or 'two_phase'")
     return (DANGLING_LEAK if dangling == "leak" else 0) | (TWO_PHASE if mode == "two_phase" else 0)
+
+
+def release_cached_memory() -> None:
+    """Returns device memory that the library's pool keeps for later builds,
+    but that no live handle uses, to the driver (pcpm_release_cached_memory)."""
+    _check(lib().pcpm_release_cached_memory(), "pcpm_release_cached_memory")
 
 
 def to_device_csr(row_ptr: np.ndarray, col: np.ndarray, device="cuda"):

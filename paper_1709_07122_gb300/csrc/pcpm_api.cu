@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <set>
 #include <vector>
@@ -13,9 +14,50 @@
 namespace pcpm {
 
 
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[kMaxDevices] = {};
+
+cudaError_t pool_for_current_device(cudaMemPool_t* out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if ((e = cudaMemPoolCreate(&pool, &props)) != cudaSuccess) return e;
+        uint64_t keep = UINT64_MAX;
+        if ((e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess) {
+            cudaMemPoolDestroy(pool);
+            return e;
+        }
+        g_pools[dev] = pool;
+    }
+    *out = g_pools[dev];
+    return cudaSuccess;
+}
+}  // namespace
+
+cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s) {
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = pool_for_current_device(&pool);
+    if (e != cudaSuccess) return e;
+    return cudaMallocFromPoolAsync(p, std::max<size_t>(bytes, 16), pool, s);
+}
+
+void pool_free(void* p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
+}
+
 cudaError_t dev_alloc(pcpm_png* g, void** p, size_t bytes) {
     bytes = std::max<size_t>(bytes, 16);
-    cudaError_t e = cudaMalloc(p, bytes);
+    cudaError_t e = pool_alloc(p, bytes, g->alloc_stream);
     if (e == cudaSuccess) g->device_bytes += bytes;
     return e;
 }
@@ -65,14 +107,15 @@ void release(pcpm_png* g) {
                     g->gunits, g->gorder, g->sunits, g->sorder, g->gacc,
                     g->bin_done, g->inv_deg, g->pr[0], g->pr[1], g->upd[0], g->upd[1], g->partials,
                     g->hist, g->state, g->wdest, g->gweight};
-    for (void* p : ptrs)
-        if (p) cudaFree(p);
+    // the caller has waited for every use of the handle's memory
+    for (void* p : ptrs) pool_free(p, g->last_stream);
     if (g->state_host) cudaFreeHost(g->state_host);
     delete g;
 }
 
 int alloc_state(pcpm_png* g) {
     const uint32_t n = g->n;
+    const cudaStream_t s = g->alloc_stream;
     CK(dev_alloc(g, (void**)&g->pr[0], (size_t)n * sizeof(float)));
     CK(dev_alloc(g, (void**)&g->pr[1], (size_t)n * sizeof(float)));
     // Update bins: two buffers (the fused iteration gathers one and scatters
@@ -81,19 +124,19 @@ int alloc_state(pcpm_png* g) {
     const size_t ubytes = (g->ne + 16) * g->upd_bytes;
     CK(dev_alloc(g, (void**)&g->upd[0], ubytes));
     CK(dev_alloc(g, (void**)&g->upd[1], ubytes));
-    CK(cudaMemset(g->upd[0], 0, ubytes));
-    CK(cudaMemset(g->upd[1], 0, ubytes));
+    CK(cudaMemsetAsync(g->upd[0], 0, ubytes, s));
+    CK(cudaMemsetAsync(g->upd[1], 0, ubytes, s));
     CK(dev_alloc(g, (void**)&g->partials, 2 * partial_slots(g) * sizeof(double)));
     CK(dev_alloc(g, (void**)&g->gacc, (size_t)n * sizeof(float)));
     CK(dev_alloc(g, (void**)&g->bin_done, (size_t)g->k * sizeof(uint32_t)));
-    CK(cudaMemset(g->gacc, 0, (size_t)n * sizeof(float)));
-    CK(cudaMemset(g->bin_done, 0, (size_t)g->k * sizeof(uint32_t)));
+    CK(cudaMemsetAsync(g->gacc, 0, (size_t)n * sizeof(float), s));
+    CK(cudaMemsetAsync(g->bin_done, 0, (size_t)g->k * sizeof(uint32_t), s));
     g->hist_cap = 1024;
     CK(dev_alloc(g, (void**)&g->hist, (size_t)g->hist_cap * sizeof(double)));
     CK(dev_alloc(g, (void**)&g->state, sizeof(DevState)));
     CK(cudaMallocHost((void**)&g->state_host, sizeof(DevState)));
     std::memset(g->state_host, 0, sizeof(DevState));
-    CK(cudaMemset(g->state, 0, sizeof(DevState)));
+    CK(cudaMemsetAsync(g->state, 0, sizeof(DevState), s));
     return PCPM_OK;
 }
 
@@ -102,14 +145,15 @@ int ensure_hist(pcpm_png* g, int needed, cudaStream_t s) {
     int cap = g->hist_cap;
     while (cap < needed) cap *= 2;
     double* h = nullptr;
-    CK(cudaMalloc((void**)&h, (size_t)cap * sizeof(double)));
+    CK(pool_alloc((void**)&h, (size_t)cap * sizeof(double), s));
     cudaError_t e = cudaMemcpyAsync(h, g->hist, (size_t)g->hist_cap * sizeof(double), cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
-        cudaFree(h);
+        pool_free(h, s);
+        note_cuda_error(e);
         return PCPM_ECUDA;
     }
-    cudaFree(g->hist);
+    pool_free(g->hist, s);
     g->device_bytes += (size_t)(cap - g->hist_cap) * sizeof(double);
     g->hist = h;
     g->hist_cap = cap;
@@ -276,6 +320,7 @@ int build_impl(const uint32_t* row_ptr, const uint32_t* col_idx, const float* we
     g->k = (uint32_t)k;
     g->m = m;
     g->last_stream = s;
+    g->alloc_stream = s;
     g->cluster = (int)opt.gather_cluster;
     g->upd_dtype = (int)opt.update_dtype;
     g->upd_bytes = opt.update_dtype == PCPM_UPDATE_F32 ? 4u : 2u;
@@ -457,9 +502,23 @@ int pcpm_export_weights(const pcpm_png* g, float* wbin) {
 
 void pcpm_free(pcpm_png* png) {
     if (!png) return;
-    cudaStreamSynchronize(png->last_stream);
+    // the handle's memory returns to the pool only once no stream can still use it
+    cudaDeviceSynchronize();
     cudaGetLastError();
     release(png);
+}
+
+int pcpm_release_cached_memory(void) {
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    for (int dev = 0; dev < kMaxDevices; ++dev) {
+        if (!g_pools[dev]) continue;
+        const cudaError_t e = cudaMemPoolTrimTo(g_pools[dev], 0);
+        if (e != cudaSuccess) {
+            note_cuda_error(e);
+            return PCPM_ECUDA;
+        }
+    }
+    return PCPM_OK;
 }
 
 int pcpm_png_get_info(const pcpm_png* g, pcpm_png_info* info) {
@@ -608,9 +667,9 @@ int pcpm_pagerank_host(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_
     cudaStream_t s = nullptr;
     auto fail = [&](cudaError_t e) { return e == cudaErrorMemoryAllocation ? PCPM_ENOMEM : PCPM_ECUDA; };
     cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&d_rp, ((size_t)n + 1) * sizeof(uint32_t));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&d_col, std::max<size_t>(m, 1) * sizeof(uint32_t));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&d_pr, (size_t)n * sizeof(float));
+    if (e == cudaSuccess) e = pool_alloc((void**)&d_rp, ((size_t)n + 1) * sizeof(uint32_t), s);
+    if (e == cudaSuccess) e = pool_alloc((void**)&d_col, std::max<size_t>(m, 1) * sizeof(uint32_t), s);
+    if (e == cudaSuccess) e = pool_alloc((void**)&d_pr, (size_t)n * sizeof(float), s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_rp, row_ptr, ((size_t)n + 1) * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && m)
@@ -625,9 +684,9 @@ int pcpm_pagerank_host(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_
     }
     if (s) cudaStreamSynchronize(s);
     if (g) pcpm_free(g);
-    cudaFree(d_rp);
-    cudaFree(d_col);
-    cudaFree(d_pr);
+    pool_free(d_rp, s);
+    pool_free(d_col, s);
+    pool_free(d_pr, s);
     if (s) cudaStreamDestroy(s);
     cudaGetLastError();
     return rc;

@@ -149,6 +149,7 @@ struct pcpm_png {
     int iters_done;
     uint64_t device_bytes;
     cudaStream_t last_stream;
+    cudaStream_t alloc_stream;  // the build's stream: device memory is allocated in its order
 };
 
 namespace pcpm {
@@ -175,7 +176,12 @@ int launch_reduce(pcpm_png* g, double tol, int hist_slot, cudaStream_t s);
 int launch_spr(pcpm_png* g, float* spr, cudaStream_t s);
 size_t partial_slots(const pcpm_png* g);
 
-// Device allocation helper that records sizes.
+// Device memory comes from one stream-ordered pool per device that keeps what
+// is freed (release threshold unlimited), so a build after a free reuses it
+// without new driver allocations; pcpm_release_cached_memory trims it.
+cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s);
+void pool_free(void* p, cudaStream_t s);
+// Device allocation of a handle's array (on g->alloc_stream), recording sizes.
 cudaError_t dev_alloc(pcpm_png* g, void** p, size_t bytes);
 
 }  // namespace pcpm

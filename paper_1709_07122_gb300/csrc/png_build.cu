@@ -163,7 +163,8 @@ __global__ void tile_kernel(const uint32_t* __restrict__ row_ptr, const uint32_t
                             uint32_t* __restrict__ tab_e, uint32_t* __restrict__ tab_u,
                             const uint32_t* __restrict__ bin_e, const uint32_t* __restrict__ bin_u,
                             uint32_t* __restrict__ dest, uint32_t* __restrict__ src, int* __restrict__ err,
-                            const float* __restrict__ weights = nullptr, float* __restrict__ wdest = nullptr) {
+                            const float* __restrict__ weights = nullptr, float* __restrict__ wdest = nullptr,
+                            uint2* __restrict__ tile_info = nullptr) {
     extern __shared__ uint32_t sh[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
     uint32_t* ce = sh + (size_t)warp * 2 * k;  // edges (count) / ID cursor (fill)
@@ -189,6 +190,7 @@ __global__ void tile_kernel(const uint32_t* __restrict__ row_ptr, const uint32_t
         const uint32_t ulo = upper_bound_u32(row_ptr, u_begin, u_end + 1, e_begin) - 1;
         const uint32_t uhi = upper_bound_u32(row_ptr, ulo, u_end + 1, e_end - 1) - 1;
         uint32_t carry_v = (e_begin > row_ptr[ulo]) ? col[e_begin - 1] : 0;
+        if (tile_info && lane == 0) tile_info[t] = make_uint2(p, ulo);
 
         for (uint32_t w0 = e_begin; w0 < e_end; w0 += 32) {
             const uint32_t e = w0 + lane;
@@ -236,6 +238,241 @@ __global__ void tile_kernel(const uint32_t* __restrict__ row_ptr, const uint32_t
             }
         }
         __syncwarp();
+    }
+}
+
+// ------------------------------------------------ staged fill of tiles
+// The fill of tile_kernel<true> writes every ID straight to its bin: with k
+// bins and thousands of tiles in flight, the half-written sectors exceed L2
+// and are evicted partial (read-modify-write in DRAM). This fill gives each
+// tile one CTA and writes every (tile, bin) run in one piece instead:
+//   stage    the tile's col and, by a max-scan of row-start marks, the local
+//            row of every edge (no per-edge search);
+//   count    each warp counts its 1/kFillWarps of the tile per key p' (edges
+//            in the low, message starts in the high half of one word);
+//   scan     per key over warps, then over keys: each warp's cursor in the
+//            tile's bin-ordered staging buffers;
+//   rank     each warp replays its slice in order, ranks equal keys with
+//            match/ballot and stages 16-bit local IDs (bit 15: message flag);
+//   copy     one warp per bin copies the bin's run of the tile out.
+// Same result as tile_kernel<true>: warps own consecutive slices and rank in
+// edge order, so the sort stays stable. Local IDs fit 16 bits because
+// q <= 32768; k <= kFillMaxK keeps the per-warp tables small.
+constexpr int kFillWarps = 8;
+constexpr uint32_t kFillSlice = kTileEdges / kFillWarps;
+constexpr uint32_t kFillMaxK = 1024;
+constexpr uint32_t kFillPerThread = kTileEdges / (kFillWarps * 32);
+static_assert(kTileEdges % (kFillWarps * 32) == 0 && kFillPerThread == 32, "32 staged edges per thread");
+static_assert(PCPM_MAX_PART_SIZE <= 32768, "local IDs must fit 15 bits");
+
+size_t fill_smem_bytes(uint32_t k, bool weighted) {
+    return (size_t)kTileEdges * (sizeof(uint32_t) + 3 * sizeof(uint16_t) + (weighted ? sizeof(float) : 0)) +
+           (size_t)(kFillWarps + 3) * k * sizeof(uint32_t) + sizeof(uint32_t);
+}
+
+// Exclusive max-scan of one value per thread over the block.
+__device__ uint32_t block_exclusive_max(uint32_t v, uint32_t* sh32) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x = max(x, y);
+    }
+    if (lane == 31) sh32[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t s = lane < nw ? sh32[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s = max(s, y);
+        }
+        sh32[lane] = s;
+    }
+    __syncthreads();
+    const uint32_t before = warp ? sh32[warp - 1] : 0;
+    const uint32_t xl = __shfl_up_sync(0xffffffffu, x, 1);
+    __syncthreads();
+    return max(before, lane ? xl : 0u);
+}
+
+__global__ void __launch_bounds__(kFillWarps * 32) fill_staged_kernel(
+    const uint32_t* __restrict__ row_ptr, const uint32_t* __restrict__ col, uint32_t n, uint32_t q, uint32_t k,
+    const uint32_t* __restrict__ tile_start, const uint2* __restrict__ tile_info, uint32_t ntiles,
+    const uint32_t* __restrict__ tab_e, const uint32_t* __restrict__ tab_u, const uint32_t* __restrict__ bin_e,
+    const uint32_t* __restrict__ bin_u, uint32_t* __restrict__ dest, uint32_t* __restrict__ src,
+    int* __restrict__ err, const float* __restrict__ weights, float* __restrict__ wdest) {
+    extern __shared__ __align__(16) unsigned char fsm[];
+    __shared__ uint32_t sh32[32];
+    uint32_t* scol = reinterpret_cast<uint32_t*>(fsm);        // the tile's col
+    uint16_t* rowof = reinterpret_cast<uint16_t*>(scol + kTileEdges);  // local row of each edge
+    uint16_t* d16 = rowof + kTileEdges;                       // staged IDs, bin order
+    uint16_t* s16 = d16 + kTileEdges;                         // staged sources, bin order
+    float* wst = reinterpret_cast<float*>(s16 + kTileEdges);  // staged weights (weighted graphs)
+    uint32_t* hist = reinterpret_cast<uint32_t*>(wst + (weights ? kTileEdges : 0));  // [warp][key]
+    uint32_t* loff = hist + (size_t)kFillWarps * k;           // k + 1 run starts in the staging buffers
+    uint32_t* gbe = loff + k + 1;                             // k: the tile's cursor in bin p' (IDs)
+    uint32_t* gbu = gbe + k;                                  // k: the same for updates
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t lt = lanemask_lt();
+
+    for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const uint2 ti = tile_info[t];
+        const uint32_t p = ti.x, ulo = ti.y;
+        const uint32_t u_begin = p * q, u_end = min(n, u_begin + q);
+        const uint32_t e_begin = row_ptr[u_begin] + (t - tile_start[p]) * kTileEdges;
+        const uint32_t e_end = (uint32_t)min((uint64_t)e_begin + kTileEdges, (uint64_t)row_ptr[u_end]);
+        const uint32_t L = e_end - e_begin;
+        // rows up to the next tile's first row (or the partition's last) cover the tile
+        const uint32_t rhi = (t + 1 < ntiles && tile_start[p + 1] > t + 1) ? tile_info[t + 1].y : u_end - 1;
+
+        // stage: col, cleared row marks and counters, cursors
+        {
+            uint32_t x[kFillPerThread];
+#pragma unroll
+            for (uint32_t j = 0; j < kFillPerThread; ++j) {
+                const uint32_t i = j * blockDim.x + tid;
+                x[j] = i < L ? __ldcs(col + e_begin + i) : 0u;
+            }
+#pragma unroll
+            for (uint32_t j = 0; j < kFillPerThread; ++j) {
+                const uint32_t i = j * blockDim.x + tid;
+                scol[i] = x[j];
+                rowof[i] = 0;
+            }
+        }
+        for (uint32_t j = tid; j < kFillWarps * k; j += blockDim.x) hist[j] = 0;
+        for (uint32_t j = tid; j < k; j += blockDim.x) {
+            gbe[j] = bin_e[j] + tab_e[(size_t)t * k + j];
+            gbu[j] = bin_u[j] + tab_u[(size_t)t * k + j];
+        }
+        __syncthreads();
+        // each non-empty row marks its first edge in the tile ...
+        for (uint32_t r = ulo + tid; r <= rhi; r += blockDim.x) {
+            const uint32_t a = row_ptr[r], b = row_ptr[r + 1];
+            if (b > a && b > e_begin && a < e_end) rowof[a > e_begin ? a - e_begin : 0] = (uint16_t)(r - ulo);
+        }
+        __syncthreads();
+        // ... and the marks carry forward: an edge belongs to the last row
+        // starting at or before it (marks rise with the position)
+        {
+            const uint32_t i0 = tid * kFillPerThread;
+            uint32_t mx = 0;
+            for (uint32_t j = 0; j < kFillPerThread; ++j) mx = max(mx, (uint32_t)rowof[i0 + j]);
+            uint32_t run = block_exclusive_max(mx, sh32);
+            for (uint32_t j = 0; j < kFillPerThread; ++j) {
+                run = max(run, (uint32_t)rowof[i0 + j]);
+                rowof[i0 + j] = (uint16_t)run;
+            }
+        }
+        __syncthreads();
+
+        // One pass over the warp's slice; body(valid, i, v, local row, key,
+        // start, peers, smask) runs once per 32 edges (warp-collective).
+        const uint32_t s_lo = min(L, warp * kFillSlice), s_hi = min(L, s_lo + kFillSlice);
+        const bool first_starts_row = e_begin == row_ptr[ulo];
+        auto walk = [&](auto&& body) {
+            uint32_t carry = 0;
+            if (s_lo > 0 && s_lo < s_hi) carry = scol[s_lo - 1];
+            else if (s_lo == 0 && !first_starts_row) carry = col[e_begin - 1];
+            for (uint32_t i0 = s_lo; i0 < s_hi; i0 += 32) {
+                const uint32_t i = i0 + lane;
+                bool valid = i < s_hi;
+                uint32_t v = 0, r = 0;
+                bool row_start = false;
+                if (valid) {
+                    v = scol[i];
+                    r = rowof[i];
+                    row_start = i == 0 ? first_starts_row : rowof[i - 1] != r;
+                }
+                uint32_t prev_v = __shfl_up_sync(0xffffffffu, v, 1);
+                if (lane == 0) prev_v = carry;
+                carry = __shfl_sync(0xffffffffu, v, 31);
+                uint32_t key = 0xffffffffu;
+                bool start = false;
+                if (valid) {
+                    if (v >= n || (!row_start && prev_v > v)) {
+                        atomicOr(err, kErrBadGraph);
+                        valid = false;
+                    } else {
+                        key = v / q;
+                        start = row_start || (prev_v / q != key);
+                    }
+                }
+                const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+                const uint32_t smask = __ballot_sync(0xffffffffu, start);
+                const uint32_t peers = __match_any_sync(0xffffffffu, key) & vmask;
+                body(valid, i, v, r, key, start, peers, smask);
+                __syncwarp();
+            }
+        };
+        // count
+        walk([&](bool valid, uint32_t, uint32_t, uint32_t, uint32_t key, bool, uint32_t peers, uint32_t smask) {
+            if (valid && lane == __ffs(peers) - 1)
+                hist[warp * k + key] += __popc(peers) | (__popc(peers & smask) << 16);
+        });
+        __syncthreads();
+        // scan: per key over warps, then over keys (both halves at once: each
+        // total is at most kTileEdges < 2^16)
+        for (uint32_t j = tid; j < k; j += blockDim.x) {
+            uint32_t run = 0;
+            for (int w = 0; w < kFillWarps; ++w) {
+                const uint32_t x = hist[w * k + j];
+                hist[w * k + j] = run;
+                run += x;
+            }
+            loff[j] = run;
+        }
+        __syncthreads();
+        {
+            const uint32_t per = (k + blockDim.x - 1) / blockDim.x;
+            const uint32_t j0 = min(k, tid * per), j1 = min(k, j0 + per);
+            uint32_t sum = 0;
+            for (uint32_t j = j0; j < j1; ++j) sum += loff[j];
+            uint32_t total;
+            uint32_t run = block_exclusive_scan(sum, &total, sh32);
+            for (uint32_t j = j0; j < j1; ++j) {
+                const uint32_t x = loff[j];
+                loff[j] = run;
+                run += x;
+            }
+            if (tid == 0) loff[k] = total;
+        }
+        __syncthreads();
+        for (uint32_t j = tid; j < k; j += blockDim.x) {
+            const uint32_t b = loff[j];
+            for (int w = 0; w < kFillWarps; ++w) hist[w * k + j] += b;
+        }
+        __syncthreads();
+        // rank and stage
+        walk([&](bool valid, uint32_t i, uint32_t v, uint32_t r, uint32_t key, bool start, uint32_t peers,
+                 uint32_t smask) {
+            if (valid) {
+                const uint32_t c = hist[warp * k + key];
+                const uint32_t pe = (c & 0xFFFFu) + __popc(peers & lt);
+                d16[pe] = (uint16_t)((v - key * q) | (start ? 0x8000u : 0u));
+                if (weights) wst[pe] = weights[e_begin + i];  // Sec. 3.5: the weight beside its ID
+                if (start) s16[(c >> 16) + __popc(peers & smask & lt)] = (uint16_t)(ulo + r - u_begin);
+            }
+            __syncwarp();
+            if (valid && lane == __ffs(peers) - 1)
+                hist[warp * k + key] += __popc(peers) | (__popc(peers & smask) << 16);
+        });
+        __syncthreads();
+        // copy each bin's run out
+        for (uint32_t j = warp; j < k; j += kFillWarps) {
+            const uint32_t a = loff[j], b = loff[j + 1];
+            const uint32_t ae = a & 0xFFFFu, be = b & 0xFFFFu, au = a >> 16, bu = b >> 16;
+            const uint32_t ge = gbe[j], gu = gbu[j], vbase = j * q;
+            for (uint32_t i = ae + lane; i < be; i += 32) {
+                const uint32_t x = d16[i];
+                dest[ge + (i - ae)] = (vbase + (x & 0x7FFFu)) | ((x & 0x8000u) ? kMsb : 0u);
+                if (weights) wdest[ge + (i - ae)] = wst[i];
+            }
+            for (uint32_t i = au + lane; i < bu; i += 32) src[gu + (i - au)] = u_begin + s16[i];
+        }
+        __syncthreads();
     }
 }
 
@@ -636,15 +873,18 @@ __global__ void scatter_units_kernel(const uint32_t* __restrict__ groups, const 
     }
 }
 
+// Build temporaries, from the library's pool in the build stream's order.
 struct TempBufs {
+    cudaStream_t s;
     std::vector<void*> ptrs;
+    explicit TempBufs(cudaStream_t stream) : s(stream) {}
     ~TempBufs() {
-        for (void* p : ptrs) cudaFree(p);
+        for (void* p : ptrs) pool_free(p, s);
     }
     template <class T>
     cudaError_t alloc(T** p, size_t count) {
         void* q = nullptr;
-        cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+        cudaError_t e = pool_alloc(&q, std::max<size_t>(count, 1) * sizeof(T), s);
         if (e == cudaSuccess) {
             ptrs.push_back(q);
             *p = (T*)q;
@@ -709,7 +949,7 @@ int build_png(pcpm_png* g, const uint32_t* row_ptr, const uint32_t* col, const p
     const uint32_t n = g->n, q = g->q, k = g->k;
     g->canonical_gather = opt.canonical_gather ? 1 : 0;
     const uint64_t m = g->m;
-    TempBufs tmp;
+    TempBufs tmp(s);
     int* d_err = nullptr;
     BCK(tmp.alloc(&d_err, 1));
     BCK(cudaMemsetAsync(d_err, 0, sizeof(int), s));
@@ -741,9 +981,13 @@ int build_png(pcpm_png* g, const uint32_t* row_ptr, const uint32_t* col, const p
     BCK(cudaFuncSetAttribute(tile_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem));
     const int sms = g->sms;
     const int tile_grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((ntiles + wpc - 1) / wpc, (uint64_t)sms * 16));
+    // (source partition, first row) of every tile, for the staged fill
+    uint2* tile_info = nullptr;
+    BCK(tmp.alloc(&tile_info, std::max<uint32_t>(ntiles, 1)));
     if (ntiles) {
         tile_kernel<false><<<tile_grid, wpc * 32, tile_smem, s>>>(row_ptr, col, n, q, k, tile_start, ntiles, tab_e,
-                                                                 tab_u, nullptr, nullptr, nullptr, nullptr, d_err);
+                                                                 tab_u, nullptr, nullptr, nullptr, nullptr, d_err,
+                                                                 nullptr, nullptr, tile_info);
         BCK(cudaGetLastError());
     }
     if ((rc = read_err(d_err, s, &h_err)) != PCPM_OK) return rc;
@@ -781,9 +1025,21 @@ int build_png(pcpm_png* g, const uint32_t* row_ptr, const uint32_t* col, const p
     BCK(dev_alloc(g, (void**)&g->src, (g->ne + 4) * sizeof(uint32_t)));
     if (ntiles) {
         if (g->weighted) BCK(dev_alloc(g, (void**)&g->wdest, dest_len * sizeof(float)));
-        tile_kernel<true><<<tile_grid, wpc * 32, tile_smem, s>>>(row_ptr, col, n, q, k, tile_start, ntiles, tab_e,
-                                                                tab_u, g->bin_e, g->bin_u, g->dest, g->src, d_err,
-                                                                g->weights_in, g->wdest);
+        if (k <= kFillMaxK) {
+            const size_t fs = fill_smem_bytes(k, g->weighted != 0);
+            BCK(cudaFuncSetAttribute(fill_staged_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fs));
+            int per_sm = 0;
+            BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fill_staged_kernel, kFillWarps * 32, fs));
+            const int fill_grid = (int)std::max<uint64_t>(
+                1, std::min<uint64_t>(ntiles, (uint64_t)sms * (uint64_t)std::max(per_sm, 1)));
+            fill_staged_kernel<<<fill_grid, kFillWarps * 32, fs, s>>>(row_ptr, col, n, q, k, tile_start, tile_info,
+                                                                     ntiles, tab_e, tab_u, g->bin_e, g->bin_u,
+                                                                     g->dest, g->src, d_err, g->weights_in, g->wdest);
+        } else {
+            tile_kernel<true><<<tile_grid, wpc * 32, tile_smem, s>>>(row_ptr, col, n, q, k, tile_start, ntiles,
+                                                                    tab_e, tab_u, g->bin_e, g->bin_u, g->dest,
+                                                                    g->src, d_err, g->weights_in, g->wdest);
+        }
         BCK(cudaGetLastError());
     }
 

@@ -48,6 +48,9 @@ GRAPHS = {
     "single_partition": lambda: (graphgen.random_graph(500, 3000, seed=8), 32768),
     "rmat10_q32768_k1": lambda: (graphgen.rmat(10, 8, seed=9), 32768),
     "rmat14_q_not_multiple": lambda: (graphgen.rmat(14, 16, seed=10), 3000),
+    # the staged fill's largest partition count, and one past it (direct fill)
+    "rmat12_q4_k1024": lambda: (graphgen.rmat(12, 16, seed=12), 4),
+    "random5000_q3_k1667": lambda: (graphgen.random_graph(5000, 40000, seed=11), 3),
 }
 
 
@@ -225,6 +228,28 @@ def test_pagerank_host_end_to_end():
     ref = oracle.pagerank(rp, col, 0.85, iters=20)["x"]
     pr, iters, res = pcpm.pagerank_host(rp, col, q, 0.85, 20)
     assert iters == 20 and l1(pr, ref) <= L1_TOL
+
+
+def test_pool_reuse_across_builds_and_trim():
+    """Freed handles return their memory to the library's pool; later builds
+    reuse it (different sizes, interleaved lifetimes) and stay bit-exact."""
+    a_rp, a_col = graphgen.rmat(14, 16, seed=21)
+    b_rp, b_col = graphgen.erdos_renyi(1 << 13, 8, seed=22)
+    ref_a, ref_b = oracle.png(a_rp, a_col, 1000), oracle.png(b_rp, b_col, 512)
+    for _ in range(3):
+        ga = pcpm.PNG.from_host(a_rp, a_col, 1000)
+        with pcpm.PNG.from_host(b_rp, b_col, 512) as gb:
+            ga.close()
+            assert_png_matches(gb.export(), ref_b)
+        with pcpm.PNG.from_host(a_rp, a_col, 1000) as ga2:
+            assert_png_matches(ga2.export(), ref_a)
+    ref = oracle.pagerank(a_rp, a_col, 0.85, iters=10)["x"]
+    for _ in range(3):  # shared-memory atomics: equal within the tolerance, not bitwise
+        assert l1(pcpm.pagerank_host(a_rp, a_col, 1000, 0.85, 10)[0], ref) <= L1_TOL
+    pcpm.release_cached_memory()
+    with pcpm.PNG.from_host(b_rp, b_col, 512) as gb:
+        assert_png_matches(gb.export(), ref_b)
+    pcpm.release_cached_memory()
 
 
 def test_errors_from_bad_inputs():
