@@ -47,6 +47,19 @@ __device__ __forceinline__ uint32_t upper_bound_u32(const uint32_t* a, uint32_t 
     return lo;
 }
 
+// v / q for v < 2^32 and q <= 2^15 without a division: with
+// m = ceil(2^64 / q), v * m / 2^64 = v / q + e where 0 <= e < 2^-32, and the
+// fraction of v / q is at most 1 - 1/q <= 1 - 2^-15, so the floor is exact.
+struct DivQ {
+    uint64_t m;  // 0 for q = 1
+    uint32_t q;
+    __device__ __forceinline__ uint32_t operator()(uint32_t v) const {
+        return m ? (uint32_t)__umul64hi((uint64_t)v, m) : v;
+    }
+};
+DivQ make_divq(uint32_t q) { return DivQ{q > 1 ? UINT64_MAX / q + 1 : 0, q}; }
+static_assert(PCPM_MAX_PART_SIZE <= 32768, "DivQ needs q <= 2^15");
+
 // Exclusive scan of one value per thread over a block of up to 1024 threads.
 __device__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* total, uint32_t* sh32) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
@@ -163,8 +176,7 @@ __global__ void tile_kernel(const uint32_t* __restrict__ row_ptr, const uint32_t
                             uint32_t* __restrict__ tab_e, uint32_t* __restrict__ tab_u,
                             const uint32_t* __restrict__ bin_e, const uint32_t* __restrict__ bin_u,
                             uint32_t* __restrict__ dest, uint32_t* __restrict__ src, int* __restrict__ err,
-                            const float* __restrict__ weights = nullptr, float* __restrict__ wdest = nullptr,
-                            uint2* __restrict__ tile_info = nullptr) {
+                            const float* __restrict__ weights = nullptr, float* __restrict__ wdest = nullptr) {
     extern __shared__ uint32_t sh[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
     uint32_t* ce = sh + (size_t)warp * 2 * k;  // edges (count) / ID cursor (fill)
@@ -190,7 +202,6 @@ __global__ void tile_kernel(const uint32_t* __restrict__ row_ptr, const uint32_t
         const uint32_t ulo = upper_bound_u32(row_ptr, u_begin, u_end + 1, e_begin) - 1;
         const uint32_t uhi = upper_bound_u32(row_ptr, ulo, u_end + 1, e_end - 1) - 1;
         uint32_t carry_v = (e_begin > row_ptr[ulo]) ? col[e_begin - 1] : 0;
-        if (tile_info && lane == 0) tile_info[t] = make_uint2(p, ulo);
 
         for (uint32_t w0 = e_begin; w0 < e_end; w0 += 32) {
             const uint32_t e = w0 + lane;
@@ -246,8 +257,8 @@ __global__ void tile_kernel(const uint32_t* __restrict__ row_ptr, const uint32_t
 // bins and thousands of tiles in flight, the half-written sectors exceed L2
 // and are evicted partial (read-modify-write in DRAM). This fill gives each
 // tile one CTA and writes every (tile, bin) run in one piece instead:
-//   stage    the tile's col and, by a max-scan of row-start marks, the local
-//            row of every edge (no per-edge search);
+//   stage    the tile's col and the local row of every edge (stage_tile: no
+//            per-edge search);
 //   count    each warp counts its 1/kFillWarps of the tile per key p' (edges
 //            in the low, message starts in the high half of one word);
 //   scan     per key over warps, then over keys: each warp's cursor in the
@@ -297,8 +308,126 @@ __device__ uint32_t block_exclusive_max(uint32_t v, uint32_t* sh32) {
     return max(before, lane ? xl : 0u);
 }
 
+// (source partition, first row) of every tile: the row owning its first edge.
+__global__ void tile_info_kernel(const uint32_t* __restrict__ row_ptr, uint32_t n, uint32_t q, uint32_t k,
+                                 const uint32_t* __restrict__ tile_start, uint32_t ntiles,
+                                 uint2* __restrict__ tile_info) {
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x) {
+        const uint32_t p = upper_bound_u32(tile_start, 0, k + 1, t) - 1;
+        const uint32_t u_begin = p * q, u_end = min(n, u_begin + q);
+        const uint32_t e_begin = row_ptr[u_begin] + (t - tile_start[p]) * kTileEdges;
+        tile_info[t] = make_uint2(p, upper_bound_u32(row_ptr, u_begin, u_end + 1, e_begin) - 1);
+    }
+}
+
+// Stages a tile for the staged count and fill: scol = its col, rowof = the
+// local row of every edge (each non-empty row marks its first edge in the
+// tile; an edge belongs to the last row starting at or before it, and the
+// marks rise with the position, so a max-scan carries them forward). Returns
+// the tile's bounds. Whole block; ends with a barrier.
+struct TileSpan {
+    uint32_t p, ulo, u_begin, e_begin, e_end;
+    bool first_starts_row;
+};
+__device__ TileSpan stage_tile(const uint32_t* __restrict__ row_ptr, const uint32_t* __restrict__ col, uint32_t n,
+                               uint32_t q, const uint32_t* __restrict__ tile_start,
+                               const uint2* __restrict__ tile_info, uint32_t ntiles, uint32_t t, uint32_t* scol,
+                               uint16_t* rowof, uint32_t* sh32) {
+    const uint32_t tid = threadIdx.x;
+    const uint2 ti = tile_info[t];
+    TileSpan sp;
+    sp.p = ti.x;
+    sp.ulo = ti.y;
+    sp.u_begin = sp.p * q;
+    const uint32_t u_end = min(n, sp.u_begin + q);
+    sp.e_begin = row_ptr[sp.u_begin] + (t - tile_start[sp.p]) * kTileEdges;
+    sp.e_end = (uint32_t)min((uint64_t)sp.e_begin + kTileEdges, (uint64_t)row_ptr[u_end]);
+    sp.first_starts_row = sp.e_begin == row_ptr[sp.ulo];
+    const uint32_t L = sp.e_end - sp.e_begin;
+    // rows up to the next tile's first row (or the partition's last) cover the tile
+    const uint32_t rhi = (t + 1 < ntiles && tile_start[sp.p + 1] > t + 1) ? tile_info[t + 1].y : u_end - 1;
+    {
+        uint32_t x[kFillPerThread];
+#pragma unroll
+        for (uint32_t j = 0; j < kFillPerThread; ++j) {
+            const uint32_t i = j * blockDim.x + tid;
+            x[j] = i < L ? __ldcs(col + sp.e_begin + i) : 0u;
+        }
+#pragma unroll
+        for (uint32_t j = 0; j < kFillPerThread; ++j) {
+            const uint32_t i = j * blockDim.x + tid;
+            scol[i] = x[j];
+            rowof[i] = 0;
+        }
+    }
+    __syncthreads();
+    for (uint32_t r = sp.ulo + tid; r <= rhi; r += blockDim.x) {
+        const uint32_t a = row_ptr[r], b = row_ptr[r + 1];
+        if (b > a && b > sp.e_begin && a < sp.e_end)
+            rowof[a > sp.e_begin ? a - sp.e_begin : 0] = (uint16_t)(r - sp.ulo);
+    }
+    __syncthreads();
+    {
+        const uint32_t i0 = tid * kFillPerThread;
+        uint32_t mx = 0;
+        for (uint32_t j = 0; j < kFillPerThread; ++j) mx = max(mx, (uint32_t)rowof[i0 + j]);
+        uint32_t run = block_exclusive_max(mx, sh32);
+        for (uint32_t j = 0; j < kFillPerThread; ++j) {
+            run = max(run, (uint32_t)rowof[i0 + j]);
+            rowof[i0 + j] = (uint16_t)run;
+        }
+    }
+    __syncthreads();
+    return sp;
+}
+
+// Count pass for k <= kFillMaxK: one CTA per tile counts edges and message
+// starts per key p' with shared-memory atomics (one packed word per key:
+// edges in the low, starts in the high half; counting needs no order) and
+// writes the tile's row of tab_e and tab_u. Same tables as tile_kernel<false>.
+__global__ void __launch_bounds__(kFillWarps * 32) count_staged_kernel(
+    const uint32_t* __restrict__ row_ptr, const uint32_t* __restrict__ col, uint32_t n, DivQ div, uint32_t k,
+    const uint32_t* __restrict__ tile_start, const uint2* __restrict__ tile_info, uint32_t ntiles,
+    uint32_t* __restrict__ tab_e, uint32_t* __restrict__ tab_u, int* __restrict__ err) {
+    extern __shared__ __align__(16) unsigned char fsm[];
+    __shared__ uint32_t sh32[32];
+    uint32_t* scol = reinterpret_cast<uint32_t*>(fsm);
+    uint16_t* rowof = reinterpret_cast<uint16_t*>(scol + kTileEdges);
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(rowof + kTileEdges);  // k packed counters
+    const uint32_t tid = threadIdx.x, q = div.q;
+    for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        for (uint32_t j = tid; j < k; j += blockDim.x) cnt[j] = 0;
+        const TileSpan sp = stage_tile(row_ptr, col, n, q, tile_start, tile_info, ntiles, t, scol, rowof, sh32);
+        const uint32_t L = sp.e_end - sp.e_begin;
+        const uint32_t prev0 = (L && !sp.first_starts_row) ? col[sp.e_begin - 1] : 0u;
+        for (uint32_t i = tid; i < L; i += blockDim.x) {
+            const uint32_t v = scol[i], r = rowof[i];
+            const bool row_start = i == 0 ? sp.first_starts_row : rowof[i - 1] != r;
+            const uint32_t prev_v = i == 0 ? prev0 : scol[i - 1];
+            if (v >= n || (!row_start && prev_v > v)) {
+                atomicOr(err, kErrBadGraph);
+                continue;
+            }
+            const uint32_t key = div(v);
+            const bool start = row_start || prev_v < key * q;  // prev_v <= v in a row
+            atomicAdd(&cnt[key], 1u | (start ? 0x10000u : 0u));
+        }
+        __syncthreads();
+        for (uint32_t j = tid; j < k; j += blockDim.x) {
+            const uint32_t c = cnt[j];
+            tab_e[(size_t)t * k + j] = c & 0xFFFFu;
+            tab_u[(size_t)t * k + j] = c >> 16;
+        }
+        __syncthreads();
+    }
+}
+
+size_t count_smem_bytes(uint32_t k) {
+    return (size_t)kTileEdges * (sizeof(uint32_t) + sizeof(uint16_t)) + (size_t)k * sizeof(uint32_t);
+}
+
 __global__ void __launch_bounds__(kFillWarps * 32) fill_staged_kernel(
-    const uint32_t* __restrict__ row_ptr, const uint32_t* __restrict__ col, uint32_t n, uint32_t q, uint32_t k,
+    const uint32_t* __restrict__ row_ptr, const uint32_t* __restrict__ col, uint32_t n, DivQ div, uint32_t k,
     const uint32_t* __restrict__ tile_start, const uint2* __restrict__ tile_info, uint32_t ntiles,
     const uint32_t* __restrict__ tab_e, const uint32_t* __restrict__ tab_u, const uint32_t* __restrict__ bin_e,
     const uint32_t* __restrict__ bin_u, uint32_t* __restrict__ dest, uint32_t* __restrict__ src,
@@ -316,62 +445,21 @@ __global__ void __launch_bounds__(kFillWarps * 32) fill_staged_kernel(
     uint32_t* gbu = gbe + k;                                  // k: the same for updates
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t lt = lanemask_lt();
+    const uint32_t q = div.q;
 
     for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const uint2 ti = tile_info[t];
-        const uint32_t p = ti.x, ulo = ti.y;
-        const uint32_t u_begin = p * q, u_end = min(n, u_begin + q);
-        const uint32_t e_begin = row_ptr[u_begin] + (t - tile_start[p]) * kTileEdges;
-        const uint32_t e_end = (uint32_t)min((uint64_t)e_begin + kTileEdges, (uint64_t)row_ptr[u_end]);
-        const uint32_t L = e_end - e_begin;
-        // rows up to the next tile's first row (or the partition's last) cover the tile
-        const uint32_t rhi = (t + 1 < ntiles && tile_start[p + 1] > t + 1) ? tile_info[t + 1].y : u_end - 1;
-
-        // stage: col, cleared row marks and counters, cursors
-        {
-            uint32_t x[kFillPerThread];
-#pragma unroll
-            for (uint32_t j = 0; j < kFillPerThread; ++j) {
-                const uint32_t i = j * blockDim.x + tid;
-                x[j] = i < L ? __ldcs(col + e_begin + i) : 0u;
-            }
-#pragma unroll
-            for (uint32_t j = 0; j < kFillPerThread; ++j) {
-                const uint32_t i = j * blockDim.x + tid;
-                scol[i] = x[j];
-                rowof[i] = 0;
-            }
-        }
         for (uint32_t j = tid; j < kFillWarps * k; j += blockDim.x) hist[j] = 0;
         for (uint32_t j = tid; j < k; j += blockDim.x) {
             gbe[j] = bin_e[j] + tab_e[(size_t)t * k + j];
             gbu[j] = bin_u[j] + tab_u[(size_t)t * k + j];
         }
-        __syncthreads();
-        // each non-empty row marks its first edge in the tile ...
-        for (uint32_t r = ulo + tid; r <= rhi; r += blockDim.x) {
-            const uint32_t a = row_ptr[r], b = row_ptr[r + 1];
-            if (b > a && b > e_begin && a < e_end) rowof[a > e_begin ? a - e_begin : 0] = (uint16_t)(r - ulo);
-        }
-        __syncthreads();
-        // ... and the marks carry forward: an edge belongs to the last row
-        // starting at or before it (marks rise with the position)
-        {
-            const uint32_t i0 = tid * kFillPerThread;
-            uint32_t mx = 0;
-            for (uint32_t j = 0; j < kFillPerThread; ++j) mx = max(mx, (uint32_t)rowof[i0 + j]);
-            uint32_t run = block_exclusive_max(mx, sh32);
-            for (uint32_t j = 0; j < kFillPerThread; ++j) {
-                run = max(run, (uint32_t)rowof[i0 + j]);
-                rowof[i0 + j] = (uint16_t)run;
-            }
-        }
-        __syncthreads();
+        const TileSpan sp = stage_tile(row_ptr, col, n, q, tile_start, tile_info, ntiles, t, scol, rowof, sh32);
+        const uint32_t ulo = sp.ulo, u_begin = sp.u_begin, e_begin = sp.e_begin, L = sp.e_end - sp.e_begin;
 
         // One pass over the warp's slice; body(valid, i, v, local row, key,
         // start, peers, smask) runs once per 32 edges (warp-collective).
         const uint32_t s_lo = min(L, warp * kFillSlice), s_hi = min(L, s_lo + kFillSlice);
-        const bool first_starts_row = e_begin == row_ptr[ulo];
+        const bool first_starts_row = sp.first_starts_row;
         auto walk = [&](auto&& body) {
             uint32_t carry = 0;
             if (s_lo > 0 && s_lo < s_hi) carry = scol[s_lo - 1];
@@ -396,8 +484,8 @@ __global__ void __launch_bounds__(kFillWarps * 32) fill_staged_kernel(
                         atomicOr(err, kErrBadGraph);
                         valid = false;
                     } else {
-                        key = v / q;
-                        start = row_start || (prev_v / q != key);
+                        key = div(v);
+                        start = row_start || prev_v < key * q;  // prev_v <= v in a row
                     }
                 }
                 const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
@@ -981,13 +1069,30 @@ int build_png(pcpm_png* g, const uint32_t* row_ptr, const uint32_t* col, const p
     BCK(cudaFuncSetAttribute(tile_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem));
     const int sms = g->sms;
     const int tile_grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((ntiles + wpc - 1) / wpc, (uint64_t)sms * 16));
-    // (source partition, first row) of every tile, for the staged fill
+    // k <= kFillMaxK: one CTA per tile (staged count and fill), which needs
+    // every tile's (source partition, first row); else one warp per tile
+    const bool staged = k <= kFillMaxK;
+    const DivQ divq = make_divq(q);
     uint2* tile_info = nullptr;
     BCK(tmp.alloc(&tile_info, std::max<uint32_t>(ntiles, 1)));
-    if (ntiles) {
+    auto staged_grid = [&](const void* f, size_t smem, int* grid) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int per_sm = 0;
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, kFillWarps * 32, smem);
+        *grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(ntiles, (uint64_t)sms * (uint64_t)std::max(per_sm, 1)));
+        return e;
+    };
+    if (ntiles && staged) {
+        tile_info_kernel<<<grid_for(ntiles, 256, 4096), 256, 0, s>>>(row_ptr, n, q, k, tile_start, ntiles, tile_info);
+        const size_t cs = count_smem_bytes(k);
+        int grid = 1;
+        BCK(staged_grid((const void*)count_staged_kernel, cs, &grid));
+        count_staged_kernel<<<grid, kFillWarps * 32, cs, s>>>(row_ptr, col, n, divq, k, tile_start, tile_info, ntiles,
+                                                             tab_e, tab_u, d_err);
+        BCK(cudaGetLastError());
+    } else if (ntiles) {
         tile_kernel<false><<<tile_grid, wpc * 32, tile_smem, s>>>(row_ptr, col, n, q, k, tile_start, ntiles, tab_e,
-                                                                 tab_u, nullptr, nullptr, nullptr, nullptr, d_err,
-                                                                 nullptr, nullptr, tile_info);
+                                                                 tab_u, nullptr, nullptr, nullptr, nullptr, d_err);
         BCK(cudaGetLastError());
     }
     if ((rc = read_err(d_err, s, &h_err)) != PCPM_OK) return rc;
@@ -1025,14 +1130,11 @@ int build_png(pcpm_png* g, const uint32_t* row_ptr, const uint32_t* col, const p
     BCK(dev_alloc(g, (void**)&g->src, (g->ne + 4) * sizeof(uint32_t)));
     if (ntiles) {
         if (g->weighted) BCK(dev_alloc(g, (void**)&g->wdest, dest_len * sizeof(float)));
-        if (k <= kFillMaxK) {
+        if (staged) {
             const size_t fs = fill_smem_bytes(k, g->weighted != 0);
-            BCK(cudaFuncSetAttribute(fill_staged_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fs));
-            int per_sm = 0;
-            BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fill_staged_kernel, kFillWarps * 32, fs));
-            const int fill_grid = (int)std::max<uint64_t>(
-                1, std::min<uint64_t>(ntiles, (uint64_t)sms * (uint64_t)std::max(per_sm, 1)));
-            fill_staged_kernel<<<fill_grid, kFillWarps * 32, fs, s>>>(row_ptr, col, n, q, k, tile_start, tile_info,
+            int fill_grid = 1;
+            BCK(staged_grid((const void*)fill_staged_kernel, fs, &fill_grid));
+            fill_staged_kernel<<<fill_grid, kFillWarps * 32, fs, s>>>(row_ptr, col, n, divq, k, tile_start, tile_info,
                                                                      ntiles, tab_e, tab_u, g->bin_e, g->bin_u,
                                                                      g->dest, g->src, d_err, g->weights_in, g->wdest);
         } else {
