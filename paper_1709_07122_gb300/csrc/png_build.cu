@@ -673,11 +673,6 @@ __global__ void inv_deg_kernel(const uint32_t* __restrict__ row_ptr, uint32_t n,
 }
 
 // In-degree of every node.
-__global__ void indegree_kernel(const uint32_t* __restrict__ col, uint64_t m, uint32_t* __restrict__ indeg) {
-    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < m; e += (uint64_t)gridDim.x * blockDim.x)
-        atomicAdd(&indeg[col[e]], 1u);
-}
-
 __device__ __forceinline__ unsigned long long block_max_u64(unsigned long long x, unsigned long long* sh) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x = max(x, __shfl_xor_sync(0xffffffffu, x, o));
@@ -691,20 +686,40 @@ __device__ __forceinline__ unsigned long long block_max_u64(unsigned long long x
     return x;
 }
 
-// Per destination partition: local IDs of the two nodes with the largest
+// Per destination partition p: local IDs of the two nodes with the largest
 // in-degree (ties to the lower ID), kNoHub below kHubMinInDegree. The gather
 // sums their updates in registers instead of contended shared-memory atomics.
-__global__ void __launch_bounds__(1024) hubs_kernel(const uint32_t* __restrict__ indeg, uint32_t n, uint32_t q,
-                                                    uint32_t* __restrict__ hubs) {
+// Every in-edge of a node of p lies in bin p, so the in-degrees are counted
+// in shared memory from the bin's IDs (one CTA per bin).
+__global__ void __launch_bounds__(1024) bin_hubs_kernel(const uint32_t* __restrict__ dest,
+                                                        const uint32_t* __restrict__ bin_e, uint32_t n, uint32_t q,
+                                                        uint32_t* __restrict__ hubs) {
+    extern __shared__ uint32_t deg[];
     __shared__ unsigned long long sh[32];
     const uint32_t p = blockIdx.x, base = p * q, len = min(q, n - base);
+    for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) deg[i] = 0;
+    __syncthreads();
+    const uint32_t e0 = bin_e[p], e1 = bin_e[p + 1];
+    constexpr uint32_t kIlp = 4;
+    for (uint32_t e = e0 + threadIdx.x; e < e1; e += kIlp * blockDim.x) {
+        uint32_t loc[kIlp];
+#pragma unroll
+        for (uint32_t j = 0; j < kIlp; ++j) {
+            const uint32_t x = e + j * blockDim.x;
+            loc[j] = x < e1 ? (__ldcs(dest + x) & kIdMask) - base : 0xFFFFFFFFu;
+        }
+#pragma unroll
+        for (uint32_t j = 0; j < kIlp; ++j)
+            if (loc[j] < len) atomicAdd(&deg[loc[j]], 1u);
+    }
+    __syncthreads();
     unsigned long long best = 0;
     for (uint32_t i = threadIdx.x; i < len; i += blockDim.x)
-        best = max(best, ((unsigned long long)indeg[base + i] << 32) | (0xFFFFFFFFu - i));
+        best = max(best, ((unsigned long long)deg[i] << 32) | (0xFFFFFFFFu - i));
     const unsigned long long b1 = block_max_u64(best, sh);
     unsigned long long second = 0;
     for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) {
-        const unsigned long long key = ((unsigned long long)indeg[base + i] << 32) | (0xFFFFFFFFu - i);
+        const unsigned long long key = ((unsigned long long)deg[i] << 32) | (0xFFFFFFFFu - i);
         if (key != b1) second = max(second, key);
     }
     const unsigned long long b2 = block_max_u64(second, sh);
@@ -822,9 +837,17 @@ __global__ void __launch_bounds__(kLayoutWarps * 32) gather_layout_kernel(
     uint32_t* cnt = keycnt[warp];
     uint32_t nmerged = 0;
     bool bad = false;
+    uint32_t p = 0;  // the warp's chunks rise, so their bins do too
     for (uint64_t ic = blockIdx.x * (uint64_t)kLayoutWarps + warp; ic < nichunks;
          ic += (uint64_t)gridDim.x * kLayoutWarps) {
-        const uint32_t p = upper_bound_u32(ichunk_start, 0, k + 1, (uint32_t)ic) - 1;
+        {  // bin of chunk ic: the last p with ichunk_start[p] <= ic, galloping from the last one
+            uint32_t step = 1;
+            while (p + step < k && ichunk_start[p + step] <= (uint32_t)ic) {
+                p += step;
+                step <<= 1;
+            }
+            p = upper_bound_u32(ichunk_start, p, min(k, p + step), (uint32_t)ic) - 1;
+        }
         const uint32_t P = bin_e[p] + ((uint32_t)ic - ichunk_start[p]) * kChunk;
         const uint32_t Pend = min(P + kChunk, bin_e[p + 1]);
         const uint32_t vbase = p * q, h0 = hubs[2 * p], h1 = hubs[2 * p + 1];
@@ -867,13 +890,22 @@ __global__ void __launch_bounds__(kLayoutWarps * 32) gather_layout_kernel(
             if (lane == (uint32_t)(__ffs(peers) - 1)) cnt[key[r]] += __popc(peers);
             __syncwarp();
         }
-        if (lane == 0) {
-            uint32_t run = 0;
-            for (uint32_t j = 0; j < kNumKeys; ++j) {
-                const uint32_t c = cnt[j];
-                cnt[j] = run;
-                run += c;
+        {  // exclusive scan of the counts: bank groups (one per lane), then hub and padding
+            const uint32_t c = cnt[lane], c_hub = cnt[kKeyHub];
+            uint32_t x = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= (uint32_t)o) x += y;
             }
+            const uint32_t banks = __shfl_sync(0xffffffffu, x, 31);
+            __syncwarp();
+            cnt[lane] = x - c;
+            if (lane == 0) {
+                cnt[kKeyHub] = banks;
+                cnt[kKeyPad] = banks + c_hub;
+            }
+            static_assert(kKeyHub == 32 && kKeyPad == 33 && kNumKeys == 34, "32 bank groups, then hub and padding");
         }
         __syncwarp();
         // gather words staged by sorted position
@@ -894,10 +926,12 @@ __global__ void __launch_bounds__(kLayoutWarps * 32) gather_layout_kernel(
         }
         __syncwarp();
         // cnt[j] now holds the end of group j; group j starts at cnt[j - 1].
-        // Inside each bank group, and in the hub group, order IDs by slot, so
-        // equal destinations sit next to each other and the gather sums them
-        // in a register before one shared-memory add.
-        for (uint32_t grp = lane; grp <= kKeyHub; grp += 32) {
+        // Inside each bank group (one per lane), and in the hub group, order
+        // IDs by slot, so equal destinations sit next to each other and the
+        // gather sums them in a register before one shared-memory add. The
+        // padding group is in slot order already.
+        {
+            const uint32_t grp = lane;
             const uint32_t g_end = cnt[grp], g_beg = grp ? cnt[grp - 1] : 0;
             for (uint32_t x = g_beg + 1; x < g_end; ++x) {
                 const uint32_t w = sorted[x];
@@ -910,6 +944,35 @@ __global__ void __launch_bounds__(kLayoutWarps * 32) gather_layout_kernel(
                 }
                 sorted[y] = w;
                 if (gweight) sortw[warp][y] = wt;
+            }
+        }
+        __syncwarp();
+        {  // the hub group holds two slots: a stable partition, first hub first
+            const uint32_t hb = cnt[kKeyHub - 1], he = cnt[kKeyHub], hub0 = q + kPadSlots;
+            uint32_t w[kChunk / 32], n0 = 0;
+            float wt[kChunk / 32];
+#pragma unroll
+            for (int r = 0; r < (int)(kChunk / 32); ++r) {
+                const uint32_t x = hb + 32 * r + lane;
+                w[r] = x < he ? sorted[x] : 0u;
+                wt[r] = (gweight && x < he) ? sortw[warp][x] : 0.0f;
+                n0 += __popc(__ballot_sync(0xffffffffu, x < he && (w[r] & kGwLocMask) == hub0));
+            }
+            __syncwarp();
+            uint32_t r0 = 0, r1 = 0;
+#pragma unroll
+            for (int r = 0; r < (int)(kChunk / 32); ++r) {
+                const uint32_t x = hb + 32 * r + lane;
+                const bool live = x < he, first = (w[r] & kGwLocMask) == hub0;
+                const uint32_t b0 = __ballot_sync(0xffffffffu, live && first);
+                const uint32_t b1 = __ballot_sync(0xffffffffu, live && !first);
+                if (live) {
+                    const uint32_t to = first ? hb + r0 + __popc(b0 & lt) : hb + n0 + r1 + __popc(b1 & lt);
+                    sorted[to] = w[r];
+                    if (gweight) sortw[warp][to] = wt[r];
+                }
+                r0 += __popc(b0);
+                r1 += __popc(b1);
             }
         }
         __syncwarp();
@@ -1168,12 +1231,10 @@ int build_png(pcpm_png* g, const uint32_t* row_ptr, const uint32_t* col, const p
     }
 
     // Hubs per bin.
-    uint32_t* indeg = nullptr;
-    BCK(tmp.alloc(&indeg, n));
-    BCK(cudaMemsetAsync(indeg, 0, (size_t)n * sizeof(uint32_t), s));
-    if (m) indegree_kernel<<<grid_for(m, 256, sms * 32), 256, 0, s>>>(col, m, indeg);
     BCK(dev_alloc(g, (void**)&g->hubs, 2 * (size_t)k * sizeof(uint32_t)));
-    hubs_kernel<<<k, 1024, 0, s>>>(indeg, n, q, g->hubs);
+    const size_t hub_smem = (size_t)q * sizeof(uint32_t);
+    BCK(cudaFuncSetAttribute(bin_hubs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hub_smem));
+    bin_hubs_kernel<<<k, 1024, hub_smem, s>>>(g->dest, g->bin_e, n, q, g->hubs);
     BCK(cudaGetLastError());
 
     // Work units, largest first. Gather: runs of at most `gper` chunks, at
