@@ -259,13 +259,14 @@ __global__ void tile_kernel(const uint32_t* __restrict__ row_ptr, const uint32_t
 // tile one CTA and writes every (tile, bin) run in one piece instead:
 //   stage    the tile's col and the local row of every edge (stage_tile: no
 //            per-edge search);
-//   count    each warp counts its 1/kFillWarps of the tile per key p' (edges
-//            in the low, message starts in the high half of one word);
+//   count    each warp counts its 1/kFillWarps of the tile per key p' with
+//            shared atomics (edges in the low, message starts in the high
+//            half of one word);
 //   scan     per key over warps, then over keys: each warp's cursor in the
 //            tile's bin-ordered staging buffers;
 //   rank     each warp replays its slice in order, ranks equal keys with
 //            match/ballot and stages 16-bit local IDs (bit 15: message flag);
-//   copy     one warp per bin copies the bin's run of the tile out.
+//   copy     one half-warp per bin copies the bin's run of the tile out.
 // Same result as tile_kernel<true>: warps own consecutive slices and rank in
 // edge order, so the sort stays stable. Local IDs fit 16 bits because
 // q <= 32768; k <= kFillMaxK keeps the per-warp tables small.
@@ -495,11 +496,19 @@ __global__ void __launch_bounds__(kFillWarps * 32) fill_staged_kernel(
                 __syncwarp();
             }
         };
-        // count
-        walk([&](bool valid, uint32_t, uint32_t, uint32_t, uint32_t key, bool, uint32_t peers, uint32_t smask) {
-            if (valid && lane == __ffs(peers) - 1)
-                hist[warp * k + key] += __popc(peers) | (__popc(peers & smask) << 16);
-        });
+        // count the warp's slice per key (no order needed: shared atomics)
+        {
+            const uint32_t prev0 = (L && !first_starts_row) ? col[e_begin - 1] : 0u;
+            for (uint32_t i = s_lo + lane; i < s_hi; i += 32) {
+                const uint32_t v = scol[i], r = rowof[i];
+                const bool row_start = i == 0 ? first_starts_row : rowof[i - 1] != r;
+                const uint32_t prev_v = i == 0 ? prev0 : scol[i - 1];
+                if (v >= n || (!row_start && prev_v > v)) continue;  // reported by the rank pass
+                const uint32_t key = div(v);
+                const bool start = row_start || prev_v < key * q;
+                atomicAdd(&hist[warp * k + key], 1u | (start ? 0x10000u : 0u));
+            }
+        }
         __syncthreads();
         // scan: per key over warps, then over keys (both halves at once: each
         // total is at most kTileEdges < 2^16)
@@ -548,17 +557,18 @@ __global__ void __launch_bounds__(kFillWarps * 32) fill_staged_kernel(
                 hist[warp * k + key] += __popc(peers) | (__popc(peers & smask) << 16);
         });
         __syncthreads();
-        // copy each bin's run out
-        for (uint32_t j = warp; j < k; j += kFillWarps) {
+        // copy each bin's run out (a half-warp per bin: runs are short)
+        const uint32_t hl = lane & 15;
+        for (uint32_t j = 2 * warp + (lane >> 4); j < k; j += 2 * kFillWarps) {
             const uint32_t a = loff[j], b = loff[j + 1];
             const uint32_t ae = a & 0xFFFFu, be = b & 0xFFFFu, au = a >> 16, bu = b >> 16;
             const uint32_t ge = gbe[j], gu = gbu[j], vbase = j * q;
-            for (uint32_t i = ae + lane; i < be; i += 32) {
+            for (uint32_t i = ae + hl; i < be; i += 16) {
                 const uint32_t x = d16[i];
                 dest[ge + (i - ae)] = (vbase + (x & 0x7FFFu)) | ((x & 0x8000u) ? kMsb : 0u);
                 if (weights) wdest[ge + (i - ae)] = wst[i];
             }
-            for (uint32_t i = au + lane; i < bu; i += 32) src[gu + (i - au)] = u_begin + s16[i];
+            for (uint32_t i = au + hl; i < bu; i += 16) src[gu + (i - au)] = u_begin + s16[i];
         }
         __syncthreads();
     }
