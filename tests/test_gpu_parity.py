@@ -51,6 +51,8 @@ GRAPHS = {
     # the staged fill's largest partition count, and one past it (direct fill)
     "rmat12_q4_k1024": lambda: (graphgen.rmat(12, 16, seed=12), 4),
     "random5000_q3_k1667": lambda: (graphgen.random_graph(5000, 40000, seed=11), 3),
+    # mostly empty rows: a tile's rows span thousands of zero-degree nodes
+    "sparse200000_q32768": lambda: (graphgen.random_graph(200000, 30000, seed=13), 32768),
 }
 
 
