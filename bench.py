@@ -64,6 +64,8 @@ def parse_args():
     ap.add_argument("--no-spmv", action="store_true", help="skip the weighted SpMV leg")
     ap.add_argument("--batched", action="store_true",
                     help="also solve 256 RMAT graphs of scales 10-18 with one captured CUDA graph launch")
+    ap.add_argument("--ppr", action="store_true",
+                    help="also run batched personalized PageRank: RMAT s22, 64 teleport columns, 20 iterations")
     ap.add_argument("--mode", choices=("fused", "two_phase"), default="two_phase",
                     help="iteration form timed for `value` (the other is reported in other_mode)")
     ap.add_argument("--ref-budget-s", type=float, default=120.0, help="reference arm: timed seconds target")
@@ -330,6 +332,61 @@ def spmv_leg(a, rp, col, m):
     return res
 
 
+def ppr_leg(a, iters: int = 20):
+    """Batched personalized PageRank (pcpm_ppr_*): RMAT scale 22 (random labels,
+    q = 32768), 64 teleport columns each uniform over 1-1000 random seed nodes,
+    `iters` iterations from R = T, timed with CUDA events on the stream. Against
+    it: the same graph's single-vector PageRank iteration, times 64."""
+    import torch
+    import graphgen
+    import paper_1709_07122_gb300 as pcpm
+    rp, col = graphgen.rmat(22, a.edge_factor, 0.57, 0.19, 0.19, seed=a.seed + 22, relabel="random")
+    n, m = rp.size - 1, int(rp[-1])
+    rng = np.random.default_rng(a.seed + 23)
+    ptr, idx = [0], []
+    for _ in range(pcpm.PPR_COLS):
+        k = int(rng.integers(1, 1001))
+        idx.extend(rng.choice(n, size=k, replace=False).tolist())
+        ptr.append(len(idx))
+    d_rp, d_col = pcpm.to_device_csr(rp, col)
+    with pcpm.PNG(d_rp, d_col, 32768) as g:
+        info = g.info
+        ne = info["num_updates"]
+        g.iterate(a.d, 3, mode="two_phase")
+        single = g.iterate_timed(a.d, 10, mode="two_phase")["span"] / 10  # ms per iteration
+        torch.cuda.synchronize()
+        c0 = time.perf_counter()
+        p = pcpm.PPR(g, np.array(ptr, np.uint32), np.array(idx, np.uint32))
+        create_ms = (time.perf_counter() - c0) * 1e3
+        with p:
+            p.run(a.d, 3)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            p.run(a.d, iters)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / iters
+            res = p.residuals()
+            pinfo = p.info
+    del d_rp, d_col
+    torch.cuda.empty_cache()
+    row = 4 * pcpm.PPR_COLS
+    # scatter: R rows read, update rows written, positions; gather: update
+    # rows read once, entry index, R_old read, R' written
+    alg = n * row + ne * row + 4 * ne + 4 * (n + 1) + ne * row + 4 * m + 4 * (n + 1) + 2 * n * row
+    peak, src = measured_peaks()
+    return {"workload": "rmat-s22-ef%g-random-labels-q32768, 64 teleport columns (1-1000 seeds each)" % a.edge_factor,
+            "n": n, "m": m, "num_updates": ne, "iters": iters, "ms_per_iter": ms,
+            "gteps_x64": m * pcpm.PPR_COLS / (ms * 1e-3) / 1e9,
+            "single_vector_ms_per_iter": single,
+            "speedup_vs_64_single_vector_iterations": 64 * single / ms,
+            "algorithmic_bytes_per_iter": alg,
+            "hbm_frac_of_%s" % src: alg / (ms * 1e-3) / 1e9 / peak,
+            "split_destinations": pinfo["split_destinations"], "create_ms": create_ms,
+            "last_l1_change_max_over_columns": float(res[-1].max())}
+
+
 def batched_leg(a, graphs: int = 256, iters: int = 20):
     """Many small independent graphs (RMAT, scales drawn from 10-18, random
     labels) solved for `iters` iterations each by one captured CUDA graph
@@ -587,6 +644,9 @@ def run_ours(a):
 
     if a.batched:
         out["batched"] = batched_leg(a)
+
+    if a.ppr:
+        out["ppr"] = ppr_leg(a)
 
     if rank == 0 and not a.no_cpu_baseline:
         gt, dt, _, y_ref = cpu_oracle_iteration(rp, col, a.d)

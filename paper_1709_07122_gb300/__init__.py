@@ -96,6 +96,12 @@ def lib(path: str | None = None):
                 "pcpm_strerror": (ctypes.c_char_p, [i32]),
                 "pcpm_last_cuda_error": (ctypes.c_char_p, []),
                 "pcpm_release_cached_memory": (i32, []),
+                "pcpm_ppr_create": (i32, [vp, vp, vp, vp, ctypes.POINTER(vp)]),
+                "pcpm_ppr_run": (i32, [vp, f32, i32, vp]),
+                "pcpm_ppr_residuals": (i32, [vp, vp, i32]),
+                "pcpm_ppr_ranks": (i32, [vp, vp, vp]),
+                "pcpm_ppr_info": (i32, [vp, ctypes.POINTER(u64), ctypes.POINTER(u32)]),
+                "pcpm_ppr_free": (None, [vp]),
                 "pcpm_build_weighted": (i32, [vp, vp, vp, u32, u64, u32, ctypes.POINTER(_Options), vp,
                                               ctypes.POINTER(vp)]),
                 "pcpm_spmv": (i32, [vp, vp, vp, vp]),
@@ -471,6 +477,74 @@ class Batch:
         if getattr(self, "_b", None) is not None and self._b.value:
             lib().pcpm_batch_free(self._b)
             self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+PPR_COLS = 64
+
+
+class PPR:
+    """Batched personalized PageRank over a PNG (pcpm_ppr_*): PPR_COLS columns,
+    column j teleporting uniformly to its seeds seed_idx[seed_ptr[j]:seed_ptr[j+1]].
+    The PNG must outlive the solver."""
+
+    def __init__(self, png: "PNG", seed_ptr, seed_idx, stream=None):
+        sp = np.ascontiguousarray(seed_ptr, dtype=np.uint32)
+        si = np.ascontiguousarray(seed_idx, dtype=np.uint32)
+        if sp.size != PPR_COLS + 1:
+            raise ValueError(f"seed_ptr needs {PPR_COLS + 1} entries")
+        self.png = png
+        self.n = png.n
+        h = ctypes.c_void_p()
+        _check(lib().pcpm_ppr_create(png._h, sp.ctypes.data_as(ctypes.c_void_p),
+                                     si.ctypes.data_as(ctypes.c_void_p) if si.size else None, _stream(stream),
+                                     ctypes.byref(h)), "pcpm_ppr_create")
+        self._h = h
+        self.iters = 0
+
+    def run(self, d: float = 0.85, iters: int = 20, stream=None):
+        """From R = T, `iters` iterations on the stream (no synchronisation)."""
+        _check(lib().pcpm_ppr_run(self._h, float(d), int(iters), _stream(stream)), "pcpm_ppr_run")
+        self.iters = int(iters)
+
+    def residuals(self, iters: int | None = None) -> np.ndarray:
+        """L1 change per column of each iteration of the last run: [iters, PPR_COLS]."""
+        it = self.iters if iters is None else int(iters)
+        out = np.empty((max(it, 1), PPR_COLS), np.float64)
+        _check(lib().pcpm_ppr_residuals(self._h, out.ctypes.data_as(ctypes.c_void_p), it), "pcpm_ppr_residuals")
+        return out[:it]
+
+    def ranks(self, out=None, stream=None):
+        """The current ranks as a CUDA float32 tensor [n, PPR_COLS]."""
+        import torch
+        out = torch.empty((self.n, PPR_COLS), dtype=torch.float32, device="cuda") if out is None else out
+        if not (out.is_cuda and out.dtype == torch.float32 and out.is_contiguous()
+                and tuple(out.shape) == (self.n, PPR_COLS)):
+            raise ValueError(f"out must be a contiguous CUDA float32 tensor of shape ({self.n}, {PPR_COLS})")
+        _check(lib().pcpm_ppr_ranks(self._h, ctypes.c_void_p(out.data_ptr()), _stream(stream)), "pcpm_ppr_ranks")
+        return out
+
+    @property
+    def info(self) -> dict:
+        b, sd = ctypes.c_uint64(0), ctypes.c_uint32(0)
+        _check(lib().pcpm_ppr_info(self._h, ctypes.byref(b), ctypes.byref(sd)), "pcpm_ppr_info")
+        return {"device_bytes": b.value, "split_destinations": sd.value}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().pcpm_ppr_free(self._h)
+            self._h = None
 
     def __del__(self):
         try:

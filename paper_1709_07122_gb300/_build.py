@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(PKG, "libpcpm.so")
-SOURCES = ["png_build.cu", "pcpm_iter.cu", "pcpm_api.cu", "pcpm_noalloc.cu", "warmstart.cu"]
+SOURCES = ["png_build.cu", "pcpm_iter.cu", "pcpm_api.cu", "pcpm_noalloc.cu", "warmstart.cu", "ppr.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -159,6 +159,10 @@ namespace pcpm {
 int build_png(pcpm_png* g, const uint32_t* row_ptr, const uint32_t* col, const pcpm_build_options& opt,
               cudaStream_t s);
 
+// out[0..n] = exclusive scan of in[0..n), out[n] = total (png_build.cu);
+// temporaries from the pool in s's order. A PCPM_* status.
+int exclusive_scan_u32(const uint32_t* in, uint32_t* out, uint64_t n, cudaStream_t s);
+
 // Iteration kernels (pcpm_iter.cu).
 int configure_kernels(pcpm_png* g);
 int pull_sum(pcpm_png* g, const float* pr_like, float* out, cudaStream_t s);

@@ -1105,6 +1105,11 @@ int read_err(int* d_err, cudaStream_t s, int* h_err) {
 
 }  // namespace
 
+int exclusive_scan_u32(const uint32_t* in, uint32_t* out, uint64_t n, cudaStream_t s) {
+    TempBufs tmp(s);
+    return scan_exclusive(in, out, n, tmp, s);
+}
+
 int build_png(pcpm_png* g, const uint32_t* row_ptr, const uint32_t* col, const pcpm_build_options& opt,
               cudaStream_t s) {
     const uint32_t n = g->n, q = g->q, k = g->k;
