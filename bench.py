@@ -391,8 +391,8 @@ def batched_leg(a, graphs: int = 256, iters: int = 20):
     """Many small independent graphs (RMAT, scales drawn from 10-18, random
     labels) solved for `iters` iterations each by one captured CUDA graph
     launch, against the same solves issued call by call on one stream. The
-    partition size is picked per scale from {2048, 8192, 32768} by timing
-    five iterations on the first graph of that scale."""
+    partition size is picked per scale from {2048, 8192, 32768} by the
+    library's autotuner (five timed iterations on the first graph of that scale)."""
     import torch
     import paper_1709_07122_gb300 as pcpm
     import graphgen
@@ -403,17 +403,11 @@ def batched_leg(a, graphs: int = 256, iters: int = 20):
     gen_s = time.perf_counter() - t0
     dev = [pcpm.to_device_csr(rp, col) for rp, col in data]
     edges = sum(int(rp[-1]) for rp, _ in data)
-    # partition size per scale
+    # partition size per scale (pcpm_autotune on the first graph of that scale)
     best_q = {}
     for s in sorted(set(scales)):
         i = scales.index(s)
-        times = {}
-        for q in (2048, 8192, 32768):
-            with pcpm.PNG(*dev[i], q) as g:
-                g.reset()
-                g.iterate(a.d, 2, mode="two_phase")
-                times[q] = g.iterate_timed(a.d, 5, mode="two_phase")["span"]
-        best_q[s] = min(times, key=times.get)
+        best_q[s], _ = pcpm.autotune(*dev[i], (2048, 8192, 32768), a.d, warmup=2, iters=5, mode="two_phase")
     handles = [pcpm.PNG(*dev[i], best_q[s]) for i, s in enumerate(scales)]
     del dev
     t1 = time.perf_counter()

@@ -226,6 +226,22 @@ int pcpm_export_weights(const pcpm_png* png, float* wbin);
  * repeated builds make no new driver allocations. */
 void pcpm_free(pcpm_png* png);
 
+/* Partition-size autotuner. The paper studies r, traffic and time against the
+ * partition size (Sec. 5.3.2); the best size depends on the graph. This builds
+ * the PNG of the device CSR for every candidate part size, resets it to the
+ * uniform start, runs `warmup` untimed and then `iters` timed iterations
+ * (pcpm_iterate_timed with d and flags on `stream`), and frees it.
+ *   part_sizes     host, `count` >= 1 candidates.
+ *   best_part_size host; receives the candidate with the least time per iteration.
+ *   ms_per_iter    host, `count` floats, nullable: each candidate's time per
+ *                  iteration, or -1 where the build rejected the size
+ *                  (PCPM_EINVAL: above PCPM_MAX_PART_SIZE, or too many partitions).
+ * PCPM_EINVAL if no candidate builds or an argument is bad; other errors from
+ * the builds and iterations are returned as they occur. Synchronises. */
+int pcpm_autotune(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t n, uint64_t m,
+                  const uint32_t* part_sizes, int count, float d, int warmup, int iters, uint32_t flags,
+                  void* stream, uint32_t* best_part_size, float* ms_per_iter);
+
 /* Returns the memory that the library's pools hold but no live handle uses
  * to the driver (cudaMemPoolTrimTo 0 on every device the library used).
  * PCPM_ECUDA if a trim fails. */

@@ -96,6 +96,8 @@ def lib(path: str | None = None):
                 "pcpm_strerror": (ctypes.c_char_p, [i32]),
                 "pcpm_last_cuda_error": (ctypes.c_char_p, []),
                 "pcpm_release_cached_memory": (i32, []),
+                "pcpm_autotune": (i32, [vp, vp, u32, u64, vp, i32, f32, i32, i32, u32, vp, ctypes.POINTER(u32),
+                                        vp]),
                 "pcpm_ppr_create": (i32, [vp, vp, vp, vp, ctypes.POINTER(vp)]),
                 "pcpm_ppr_run": (i32, [vp, f32, i32, vp]),
                 "pcpm_ppr_residuals": (i32, [vp, vp, i32]),
@@ -154,6 +156,22 @@ def _flags(dangling: str, mode: str = "fused") -> int:
     if mode not in ("fused", "two_phase"):
         raise ValueError("mode must be 'fused' or 'two_phase'")
     return (DANGLING_LEAK if dangling == "leak" else 0) | (TWO_PHASE if mode == "two_phase" else 0)
+
+
+def autotune(row_ptr, col, part_sizes=(2048, 4096, 8192, 16384, 32768), d: float = 0.85, warmup: int = 2,
+             iters: int = 5, dangling: str = "uniform", mode: str = "two_phase", stream=None):
+    """Partition-size autotuner (pcpm_autotune) on a device CSR: returns
+    (best part size, {part size: ms per iteration, or None if rejected})."""
+    cand = np.ascontiguousarray(part_sizes, dtype=np.uint32)
+    ms = np.empty(cand.size, np.float32)
+    best = ctypes.c_uint32(0)
+    n = row_ptr.numel() - 1
+    m = int(row_ptr[-1].item()) & 0xFFFFFFFF
+    _check(lib().pcpm_autotune(_dev_u32(row_ptr), _dev_u32(col), n, m, cand.ctypes.data_as(ctypes.c_void_p),
+                               int(cand.size), float(d), int(warmup), int(iters), _flags(dangling, mode),
+                               _stream(stream), ctypes.byref(best), ms.ctypes.data_as(ctypes.c_void_p)),
+           "pcpm_autotune")
+    return best.value, {int(q): (float(t) if t >= 0 else None) for q, t in zip(cand, ms)}
 
 
 def release_cached_memory() -> None:

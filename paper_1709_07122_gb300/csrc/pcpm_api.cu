@@ -508,6 +508,35 @@ void pcpm_free(pcpm_png* png) {
     release(png);
 }
 
+int pcpm_autotune(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t n, uint64_t m,
+                  const uint32_t* part_sizes, int count, float d, int warmup, int iters, uint32_t flags,
+                  void* stream, uint32_t* best_part_size, float* ms_per_iter) {
+    if (!part_sizes || count < 1 || !best_part_size || warmup < 0 || iters < 1 || bad_damping(d) ||
+        (flags & ~kAllFlags))
+        return PCPM_EINVAL;
+    float best = -1.0f;
+    for (int i = 0; i < count; ++i) {
+        if (ms_per_iter) ms_per_iter[i] = -1.0f;
+        pcpm_png* g = nullptr;
+        int rc = pcpm_build(row_ptr, col_idx, n, m, part_sizes[i], stream, &g);
+        if (rc == PCPM_EINVAL) continue;
+        if (rc != PCPM_OK) return rc;
+        float kms[PCPM_NUM_PHASES + 1] = {};
+        rc = pcpm_reset(g, nullptr, stream);
+        if (rc == PCPM_OK && warmup > 0) rc = pcpm_iterate(g, d, warmup, 0.0, flags, nullptr, nullptr, stream);
+        if (rc == PCPM_OK) rc = pcpm_iterate_timed(g, d, iters, flags, kms, stream);
+        pcpm_free(g);
+        if (rc != PCPM_OK) return rc;
+        const float ms = kms[PCPM_NUM_PHASES] / (float)iters;
+        if (ms_per_iter) ms_per_iter[i] = ms;
+        if (best < 0.0f || ms < best) {
+            best = ms;
+            *best_part_size = part_sizes[i];
+        }
+    }
+    return best < 0.0f ? PCPM_EINVAL : PCPM_OK;
+}
+
 int pcpm_release_cached_memory(void) {
     std::lock_guard<std::mutex> lock(g_pool_mu);
     for (int dev = 0; dev < kMaxDevices; ++dev) {

@@ -254,6 +254,18 @@ def test_pool_reuse_across_builds_and_trim():
     pcpm.release_cached_memory()
 
 
+def test_autotune_picks_the_fastest_valid_part_size():
+    rp, col = graphgen.rmat(14, 16, seed=40)
+    d_rp, d_col = pcpm.to_device_csr(rp, col)
+    best, ms = pcpm.autotune(d_rp, d_col, (1024, 4096, 16384, 40000), iters=3)
+    assert ms[40000] is None  # above the largest partition size: rejected, not fatal
+    valid = {q: t for q, t in ms.items() if t is not None}
+    assert set(valid) == {1024, 4096, 16384} and all(t > 0 for t in valid.values())
+    assert best == min(valid, key=valid.get)
+    with pytest.raises(pcpm.PcpmError):
+        pcpm.autotune(d_rp, d_col, (40000, 0))
+
+
 def test_errors_from_bad_inputs():
     rp = np.array([0, 2, 3, 3], np.uint32)
     unsorted = np.array([2, 1, 0], np.uint32)
