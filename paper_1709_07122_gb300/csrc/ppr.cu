@@ -419,30 +419,28 @@ int ppr_build(pcpm_ppr* h, const std::vector<uint32_t>& seed_node, const std::ve
     // by source: upos
     PCK(ppr_alloc(h, (void**)&h->uptr, ((size_t)n + 1) * sizeof(uint32_t)));
     PCK(ppr_alloc(h, (void**)&h->upos, std::max<uint64_t>(h->ne, 1) * sizeof(uint32_t)));
-    uint32_t* cnt = nullptr;
-    PCK(pool_alloc((void**)&cnt, ((size_t)n + 1) * sizeof(uint32_t), s));
+    struct Scratch {  // a build temporary, returned to the pool in s's order on every path
+        uint32_t* p = nullptr;
+        cudaStream_t s;
+        ~Scratch() { pool_free(p, s); }
+    } cnt{nullptr, s};
+    PCK(pool_alloc((void**)&cnt.p, ((size_t)n + 1) * sizeof(uint32_t), s));
     int rc = PCPM_OK;
-    auto fail = [&](int code) {
-        pool_free(cnt, s);
-        return code;
-    };
-    if (cudaMemsetAsync(cnt, 0, (size_t)n * sizeof(uint32_t), s) != cudaSuccess) return fail(PCPM_ECUDA);
-    if (h->ne) count_keys_kernel<<<grid, 256, 0, s>>>(g->src, h->ne, 0xFFFFFFFFu, cnt);
-    if ((rc = exclusive_scan_u32(cnt, h->uptr, n, s)) != PCPM_OK) return fail(rc);
-    if (cudaMemcpyAsync(cnt, h->uptr, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-        return fail(PCPM_ECUDA);
-    if (h->ne) fill_by_source_kernel<<<grid, 256, 0, s>>>(g->src, h->ne, cnt, h->upos);
+    PCK(cudaMemsetAsync(cnt.p, 0, (size_t)n * sizeof(uint32_t), s));
+    if (h->ne) count_keys_kernel<<<grid, 256, 0, s>>>(g->src, h->ne, 0xFFFFFFFFu, cnt.p);
+    if ((rc = exclusive_scan_u32(cnt.p, h->uptr, n, s)) != PCPM_OK) return rc;
+    PCK(cudaMemcpyAsync(cnt.p, h->uptr, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    if (h->ne) fill_by_source_kernel<<<grid, 256, 0, s>>>(g->src, h->ne, cnt.p, h->upos);
     // by destination: uidx
     PCK(ppr_alloc(h, (void**)&h->colptr, ((size_t)n + 1) * sizeof(uint32_t)));
     PCK(ppr_alloc(h, (void**)&h->uidx, std::max<uint64_t>(h->m, 1) * sizeof(uint32_t)));
-    if (cudaMemsetAsync(cnt, 0, (size_t)n * sizeof(uint32_t), s) != cudaSuccess) return fail(PCPM_ECUDA);
-    if (h->m) count_keys_kernel<<<grid, 256, 0, s>>>(g->dest, h->m, kIdMask, cnt);
-    if ((rc = exclusive_scan_u32(cnt, h->colptr, n, s)) != PCPM_OK) return fail(rc);
-    if (cudaMemcpyAsync(cnt, h->colptr, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-        return fail(PCPM_ECUDA);
-    if (h->m) fill_by_destination_kernel<<<grid, 256, 0, s>>>(g->dest, h->m, g->chunk_base, g->nchunks, cnt, h->uidx);
-    if ((rc = launch_status()) != PCPM_OK) return fail(rc);
-    pool_free(cnt, s);
+    PCK(cudaMemsetAsync(cnt.p, 0, (size_t)n * sizeof(uint32_t), s));
+    if (h->m) count_keys_kernel<<<grid, 256, 0, s>>>(g->dest, h->m, kIdMask, cnt.p);
+    if ((rc = exclusive_scan_u32(cnt.p, h->colptr, n, s)) != PCPM_OK) return rc;
+    PCK(cudaMemcpyAsync(cnt.p, h->colptr, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    if (h->m)
+        fill_by_destination_kernel<<<grid, 256, 0, s>>>(g->dest, h->m, g->chunk_base, g->nchunks, cnt.p, h->uidx);
+    if ((rc = launch_status()) != PCPM_OK) return rc;
     // destinations split into pieces (found on the host from colptr)
     std::vector<uint32_t> cp((size_t)n + 1);
     PCK(cudaMemcpyAsync(cp.data(), h->colptr, ((size_t)n + 1) * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));

@@ -134,6 +134,16 @@ def test_bad_seeds_rejected():
                 p.run(1.0, 3)
 
 
+def test_edgeless_graph_keeps_the_teleport():
+    n = 10  # every node dangling, fewer nodes than gather lanes; seeds shared across columns
+    rp = np.zeros(n + 1, np.uint32)
+    ptr = np.arange(C + 1, dtype=np.uint32)
+    idx = (np.arange(C) % n).astype(np.uint32)
+    r, res, _ = run_case(rp, np.zeros(0, np.uint32), 4, ptr, idx, 0.85, 3)
+    np.testing.assert_allclose(r, oppr.teleport(n, ptr, idx), atol=1e-7)
+    assert np.abs(res).max() <= 1e-6
+
+
 def test_full_size_rmat22_two_iterations():
     """The batched workload's graph (RMAT s22, q = 32768) and seed mix, two
     iterations against the FP64 oracle."""
