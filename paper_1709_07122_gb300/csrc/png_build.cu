@@ -274,7 +274,8 @@ constexpr int kFillWarps = 8;
 constexpr uint32_t kFillSlice = kTileEdges / kFillWarps;
 constexpr uint32_t kFillMaxK = 1024;
 constexpr uint32_t kFillPerThread = kTileEdges / (kFillWarps * 32);
-static_assert(kTileEdges % (kFillWarps * 32) == 0 && kFillPerThread == 32, "32 staged edges per thread");
+static_assert(kTileEdges % (kFillWarps * 32) == 0 && kFillPerThread == 32,
+              "32 staged edges per thread: four 16-byte words of 2-byte row marks");
 static_assert(PCPM_MAX_PART_SIZE <= 32768, "local IDs must fit 15 bits");
 
 size_t fill_smem_bytes(uint32_t k, bool weighted) {
@@ -369,13 +370,30 @@ __device__ TileSpan stage_tile(const uint32_t* __restrict__ row_ptr, const uint3
     }
     __syncthreads();
     {
-        const uint32_t i0 = tid * kFillPerThread;
+        // a thread's 32 consecutive marks as four 16-byte words (scalar 2-byte
+        // accesses at a 64-byte stride would hit two banks per warp)
+        uint4* mine = reinterpret_cast<uint4*>(rowof + tid * kFillPerThread);
+        uint4 w[4];
         uint32_t mx = 0;
-        for (uint32_t j = 0; j < kFillPerThread; ++j) mx = max(mx, (uint32_t)rowof[i0 + j]);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            w[c] = mine[c];
+            mx = max(mx, max(max(max(w[c].x & 0xFFFFu, w[c].x >> 16), max(w[c].y & 0xFFFFu, w[c].y >> 16)),
+                             max(max(w[c].z & 0xFFFFu, w[c].z >> 16), max(w[c].w & 0xFFFFu, w[c].w >> 16))));
+        }
         uint32_t run = block_exclusive_max(mx, sh32);
-        for (uint32_t j = 0; j < kFillPerThread; ++j) {
-            run = max(run, (uint32_t)rowof[i0 + j]);
-            rowof[i0 + j] = (uint16_t)run;
+        auto carry2 = [&run](uint32_t x) {  // two marks, low half first
+            const uint32_t lo = run = max(run, x & 0xFFFFu);
+            const uint32_t hi = run = max(run, x >> 16);
+            return lo | (hi << 16);
+        };
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            w[c].x = carry2(w[c].x);
+            w[c].y = carry2(w[c].y);
+            w[c].z = carry2(w[c].z);
+            w[c].w = carry2(w[c].w);
+            mine[c] = w[c];
         }
     }
     __syncthreads();
