@@ -66,6 +66,7 @@ def parse_args():
                     help="also solve 256 RMAT graphs of scales 10-18 with one captured CUDA graph launch")
     ap.add_argument("--ppr", action="store_true",
                     help="also run batched personalized PageRank: RMAT s22, 64 teleport columns, 20 iterations")
+    ap.add_argument("--ppr-scale", type=int, default=22, help="RMAT scale of the --ppr leg (22: the batched workload)")
     ap.add_argument("--mode", choices=("fused", "two_phase"), default="two_phase",
                     help="iteration form timed for `value` (the other is reported in other_mode)")
     ap.add_argument("--ref-budget-s", type=float, default=120.0, help="reference arm: timed seconds target")
@@ -333,14 +334,14 @@ def spmv_leg(a, rp, col, m):
 
 
 def ppr_leg(a, iters: int = 20):
-    """Batched personalized PageRank (pcpm_ppr_*): RMAT scale 22 (random labels,
+    """Batched personalized PageRank (pcpm_ppr_*): RMAT scale 22 (--ppr-scale; random labels,
     q = 32768), 64 teleport columns each uniform over 1-1000 random seed nodes,
     `iters` iterations from R = T, timed with CUDA events on the stream. Against
     it: the same graph's single-vector PageRank iteration, times 64."""
     import torch
     import graphgen
     import paper_1709_07122_gb300 as pcpm
-    rp, col = graphgen.rmat(22, a.edge_factor, 0.57, 0.19, 0.19, seed=a.seed + 22, relabel="random")
+    rp, col = graphgen.rmat(a.ppr_scale, a.edge_factor, 0.57, 0.19, 0.19, seed=a.seed + 22, relabel="random")
     n, m = rp.size - 1, int(rp[-1])
     rng = np.random.default_rng(a.seed + 23)
     ptr, idx = [0], []
@@ -376,7 +377,8 @@ def ppr_leg(a, iters: int = 20):
     # rows read once, entry index, R_old read, R' written
     alg = n * row + ne * row + 4 * ne + 4 * (n + 1) + ne * row + 4 * m + 4 * (n + 1) + 2 * n * row
     peak, src = measured_peaks()
-    return {"workload": "rmat-s22-ef%g-random-labels-q32768, 64 teleport columns (1-1000 seeds each)" % a.edge_factor,
+    return {"workload": "rmat-s%d-ef%g-random-labels-q32768, 64 teleport columns (1-1000 seeds each)"
+                        % (a.ppr_scale, a.edge_factor),
             "n": n, "m": m, "num_updates": ne, "iters": iters, "ms_per_iter": ms,
             "gteps_x64": m * pcpm.PPR_COLS / (ms * 1e-3) / 1e9,
             "single_vector_ms_per_iter": single,

@@ -263,19 +263,21 @@ __global__ void __launch_bounds__(kPprThreads) ppr_gather_kernel(
             e0 = colptr[v + 2];
             prefetch(v + 1, b0, e0);
         }
-        // rows of v: the first 16 indices are in tv, the rest are loaded here
+        // rows of v: the first 16 indices are in tv; each later chunk's
+        // indices load while the previous chunk's rows are in flight
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
         const uint32_t nb = live ? (e - b + 15) / 16 : 0u;
         const uint32_t nbmax = max(nb, __shfl_xor_sync(kAll, nb, 16));
+        uint32_t tc = tv;
         for (uint32_t it = 0; it < nbmax; ++it) {
             const uint32_t c0 = b + 16 * it;
-            const uint32_t tc = it == 0 ? tv : (live && c0 + hl < e ? uidx[c0 + hl] : 0u);
             float4 x[16];
 #pragma unroll
             for (uint32_t i = 0; i < 16; ++i) {
                 const uint32_t t = __shfl_sync(kAll, tc, i, 16);
                 x[i] = (live && c0 + i < e) ? ld4(upd + (size_t)t * kCols + 4 * hl) : make_float4(0.f, 0.f, 0.f, 0.f);
             }
+            tc = (live && c0 + 16 + hl < e) ? uidx[c0 + 16 + hl] : 0u;
 #pragma unroll
             for (uint32_t i = 0; i < 16; ++i) acc = add4(acc, x[i]);
         }
