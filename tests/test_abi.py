@@ -72,6 +72,27 @@ def test_invalid_arguments_rejected_before_any_launch(L):
     assert L.pcpm_pagerank_host(rp, col, 4, 4, 2, 0.85, 5, 0.0, 0x80, out, None, None) == -1
 
 
+def test_ppr_autotune_and_pool_entries_check_arguments_on_the_host(L):
+    h = ctypes.c_void_p()
+    ptr = (ctypes.c_uint32 * 65)(*range(65))
+    idx = (ctypes.c_uint32 * 64)(*range(64))
+    assert L.pcpm_ppr_create(None, ptr, idx, None, ctypes.byref(h)) == -1
+    assert L.pcpm_ppr_run(None, 0.85, 1, None) == -1
+    assert L.pcpm_ppr_residuals(None, None, 0) == -1
+    assert L.pcpm_ppr_ranks(None, None, None) == -1
+    assert L.pcpm_ppr_info(None, None, None) == -1
+    L.pcpm_ppr_free(None)  # null-safe
+    sizes = (ctypes.c_uint32 * 2)(1024, 4096)
+    best = ctypes.c_uint32(0)
+    dev = ctypes.c_void_p(16)
+    assert L.pcpm_autotune(dev, dev, 10, 0, sizes, 0, 0.85, 1, 1, 0, None, ctypes.byref(best), None) == -1  # no candidates
+    assert L.pcpm_autotune(dev, dev, 10, 0, sizes, 2, 0.85, 1, 0, 0, None, ctypes.byref(best), None) == -1  # iters = 0
+    assert L.pcpm_autotune(dev, dev, 10, 0, sizes, 2, 1.5, 1, 1, 0, None, ctypes.byref(best), None) == -1  # bad d
+    assert L.pcpm_autotune(dev, dev, 10, 0, sizes, 2, 0.85, 1, 1, 0x80, None, ctypes.byref(best), None) == -1  # flags
+    assert L.pcpm_autotune(dev, dev, 10, 0, None, 2, 0.85, 1, 1, 0, None, ctypes.byref(best), None) == -1
+    assert L.pcpm_release_cached_memory() == 0  # no pool was created in this process
+
+
 def test_binding_fails_loudly_without_library(tmp_path):
     saved = pcpm._lib
     try:
