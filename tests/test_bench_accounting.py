@@ -1,0 +1,57 @@
+"""The benchmark's algorithmic bytes (the numerator of every roofline
+fraction) against the per-kernel formulas stated with the kernels, on the
+RMAT s24 benchmark graph's sizes, and the paper's Eq. 5 model."""
+import importlib.util
+import os
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+# RMAT scale 24, edge factor 16, random labels, q = 32768
+S24 = {"n": 16_777_216, "num_edges": 263_434_146, "num_updates": 149_444_304, "num_partitions": 512}
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench_module", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_two_phase_bytes_per_kernel(bench):
+    n, m, ne, k = S24["n"], S24["num_edges"], S24["num_updates"], S24["num_partitions"]
+    b = bench.algorithmic_bytes(S24, mode="two_phase")
+    # gather + apply: destination IDs, updates, chunk bases, bin starts, hubs; PR_old, 1/outdeg, PR'
+    assert b["gather_apply"] == 4 * m + 4 * ne + 4 * ((m + 255) // 256) + 8 * (k + 1) + 8 * k + 12 * n
+    assert b["gather_apply"] == 1_856_964_752  # the figure the bench line reports
+    # scatter: srcIdx read and update write, segment table, SPR staging (PR and 1/outdeg)
+    assert b["scatter"] == 8 * ne + 8 * k * k + 8 * n == 1_331_869_312
+    assert b["reduce"] == 16 * k
+
+
+def test_fused_form_drops_the_spr_staging(bench):
+    two = bench.algorithmic_bytes(S24, mode="two_phase")
+    fused = bench.algorithmic_bytes(S24, mode="fused")
+    assert fused["scatter"] == 0
+    assert fused["gather_apply"] == two["gather_apply"] + two["scatter"] - 8 * S24["n"]
+    per_edge = sum(fused.values()) / S24["num_edges"]
+    assert 11.5 < per_edge < 11.7  # about 4 + 12/r + 12n/m with r = 1.76, m/n = 15.7
+
+
+def test_sixteen_bit_bins_save_two_bytes_per_update_each_way(bench):
+    info16 = dict(S24, update_bytes=2)
+    a = bench.algorithmic_bytes(S24, mode="two_phase")
+    b = bench.algorithmic_bytes(info16, mode="two_phase")
+    assert a["gather_apply"] - b["gather_apply"] == 2 * S24["num_updates"]
+    assert a["scatter"] - b["scatter"] == 2 * S24["num_updates"]
+
+
+def test_eq5_model(bench):
+    # Eq. 5 with d_i = d_v = 4: m (4 (1 + 1/r) + 8/r) + 4 k^2 + 8 n
+    m, ne = S24["num_edges"], S24["num_updates"]
+    r = m / ne
+    want = m * (4 * (1 + 1 / r) + 8 / r) + 4 * 512 * 512 + 8 * S24["n"]
+    assert bench.eq5_bytes(S24) == pytest.approx(want)
+    assert 11.2 < bench.eq5_bytes(S24) / m < 11.4
