@@ -387,13 +387,21 @@ def pagerank_host(row_ptr: np.ndarray, col: np.ndarray, part_size: int, d: float
 def rank_stats_noalloc(x, y, row_ptr, out=None, stream=None):
     """(L1 change between x and y, dangling mass of x) in FP64 through the
     allocation-free entry point. x, y: CUDA float32 [n]; row_ptr: CUDA 32-bit
-    integer [n+1]; out: CUDA float64 [2] (allocated here by torch if None)."""
+    integer [n+1]; out: CUDA float64 [2].
+
+    The entry point itself allocates nothing. With out=None this wrapper
+    allocates the result through torch, so a caller that must not allocate
+    (inside an allocator callback, or with all device memory reserved up
+    front) passes a preallocated `out`."""
     import torch
     n = row_ptr.numel() - 1
     _f32_dev(x, n)
     _f32_dev(y, n)
     if out is None:
         out = torch.empty(2, dtype=torch.float64, device="cuda")
+    elif not (isinstance(out, torch.Tensor) and out.is_cuda and out.dtype == torch.float64
+              and out.is_contiguous() and out.numel() >= 2):
+        raise TypeError("out: expected a contiguous CUDA float64 tensor of at least 2 elements")
     _check(lib().pcpm_rank_stats_noalloc(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
                                          _dev_u32(row_ptr), n, ctypes.c_void_p(out.data_ptr()), _stream(stream)),
            "pcpm_rank_stats_noalloc")

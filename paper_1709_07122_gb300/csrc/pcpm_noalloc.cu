@@ -91,18 +91,41 @@ double* g_partials_addr[kMaxDevices] = {};
 // once per device (the symbol's host-side name is not a device address).
 int partials_address(double** out) {
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PCPM_ECUDA;
+    if (const cudaError_t e = cudaGetDevice(&dev); e != cudaSuccess) {
+        note_cuda_error(e);
+        return PCPM_ECUDA;
+    }
+    if (dev < 0 || dev >= kMaxDevices) {
+        note_cuda_error(cudaErrorInvalidDevice);
+        return PCPM_ECUDA;
+    }
     std::lock_guard<std::mutex> lock(g_setup_mutex);
     if (!g_partials_addr[dev]) {
         void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_partials) != cudaSuccess || !p) {
-            cudaGetLastError();
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+        if (e != cudaSuccess || !p) {
+            note_cuda_error(e != cudaSuccess ? e : cudaErrorInvalidSymbol);
             return PCPM_ECUDA;
         }
         g_partials_addr[dev] = static_cast<double*>(p);
     }
     *out = g_partials_addr[dev];
     return PCPM_OK;
+}
+
+// Launches f<<<blocks, kNoAllocThreads, 0, s>>>(args...) and returns this
+// launch's own status: an error some earlier call left pending is neither
+// cleared nor blamed on this one.
+template <class... Params, class... Args>
+int launch(void (*f)(Params...), unsigned blocks, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(kNoAllocThreads);
+    cfg.stream = s;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, f, args...);
+    if (e == cudaSuccess) return PCPM_OK;
+    note_cuda_error(e);
+    return PCPM_ECUDA;
 }
 
 }  // namespace
@@ -114,10 +137,10 @@ extern "C" int pcpm_rank_stats_noalloc(const float* x, const float* y, const uin
     const uint64_t blocks = ((uint64_t)n + pcpm::kNoAllocNodesPerBlock - 1) / pcpm::kNoAllocNodesPerBlock;
     if (blocks > PCPM_NOALLOC_MAX_BLOCKS) return PCPM_ESCRATCH;
     double* partials = nullptr;
-    const int rc = pcpm::partials_address(&partials);
+    int rc = pcpm::partials_address(&partials);
     if (rc != PCPM_OK) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    pcpm::stats_partials_kernel<<<(unsigned)blocks, pcpm::kNoAllocThreads, 0, s>>>(x, y, row_ptr, n, partials);
-    pcpm::stats_final_kernel<<<1, pcpm::kNoAllocThreads, 0, s>>>(partials, (int)blocks, out);
-    return cudaGetLastError() == cudaSuccess ? PCPM_OK : PCPM_ECUDA;
+    rc = pcpm::launch(pcpm::stats_partials_kernel, (unsigned)blocks, s, x, y, row_ptr, n, partials);
+    if (rc != PCPM_OK) return rc;
+    return pcpm::launch(pcpm::stats_final_kernel, 1u, s, (const double*)partials, (int)blocks, out);
 }
