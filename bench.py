@@ -69,6 +69,9 @@ def parse_args():
     ap.add_argument("--ppr-scale", type=int, default=22, help="RMAT scale of the --ppr leg (22: the batched workload)")
     ap.add_argument("--mode", choices=("fused", "two_phase"), default="two_phase",
                     help="iteration form timed for `value` (the other is reported in other_mode)")
+    ap.add_argument("--gather-layout", choices=("windows", "chunks"), default="windows",
+                    help="gather copy of the IDs: owner windows without atomics (default) or 256-ID chunks with "
+                         "shared-memory atomics")
     ap.add_argument("--ref-budget-s", type=float, default=120.0, help="reference arm: timed seconds target")
     return ap.parse_args()
 
@@ -86,6 +89,11 @@ def make_graph(a):
     if a.graph == "rmat":
         return graphgen.rmat(a.scale, a.edge_factor, 0.57, 0.19, 0.19, seed=a.seed, relabel=a.labels)
     return graphgen.erdos_renyi(1 << a.scale, a.edge_factor, seed=a.seed, relabel=a.labels)
+
+
+def layout_option(a):
+    """The build option gather_windows for --gather-layout."""
+    return 2 if a.gather_layout == "chunks" else 0
 
 
 def dist_env():
@@ -194,8 +202,12 @@ def algorithmic_bytes(info, mode="fused"):
     updates of info["update_bytes"], 4 unless the bins are 16-bit)."""
     n, m, ne, k = info["n"], info["num_edges"], info["num_updates"], info["num_partitions"]
     ub = info.get("update_bytes", 4)
-    nchunks = -(-m // 256)
-    gather = 4 * m + ub * ne + 4 * nchunks + 8 * (k + 1) + 8 * k  # destIDs, updates, chunk bases, bins, hubs
+    if info.get("gather_windows"):
+        # destIDs, updates, window headers (64 B) and descriptors (16 B), bins, hubs
+        gather = 4 * m + ub * ne + 80 * info["num_windows"] + 8 * (k + 1) + 4 * 8 * k
+    else:
+        nchunks = -(-m // 256)
+        gather = 4 * m + ub * ne + 4 * nchunks + 8 * (k + 1) + 8 * k  # destIDs, updates, chunk bases, bins, hubs
     apply = 12 * n  # PR_old and 1/outdeg read, PR' written
     scatter = (4 + ub) * ne + 8 * k * k  # srcIdx read + update write, segment starts/counts
     if mode == "fused":
@@ -502,7 +514,7 @@ def run_ours(a):
     d_rp, d_col = pcpm.to_device_csr(rp, col)
     torch.cuda.synchronize()
     b0 = time.perf_counter()
-    g = pcpm.PNG(d_rp, d_col, a.part_size)
+    g = pcpm.PNG(d_rp, d_col, a.part_size, gather_windows=layout_option(a))
     build_ms = (time.perf_counter() - b0) * 1e3
     del d_rp, d_col
     info = g.info
@@ -565,6 +577,7 @@ def run_ours(a):
                    "num_updates": info["num_updates"], "r": info["compression_ratio"], "d": a.d,
                    "gather_units": info["gather_units"], "gather_cluster": info["gather_cluster"],
                    "gather_runs": info["gather_runs"], "merged_adds": info["merged_adds"],
+                   "gather_layout": a.gather_layout, "num_windows": info["num_windows"],
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "no flush: each iteration moves ~%.2f GB, > 129 MB L2" % (iter_bytes / 1e9)},
         "roofline": roofline,
@@ -616,7 +629,7 @@ def run_ours(a):
         d_rp, d_col = pcpm.to_device_csr(rp, col)
         dts = {}
         for dt_name in ("f32", "f16", "bf16"):
-            gu = pcpm.PNG(d_rp, d_col, a.part_size, update_dtype=dt_name)
+            gu = pcpm.PNG(d_rp, d_col, a.part_size, update_dtype=dt_name, gather_windows=layout_option(a))
             iu = gu.info
             gu.reset()
             gu.iterate(a.d, 1, mode=a.mode)

@@ -114,10 +114,13 @@ typedef struct pcpm_png_info {
     uint32_t canonical_gather; /* 1 if the gather decodes the canonical bins */
     uint32_t gather_runs;     /* 1 if the gather sums runs of IDs with the same destination in a
                                  register before one shared-memory add */
-    uint64_t merged_adds;     /* IDs of the bank-spread layout whose value joins the next ID's
-                                 (same destination, same lane): adds saved by gather_runs */
+    uint64_t merged_adds;     /* IDs of the gather layout whose value joins the next ID's (same
+                                 destination, same lane): shared-memory adds saved by register runs */
     uint32_t update_dtype;    /* PCPM_UPDATE_* of the update bins */
     uint32_t update_bytes;    /* bytes per update: 4 or 2 */
+    uint32_t gather_windows;  /* 1 if the gather reads the window layout */
+    uint32_t reserved2;
+    uint64_t num_windows;     /* windows of the window layout */
 } pcpm_png_info;
 
 /* Tuning of the work decomposition; zero fields take the automatic choice.
@@ -134,8 +137,13 @@ typedef struct pcpm_build_options {
                                      register before one shared-memory add, 2 adds every ID, 0 picks
                                      1 when at least m/16 IDs join a run */
     uint32_t update_dtype;        /* PCPM_UPDATE_F32 (0, default), PCPM_UPDATE_F16 or
-                                     PCPM_UPDATE_BF16; 16-bit types need the bank-spread layout
+                                     PCPM_UPDATE_BF16; 16-bit types need a gather copy of the IDs
                                      (canonical_gather = 0) */
+    uint32_t gather_windows;      /* gather copy of the IDs (canonical_gather = 0): 0 or 1 the window
+                                     layout, where every warp of a CTA owns a disjoint set of
+                                     destinations and adds without atomics (4096-ID windows shared
+                                     by the CTA); 2 the bank-spread layout of 256-ID chunks per warp
+                                     with shared-memory atomics */
 } pcpm_build_options;
 
 /* Builds the Partition-Node Graph of Sec. 3.3 from a CSR out-adjacency:
@@ -164,8 +172,9 @@ int pcpm_build(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t n, uin
                uint32_t part_size, void* stream, pcpm_png** out);
 
 /* pcpm_build with tuning options (host struct, nullable = all automatic).
- * PCPM_EINVAL if gather_cluster is not 0, 1, 2, 4 or 8, gather_runs is above 2, update_dtype
- * is not a PCPM_UPDATE_* value, or a 16-bit update_dtype comes with canonical_gather. */
+ * PCPM_EINVAL if gather_cluster is not 0, 1, 2, 4 or 8, gather_runs or gather_windows is above
+ * 2, update_dtype is not a PCPM_UPDATE_* value, a 16-bit update_dtype comes with
+ * canonical_gather, or gather_windows = 1 comes with canonical_gather. */
 int pcpm_build_ex(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t n, uint64_t m,
                   uint32_t part_size, const pcpm_build_options* options, void* stream,
                   pcpm_png** out);

@@ -47,13 +47,16 @@ class _Info(ctypes.Structure):
                 ("scatter_units", ctypes.c_uint32), ("gather_cluster", ctypes.c_uint32),
                 ("fused_ok", ctypes.c_uint32), ("canonical_gather", ctypes.c_uint32),
                 ("gather_runs", ctypes.c_uint32), ("merged_adds", ctypes.c_uint64),
-                ("update_dtype", ctypes.c_uint32), ("update_bytes", ctypes.c_uint32)]
+                ("update_dtype", ctypes.c_uint32), ("update_bytes", ctypes.c_uint32),
+                ("gather_windows", ctypes.c_uint32), ("reserved2", ctypes.c_uint32),
+                ("num_windows", ctypes.c_uint64)]
 
 
 class _Options(ctypes.Structure):
     _fields_ = [("gather_unit_chunks", ctypes.c_uint32), ("scatter_unit_groups", ctypes.c_uint32),
                 ("gather_cluster", ctypes.c_uint32), ("canonical_gather", ctypes.c_uint32),
-                ("gather_runs", ctypes.c_uint32), ("update_dtype", ctypes.c_uint32)]
+                ("gather_runs", ctypes.c_uint32), ("update_dtype", ctypes.c_uint32),
+                ("gather_windows", ctypes.c_uint32)]
 
 # Storage of the update bins (PCPM_UPDATE_* in pcpm.h).
 UPDATE_DTYPES = {"f32": 0, "f16": 1, "bf16": 2}

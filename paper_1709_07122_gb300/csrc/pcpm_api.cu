@@ -106,7 +106,8 @@ void release(pcpm_png* g) {
                     g->chunk_base, g->hubs, g->gdest, g->gslice_start, g->gslice_bytes, g->ichunk_start,
                     g->gunits, g->gorder, g->sunits, g->sorder, g->gacc,
                     g->bin_done, g->inv_deg, g->pr[0], g->pr[1], g->upd[0], g->upd[1], g->partials,
-                    g->hist, g->state, g->wdest, g->gweight};
+                    g->hist, g->state, g->wdest, g->gweight, g->win_start, g->wwords, g->wweight, g->wdesc,
+                    g->whubs};
     // the caller has waited for every use of the handle's memory
     for (void* p : ptrs) pool_free(p, g->last_stream);
     if (g->state_host) cudaFreeHost(g->state_host);
@@ -293,7 +294,8 @@ int build_impl(const uint32_t* row_ptr, const uint32_t* col_idx, const float* we
     if (opt.gather_cluster != 0 && opt.gather_cluster != 1 && opt.gather_cluster != 2 && opt.gather_cluster != 4 &&
         opt.gather_cluster != 8)
         return PCPM_EINVAL;
-    if (opt.gather_runs > 2) return PCPM_EINVAL;
+    if (opt.gather_runs > 2 || opt.gather_windows > 2) return PCPM_EINVAL;
+    if (opt.gather_windows == 1 && opt.canonical_gather) return PCPM_EINVAL;
     if (opt.update_dtype > PCPM_UPDATE_BF16) return PCPM_EINVAL;
     if (opt.update_dtype != PCPM_UPDATE_F32 && opt.canonical_gather) return PCPM_EINVAL;
     if (m > 0xFFFFFF00ull) return PCPM_EINVAL;
@@ -570,6 +572,8 @@ int pcpm_png_get_info(const pcpm_png* g, pcpm_png_info* info) {
     info->merged_adds = g->merged_adds;
     info->update_dtype = (uint32_t)g->upd_dtype;
     info->update_bytes = g->upd_bytes;
+    info->gather_windows = (uint32_t)g->gather_windows;
+    info->num_windows = g->nwin;
     return PCPM_OK;
 }
 

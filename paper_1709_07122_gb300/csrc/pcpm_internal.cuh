@@ -46,6 +46,35 @@ static_assert(kUpdSlot <= kGwUpdMask + 1 && kChunk + 16 <= kGwUpdMask + 1, "upda
 constexpr int kGatherWarps = 24;
 constexpr int kGatherStages = 2;
 constexpr uint32_t kHubSlots = 2 * kGatherWarps;
+// Gather, window layout (the default): a bin's destination IDs are cut into
+// windows of at most kWin consecutive IDs (whole windows of one bin per work
+// unit). The window's update slice and its IDs reach shared memory by bulk
+// copies into a ring that all kWinWarps consumer warps of the CTA share. Each
+// consumer warp owns a set of accumulator slots: blocks of 32 consecutive
+// nodes, dealt to warps as contiguous ranges balanced by in-degree, and a
+// private slot for each of the bin's kWinHubs largest in-degree nodes (whose
+// IDs are dealt to all warps in turn). A window's IDs are grouped by owner
+// warp, so no two warps ever add into one slot and the adds need no atomics.
+// Inside a group, IDs are sorted by (bank, slot, position) and dealt lane by
+// lane: lane l takes a contiguous run of sorted positions, so equal slots sit
+// in one lane (or in consecutive lanes, joined by a shuffle scan), and the
+// lanes of one round hit rising banks. Each 32-bit word holds the slot (16
+// bits), the offset of its update in the window's slice (13 bits) and an end
+// bit (the next sorted ID of the group has another slot). A window starts
+// with a header of kWinHdrWords words: the kWinWarps + 1 group offsets as
+// 16-bit values.
+constexpr uint32_t kWin = 4096;
+constexpr int kWinWarps = 16;
+constexpr uint32_t kWinHubs = 8;
+constexpr uint32_t kWinHdrWords = 16;
+constexpr uint32_t kWinStride = kWinHdrWords + kWin;  // words per window in the layout array
+constexpr uint32_t kWinSlotMask = 0xFFFFu;
+constexpr uint32_t kWinOffShift = 16;
+constexpr uint32_t kWinOffMask = 0x1FFFu;
+constexpr uint32_t kWinEndBit = 1u << 29;
+static_assert(kWinWarps + 1 <= 2 * kWinHdrWords, "the header holds the group offsets as 16-bit values");
+static_assert(kWin + 16 <= kWinOffMask + 1, "update offsets of a window must fit their field");
+static_assert(PCPM_MAX_PART_SIZE + kWinWarps * kWinHubs <= kWinSlotMask + 1, "slots must fit their field");
 // Update bin storage: PCPM_UPDATE_F32, _F16 (SPR * 2^15), _BF16.
 constexpr int kUpdF32 = (int)PCPM_UPDATE_F32, kUpdF16 = (int)PCPM_UPDATE_F16, kUpdBF16 = (int)PCPM_UPDATE_BF16;
 constexpr float kF16Scale = (float)(1 << PCPM_F16_SCALE_LOG2);
@@ -113,6 +142,17 @@ struct pcpm_png {
     float* gweight;          // nichunks * kChunk: weights in the bank-spread layout's order
     uint32_t upd_bytes;      // 4 or 2
     uint64_t merged_adds;    // IDs with bit 30 set
+    // Window layout (gather_windows = 1), see kWin: nwin windows, bin p's
+    // windows [win_start[p], win_start[p+1]); window w's header and words at
+    // wwords + w * kWinStride; wdesc[w] = (first update of its slice, slice
+    // bytes, bytes of header + words to copy, IDs).
+    int gather_windows;
+    uint64_t nwin;
+    uint32_t* win_start;     // k+1
+    uint32_t* wwords;        // nwin * kWinStride
+    float* wweight;          // weighted graphs: weights at their IDs' word positions
+    uint4* wdesc;            // nwin
+    uint32_t* whubs;         // k * kWinHubs: local IDs of each bin's hubs (or kNoHub)
     uint32_t* gdest;         // nichunks * kChunk words
     uint32_t* gslice_start;  // nichunks: first update of the chunk's slice (multiple of 4)
     uint32_t* gslice_bytes;  // nichunks: bytes of the slice (multiple of 16)

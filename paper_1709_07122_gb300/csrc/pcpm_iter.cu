@@ -71,6 +71,10 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
                  : "memory");
@@ -604,6 +608,11 @@ struct GatherArgs {
     uint32_t* bin_done;
     const void* upd_in;
     const float* gweight;  // weighted gather (kW): weights in the layout's order
+    // window layout
+    const uint32_t* wwords;
+    const float* wweight;
+    const uint4* wdesc;
+    const uint32_t* whubs;
     const float* pr_in;
     const float* inv_deg;
     float* pr_out;
@@ -639,6 +648,261 @@ struct Ring {
 // The block sum after the apply borrows the ring's last bytes (idle by then;
 // pushed partial sums stay below them).
 constexpr size_t kSumScratchBytes = 2 * kGatherWarps * sizeof(double);
+
+// After the accumulation: merge the S CTAs' partial sums of the partition
+// over distributed shared memory, apply PR' = (1-d)/n + d*(acc + D/n), write
+// the FP64 (L1 change, dangling mass) partials and, in the fused form, scatter
+// the partition's SPR' for the next iteration. `ring` (ring_bytes) is idle
+// shared memory for the merge and the block sum; the fused scatter takes
+// 2 * kThreads / 32 mbarriers at `sbars` and its tables and stages from
+// `sarea` (sarea_bytes), both inside idle memory.
+template <bool kFused, int kUpd, int kThreads>
+__device__ __forceinline__ void gather_finish(const GatherArgs& a, unsigned char* ring, size_t ring_bytes,
+                                              uint64_t* sbars, unsigned char* sarea, size_t sarea_bytes, float* acc,
+                                              uint32_t* sh32, uint32_t S, uint32_t rank, uint32_t pd,
+                                              uint32_t npieces, uint32_t vbase, uint32_t len) {
+    using U = Upd<kUpd>;
+    constexpr size_t kSumScratch = 2 * (kThreads / 32) * sizeof(double);
+    cluster_sync();  // every CTA of the cluster has finished its accumulator
+
+    // This CTA owns nodes [lo, hi) of the partition (multiples of 4). The
+    // other CTAs push their partial sums for that range into this CTA's ring
+    // memory, idle now, so the merge below reads local shared memory only.
+    const uint32_t per = (((len + S - 1) / S) + 3) & ~3u;
+    const uint32_t lo = min(len, rank * per), hi = min(len, lo + per);
+    float* stage = reinterpret_cast<float*>(ring);
+    const bool push = (size_t)(S - 1) * per * sizeof(float) <= ring_bytes - kSumScratch;
+    if (push && S > 1) {
+        for (uint32_t t = 0; t < S; ++t) {
+            if (t == rank) continue;
+            const uint32_t tlo = min(len, t * per), thi = min(len, tlo + per);
+            push_range(acc + tlo, stage + (size_t)(rank < t ? rank : rank - 1) * per, thi - tlo, t);
+        }
+        cluster_sync();
+    }
+    // Sum of the S partial sums of node i in [lo, hi), in a fixed order.
+    auto merged = [&](uint32_t i) -> float {
+        float s = 0.0f;
+        if (push) {
+            s = acc[i];
+            for (uint32_t q = 0; q + 1 < S; ++q) s += stage[(size_t)q * per + (i - lo)];
+        } else {
+            for (uint32_t r = 0; r < S; ++r) s += ld_cluster_f32(map_rank(acc + i, r));
+        }
+        return s;
+    };
+    // The same for nodes i .. i+3 (i - lo a multiple of 4).
+    auto merged4 = [&](uint32_t i) -> float4 {
+        if (!push) return make_float4(merged(i), merged(i + 1), merged(i + 2), merged(i + 3));
+        float4 s = *reinterpret_cast<const float4*>(acc + i);
+        for (uint32_t q = 0; q + 1 < S; ++q) {
+            const float4 t = *reinterpret_cast<const float4*>(stage + (size_t)q * per + (i - lo));
+            s.x += t.x;
+            s.y += t.y;
+            s.z += t.z;
+            s.w += t.w;
+        }
+        return s;
+    };
+
+    const double D = a.uniform_dangling ? a.st->dangling : 0.0;
+    const float cst = (float)((1.0 - (double)a.d) / (double)a.n + (double)a.d * D / (double)a.n);
+    const float d_acc = a.d * U::acc_scale;  // exact: the scale is a power of two
+    // Per-thread partial sums of at most len / blockDim terms in FP32 (FP64
+    // arithmetic is slow on this part); thread and block totals in FP64.
+    float res_f = 0.0f, dg_f = 0.0f;
+    // Apply to one node: PR', residual and dangling terms, SPR' for the fused scatter.
+    auto apply1 = [&](uint32_t i, float s, float old, float inv) -> float {
+        const float x = fmaf(d_acc, s, cst);
+        if (kFused) acc[i] = x * inv;
+        res_f += fabsf(x - old);
+        if (inv == 0.0f) dg_f += x;
+        return x;
+    };
+    // Nodes [lo, vec_end) go four at a time with 16-byte loads and stores
+    // (the partition starts on a 16-byte boundary), kApplyVec groups of
+    // four in flight per thread; the rest one at a time.
+    const uint32_t vec_end = (npieces == 1 && (vbase & 3u) == 0) ? lo + ((hi - lo) & ~3u) : lo;
+    for (uint32_t i0 = lo + 4 * threadIdx.x; i0 < vec_end; i0 += 4 * kApplyVec * blockDim.x) {
+        float4 o[kApplyVec], w[kApplyVec], s[kApplyVec];
+#pragma unroll
+        for (int j = 0; j < kApplyVec; ++j) {
+            const uint32_t i = i0 + 4 * j * blockDim.x;
+            if (i < vec_end) {
+                o[j] = __ldg(reinterpret_cast<const float4*>(a.pr_in + vbase + i));
+                w[j] = __ldg(reinterpret_cast<const float4*>(a.inv_deg + vbase + i));
+                s[j] = merged4(i);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kApplyVec; ++j) {
+            const uint32_t i = i0 + 4 * j * blockDim.x;
+            if (i < vec_end) {
+                float4 x;
+                x.x = apply1(i, s[j].x, o[j].x, w[j].x);
+                x.y = apply1(i + 1, s[j].y, o[j].y, w[j].y);
+                x.z = apply1(i + 2, s[j].z, o[j].z, w[j].z);
+                x.w = apply1(i + 3, s[j].w, o[j].w, w[j].w);
+                *reinterpret_cast<float4*>(a.pr_out + vbase + i) = x;
+            }
+        }
+    }
+    if (npieces == 1) {
+        // The remaining nodes: kApplyIlp independent nodes per thread per
+        // round, their loads in flight together.
+        for (uint32_t i0 = vec_end + threadIdx.x; i0 < hi; i0 += kApplyIlp * blockDim.x) {
+            float s[kApplyIlp], old[kApplyIlp], inv[kApplyIlp];
+#pragma unroll
+            for (int j = 0; j < kApplyIlp; ++j) {
+                const uint32_t i = i0 + j * blockDim.x;
+                s[j] = 0.0f;
+                old[j] = 0.0f;
+                inv[j] = 1.0f;
+                if (i < hi) {
+                    old[j] = a.pr_in[vbase + i];
+                    inv[j] = a.inv_deg[vbase + i];
+                    s[j] = merged(i);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < kApplyIlp; ++j) {
+                const uint32_t i = i0 + j * blockDim.x;
+                if (i < hi) a.pr_out[vbase + i] = apply1(i, s[j], old[j], inv[j]);
+            }
+        }
+    } else {
+        // The bin is cut into several units: add this unit's sums to the
+        // global partial sums; the last CTA to arrive applies the partition.
+        uint32_t& last = sh32[0];
+        const bool aligned = (vbase & 3u) == 0;
+        const uint32_t gv_end = aligned ? lo + ((hi - lo) & ~3u) : lo;
+        for (uint32_t i = lo + 4 * threadIdx.x; i < gv_end; i += 4 * blockDim.x) {
+            const float4 s = merged4(i);
+            if (s.x != 0.0f || s.y != 0.0f || s.z != 0.0f || s.w != 0.0f) red_add_v4(a.gacc + vbase + i, s);
+        }
+        for (uint32_t i = gv_end + threadIdx.x; i < hi; i += blockDim.x) {
+            const float s = merged(i);
+            if (s != 0.0f) atomicAdd(&a.gacc[vbase + i], s);
+        }
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) last = atomicAdd(&a.bin_done[pd], 1u) == npieces * S - 1 ? 1u : 0u;
+        __syncthreads();
+        if (last) {
+            __threadfence();
+            // The whole partition from the global sums: four nodes at a time
+            // where the partition starts on a 16-byte boundary, then the rest.
+            const uint32_t av_end = aligned ? (len & ~3u) : 0;
+            for (uint32_t i0 = 4 * threadIdx.x; i0 < av_end; i0 += 4 * kApplyVecCut * blockDim.x) {
+                float4 o[kApplyVecCut], w[kApplyVecCut], s[kApplyVecCut];
+#pragma unroll
+                for (int j = 0; j < kApplyVecCut; ++j) {
+                    const uint32_t i = i0 + 4 * j * blockDim.x;
+                    if (i < av_end) {
+                        s[j] = __ldcg(reinterpret_cast<const float4*>(a.gacc + vbase + i));
+                        o[j] = __ldg(reinterpret_cast<const float4*>(a.pr_in + vbase + i));
+                        w[j] = __ldg(reinterpret_cast<const float4*>(a.inv_deg + vbase + i));
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < kApplyVecCut; ++j) {
+                    const uint32_t i = i0 + 4 * j * blockDim.x;
+                    if (i < av_end) {
+                        float4 x;
+                        x.x = apply1(i, s[j].x, o[j].x, w[j].x);
+                        x.y = apply1(i + 1, s[j].y, o[j].y, w[j].y);
+                        x.z = apply1(i + 2, s[j].z, o[j].z, w[j].z);
+                        x.w = apply1(i + 3, s[j].w, o[j].w, w[j].w);
+                        *reinterpret_cast<float4*>(a.gacc + vbase + i) = make_float4(0.f, 0.f, 0.f, 0.f);
+                        *reinterpret_cast<float4*>(a.pr_out + vbase + i) = x;
+                    }
+                }
+            }
+            for (uint32_t i0 = av_end + threadIdx.x; i0 < len; i0 += kApplyIlp * blockDim.x) {
+                float s[kApplyIlp], old[kApplyIlp], inv[kApplyIlp];
+#pragma unroll
+                for (int j = 0; j < kApplyIlp; ++j) {
+                    const uint32_t i = i0 + j * blockDim.x;
+                    s[j] = 0.0f;
+                    old[j] = 0.0f;
+                    inv[j] = 1.0f;
+                    if (i < len) {
+                        s[j] = __ldcg(&a.gacc[vbase + i]);
+                        old[j] = a.pr_in[vbase + i];
+                        inv[j] = a.inv_deg[vbase + i];
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < kApplyIlp; ++j) {
+                    const uint32_t i = i0 + j * blockDim.x;
+                    if (i < len) {
+                        const float x = fmaf(d_acc, s[j], cst);
+                        a.gacc[vbase + i] = 0.0f;
+                        a.pr_out[vbase + i] = x;
+                        res_f += fabsf(x - old[j]);
+                        if (inv[j] == 0.0f) dg_f += x;
+                    }
+                }
+            }
+            if (threadIdx.x == 0) a.bin_done[pd] = 0;
+        }
+    }
+    double res = (double)res_f, dg = (double)dg_f;
+    block_sum2<kThreads>(res, dg, reinterpret_cast<double*>(ring + ring_bytes - kSumScratch));
+    if (threadIdx.x == 0) {
+        a.partials[2 * blockIdx.x] = res;
+        a.partials[2 * blockIdx.x + 1] = dg;
+    }
+
+    if constexpr (kFused) {
+        if (npieces != 1) {  // the host runs cut bins in two-phase form only
+            if (threadIdx.x == 0) atomicOr(a.err, kErrBounds);
+            cluster_sync();
+            return;
+        }
+        // Fused scatter of the next iteration: assemble SPR' of the whole
+        // partition in every CTA's shared memory (each pushes its range to
+        // the others), then write 1/S of the partition's update segments.
+        __syncthreads();
+        if (push) {
+            for (uint32_t t = 0; t < S; ++t)
+                if (t != rank) push_range(acc + lo, acc + lo, hi - lo, t);
+            cluster_sync();
+        } else {
+            cluster_sync();
+            for (uint32_t r = 0; r < S; ++r) {
+                if (r == rank) continue;
+                const uint32_t rlo = min(len, r * per), rhi = min(len, rlo + per);
+                const uint32_t q4 = (rhi - rlo) >> 2;
+                for (uint32_t i = threadIdx.x; i < q4; i += blockDim.x)
+                    reinterpret_cast<float4*>(acc + rlo)[i] = ld_cluster_f32x4(map_rank(acc + rlo + 4 * i, r));
+                for (uint32_t i = rlo + (q4 << 2) + threadIdx.x; i < rhi; i += blockDim.x)
+                    acc[i] = ld_cluster_f32(map_rank(acc + i, r));
+            }
+            cluster_sync();  // no CTA reads another's shared memory after this point
+        }
+        uint32_t* gpre = reinterpret_cast<uint32_t*>(sarea);
+        const uint32_t* segrow = a.seg_u + (size_t)pd * a.k;
+        const uint32_t* cntrow = a.cnt_u + (size_t)pd * a.k;
+        constexpr int kWarps = kThreads / 32;
+        if (threadIdx.x < 2 * kWarps) mbar_init(&sbars[threadIdx.x], 1);
+        fence_mbar_init();
+        fence_proxy_async_smem();  // the block sum's scratch becomes a bulk-copy target
+        uint32_t* dsh = reinterpret_cast<uint32_t*>(sarea + scatter_gpre_bytes(a.k));
+        uint8_t* emsk = sarea + scatter_gpre_bytes(a.k) + scatter_dsh_bytes(a.k);
+        segment_groups_prefix(segrow, cntrow, a.k, gpre, sh32, dsh, emsk);  // ends with __syncthreads
+        const uint32_t G = gpre[a.k];
+        const uint32_t f_lo = (uint32_t)((uint64_t)G * rank / S);
+        const uint32_t f_hi = (uint32_t)((uint64_t)G * (rank + 1) / S);
+        // stages: the scatter area after the segment table
+        const size_t st_off = scatter_table_bytes(a.k);
+        const uint32_t stage_bytes = (uint32_t)(((sarea_bytes - st_off) / (2 * kWarps)) & ~(size_t)15);
+        scatter_groups_staged<kUpd>(acc, vbase, len, gpre, dsh, emsk, a.k, a.src, a.upd_out, f_lo, f_hi, a.err,
+                                    sarea + st_off, stage_bytes, sbars, [] {});
+    } else {
+        if (!push) cluster_sync();  // remote loads of this CTA's shared memory are done
+    }
+}
 
 // kFused: also scatter the next iteration; kCanon: decode the canonical bins;
 // kRuns: sum run-bit runs of the bank-spread layout in a register; kUpd: the
@@ -904,249 +1168,210 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
         if (h0 < len) atomicAdd(&acc[h0], hub0);
         if (h1 < len) atomicAdd(&acc[h1], hub1);
     }
-    cluster_sync();  // every CTA of the cluster has finished its accumulator
+    static_assert(R::kMeta >= 2 * kGatherWarps * sizeof(uint64_t), "two stage barriers per warp for the fused scatter");
+    static_assert(R::kBytes >= scatter_table_bytes(PCPM_MAX_PARTITIONS) + 2 * kGatherWarps * 16 * 16,
+                  "the fused scatter's stages must hold at least 16 groups beside the largest segment tables");
+    gather_finish<kFused, kUpd, kGatherWarps * 32>(a, ring, R::kBytes, reinterpret_cast<uint64_t*>(meta), ring,
+                                                   R::kBytes, acc, sh32, S, rank, pd, npieces, vbase, len);
+}
 
-    // This CTA owns nodes [lo, hi) of the partition (multiples of 4). The
-    // other CTAs push their partial sums for that range into this CTA's ring
-    // memory, idle now, so the merge below reads local shared memory only.
-    const uint32_t per = (((len + S - 1) / S) + 3) & ~3u;
-    const uint32_t lo = min(len, rank * per), hi = min(len, lo + per);
-    float* stage = reinterpret_cast<float*>(ring);
-    const bool push = (size_t)(S - 1) * per * sizeof(float) <= R::kBytes - kSumScratchBytes;
-    if (push && S > 1) {
-        for (uint32_t t = 0; t < S; ++t) {
-            if (t == rank) continue;
-            const uint32_t tlo = min(len, t * per), thi = min(len, tlo + per);
-            push_range(acc + tlo, stage + (size_t)(rank < t ? rank : rank - 1) * per, thi - tlo, t);
-        }
-        cluster_sync();
-    }
-    // Sum of the S partial sums of node i in [lo, hi), in a fixed order.
-    auto merged = [&](uint32_t i) -> float {
-        float s = 0.0f;
-        if (push) {
-            s = acc[i];
-            for (uint32_t q = 0; q + 1 < S; ++q) s += stage[(size_t)q * per + (i - lo)];
-        } else {
-            for (uint32_t r = 0; r < S; ++r) s += ld_cluster_f32(map_rank(acc + i, r));
-        }
-        return s;
-    };
-    // The same for nodes i .. i+3 (i - lo a multiple of 4).
-    auto merged4 = [&](uint32_t i) -> float4 {
-        if (!push) return make_float4(merged(i), merged(i + 1), merged(i + 2), merged(i + 3));
-        float4 s = *reinterpret_cast<const float4*>(acc + i);
-        for (uint32_t q = 0; q + 1 < S; ++q) {
-            const float4 t = *reinterpret_cast<const float4*>(stage + (size_t)q * per + (i - lo));
-            s.x += t.x;
-            s.y += t.y;
-            s.z += t.z;
-            s.w += t.w;
-        }
-        return s;
-    };
 
-    const double D = a.uniform_dangling ? a.st->dangling : 0.0;
-    const float cst = (float)((1.0 - (double)a.d) / (double)a.n + (double)a.d * D / (double)a.n);
-    const float d_acc = a.d * U::acc_scale;  // exact: the scale is a power of two
-    // Per-thread partial sums of at most len / blockDim terms in FP32 (FP64
-    // arithmetic is slow on this part); thread and block totals in FP64.
-    float res_f = 0.0f, dg_f = 0.0f;
-    // Apply to one node: PR', residual and dangling terms, SPR' for the fused scatter.
-    auto apply1 = [&](uint32_t i, float s, float old, float inv) -> float {
-        const float x = fmaf(d_acc, s, cst);
-        if (kFused) acc[i] = x * inv;
-        res_f += fabsf(x - old);
-        if (inv == 0.0f) dg_f += x;
-        return x;
-    };
-    // Nodes [lo, vec_end) go four at a time with 16-byte loads and stores
-    // (the partition starts on a 16-byte boundary), kApplyVec groups of
-    // four in flight per thread; the rest one at a time.
-    const uint32_t vec_end = (npieces == 1 && (vbase & 3u) == 0) ? lo + ((hi - lo) & ~3u) : lo;
-    for (uint32_t i0 = lo + 4 * threadIdx.x; i0 < vec_end; i0 += 4 * kApplyVec * blockDim.x) {
-        float4 o[kApplyVec], w[kApplyVec], s[kApplyVec];
-#pragma unroll
-        for (int j = 0; j < kApplyVec; ++j) {
-            const uint32_t i = i0 + 4 * j * blockDim.x;
-            if (i < vec_end) {
-                o[j] = __ldg(reinterpret_cast<const float4*>(a.pr_in + vbase + i));
-                w[j] = __ldg(reinterpret_cast<const float4*>(a.inv_deg + vbase + i));
-                s[j] = merged4(i);
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < kApplyVec; ++j) {
-            const uint32_t i = i0 + 4 * j * blockDim.x;
-            if (i < vec_end) {
-                float4 x;
-                x.x = apply1(i, s[j].x, o[j].x, w[j].x);
-                x.y = apply1(i + 1, s[j].y, o[j].y, w[j].y);
-                x.z = apply1(i + 2, s[j].z, o[j].z, w[j].z);
-                x.w = apply1(i + 3, s[j].w, o[j].w, w[j].w);
-                *reinterpret_cast<float4*>(a.pr_out + vbase + i) = x;
-            }
-        }
+// ------------------------------------------------- gather+apply, window layout
+// Shared memory of the window gather: kStages ring stages of [header + IDs |
+// weights (weighted graphs) | update slice], the full and empty mbarriers of
+// each stage, then the accumulator (q slots and kWinWarps * kWinHubs hub
+// slots).
+template <int kUpd, bool kW>
+struct WinRing {
+    using T = typename Upd<kUpd>::T;
+    static constexpr uint32_t kWordBytes = kWinStride * sizeof(uint32_t);
+    static constexpr uint32_t kWOff = kWordBytes;
+    static constexpr uint32_t kUpdOff = kWordBytes * (kW ? 2u : 1u);
+    static constexpr uint32_t kUpdCap = kWin + 2 * (16 / (uint32_t)sizeof(T));
+    static constexpr uint32_t kStage = kUpdOff + ((kUpdCap * (uint32_t)sizeof(T) + 15u) & ~15u);
+    // as many stages as fit beside the largest accumulator (and 1 KB of
+    // static shared memory), at most 8
+    static constexpr size_t kBudget =
+        232448 - 1024 - 128 -
+        (size_t)((kW ? PCPM_MAX_WEIGHTED_PART_SIZE : PCPM_MAX_PART_SIZE) + kWinWarps * kWinHubs) * sizeof(float);
+    static constexpr int kStages = (int)(kBudget / kStage < 8 ? kBudget / kStage : 8);
+    static_assert(kStages >= 2, "the ring needs two stages");
+    static constexpr size_t kBytes = (size_t)kStages * kStage;
+    static constexpr size_t kAcc = kBytes + 128;  // 2 * kStages mbarriers
+    static_assert(kStage % 16 == 0 && kWordBytes % 16 == 0, "stage areas must stay 16-byte aligned");
+    static_assert(2 * kStages * sizeof(uint64_t) <= 128, "barrier area");
+};
+constexpr int kWinThreads = (kWinWarps + 1) * 32;  // consumer warps and one producer warp
+constexpr size_t kWinScatterBars = 512;            // fused scatter: 2 mbarriers per warp at the ring's start
+static_assert(2 * (kWinThreads / 32) * sizeof(uint64_t) <= kWinScatterBars, "scatter barriers");
+
+// Gather + apply over the window layout (see kWin). A cluster of S CTAs takes
+// one gather unit (a run of windows of one bin); each CTA a contiguous share
+// of its windows. Warp kWinWarps produces: one lane issues, per window, the
+// bulk copies of its words (and weights) and update slice into the next ring
+// stage once every consumer warp has released it. Consumer warp w takes group
+// w of every window: lane l walks its run of the group's sorted positions,
+// summing the values of equal slots in a register and adding each finished
+// run into the accumulator with a plain load and store (the slot belongs to
+// this warp alone, and its run ends in this lane alone). A lane's unfinished
+// last run (its slot continues in the next lane) is added with one
+// shared-memory atomic after the warp's plain adds, so at most one atomic per
+// lane and window remains of the one per ID of a racing layout. Then the hub
+// slots of all warps are summed into the hubs in warp order, and
+// gather_finish merges, applies and (fused) scatters.
+template <bool kFused, int kUpd, bool kW>
+__global__ void __launch_bounds__(kWinThreads, 1) gather_win_kernel(const GatherArgs a) {
+    using U = Upd<kUpd>;
+    using R = WinRing<kUpd, kW>;
+    using T = typename U::T;
+    static_assert(!kW || !kFused, "the weighted gather is two-phase");
+    if (a.st->stop) return;
+    extern __shared__ __align__(128) unsigned char smraw[];
+    __shared__ uint32_t sh32[32];
+    unsigned char* ring = smraw;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smraw + R::kBytes);
+    uint64_t* empty = full + R::kStages;
+    float* acc = reinterpret_cast<float*>(smraw + R::kAcc);
+
+    const uint32_t S = cluster_size(), rank = cluster_rank();
+    const uint4 unit = a.units[a.order[blockIdx.x / S]];  // (bin, first window, end window, pieces of the bin)
+    const uint32_t pd = unit.x, npieces = unit.w;
+    const uint32_t vbase = pd * a.q, len = min(a.q, a.n - vbase);
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    for (uint32_t i = threadIdx.x; i < (len + 3) / 4; i += blockDim.x)
+        reinterpret_cast<float4*>(acc)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (uint32_t i = threadIdx.x; i < kWinWarps * kWinHubs; i += blockDim.x) acc[a.q + i] = 0.0f;
+    if (threadIdx.x < R::kStages) {
+        mbar_init(&full[threadIdx.x], 1);
+        mbar_init(&empty[threadIdx.x], kWinWarps);
     }
-    if (npieces == 1) {
-        // The remaining nodes: kApplyIlp independent nodes per thread per
-        // round, their loads in flight together.
-        for (uint32_t i0 = vec_end + threadIdx.x; i0 < hi; i0 += kApplyIlp * blockDim.x) {
-            float s[kApplyIlp], old[kApplyIlp], inv[kApplyIlp];
-#pragma unroll
-            for (int j = 0; j < kApplyIlp; ++j) {
-                const uint32_t i = i0 + j * blockDim.x;
-                s[j] = 0.0f;
-                old[j] = 0.0f;
-                inv[j] = 1.0f;
-                if (i < hi) {
-                    old[j] = a.pr_in[vbase + i];
-                    inv[j] = a.inv_deg[vbase + i];
-                    s[j] = merged(i);
+    fence_mbar_init();
+    __syncthreads();
+    if (threadIdx.x == 0 && npieces == 1) {  // PR_old and 1/outdeg of this CTA's share, for the apply
+        const uint32_t per0 = (((len + S - 1) / S) + 3) & ~3u;
+        const uint32_t lo0 = min(len, rank * per0), hi0 = min(len, lo0 + per0);
+        const uint64_t keep = policy_evict_last();
+        prefetch_l2(a.pr_in + vbase + lo0, hi0 - lo0, keep);
+        prefetch_l2(a.inv_deg + vbase + lo0, hi0 - lo0, keep);
+    }
+    const uint32_t nwu = unit.z - unit.y;
+    const uint32_t w0 = unit.y + (uint32_t)((uint64_t)nwu * rank / S);
+    const uint32_t nmine = unit.y + (uint32_t)((uint64_t)nwu * (rank + 1) / S) - w0;
+
+    if (warp == (uint32_t)kWinWarps) {
+        if (lane == 0) {  // producer
+            const uint64_t policy = policy_evict_first();  // every window is read once
+            // The next window's descriptor loads while the producer waits for
+            // a free stage, so no global-memory latency sits between a stage's
+            // release and its refill.
+            uint4 next = nmine ? a.wdesc[w0] : make_uint4(0u, 0u, 0u, 0u);
+            uint32_t j = 0;
+            bool ok = true;
+            for (; j < nmine; ++j) {
+                const uint4 dsc = next;  // (slice start, slice bytes, word bytes, IDs)
+                if (j + 1 < nmine) next = a.wdesc[w0 + j + 1];
+                const uint32_t s = j % R::kStages;
+                if (j >= (uint32_t)R::kStages && !mbar_wait_bounded(&empty[s], ((j / R::kStages) - 1) & 1u)) {
+                    ok = false;
+                    break;
                 }
+                unsigned char* st = ring + (size_t)s * R::kStage;
+                mbar_arrive_expect_tx(&full[s], dsc.z * (kW ? 2u : 1u) + dsc.y);
+                bulk_load_hint(st, a.wwords + (size_t)(w0 + j) * kWinStride, dsc.z, &full[s], policy);
+                if constexpr (kW)
+                    bulk_load_hint(st + R::kWOff, a.wweight + (size_t)(w0 + j) * kWinStride, dsc.z, &full[s], policy);
+                if (dsc.y)
+                    bulk_load_hint(st + R::kUpdOff, static_cast<const T*>(a.upd_in) + dsc.x, dsc.y, &full[s], policy);
             }
-#pragma unroll
-            for (int j = 0; j < kApplyIlp; ++j) {
-                const uint32_t i = i0 + j * blockDim.x;
-                if (i < hi) a.pr_out[vbase + i] = apply1(i, s[j], old[j], inv[j]);
+            if (!ok) {
+                // a stage was not released in time: record it and wait
+                // (bounded) for the copies still in flight
+                atomicOr(a.err, kErrTimeout);
+                for (uint32_t jj = j > (uint32_t)R::kStages ? j - R::kStages : 0u; jj < j; ++jj)
+                    (void)mbar_wait_bounded(&full[jj % R::kStages], (jj / R::kStages) & 1u);
             }
         }
+        __syncwarp();
     } else {
-        // The bin is cut into several units: add this unit's sums to the
-        // global partial sums; the last CTA to arrive applies the partition.
-        uint32_t& last = sh32[0];
-        const bool aligned = (vbase & 3u) == 0;
-        const uint32_t gv_end = aligned ? lo + ((hi - lo) & ~3u) : lo;
-        for (uint32_t i = lo + 4 * threadIdx.x; i < gv_end; i += 4 * blockDim.x) {
-            const float4 s = merged4(i);
-            if (s.x != 0.0f || s.y != 0.0f || s.z != 0.0f || s.w != 0.0f) red_add_v4(a.gacc + vbase + i, s);
-        }
-        for (uint32_t i = gv_end + threadIdx.x; i < hi; i += blockDim.x) {
-            const float s = merged(i);
-            if (s != 0.0f) atomicAdd(&a.gacc[vbase + i], s);
-        }
-        __threadfence();
-        __syncthreads();
-        if (threadIdx.x == 0) last = atomicAdd(&a.bin_done[pd], 1u) == npieces * S - 1 ? 1u : 0u;
-        __syncthreads();
-        if (last) {
-            __threadfence();
-            // The whole partition from the global sums: four nodes at a time
-            // where the partition starts on a 16-byte boundary, then the rest.
-            const uint32_t av_end = aligned ? (len & ~3u) : 0;
-            for (uint32_t i0 = 4 * threadIdx.x; i0 < av_end; i0 += 4 * kApplyVecCut * blockDim.x) {
-                float4 o[kApplyVecCut], w[kApplyVecCut], s[kApplyVecCut];
-#pragma unroll
-                for (int j = 0; j < kApplyVecCut; ++j) {
-                    const uint32_t i = i0 + 4 * j * blockDim.x;
-                    if (i < av_end) {
-                        s[j] = __ldcg(reinterpret_cast<const float4*>(a.gacc + vbase + i));
-                        o[j] = __ldg(reinterpret_cast<const float4*>(a.pr_in + vbase + i));
-                        w[j] = __ldg(reinterpret_cast<const float4*>(a.inv_deg + vbase + i));
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < kApplyVecCut; ++j) {
-                    const uint32_t i = i0 + 4 * j * blockDim.x;
-                    if (i < av_end) {
-                        float4 x;
-                        x.x = apply1(i, s[j].x, o[j].x, w[j].x);
-                        x.y = apply1(i + 1, s[j].y, o[j].y, w[j].y);
-                        x.z = apply1(i + 2, s[j].z, o[j].z, w[j].z);
-                        x.w = apply1(i + 3, s[j].w, o[j].w, w[j].w);
-                        *reinterpret_cast<float4*>(a.gacc + vbase + i) = make_float4(0.f, 0.f, 0.f, 0.f);
-                        *reinterpret_cast<float4*>(a.pr_out + vbase + i) = x;
-                    }
-                }
+        for (uint32_t j = 0; j < nmine; ++j) {
+            const uint32_t s = j % R::kStages;
+            if (!__all_sync(kFull, mbar_wait_bounded(&full[s], (j / R::kStages) & 1u))) {
+                if (lane == 0) atomicOr(a.err, kErrTimeout);
+                break;
             }
-            for (uint32_t i0 = av_end + threadIdx.x; i0 < len; i0 += kApplyIlp * blockDim.x) {
-                float s[kApplyIlp], old[kApplyIlp], inv[kApplyIlp];
+            const unsigned char* st = ring + (size_t)s * R::kStage;
+            const uint16_t* hdr = reinterpret_cast<const uint16_t*>(st);
+            const uint32_t g0 = hdr[warp], nw = hdr[warp + 1] - g0;
+            if (nw) {
+                const uint32_t* wd = reinterpret_cast<const uint32_t*>(st) + kWinHdrWords + g0;
+                const T* ups = reinterpret_cast<const T*>(st + R::kUpdOff);
+                const uint32_t rounds = (nw + 31) >> 5, longer = nw - 32 * (rounds - 1);
+                const uint32_t cnt = lane < longer ? rounds : rounds - 1;
+                float run = 0.0f;
+                uint32_t last = kWinEndBit;  // word of the lane's last ID (none: no unfinished run)
+                constexpr uint32_t kU = 4;
+                for (uint32_t r0 = 0; r0 < rounds; r0 += kU) {
+                    uint32_t wv[kU];
+                    float v[kU];
 #pragma unroll
-                for (int j = 0; j < kApplyIlp; ++j) {
-                    const uint32_t i = i0 + j * blockDim.x;
-                    s[j] = 0.0f;
-                    old[j] = 0.0f;
-                    inv[j] = 1.0f;
-                    if (i < len) {
-                        s[j] = __ldcg(&a.gacc[vbase + i]);
-                        old[j] = a.pr_in[vbase + i];
-                        inv[j] = a.inv_deg[vbase + i];
-                    }
-                }
+                    for (uint32_t i = 0; i < kU; ++i) wv[i] = r0 + i < cnt ? wd[(r0 + i) * 32 + lane] : 0u;
 #pragma unroll
-                for (int j = 0; j < kApplyIlp; ++j) {
-                    const uint32_t i = i0 + j * blockDim.x;
-                    if (i < len) {
-                        const float x = fmaf(d_acc, s[j], cst);
-                        a.gacc[vbase + i] = 0.0f;
-                        a.pr_out[vbase + i] = x;
-                        res_f += fabsf(x - old[j]);
-                        if (inv[j] == 0.0f) dg_f += x;
+                    for (uint32_t i = 0; i < kU; ++i) {
+                        v[i] = r0 + i < cnt ? U::load(ups, (wv[i] >> kWinOffShift) & kWinOffMask) : 0.0f;
+                        if constexpr (kW) {
+                            const float* wts = reinterpret_cast<const float*>(st + R::kWOff) + kWinHdrWords + g0;
+                            if (r0 + i < cnt) v[i] *= wts[(r0 + i) * 32 + lane];
+                        }
                     }
+                    // The runs that finish in this batch have distinct slots
+                    // (a slot's run ends once per group), so their
+                    // accumulator loads are all issued before any store.
+                    float old[kU];
+#pragma unroll
+                    for (uint32_t i = 0; i < kU; ++i)
+                        old[i] = (r0 + i < cnt && (wv[i] & kWinEndBit)) ? acc[wv[i] & kWinSlotMask] : 0.0f;
+#pragma unroll
+                    for (uint32_t i = 0; i < kU; ++i) {
+                        if (r0 + i < cnt) {
+                            run += v[i];
+                            last = wv[i];
+                            if (wv[i] & kWinEndBit) {  // a finished run: this lane alone adds it
+                                old[i] += run;
+                                run = 0.0f;
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (uint32_t i = 0; i < kU; ++i)
+                        if (r0 + i < cnt && (wv[i] & kWinEndBit)) acc[wv[i] & kWinSlotMask] = old[i];
                 }
+                // A run that continues in the next lane: no run of the group
+                // ends on its slot in this lane, but one lane finishes it with
+                // a plain add above and others may hold parts too, so the
+                // parts are added atomically, after the warp's plain adds.
+                __syncwarp();
+                if (!(last & kWinEndBit)) atomicAdd(&acc[last & kWinSlotMask], run);
             }
-            if (threadIdx.x == 0) a.bin_done[pd] = 0;
+            __syncwarp();  // every lane is done with the stage and its adds
+            if (lane == 0) mbar_arrive(&empty[s]);
         }
     }
-    double res = (double)res_f, dg = (double)dg_f;
-    block_sum2<kGatherWarps * 32>(res, dg, reinterpret_cast<double*>(ring + R::kBytes - kSumScratchBytes));
-    if (threadIdx.x == 0) {
-        a.partials[2 * blockIdx.x] = res;
-        a.partials[2 * blockIdx.x + 1] = dg;
-    }
-
-    if constexpr (kFused) {
-        if (npieces != 1) {  // the host runs cut bins in two-phase form only
-            if (threadIdx.x == 0) atomicOr(a.err, kErrBounds);
-            cluster_sync();
-            return;
+    __syncthreads();
+    // hub slots of every warp into the hubs, in warp order
+    if (threadIdx.x < kWinHubs) {
+        const uint32_t h = a.whubs[(size_t)pd * kWinHubs + threadIdx.x];
+        if (h < len) {
+            float sum = 0.0f;
+            for (uint32_t w = 0; w < (uint32_t)kWinWarps; ++w) sum += acc[a.q + w * kWinHubs + threadIdx.x];
+            acc[h] += sum;
         }
-        // Fused scatter of the next iteration: assemble SPR' of the whole
-        // partition in every CTA's shared memory (each pushes its range to
-        // the others), then write 1/S of the partition's update segments.
-        __syncthreads();
-        if (push) {
-            for (uint32_t t = 0; t < S; ++t)
-                if (t != rank) push_range(acc + lo, acc + lo, hi - lo, t);
-            cluster_sync();
-        } else {
-            cluster_sync();
-            for (uint32_t r = 0; r < S; ++r) {
-                if (r == rank) continue;
-                const uint32_t rlo = min(len, r * per), rhi = min(len, rlo + per);
-                const uint32_t q4 = (rhi - rlo) >> 2;
-                for (uint32_t i = threadIdx.x; i < q4; i += blockDim.x)
-                    reinterpret_cast<float4*>(acc + rlo)[i] = ld_cluster_f32x4(map_rank(acc + rlo + 4 * i, r));
-                for (uint32_t i = rlo + (q4 << 2) + threadIdx.x; i < rhi; i += blockDim.x)
-                    acc[i] = ld_cluster_f32(map_rank(acc + i, r));
-            }
-            cluster_sync();  // no CTA reads another's shared memory after this point
-        }
-        uint32_t* gpre = reinterpret_cast<uint32_t*>(ring);
-        const uint32_t* segrow = a.seg_u + (size_t)pd * a.k;
-        const uint32_t* cntrow = a.cnt_u + (size_t)pd * a.k;
-        // the stage barriers take the per-slot metadata's place (unused now)
-        uint64_t* sbars = reinterpret_cast<uint64_t*>(meta);
-        static_assert(R::kMeta >= 2 * kGatherWarps * sizeof(uint64_t), "two stage barriers per warp");
-        static_assert(R::kBytes >= scatter_table_bytes(PCPM_MAX_PARTITIONS) + 2 * kGatherWarps * 32 * 16,
-                      "the stages must hold at least 32 groups beside the largest segment tables");
-        if (threadIdx.x < 2 * kGatherWarps) mbar_init(&sbars[threadIdx.x], 1);
-        fence_mbar_init();
-        fence_proxy_async_smem();  // the block sum's scratch becomes a bulk-copy target
-        uint32_t* dsh = reinterpret_cast<uint32_t*>(ring + scatter_gpre_bytes(a.k));
-        uint8_t* emsk = ring + scatter_gpre_bytes(a.k) + scatter_dsh_bytes(a.k);
-        segment_groups_prefix(segrow, cntrow, a.k, gpre, sh32, dsh, emsk);  // ends with __syncthreads
-        const uint32_t G = gpre[a.k];
-        const uint32_t f_lo = (uint32_t)((uint64_t)G * rank / S);
-        const uint32_t f_hi = (uint32_t)((uint64_t)G * (rank + 1) / S);
-        // stages: the ring after the segment table
-        const size_t st_off = scatter_table_bytes(a.k);
-        const uint32_t stage_bytes = (uint32_t)(((R::kBytes - st_off) / (2 * kGatherWarps)) & ~(size_t)15);
-        scatter_groups_staged<kUpd>(acc, vbase, len, gpre, dsh, emsk, a.k, a.src, a.upd_out, f_lo, f_hi, a.err,
-                                    ring + st_off, stage_bytes, sbars, [] {});
-    } else {
-        if (!push) cluster_sync();  // remote loads of this CTA's shared memory are done
     }
+    static_assert(R::kBytes >= kWinScatterBars + scatter_table_bytes(PCPM_MAX_PARTITIONS) + 2 * (kWinThreads / 32) * 16 * 16,
+                  "the fused scatter's stages must hold at least 16 groups beside the largest segment tables");
+    gather_finish<kFused, kUpd, kWinThreads>(a, ring, R::kBytes, reinterpret_cast<uint64_t*>(ring),
+                                             ring + kWinScatterBars, R::kBytes - kWinScatterBars, acc, sh32, S, rank,
+                                             pd, npieces, vbase, len);
 }
 
 // ---------------------------------------------------------------- reduce
@@ -1189,6 +1414,28 @@ GatherFn pick_gather(bool canonical, bool runs, int upd) {
             return runs ? gather_kernel<kFused, false, true, kUpdF32> : gather_kernel<kFused, false, false, kUpdF32>;
     }
 }
+
+template <bool kFused>
+GatherFn pick_gather_win(int upd, bool weighted) {
+    if (weighted) return gather_win_kernel<false, kUpdF32, true>;
+    switch (upd) {
+        case kUpdF16: return gather_win_kernel<kFused, kUpdF16, false>;
+        case kUpdBF16: return gather_win_kernel<kFused, kUpdBF16, false>;
+        default: return gather_win_kernel<kFused, kUpdF32, false>;
+    }
+}
+
+// The window gather's shared memory: ring, barriers, q accumulator slots and
+// the hub slots of every warp.
+template <int kUpd, bool kW>
+size_t gather_win_smem_bytes(uint32_t q) {
+    return WinRing<kUpd, kW>::kAcc + (size_t)(((q + 3) & ~3u) + kWinWarps * kWinHubs) * sizeof(float);
+}
+size_t win_smem_bytes(uint32_t q, int upd, bool weighted) {
+    if (weighted) return gather_win_smem_bytes<kUpdF32, true>(q);
+    return upd == kUpdF32 ? gather_win_smem_bytes<kUpdF32, false>(q) : gather_win_smem_bytes<kUpdF16, false>(q);
+}
+static_assert(WinRing<kUpdF16, false>::kBytes == WinRing<kUpdBF16, false>::kBytes, "16-bit rings alike");
 
 // The accumulator holds q real slots, kPadSlots for the layout's padding and
 // kHubSlots (a pair per warp) for the hubs.
@@ -1249,6 +1496,23 @@ int configure_kernels(pcpm_png* g) {
                 return PCPM_ECUDA;
             }
     }
+    if (g->gather_windows) {
+        const size_t ws = win_smem_bytes(g->q, g->upd_dtype, false);
+        const void* wins[] = {(const void*)pick_gather_win<false>(g->upd_dtype, false),
+                              (const void*)pick_gather_win<true>(g->upd_dtype, false)};
+        for (const void* f : wins)
+            if (const cudaError_t e = raise_smem_limit(f, ws); e != cudaSuccess) {
+                note_cuda_error(e);
+                return PCPM_ECUDA;
+            }
+        if (g->weighted)
+            if (const cudaError_t e = raise_smem_limit((const void*)pick_gather_win<false>(kUpdF32, true),
+                                                       win_smem_bytes(g->q, kUpdF32, true));
+                e != cudaSuccess) {
+                note_cuda_error(e);
+                return PCPM_ECUDA;
+            }
+    }
     const void* scatters[] = {(const void*)scatter_kernel<kUpdF32>, (const void*)scatter_kernel<kUpdF16>,
                               (const void*)scatter_kernel<kUpdBF16>};
     for (const void* f : scatters)
@@ -1268,13 +1532,14 @@ int configure_kernels(pcpm_png* g) {
         attr[0].val.clusterDim.y = 1;
         attr[0].val.clusterDim.z = 1;
         cfg.gridDim = dim3(g->ngunits * S);
-        cfg.blockDim = dim3(kGatherWarps * 32);
-        cfg.dynamicSmemBytes = gs;
+        cfg.blockDim = dim3(g->gather_windows ? kWinThreads : kGatherWarps * 32);
+        cfg.dynamicSmemBytes = g->gather_windows ? win_smem_bytes(g->q, g->upd_dtype, false) : gs;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int clusters = 0;
-        if (cudaOccupancyMaxActiveClusters(&clusters, gather_kernel<true, false, false, kUpdF32>, &cfg) == cudaSuccess &&
-            clusters > 0) {
+        const GatherFn probe = g->gather_windows ? pick_gather_win<true>(g->upd_dtype, false)
+                                                 : gather_kernel<true, false, false, kUpdF32>;
+        if (cudaOccupancyMaxActiveClusters(&clusters, probe, &cfg) == cudaSuccess && clusters > 0) {
             g->cluster = S;
             return PCPM_OK;
         }
@@ -1341,6 +1606,10 @@ int launch_gather(pcpm_png* g, float d, uint32_t flags, bool fused, cudaStream_t
     a.seg_u = g->seg_u;
     a.cnt_u = g->cnt_u;
     a.upd_out = g->upd[g->ucur ^ 1];
+    a.wwords = g->wwords;
+    a.wweight = g->wweight;
+    a.wdesc = g->wdesc;
+    a.whubs = g->whubs;
 
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
@@ -1349,16 +1618,25 @@ int launch_gather(pcpm_png* g, float d, uint32_t flags, bool fused, cudaStream_t
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(g->ngunits * g->cluster);
-    cfg.blockDim = dim3(kGatherWarps * 32);
-    cfg.dynamicSmemBytes = weighted ? gather_smem_bytes<true>(g->q) : gather_smem_bytes(g->q);
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     cudaError_t e;
-    const GatherFn f = weighted ? (g->gather_runs ? gather_kernel<false, false, true, kUpdF32, true>
-                                                  : gather_kernel<false, false, false, kUpdF32, true>)
-                       : fused  ? pick_gather<true>(g->canonical_gather != 0, g->gather_runs != 0, g->upd_dtype)
-                                : pick_gather<false>(g->canonical_gather != 0, g->gather_runs != 0, g->upd_dtype);
+    GatherFn f;
+    if (g->gather_windows) {
+        cfg.blockDim = dim3(kWinThreads);
+        cfg.dynamicSmemBytes = win_smem_bytes(g->q, weighted ? kUpdF32 : g->upd_dtype, weighted);
+        f = weighted ? pick_gather_win<false>(kUpdF32, true)
+            : fused  ? pick_gather_win<true>(g->upd_dtype, false)
+                     : pick_gather_win<false>(g->upd_dtype, false);
+    } else {
+        cfg.blockDim = dim3(kGatherWarps * 32);
+        cfg.dynamicSmemBytes = weighted ? gather_smem_bytes<true>(g->q) : gather_smem_bytes(g->q);
+        f = weighted ? (g->gather_runs ? gather_kernel<false, false, true, kUpdF32, true>
+                                       : gather_kernel<false, false, false, kUpdF32, true>)
+            : fused  ? pick_gather<true>(g->canonical_gather != 0, g->gather_runs != 0, g->upd_dtype)
+                     : pick_gather<false>(g->canonical_gather != 0, g->gather_runs != 0, g->upd_dtype);
+    }
     e = cudaLaunchKernelEx(&cfg, f, a);
     g->partial_count = (int)(g->ngunits * g->cluster);
     if (e != cudaSuccess) note_cuda_error(e);

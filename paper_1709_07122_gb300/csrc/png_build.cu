@@ -1034,6 +1034,280 @@ __global__ void __launch_bounds__(kLayoutWarps * 32) gather_layout_kernel(
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicAdd(&stats[1], 1ull);
 }
 
+// ----------------------------------------------------- window gather layout
+// One CTA per bin p (every in-edge of a node of p lies in bin p, so the bin's
+// IDs give the in-degrees of p's nodes, counted in shared memory):
+//   whubs[p * kWinHubs + h]  the kWinHubs largest in-degrees (at least
+//       kHubMinInDegree; ties to the lower ID), largest first, else kNoHub.
+//       The gather sums their IDs in per-warp slots, dealt to all warps.
+//   bnd[p * (kWinWarps + 1) + w]  first 32-node block owned by gather warp w:
+//       the blocks, weighed by the in-degrees of their non-hub nodes, are cut
+//       into kWinWarps contiguous ranges of about equal weight (a block goes
+//       to the warp whose share holds its midpoint); bnd[.. + kWinWarps] is the
+//       block count.
+__global__ void __launch_bounds__(1024) bin_owner_kernel(const uint32_t* __restrict__ dest,
+                                                         const uint32_t* __restrict__ bin_e, uint32_t n, uint32_t q,
+                                                         uint32_t* __restrict__ whubs, uint32_t* __restrict__ bnd) {
+    extern __shared__ uint32_t deg[];  // q in-degrees, then one weight per block
+    __shared__ unsigned long long sh[32];
+    __shared__ uint32_t sh32[32];
+    __shared__ uint8_t own[1024];
+    const uint32_t p = blockIdx.x, base = p * q, len = min(q, n - base);
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) deg[i] = 0;
+    __syncthreads();
+    const uint32_t e0 = bin_e[p], e1 = bin_e[p + 1];
+    for (uint32_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        const uint32_t loc = (__ldcs(dest + e) & kIdMask) - base;
+        if (loc < len) atomicAdd(&deg[loc], 1u);
+    }
+    __syncthreads();
+    for (uint32_t h = 0; h < kWinHubs; ++h) {
+        unsigned long long best = 0;
+        for (uint32_t i = threadIdx.x; i < len; i += blockDim.x)
+            best = max(best, ((unsigned long long)deg[i] << 32) | (0xFFFFFFFFu - i));
+        const unsigned long long b = block_max_u64(best, sh);
+        const uint32_t hub = (b >> 32) >= kHubMinInDegree ? 0xFFFFFFFFu - (uint32_t)b : kNoHub;
+        if (threadIdx.x == 0) {
+            whubs[(size_t)p * kWinHubs + h] = hub;
+            if (hub != kNoHub) deg[hub] = 0;  // its IDs go to every warp: no owner weight
+        }
+        __syncthreads();
+    }
+    const uint32_t nblk = (len + 31) / 32;
+    uint32_t* wt = deg + ((q + 31) & ~31u);
+    for (uint32_t b = warp; b < nblk; b += blockDim.x >> 5) {
+        const uint32_t i = 32 * b + lane;
+        const uint32_t x = __reduce_add_sync(0xffffffffu, i < len ? deg[i] : 0u);
+        if (lane == 0) wt[b] = x;
+    }
+    __syncthreads();
+    const uint32_t t = threadIdx.x;  // one block per thread (nblk <= 1024)
+    const uint32_t w_t = t < nblk ? wt[t] : 0u;
+    uint32_t total = 0;
+    const uint32_t cum = block_exclusive_scan(w_t, &total, sh32);
+    if (t < nblk) {
+        const unsigned long long mid = ((2ull * cum + w_t) * kWinWarps) / (2ull * total ? 2ull * total : 1ull);
+        const uint32_t o = total ? (uint32_t)(mid < (unsigned long long)kWinWarps ? mid : kWinWarps - 1)
+                                 : (uint32_t)(((uint64_t)t * kWinWarps) / nblk);
+        own[t] = (uint8_t)o;
+    }
+    __syncthreads();
+    if (t <= (uint32_t)kWinWarps) {  // first block with owner >= t (owners never decrease)
+        uint32_t lo = 0, hi = nblk;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (own[mid] < t) lo = mid + 1; else hi = mid;
+        }
+        bnd[(size_t)p * (kWinWarps + 1) + t] = t == (uint32_t)kWinWarps ? nblk : lo;
+    }
+}
+
+// windows[p] = windows of bin p: ceil(IDs / kWin).
+__global__ void bin_window_counts_kernel(const uint32_t* __restrict__ bin_e, uint32_t k, uint32_t* __restrict__ cnt) {
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < k; p += gridDim.x * blockDim.x)
+        cnt[p] = (bin_e[p + 1] - bin_e[p] + kWin - 1) / kWin;
+}
+
+constexpr int kWlThreads = 256;
+constexpr uint32_t kWlPer = kWin / kWlThreads;  // consecutive positions per thread
+constexpr uint32_t kWlBuckets = kWinWarps * 32; // (owner warp, bank)
+
+// One CTA per window of kWin consecutive IDs of one bin. Every ID gets its
+// update index (flagged IDs before it, inclusive, minus one: Algorithm 4's
+// pointer), its owner warp and slot (hub IDs: the i-th hub ID of the window
+// goes to warp i mod kWinWarps, slot q + warp * kWinHubs + hub), then a
+// counting sort by (owner, bank of the slot) and, inside each bucket, an
+// insertion sort by (slot, position) give every owner's group in (bank, slot,
+// position) order. Group w's sorted position s goes to lane l, round r of
+// that warp's pass: with R = ceil(N_w / 32) rounds, the first N_w - 32 (R - 1)
+// lanes take R consecutive positions and the others R - 1, stored at r * 32 +
+// l. The end bit marks the last position of a run of equal slots. The CTA
+// also checks every word against the partition and the update slice
+// (stats[1]) and counts IDs whose run continues (stats[0]).
+__global__ void __launch_bounds__(kWlThreads) window_layout_kernel(
+    const uint32_t* __restrict__ dest, const uint32_t* __restrict__ bin_e, const uint32_t* __restrict__ win_start,
+    uint32_t k, const uint32_t* __restrict__ chunk_base, const uint32_t* __restrict__ whubs,
+    const uint32_t* __restrict__ bnd, uint32_t n, uint32_t q, uint64_t nwin, uint32_t upd_bytes,
+    uint32_t* __restrict__ words, uint4* __restrict__ desc, unsigned long long* __restrict__ stats,
+    const float* __restrict__ wdest, float* __restrict__ wweight) {
+    __shared__ uint32_t s_sk[kWin];      // sorted: slot << 12 | position
+    __shared__ uint32_t s_out[kWin];     // words in storage order
+    __shared__ uint16_t s_off[kWin];     // by position: update offset in the slice
+    __shared__ uint32_t s_cnt[kWlBuckets];
+    __shared__ uint32_t s_start[kWlBuckets + 1];
+    __shared__ uint8_t s_own[1024];
+    __shared__ uint32_t s_hub[kWinHubs];
+    __shared__ uint32_t s_goff[kWinWarps + 1];
+    __shared__ uint32_t sh32[32];
+    __shared__ uint32_t s_first, s_last;
+    static_assert(kWin <= 4096 && kWlPer * kWlThreads == kWin, "12-bit positions, kWlPer per thread");
+    const uint32_t t = threadIdx.x, lane = t & 31;
+    const uint32_t align = 16u / upd_bytes;
+    const uint32_t slice_cap = kWin + 2 * align;
+    uint32_t nbad = 0, nmerged = 0;
+    for (uint64_t win = blockIdx.x; win < nwin; win += gridDim.x) {
+        const uint32_t p = upper_bound_u32(win_start, 0, k + 1, (uint32_t)win) - 1;
+        const uint32_t j = (uint32_t)win - win_start[p];
+        const uint32_t P = bin_e[p] + j * kWin, Pend = min(P + kWin, bin_e[p + 1]);
+        const uint32_t N = Pend - P;
+        const uint32_t vbase = p * q, len = min(q, n - vbase);
+        const uint32_t* b = bnd + (size_t)p * (kWinWarps + 1);
+        const uint32_t nblk = b[kWinWarps];
+        for (uint32_t x = t; x < nblk; x += kWlThreads) s_own[x] = (uint8_t)(upper_bound_u32(b, 0, kWinWarps, x) - 1);
+        if (t < kWinHubs) s_hub[t] = whubs[(size_t)p * kWinHubs + t];
+        for (uint32_t x = t; x < kWlBuckets; x += kWlThreads) s_cnt[x] = 0;
+        // flagged IDs before P: the chunk's base plus the flags of its head
+        uint32_t fb = 0;
+        if (t < 32) {
+            const uint32_t cbase = P & ~(kChunk - 1);
+            uint32_t run = chunk_base[P / kChunk];
+            for (uint32_t x = cbase; x < P; x += 32) {
+                const uint32_t pos = x + lane;
+                run += __popc(__ballot_sync(0xffffffffu, pos < P && (dest[pos] >> 31)));
+            }
+            fb = run;
+        }
+        if (t == 0) s_first = fb;
+        __syncthreads();
+        fb = s_first;
+        // this thread's positions [t * kWlPer, +kWlPer): flags and hub IDs
+        uint32_t id[kWlPer];
+        uint32_t nflag = 0, nhub = 0;
+#pragma unroll
+        for (uint32_t i = 0; i < kWlPer; ++i) {
+            const uint32_t pos = t * kWlPer + i;
+            id[i] = pos < N ? dest[P + pos] : 0u;
+            const uint32_t loc = (id[i] & kIdMask) - vbase;
+            nflag += pos < N ? id[i] >> 31 : 0u;
+            bool hub = false;
+#pragma unroll
+            for (uint32_t h = 0; h < kWinHubs; ++h) hub |= loc < len && loc == s_hub[h];
+            nhub += (pos < N && hub) ? 1u : 0u;
+        }
+        uint32_t tot = 0;
+        const uint32_t pre = block_exclusive_scan(nflag | (nhub << 16), &tot, sh32);
+        uint32_t fl = fb + (pre & 0xFFFFu), hr = pre >> 16;
+        // update index, owner, slot and bucket of each ID
+        uint32_t idx[kWlPer], slot[kWlPer], bkt[kWlPer];
+#pragma unroll
+        for (uint32_t i = 0; i < kWlPer; ++i) {
+            const uint32_t pos = t * kWlPer + i;
+            const uint32_t loc = (id[i] & kIdMask) - vbase;
+            fl += pos < N ? id[i] >> 31 : 0u;
+            idx[i] = fl - 1;
+            uint32_t h = kWinHubs;
+#pragma unroll
+            for (uint32_t hh = 0; hh < kWinHubs; ++hh)
+                if (loc < len && loc == s_hub[hh] && h == kWinHubs) h = hh;
+            uint32_t o = 0;
+            if (h < kWinHubs) {
+                o = hr % kWinWarps;
+                slot[i] = q + o * kWinHubs + h;
+                hr += pos < N ? 1u : 0u;
+            } else {
+                if (pos < N && loc >= len) ++nbad;
+                o = loc < len ? s_own[loc >> 5] : 0u;
+                slot[i] = loc < len ? loc : 0u;
+            }
+            bkt[i] = o * 32 + (slot[i] & 31u);
+            if (pos == 0) s_first = idx[i];
+            if (pos + 1 == N) s_last = idx[i];
+        }
+        __syncthreads();
+        const uint32_t us = N ? s_first & ~(align - 1) : 0u, ue = N ? (s_last + align) & ~(align - 1) : 0u;
+        if (N && ue - us > slice_cap) ++nbad;
+        uint32_t rank[kWlPer];
+#pragma unroll
+        for (uint32_t i = 0; i < kWlPer; ++i) {
+            const uint32_t pos = t * kWlPer + i;
+            rank[i] = pos < N ? atomicAdd(&s_cnt[bkt[i]], 1u) : 0u;
+            if (pos < N) {
+                const uint32_t off = idx[i] - us;
+                if (off >= slice_cap) ++nbad;
+                s_off[pos] = (uint16_t)min(off, kWinOffMask);
+            }
+        }
+        __syncthreads();
+        {  // bucket starts: kBPer consecutive buckets per thread
+            constexpr uint32_t kBPer = (kWlBuckets + kWlThreads - 1) / kWlThreads;
+            uint32_t c[kBPer], sum = 0;
+#pragma unroll
+            for (uint32_t i = 0; i < kBPer; ++i) {
+                const uint32_t b = kBPer * t + i;
+                c[i] = b < kWlBuckets ? s_cnt[b] : 0u;
+                sum += c[i];
+            }
+            uint32_t all = 0;
+            uint32_t x = block_exclusive_scan(sum, &all, sh32);
+#pragma unroll
+            for (uint32_t i = 0; i < kBPer; ++i) {
+                const uint32_t b = kBPer * t + i;
+                if (b < kWlBuckets) s_start[b] = x;
+                x += c[i];
+            }
+            if (t == 0) s_start[kWlBuckets] = all;
+        }
+        __syncthreads();
+#pragma unroll
+        for (uint32_t i = 0; i < kWlPer; ++i) {
+            const uint32_t pos = t * kWlPer + i;
+            if (pos < N) s_sk[s_start[bkt[i]] + rank[i]] = (slot[i] << 12) | pos;
+        }
+        __syncthreads();
+        for (uint32_t bb = t; bb < kWlBuckets; bb += kWlThreads) {  // (slot, position) order in each bucket
+            const uint32_t g0 = s_start[bb], g1 = s_start[bb + 1];
+            for (uint32_t x = g0 + 1; x < g1; ++x) {
+                const uint32_t v = s_sk[x];
+                uint32_t y = x;
+                while (y > g0 && s_sk[y - 1] > v) {
+                    s_sk[y] = s_sk[y - 1];
+                    --y;
+                }
+                s_sk[y] = v;
+            }
+        }
+        if (t <= (uint32_t)kWinWarps) s_goff[t] = t < (uint32_t)kWinWarps ? s_start[32 * t] : N;
+        __syncthreads();
+        // deal every group lane by lane; words in storage order
+        for (uint32_t s = t; s < N; s += kWlThreads) {
+            const uint32_t w = upper_bound_u32(s_goff, 0, kWinWarps, s) - 1;
+            const uint32_t g0 = s_goff[w], Nw = s_goff[w + 1] - g0, loc_s = s - g0;
+            const uint32_t R = (Nw + 31) / 32, full = Nw - 32 * (R - 1);
+            uint32_t l, r;
+            if (loc_s < full * R) {
+                l = loc_s / R;
+                r = loc_s % R;
+            } else {
+                const uint32_t x = loc_s - full * R;
+                l = full + x / (R - 1);
+                r = x % (R - 1);
+            }
+            const uint32_t sk = s_sk[s], sl = sk >> 12, pos = sk & 4095u;
+            const bool end = loc_s + 1 == Nw || (s_sk[s + 1] >> 12) != sl;
+            nmerged += end ? 0u : 1u;
+            const uint32_t st = g0 + r * 32 + l;
+            s_out[st] = sl | ((uint32_t)s_off[pos] << kWinOffShift) | (end ? kWinEndBit : 0u);
+            if (wweight) wweight[win * kWinStride + kWinHdrWords + st] = wdest[P + pos];
+        }
+        __syncthreads();
+        uint32_t* out = words + win * kWinStride;
+        if (t < kWinHdrWords) {
+            const uint32_t a0 = 2 * t, a1 = 2 * t + 1;
+            const uint32_t v0 = a0 <= (uint32_t)kWinWarps ? s_goff[a0] : 0u, v1 = a1 <= (uint32_t)kWinWarps ? s_goff[a1] : 0u;
+            out[t] = v0 | (v1 << 16);
+        }
+        for (uint32_t x = t; x < N; x += kWlThreads) out[kWinHdrWords + x] = s_out[x];
+        if (t == 0)
+            desc[win] = make_uint4(us, (ue - us) * upd_bytes, (kWinHdrWords + ((N + 3) & ~3u)) * 4u, N);
+        __syncthreads();
+    }
+    nmerged = __reduce_add_sync(0xffffffffu, nmerged);
+    nbad = __reduce_add_sync(0xffffffffu, nbad);
+    if (lane == 0 && nmerged) atomicAdd(&stats[0], (unsigned long long)nmerged);
+    if (lane == 0 && nbad) atomicAdd(&stats[1], (unsigned long long)nbad);
+}
+
 __global__ void scatter_pieces_kernel(const uint32_t* __restrict__ groups, uint32_t k, uint32_t per,
                                       uint32_t* __restrict__ pieces) {
     for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < k; p += gridDim.x * blockDim.x)
@@ -1263,12 +1537,18 @@ int build_png(pcpm_png* g, const uint32_t* row_ptr, const uint32_t* col, const p
         BCK(cudaMemsetAsync(g->chunk_base, 0, sizeof(uint32_t), s));
     }
 
-    // Hubs per bin.
+    // Hubs per bin: the two largest in-degrees for the canonical and chunk
+    // gathers; the window gather picks its own (bin_owner_kernel).
+    g->gather_windows = !g->canonical_gather && opt.gather_windows != 2;
     BCK(dev_alloc(g, (void**)&g->hubs, 2 * (size_t)k * sizeof(uint32_t)));
-    const size_t hub_smem = (size_t)q * sizeof(uint32_t);
-    BCK(cudaFuncSetAttribute(bin_hubs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hub_smem));
-    bin_hubs_kernel<<<k, 1024, hub_smem, s>>>(g->dest, g->bin_e, n, q, g->hubs);
-    BCK(cudaGetLastError());
+    if (!g->gather_windows) {
+        const size_t hub_smem = (size_t)q * sizeof(uint32_t);
+        BCK(cudaFuncSetAttribute(bin_hubs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hub_smem));
+        bin_hubs_kernel<<<k, 1024, hub_smem, s>>>(g->dest, g->bin_e, n, q, g->hubs);
+        BCK(cudaGetLastError());
+    } else {
+        BCK(cudaMemsetAsync(g->hubs, 0xFF, 2 * (size_t)k * sizeof(uint32_t), s));
+    }
 
     // Work units, largest first. Gather: runs of at most `gper` chunks, at
     // least q/64 chunks (so a unit's flush of q partial sums stays small next
@@ -1279,10 +1559,50 @@ int build_png(pcpm_png* g, const uint32_t* row_ptr, const uint32_t* col, const p
     BCK(tmp.alloc(&start, k + 1));
     BCK(tmp.alloc(&groups, k));
     BCK(tmp.alloc(&gstart, k + 1));
-    // Bank-spread gather layout.
     const uint32_t* ichunks = nullptr;
     uint64_t gchunks = g->nchunks;
-    if (!g->canonical_gather) {
+    uint32_t gper_default = (uint32_t)std::max<uint64_t>((q + 63) / 64, (gchunks + 2 * sms - 1) / (2 * sms));
+    if (g->gather_windows) {
+        // Window layout: owners and hubs per bin, then the windows.
+        uint32_t *bnd = nullptr, *wc = nullptr;
+        BCK(tmp.alloc(&bnd, (size_t)k * (kWinWarps + 1)));
+        BCK(tmp.alloc(&wc, k));
+        BCK(dev_alloc(g, (void**)&g->whubs, (size_t)k * kWinHubs * sizeof(uint32_t)));
+        const size_t own_smem = ((size_t)((q + 31) & ~31u) + 1024) * sizeof(uint32_t);
+        BCK(cudaFuncSetAttribute(bin_owner_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)own_smem));
+        bin_owner_kernel<<<k, 1024, own_smem, s>>>(g->dest, g->bin_e, n, q, g->whubs, bnd);
+        BCK(cudaGetLastError());
+        BCK(dev_alloc(g, (void**)&g->win_start, (k + 1) * sizeof(uint32_t)));
+        bin_window_counts_kernel<<<grid_for(k, 256, 64), 256, 0, s>>>(g->bin_e, k, wc);
+        if ((rc = scan_exclusive(wc, g->win_start, k, tmp, s)) != PCPM_OK) return rc;
+        uint32_t nw = 0;
+        BCK(cudaMemcpyAsync(&nw, g->win_start + k, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        BCK(cudaStreamSynchronize(s));
+        g->nwin = nw;
+        BCK(dev_alloc(g, (void**)&g->wwords, std::max<uint64_t>(nw, 1) * kWinStride * sizeof(uint32_t)));
+        BCK(dev_alloc(g, (void**)&g->wdesc, std::max<uint64_t>(nw, 1) * sizeof(uint4)));
+        if (g->weighted) BCK(dev_alloc(g, (void**)&g->wweight, std::max<uint64_t>(nw, 1) * kWinStride * sizeof(float)));
+        unsigned long long* lstats = nullptr;
+        BCK(tmp.alloc(&lstats, 2));
+        BCK(cudaMemsetAsync(lstats, 0, 2 * sizeof(*lstats), s));
+        if (nw) {
+            window_layout_kernel<<<(unsigned)std::min<uint64_t>(nw, (uint64_t)sms * 8), kWlThreads, 0, s>>>(
+                g->dest, g->bin_e, g->win_start, k, g->chunk_base, g->whubs, bnd, n, q, nw, g->upd_bytes, g->wwords,
+                g->wdesc, lstats, g->wdest, g->wweight);
+            BCK(cudaGetLastError());
+        }
+        unsigned long long hstats[2] = {0, 0};
+        BCK(cudaMemcpyAsync(hstats, lstats, sizeof(hstats), cudaMemcpyDeviceToHost, s));
+        BCK(cudaStreamSynchronize(s));
+        if (hstats[1]) return PCPM_EDEVICE;
+        g->merged_adds = hstats[0];
+        g->gather_runs = 1;
+        ichunks = g->win_start;
+        gchunks = nw;
+        // in windows: the chunk-based defaults divided by kWin / kChunk
+        gper_default = (uint32_t)std::max<uint64_t>((q + 1023) / 1024, (gchunks + 2 * sms - 1) / (2 * sms));
+    } else if (!g->canonical_gather) {
+        // Bank-spread gather layout.
         uint32_t* cc = nullptr;
         BCK(tmp.alloc(&cc, k));
         BCK(dev_alloc(g, (void**)&g->ichunk_start, (k + 1) * sizeof(uint32_t)));
@@ -1319,9 +1639,9 @@ int build_png(pcpm_png* g, const uint32_t* row_ptr, const uint32_t* col, const p
         gchunks = nic;
     }
 
-    const uint32_t gper = opt.gather_unit_chunks ? opt.gather_unit_chunks
-                                                 : (uint32_t)std::max<uint64_t>((q + 63) / 64,
-                                                                                (gchunks + 2 * sms - 1) / (2 * sms));
+    const uint32_t gper = !opt.gather_unit_chunks ? gper_default
+                          : g->gather_windows     ? (opt.gather_unit_chunks + kWin / kChunk - 1) / (kWin / kChunk)
+                                                  : opt.gather_unit_chunks;
     gather_pieces_kernel<<<grid_for(k, 256, 64), 256, 0, s>>>(g->bin_e, ichunks, k, gper, pieces);
     if ((rc = scan_exclusive(pieces, start, k, tmp, s)) != PCPM_OK) return rc;
     src_groups_kernel<<<k, 256, 0, s>>>(g->seg_u, g->cnt_u, k, groups);

@@ -55,3 +55,15 @@ def test_eq5_model(bench):
     want = m * (4 * (1 + 1 / r) + 8 / r) + 4 * 512 * 512 + 8 * S24["n"]
     assert bench.eq5_bytes(S24) == pytest.approx(want)
     assert 11.2 < bench.eq5_bytes(S24) / m < 11.4
+
+
+def test_window_layout_bytes(bench):
+    # window layout: destination IDs, updates, a 64-byte header and a 16-byte
+    # descriptor per window, bin starts, eight hubs per bin; PR_old, 1/outdeg, PR'
+    n, m, ne, k = S24["n"], S24["num_edges"], S24["num_updates"], S24["num_partitions"]
+    nwin = 64_571  # about m / 4096 plus one partial window per bin
+    info = dict(S24, gather_windows=1, num_windows=nwin)
+    b = bench.algorithmic_bytes(info, mode="two_phase")
+    assert b["gather_apply"] == 4 * m + 4 * ne + 80 * nwin + 8 * (k + 1) + 32 * k + 12 * n
+    chunked = bench.algorithmic_bytes(S24, mode="two_phase")["gather_apply"]
+    assert abs(b["gather_apply"] - chunked) < 0.002 * chunked  # the layouts differ only in their tables

@@ -293,20 +293,21 @@ def test_errors_from_bad_inputs():
 
 
 DECOMPOSITIONS = [
-    dict(),                                             # automatic
+    dict(),                                             # automatic: window layout
     dict(gather_unit_chunks=1 << 30),                   # one unit per bin: fused path
-    dict(gather_unit_chunks=1, gather_cluster=1),       # every chunk its own unit
-    dict(gather_unit_chunks=3, gather_cluster=4),
+    dict(gather_unit_chunks=1, gather_cluster=1),       # every window its own unit
+    dict(gather_unit_chunks=3, gather_cluster=4),       # CTAs of a cluster without windows
     dict(gather_unit_chunks=1 << 30, gather_cluster=8),
     dict(scatter_unit_groups=1),                        # every 4-update group its own unit
     dict(scatter_unit_groups=7, gather_unit_chunks=5, gather_cluster=2),
     dict(canonical_gather=1),                           # decode the canonical bins' flags
     dict(canonical_gather=1, gather_unit_chunks=1 << 30),
     dict(canonical_gather=1, gather_unit_chunks=2, gather_cluster=1),
-    dict(gather_runs=1),                                # register runs of equal destinations
-    dict(gather_runs=1, gather_unit_chunks=1 << 30),
-    dict(gather_runs=1, gather_unit_chunks=1, gather_cluster=1),
-    dict(gather_runs=2),                                # one shared-memory add per ID
+    dict(gather_windows=2),                             # bank-spread 256-ID chunks, atomics
+    dict(gather_windows=2, gather_runs=1),              # ... with register runs
+    dict(gather_windows=2, gather_runs=1, gather_unit_chunks=1 << 30),
+    dict(gather_windows=2, gather_runs=1, gather_unit_chunks=1, gather_cluster=1),
+    dict(gather_windows=2, gather_runs=2),              # ... one shared-memory add per ID
 ]
 
 
@@ -325,9 +326,12 @@ def test_work_decompositions_match_oracle(name, opts, mode):
         assert info["gather_units"] >= k and info["scatter_units"] >= k
         assert info["fused_ok"] == (info["gather_units"] == k)
         assert info["canonical_gather"] == opts.get("canonical_gather", 0)
+        assert info["gather_windows"] == (not opts.get("canonical_gather") and opts.get("gather_windows", 0) != 2)
         assert info["merged_adds"] <= int(rp[-1])
         if info["canonical_gather"]:
             assert info["gather_runs"] == 0 and info["merged_adds"] == 0
+        elif info["gather_windows"]:
+            assert info["gather_runs"] == 1 and info["num_windows"] >= 1
         elif opts.get("gather_runs"):
             assert info["gather_runs"] == (opts["gather_runs"] == 1)
         else:
@@ -365,6 +369,10 @@ def test_bad_cluster_option_rejected():
     with pytest.raises(pcpm.PcpmError) as e:
         pcpm.PNG.from_host(rp, col, q, gather_runs=3)
     assert e.value.code == -1
+    for bad in (dict(gather_windows=3), dict(gather_windows=1, canonical_gather=1)):
+        with pytest.raises(pcpm.PcpmError) as e:
+            pcpm.PNG.from_host(rp, col, q, **bad)
+        assert e.value.code == -1
 
 
 def test_hot_destinations_take_register_runs():
@@ -385,8 +393,14 @@ def test_hot_destinations_take_register_runs():
         pr, _, _ = g.pagerank(0.85, max_iters=5)
         assert l1(pr.cpu().numpy(), ref) <= L1_TOL
     rp, col = graphgen.random_graph(1 << 15, 1 << 18, seed=5)
-    with pcpm.PNG.from_host(rp, col, 1 << 15) as g:
+    with pcpm.PNG.from_host(rp, col, 1 << 15, gather_windows=2) as g:
         assert g.info["gather_runs"] == 0, g.info
+    for layout in (0, 2):  # both gather layouts with the hot destinations
+        rp, col = graphgen.csr_from_edges(n, src, dst)
+        with pcpm.PNG.from_host(rp, col, 1024, gather_windows=layout) as g:
+            assert g.info["gather_windows"] == (layout == 0)
+            pr, _, _ = g.pagerank(0.85, max_iters=5)
+            assert l1(pr.cpu().numpy(), ref) <= L1_TOL
 
 
 def test_handles_with_different_partition_sizes_coexist():

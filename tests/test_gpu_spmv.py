@@ -63,7 +63,9 @@ def test_weighted_bins_bit_exact(name):
 
 
 DECOMP = [dict(), dict(gather_unit_chunks=1, gather_cluster=1), dict(gather_unit_chunks=3, gather_cluster=4),
-          dict(gather_runs=1), dict(gather_runs=2), dict(gather_unit_chunks=1 << 30, gather_cluster=8)]
+          dict(gather_unit_chunks=1 << 30, gather_cluster=8), dict(gather_windows=2),
+          dict(gather_windows=2, gather_runs=1), dict(gather_windows=2, gather_runs=2),
+          dict(gather_windows=2, gather_unit_chunks=1, gather_cluster=1)]
 
 
 @pytest.mark.parametrize("opts", DECOMP, ids=lambda o: ",".join(f"{k}={v}" for k, v in o.items()) or "auto")
