@@ -64,7 +64,7 @@ constexpr uint32_t kHubSlots = 2 * kGatherWarps;
 // with a header of kWinHdrWords words: the kWinWarps + 1 group offsets as
 // 16-bit values.
 constexpr uint32_t kWin = 4096;
-constexpr int kWinWarps = 16;
+constexpr int kWinWarps = 12;
 constexpr uint32_t kWinHubs = 8;
 constexpr uint32_t kWinHdrWords = 16;
 constexpr uint32_t kWinStride = kWinHdrWords + kWin;  // words per window in the layout array

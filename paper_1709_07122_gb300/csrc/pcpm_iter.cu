@@ -1310,7 +1310,7 @@ __global__ void __launch_bounds__(kWinThreads, 1) gather_win_kernel(const Gather
                 const uint32_t cnt = lane < longer ? rounds : rounds - 1;
                 float run = 0.0f;
                 uint32_t last = kWinEndBit;  // word of the lane's last ID (none: no unfinished run)
-                constexpr uint32_t kU = 4;
+                constexpr uint32_t kU = 3;
                 for (uint32_t r0 = 0; r0 < rounds; r0 += kU) {
                     uint32_t wv[kU];
                     float v[kU];
