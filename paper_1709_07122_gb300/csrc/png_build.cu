@@ -1057,9 +1057,17 @@ __global__ void __launch_bounds__(1024) bin_owner_kernel(const uint32_t* __restr
     for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) deg[i] = 0;
     __syncthreads();
     const uint32_t e0 = bin_e[p], e1 = bin_e[p + 1];
-    for (uint32_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-        const uint32_t loc = (__ldcs(dest + e) & kIdMask) - base;
-        if (loc < len) atomicAdd(&deg[loc], 1u);
+    constexpr uint32_t kIlp = 4;  // independent loads in flight per thread
+    for (uint32_t e = e0 + threadIdx.x; e < e1; e += kIlp * blockDim.x) {
+        uint32_t loc[kIlp];
+#pragma unroll
+        for (uint32_t j = 0; j < kIlp; ++j) {
+            const uint32_t x = e + j * blockDim.x;
+            loc[j] = x < e1 ? (__ldcs(dest + x) & kIdMask) - base : 0xFFFFFFFFu;
+        }
+#pragma unroll
+        for (uint32_t j = 0; j < kIlp; ++j)
+            if (loc[j] < len) atomicAdd(&deg[loc[j]], 1u);
     }
     __syncthreads();
     for (uint32_t h = 0; h < kWinHubs; ++h) {
@@ -1110,196 +1118,255 @@ __global__ void bin_window_counts_kernel(const uint32_t* __restrict__ bin_e, uin
 }
 
 constexpr int kWlThreads = 256;
-constexpr uint32_t kWlPer = kWin / kWlThreads;  // consecutive positions per thread
-constexpr uint32_t kWlBuckets = kWinWarps * 32; // (owner warp, bank)
+constexpr int kWlWarps = kWlThreads / 32;
+constexpr uint32_t kWlSpan = kWin / kWlWarps;   // consecutive items per warp
+constexpr uint32_t kWlSteps = kWlSpan / 32;     // 32-item steps per warp
+constexpr uint32_t kWlOwnerBuckets = 32 + kWinHubs;   // per owner: 32 banks, then one per hub
+constexpr uint32_t kWlBuckets = kWinWarps * kWlOwnerBuckets;
+constexpr uint32_t kWlSlotBins = (PCPM_MAX_PART_SIZE + kWinWarps * kWinHubs + 31) / 32;  // slot >> 5
+constexpr uint32_t kWlMaxBins = kWlSlotBins > kWlBuckets ? kWlSlotBins : kWlBuckets;
+static_assert(kWin <= 4096 && kWin % (32 * kWlWarps) == 0, "12-bit positions, whole steps per warp");
 
-// One CTA per window of kWin consecutive IDs of one bin. Every ID gets its
-// update index (flagged IDs before it, inclusive, minus one: Algorithm 4's
-// pointer), its owner warp and slot (hub IDs: the i-th hub ID of the window
-// goes to warp i mod kWinWarps, slot q + warp * kWinHubs + hub), then a
-// counting sort by (owner, bank of the slot) and, inside each bucket, an
-// insertion sort by (slot, position) give every owner's group in (bank, slot,
-// position) order. Group w's sorted position s goes to lane l, round r of
-// that warp's pass: with R = ceil(N_w / 32) rounds, the first N_w - 32 (R - 1)
-// lanes take R consecutive positions and the others R - 1, stored at r * 32 +
-// l. The end bit marks the last position of a run of equal slots. The CTA
-// also checks every word against the partition and the update slice
-// (stats[1]) and counts IDs whose run continues (stats[0]).
-__global__ void __launch_bounds__(kWlThreads) window_layout_kernel(
+// Dynamic shared memory of window_layout_kernel.
+constexpr size_t kWlSmemSk = 0;                                          // u32[kWin]
+constexpr size_t kWlSmemTmp = kWlSmemSk + kWin * 4;                      // u32[kWin]
+constexpr size_t kWlSmemOff = kWlSmemTmp + kWin * 4;                     // u16[kWin]
+constexpr size_t kWlSmemCnt = kWlSmemOff + kWin * 2;                     // u16[kWlWarps][kWlMaxBins]
+constexpr size_t kWlSmemStart = kWlSmemCnt + ((kWlWarps * kWlMaxBins * 2 + 15) & ~(size_t)15);  // u32[kWlMaxBins + 1]
+constexpr size_t kWlSmemBytes = kWlSmemStart + (kWlMaxBins + 1) * 4;
+
+// One stable counting-sort pass over the window's items. Each thread holds
+// kWlSteps items in warp-major order (warp w, step i, lane l holds item
+// w * kWlSpan + 32 i + l, and an item's index is its order):
+// out[start(key) + items of the same key before it] = val. Keys >= kBins
+// mark absent items. Per-warp ranks come from match_any, then each bin's
+// counts are turned into prefixes over the warps and a block scan gives the
+// bin starts.
+template <uint32_t kBins>
+__device__ __forceinline__ void stable_pass(const uint32_t (&key)[kWlSteps], const uint32_t (&val)[kWlSteps],
+                                            uint32_t* out, uint16_t* wcnt, uint32_t* start, uint32_t* sh32) {
+    static_assert(kBins <= kWlMaxBins, "bins");
+    const uint32_t t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const uint32_t lt = lanemask_lt();
+    for (uint32_t x = t; x < kWlWarps * kBins; x += kWlThreads) wcnt[x] = 0;
+    __syncthreads();
+    uint16_t* mine = wcnt + warp * kBins;
+    uint32_t rank[kWlSteps];
+#pragma unroll
+    for (uint32_t i = 0; i < kWlSteps; ++i) {
+        const uint32_t k = key[i];
+        const uint32_t peers = __match_any_sync(0xffffffffu, k);
+        const uint32_t base = k < kBins ? (uint32_t)mine[k] : 0u;
+        rank[i] = base + __popc(peers & lt);
+        __syncwarp();
+        if (k < kBins && lane == (uint32_t)(__ffs(peers) - 1)) mine[k] = (uint16_t)(base + __popc(peers));
+        __syncwarp();
+    }
+    __syncthreads();
+    constexpr uint32_t kPer = (kBins + kWlThreads - 1) / kWlThreads;
+    uint32_t c[kPer], sum = 0;
+#pragma unroll
+    for (uint32_t j = 0; j < kPer; ++j) {
+        const uint32_t b = kPer * t + j;
+        uint32_t tot = 0;
+        if (b < kBins)
+            for (uint32_t w = 0; w < (uint32_t)kWlWarps; ++w) {
+                const uint32_t x = wcnt[w * kBins + b];
+                wcnt[w * kBins + b] = (uint16_t)tot;
+                tot += x;
+            }
+        c[j] = tot;
+        sum += tot;
+    }
+    uint32_t all = 0;
+    uint32_t x = block_exclusive_scan(sum, &all, sh32);
+#pragma unroll
+    for (uint32_t j = 0; j < kPer; ++j) {
+        const uint32_t b = kPer * t + j;
+        if (b < kBins) start[b] = x;
+        x += c[j];
+    }
+    if (t == 0) start[kBins] = all;
+    __syncthreads();
+#pragma unroll
+    for (uint32_t i = 0; i < kWlSteps; ++i)
+        if (key[i] < kBins) out[start[key[i]] + mine[key[i]] + rank[i]] = val[i];
+    __syncthreads();
+}
+
+// One CTA per window of kWin consecutive IDs of one bin (each CTA takes a
+// contiguous range of windows, so the bin's owner table is rebuilt only when
+// the bin changes). Warp w reads IDs [w * kWlSpan, +kWlSpan) of the window in
+// steps of 32; ballots give every ID its update index (flagged IDs before it,
+// inclusive, minus one: Algorithm 4's pointer) and the hub IDs their rank.
+// Every ID gets its owner warp and slot (the i-th hub ID of the window goes to
+// warp i mod kWinWarps, slot q + warp * kWinHubs + hub). Two stable counting
+// sorts, first by slot / 32 and then by bucket (per owner, the 32 banks of
+// the slot, then one bucket per hub), leave every owner's group in (bank,
+// slot, position) order with its hub IDs last. Group w's sorted position s
+// goes to lane l, round r of that warp's pass: with R = ceil(N_w / 32)
+// rounds, the first N_w - 32 (R - 1) lanes take R consecutive positions and
+// the others R - 1, stored at r * 32 + l. The end bit marks the last position
+// of a run of equal slots. The CTA checks every word against the partition
+// and the update slice (stats[1]) and counts IDs whose run continues
+// (stats[0]).
+__global__ void __launch_bounds__(kWlThreads, 2) window_layout_kernel(
     const uint32_t* __restrict__ dest, const uint32_t* __restrict__ bin_e, const uint32_t* __restrict__ win_start,
     uint32_t k, const uint32_t* __restrict__ chunk_base, const uint32_t* __restrict__ whubs,
     const uint32_t* __restrict__ bnd, uint32_t n, uint32_t q, uint64_t nwin, uint32_t upd_bytes,
     uint32_t* __restrict__ words, uint4* __restrict__ desc, unsigned long long* __restrict__ stats,
     const float* __restrict__ wdest, float* __restrict__ wweight) {
-    __shared__ uint32_t s_sk[kWin];      // sorted: slot << 12 | position
-    __shared__ uint32_t s_out[kWin];     // words in storage order
-    __shared__ uint16_t s_off[kWin];     // by position: update offset in the slice
-    __shared__ uint32_t s_cnt[kWlBuckets];
-    __shared__ uint32_t s_start[kWlBuckets + 1];
+    extern __shared__ __align__(16) unsigned char wl_smem[];
+    uint32_t* s_sk = reinterpret_cast<uint32_t*>(wl_smem + kWlSmemSk);    // sorted: slot << 12 | position
+    uint32_t* s_tmp = reinterpret_cast<uint32_t*>(wl_smem + kWlSmemTmp);  // after the first pass
+    uint16_t* s_off = reinterpret_cast<uint16_t*>(wl_smem + kWlSmemOff);  // by position: offset in the slice
+    uint16_t* s_wcnt = reinterpret_cast<uint16_t*>(wl_smem + kWlSmemCnt);
+    uint32_t* s_start = reinterpret_cast<uint32_t*>(wl_smem + kWlSmemStart);
     __shared__ uint8_t s_own[1024];
     __shared__ uint32_t s_hub[kWinHubs];
+    __shared__ uint32_t s_bnd[kWinWarps + 1];
     __shared__ uint32_t s_goff[kWinWarps + 1];
+    __shared__ uint32_t s_wtot[kWlWarps][2];
     __shared__ uint32_t sh32[32];
-    __shared__ uint32_t s_first, s_last;
-    static_assert(kWin <= 4096 && kWlPer * kWlThreads == kWin, "12-bit positions, kWlPer per thread");
-    const uint32_t t = threadIdx.x, lane = t & 31;
+    __shared__ uint32_t s_fb, s_first, s_last;
+    const uint32_t t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const uint32_t lt = lanemask_lt();
     const uint32_t align = 16u / upd_bytes;
     const uint32_t slice_cap = kWin + 2 * align;
     uint32_t nbad = 0, nmerged = 0;
-    for (uint64_t win = blockIdx.x; win < nwin; win += gridDim.x) {
+    const uint64_t per = (nwin + gridDim.x - 1) / gridDim.x;
+    const uint64_t wb0 = blockIdx.x * per;
+    const uint64_t wbeg = wb0 < nwin ? wb0 : nwin, wend = wbeg + per < nwin ? wbeg + per : nwin;
+    uint32_t cached = 0xFFFFFFFFu;
+    for (uint64_t win = wbeg; win < wend; ++win) {
         const uint32_t p = upper_bound_u32(win_start, 0, k + 1, (uint32_t)win) - 1;
         const uint32_t j = (uint32_t)win - win_start[p];
         const uint32_t P = bin_e[p] + j * kWin, Pend = min(P + kWin, bin_e[p + 1]);
         const uint32_t N = Pend - P;
         const uint32_t vbase = p * q, len = min(q, n - vbase);
-        const uint32_t* b = bnd + (size_t)p * (kWinWarps + 1);
-        const uint32_t nblk = b[kWinWarps];
-        for (uint32_t x = t; x < nblk; x += kWlThreads) s_own[x] = (uint8_t)(upper_bound_u32(b, 0, kWinWarps, x) - 1);
-        if (t < kWinHubs) s_hub[t] = whubs[(size_t)p * kWinHubs + t];
-        for (uint32_t x = t; x < kWlBuckets; x += kWlThreads) s_cnt[x] = 0;
-        // flagged IDs before P: the chunk's base plus the flags of its head
-        uint32_t fb = 0;
-        if (t < 32) {
+        if (p != cached) {  // the bin's hubs and owner table
+            if (t < kWinHubs) s_hub[t] = whubs[(size_t)p * kWinHubs + t];
+            if (t <= (uint32_t)kWinWarps) s_bnd[t] = bnd[(size_t)p * (kWinWarps + 1) + t];
+            __syncthreads();
+            const uint32_t nblk = s_bnd[kWinWarps];
+            for (uint32_t x = t; x < nblk; x += kWlThreads)
+                s_own[x] = (uint8_t)(upper_bound_u32(s_bnd, 0, kWinWarps, x) - 1);
+            cached = p;
+        }
+        if (warp == 0) {  // flagged IDs before P: the chunk's base plus the flags of its head
             const uint32_t cbase = P & ~(kChunk - 1);
             uint32_t run = chunk_base[P / kChunk];
             for (uint32_t x = cbase; x < P; x += 32) {
                 const uint32_t pos = x + lane;
                 run += __popc(__ballot_sync(0xffffffffu, pos < P && (dest[pos] >> 31)));
             }
-            fb = run;
+            if (lane == 0) s_fb = run;
         }
-        if (t == 0) s_first = fb;
-        __syncthreads();
-        fb = s_first;
-        // this thread's positions [t * kWlPer, +kWlPer): flags and hub IDs
-        uint32_t id[kWlPer];
-        uint32_t nflag = 0, nhub = 0;
+        // this warp's IDs: flags (inclusive within the warp) and hub ranks
+        uint32_t loc[kWlSteps], rel[kWlSteps], hx[kWlSteps];
+        uint32_t frun = 0, hrun = 0;
 #pragma unroll
-        for (uint32_t i = 0; i < kWlPer; ++i) {
-            const uint32_t pos = t * kWlPer + i;
-            id[i] = pos < N ? dest[P + pos] : 0u;
-            const uint32_t loc = (id[i] & kIdMask) - vbase;
-            nflag += pos < N ? id[i] >> 31 : 0u;
-            bool hub = false;
-#pragma unroll
-            for (uint32_t h = 0; h < kWinHubs; ++h) hub |= loc < len && loc == s_hub[h];
-            nhub += (pos < N && hub) ? 1u : 0u;
-        }
-        uint32_t tot = 0;
-        const uint32_t pre = block_exclusive_scan(nflag | (nhub << 16), &tot, sh32);
-        uint32_t fl = fb + (pre & 0xFFFFu), hr = pre >> 16;
-        // update index, owner, slot and bucket of each ID
-        uint32_t idx[kWlPer], slot[kWlPer], bkt[kWlPer];
-#pragma unroll
-        for (uint32_t i = 0; i < kWlPer; ++i) {
-            const uint32_t pos = t * kWlPer + i;
-            const uint32_t loc = (id[i] & kIdMask) - vbase;
-            fl += pos < N ? id[i] >> 31 : 0u;
-            idx[i] = fl - 1;
+        for (uint32_t i = 0; i < kWlSteps; ++i) {
+            const uint32_t pos = warp * kWlSpan + 32 * i + lane;
+            const bool valid = pos < N;
+            const uint32_t id = valid ? dest[P + pos] : 0u;
+            loc[i] = (id & kIdMask) - vbase;
             uint32_t h = kWinHubs;
 #pragma unroll
             for (uint32_t hh = 0; hh < kWinHubs; ++hh)
-                if (loc < len && loc == s_hub[hh] && h == kWinHubs) h = hh;
-            uint32_t o = 0;
-            if (h < kWinHubs) {
-                o = hr % kWinWarps;
-                slot[i] = q + o * kWinHubs + h;
-                hr += pos < N ? 1u : 0u;
-            } else {
-                if (pos < N && loc >= len) ++nbad;
-                o = loc < len ? s_own[loc >> 5] : 0u;
-                slot[i] = loc < len ? loc : 0u;
-            }
-            bkt[i] = o * 32 + (slot[i] & 31u);
-            if (pos == 0) s_first = idx[i];
-            if (pos + 1 == N) s_last = idx[i];
+                if (valid && loc[i] < len && loc[i] == s_hub[hh] && h == kWinHubs) h = hh;
+            const uint32_t bf = __ballot_sync(0xffffffffu, valid && (id >> 31));
+            const uint32_t bh = __ballot_sync(0xffffffffu, h < kWinHubs);
+            rel[i] = frun + __popc(bf & (lt | (1u << lane)));
+            hx[i] = h | ((hrun + __popc(bh & lt)) << 8);
+            frun += __popc(bf);
+            hrun += __popc(bh);
         }
-        __syncthreads();
-        const uint32_t us = N ? s_first & ~(align - 1) : 0u, ue = N ? (s_last + align) & ~(align - 1) : 0u;
-        if (N && ue - us > slice_cap) ++nbad;
-        uint32_t rank[kWlPer];
+        if (lane == 0) {
+            s_wtot[warp][0] = frun;
+            s_wtot[warp][1] = hrun;
+        }
+        __syncthreads();  // s_fb, s_own, warp totals
+        uint32_t fbase = 0, hbase = 0;
+        for (uint32_t w = 0; w < warp; ++w) {
+            fbase += s_wtot[w][0];
+            hbase += s_wtot[w][1];
+        }
+        const uint32_t fb0 = s_fb;  // the ID before P belongs to update fb0 - 1
+        uint32_t key[kWlSteps], val[kWlSteps];
 #pragma unroll
-        for (uint32_t i = 0; i < kWlPer; ++i) {
-            const uint32_t pos = t * kWlPer + i;
-            rank[i] = pos < N ? atomicAdd(&s_cnt[bkt[i]], 1u) : 0u;
+        for (uint32_t i = 0; i < kWlSteps; ++i) {
+            const uint32_t pos = warp * kWlSpan + 32 * i + lane;
+            const bool valid = pos < N;
+            rel[i] += fbase;  // update index - (fb0 - 1)
+            const uint32_t h = hx[i] & 0xFFu;
+            uint32_t sl;
+            if (h < kWinHubs) {
+                sl = q + ((hbase + (hx[i] >> 8)) % kWinWarps) * kWinHubs + h;
+            } else {
+                const bool in = loc[i] < len;
+                if (valid && !in) ++nbad;
+                sl = in ? loc[i] : 0u;
+            }
+            if (pos == 0) s_first = fb0 - 1 + rel[i];
+            if (valid && pos + 1 == N) s_last = fb0 - 1 + rel[i];
+            key[i] = valid ? sl >> 5 : kWlSlotBins;
+            val[i] = (sl << 12) | pos;
+        }
+        stable_pass<kWlSlotBins>(key, val, s_tmp, s_wcnt, s_start, sh32);
+        const uint32_t us = N ? s_first & ~(align - 1) : 0u, ue = N ? (s_last + align) & ~(align - 1) : 0u;
+        if (t == 0 && N && ue - us > slice_cap) ++nbad;
+#pragma unroll
+        for (uint32_t i = 0; i < kWlSteps; ++i) {
+            const uint32_t pos = warp * kWlSpan + 32 * i + lane;
             if (pos < N) {
-                const uint32_t off = idx[i] - us;
+                const uint32_t off = fb0 - 1 + rel[i] - us;
                 if (off >= slice_cap) ++nbad;
                 s_off[pos] = (uint16_t)min(off, kWinOffMask);
             }
         }
-        __syncthreads();
-        {  // bucket starts: kBPer consecutive buckets per thread
-            constexpr uint32_t kBPer = (kWlBuckets + kWlThreads - 1) / kWlThreads;
-            uint32_t c[kBPer], sum = 0;
+        // second pass, in the first pass's order: by bucket
 #pragma unroll
-            for (uint32_t i = 0; i < kBPer; ++i) {
-                const uint32_t b = kBPer * t + i;
-                c[i] = b < kWlBuckets ? s_cnt[b] : 0u;
-                sum += c[i];
-            }
-            uint32_t all = 0;
-            uint32_t x = block_exclusive_scan(sum, &all, sh32);
-#pragma unroll
-            for (uint32_t i = 0; i < kBPer; ++i) {
-                const uint32_t b = kBPer * t + i;
-                if (b < kWlBuckets) s_start[b] = x;
-                x += c[i];
-            }
-            if (t == 0) s_start[kWlBuckets] = all;
+        for (uint32_t i = 0; i < kWlSteps; ++i) {
+            const uint32_t item = warp * kWlSpan + 32 * i + lane;
+            const bool valid = item < N;
+            const uint32_t v = valid ? s_tmp[item] : 0u, sl = v >> 12;
+            uint32_t b = kWlBuckets;
+            if (valid)
+                b = sl >= q ? ((sl - q) / kWinHubs) * kWlOwnerBuckets + 32 + (sl - q) % kWinHubs
+                            : (uint32_t)s_own[sl >> 5] * kWlOwnerBuckets + (sl & 31u);
+            key[i] = b;
+            val[i] = v;
         }
+        stable_pass<kWlBuckets>(key, val, s_sk, s_wcnt, s_start, sh32);
+        if (t <= (uint32_t)kWinWarps) s_goff[t] = t < (uint32_t)kWinWarps ? s_start[kWlOwnerBuckets * t] : N;
         __syncthreads();
-#pragma unroll
-        for (uint32_t i = 0; i < kWlPer; ++i) {
-            const uint32_t pos = t * kWlPer + i;
-            if (pos < N) s_sk[s_start[bkt[i]] + rank[i]] = (slot[i] << 12) | pos;
-        }
-        __syncthreads();
-        for (uint32_t bb = t; bb < kWlBuckets; bb += kWlThreads) {  // (slot, position) order in each bucket
-            const uint32_t g0 = s_start[bb], g1 = s_start[bb + 1];
-            for (uint32_t x = g0 + 1; x < g1; ++x) {
-                const uint32_t v = s_sk[x];
-                uint32_t y = x;
-                while (y > g0 && s_sk[y - 1] > v) {
-                    s_sk[y] = s_sk[y - 1];
-                    --y;
-                }
-                s_sk[y] = v;
-            }
-        }
-        if (t <= (uint32_t)kWinWarps) s_goff[t] = t < (uint32_t)kWinWarps ? s_start[32 * t] : N;
-        __syncthreads();
-        // deal every group lane by lane; words in storage order
-        for (uint32_t s = t; s < N; s += kWlThreads) {
-            const uint32_t w = upper_bound_u32(s_goff, 0, kWinWarps, s) - 1;
-            const uint32_t g0 = s_goff[w], Nw = s_goff[w + 1] - g0, loc_s = s - g0;
-            const uint32_t R = (Nw + 31) / 32, full = Nw - 32 * (R - 1);
-            uint32_t l, r;
-            if (loc_s < full * R) {
-                l = loc_s / R;
-                r = loc_s % R;
-            } else {
-                const uint32_t x = loc_s - full * R;
-                l = full + x / (R - 1);
-                r = x % (R - 1);
-            }
-            const uint32_t sk = s_sk[s], sl = sk >> 12, pos = sk & 4095u;
-            const bool end = loc_s + 1 == Nw || (s_sk[s + 1] >> 12) != sl;
-            nmerged += end ? 0u : 1u;
-            const uint32_t st = g0 + r * 32 + l;
-            s_out[st] = sl | ((uint32_t)s_off[pos] << kWinOffShift) | (end ? kWinEndBit : 0u);
-            if (wweight) wweight[win * kWinStride + kWinHdrWords + st] = wdest[P + pos];
-        }
-        __syncthreads();
+        // deal every group lane by lane: one (group, lane) pair per thread
         uint32_t* out = words + win * kWinStride;
+        for (uint32_t pr = t; pr < (uint32_t)kWinWarps * 32; pr += kWlThreads) {
+            const uint32_t w = pr >> 5, l = pr & 31;  // w is warp-uniform
+            const uint32_t g0 = s_goff[w], Nw = s_goff[w + 1] - g0;
+            if (Nw == 0) continue;
+            const uint32_t R = (Nw + 31) / 32, longer = Nw - 32 * (R - 1);
+            const uint32_t cnt = l < longer ? R : R - 1;
+            const uint32_t st0 = l < longer ? l * R : longer * R + (l - longer) * (R - 1);
+            for (uint32_t r = 0; r < cnt; ++r) {
+                const uint32_t s = g0 + st0 + r;
+                const uint32_t sk = s_sk[s], sl = sk >> 12, pos = sk & 4095u;
+                const bool end = st0 + r + 1 == Nw || (s_sk[s + 1] >> 12) != sl;
+                nmerged += end ? 0u : 1u;
+                const uint32_t o = kWinHdrWords + g0 + r * 32 + l;
+                out[o] = sl | ((uint32_t)s_off[pos] << kWinOffShift) | (end ? kWinEndBit : 0u);
+                if (wweight) wweight[win * kWinStride + o] = wdest[P + pos];
+            }
+        }
         if (t < kWinHdrWords) {
             const uint32_t a0 = 2 * t, a1 = 2 * t + 1;
-            const uint32_t v0 = a0 <= (uint32_t)kWinWarps ? s_goff[a0] : 0u, v1 = a1 <= (uint32_t)kWinWarps ? s_goff[a1] : 0u;
+            const uint32_t v0 = a0 <= (uint32_t)kWinWarps ? s_goff[a0] : 0u;
+            const uint32_t v1 = a1 <= (uint32_t)kWinWarps ? s_goff[a1] : 0u;
             out[t] = v0 | (v1 << 16);
         }
-        for (uint32_t x = t; x < N; x += kWlThreads) out[kWinHdrWords + x] = s_out[x];
-        if (t == 0)
-            desc[win] = make_uint4(us, (ue - us) * upd_bytes, (kWinHdrWords + ((N + 3) & ~3u)) * 4u, N);
+        if (t == 0) desc[win] = make_uint4(us, (ue - us) * upd_bytes, (kWinHdrWords + ((N + 3) & ~3u)) * 4u, N);
         __syncthreads();
     }
     nmerged = __reduce_add_sync(0xffffffffu, nmerged);
@@ -1586,7 +1653,9 @@ int build_png(pcpm_png* g, const uint32_t* row_ptr, const uint32_t* col, const p
         BCK(tmp.alloc(&lstats, 2));
         BCK(cudaMemsetAsync(lstats, 0, 2 * sizeof(*lstats), s));
         if (nw) {
-            window_layout_kernel<<<(unsigned)std::min<uint64_t>(nw, (uint64_t)sms * 8), kWlThreads, 0, s>>>(
+            BCK(cudaFuncSetAttribute(window_layout_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kWlSmemBytes));
+            window_layout_kernel<<<(unsigned)std::min<uint64_t>(nw, (uint64_t)sms * 8), kWlThreads, kWlSmemBytes, s>>>(
                 g->dest, g->bin_e, g->win_start, k, g->chunk_base, g->whubs, bnd, n, q, nw, g->upd_bytes, g->wwords,
                 g->wdesc, lstats, g->wdest, g->wweight);
             BCK(cudaGetLastError());
