@@ -231,22 +231,28 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def recorded_traffic(kernel: str, workload: str):
-    """DRAM bytes per launch from a committed ncu summary, valid only while the
-    kernel source is unchanged since the capture (sha256 recorded there)."""
+def recorded_traffic(kernel: str, layout: str, algorithmic: int):
+    """DRAM bytes per launch of `kernel`: the ratio of DRAM bytes to
+    algorithmic bytes from a committed single-kernel ncu capture (on a smaller
+    graph of the same family, profiles/traffic.json) times this workload's
+    algorithmic bytes. None unless the kernel sources are unchanged since the
+    capture and the capture is of the same gather layout."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
-        return None
+        return None, None
     with open(path) as f:
         rec = json.load(f)
     for name, sha in rec.get("source_sha256", {}).items():
         src = os.path.join(ROOT, "paper_1709_07122_gb300", "csrc", name)
         if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest() != sha:
-            return None
+            return None, None
     entry = rec.get("kernels", {}).get(kernel)
-    if not entry or rec.get("workload") != workload:
-        return None
-    return entry.get("dram_bytes_per_launch")
+    if not entry or entry.get("layout") != layout:
+        return None, None
+    ratio = entry["dram_bytes"] / entry["algorithmic_bytes"]
+    note = "ncu DRAM/algorithmic ratio %.3f from a single-kernel capture on %s, times this workload's " \
+           "algorithmic bytes" % (ratio, entry["capture_workload"])
+    return int(round(ratio * algorithmic)), note
 
 
 # ---------------------------------------------------------------- CPU side
@@ -548,9 +554,10 @@ def run_ours(a):
     achieved = ab[dom] / (dom_ms * 1e-3) / 1e9
     wl = workload_name(a)
     kname = dom + (" (fused: gather, apply, next scatter)" if a.mode == "fused" and dom == "gather_apply" else "")
+    traffic, traffic_note = recorded_traffic(dom, a.gather_layout, ab[dom])
     roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved,
                 "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
-                "traffic": recorded_traffic(dom, wl), "algorithmic_bytes": ab[dom]}
+                "traffic": traffic, "traffic_source": traffic_note, "algorithmic_bytes": ab[dom]}
     iter_bytes = sum(ab.values())
 
     # The other iteration form, timed the same way: two-phase gives the
