@@ -52,7 +52,8 @@ def build(force: bool = False) -> str:
     """Compiles pcpm_oracle.c into a shared library next to it."""
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-        subprocess.run(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"], check=True)
+        subprocess.run(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread", "-o", tmp, _SRC, "-lm"],
+                       check=True)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -66,6 +67,13 @@ def _load():
             lib.oracle_pagerank.argtypes = [ctypes.c_uint32, _u32p, _u32p, ctypes.c_double, ctypes.c_int,
                                             ctypes.c_int, vp, vp, vp, vp]
             lib.oracle_pagerank.restype = ctypes.c_int
+            lib.oracle_pagerank_mt.argtypes = [ctypes.c_uint32, _u32p, _u32p, ctypes.c_double, ctypes.c_int,
+                                               ctypes.c_int, vp, vp, vp, vp, ctypes.c_int]
+            lib.oracle_pagerank_mt.restype = ctypes.c_int
+            lib.oracle_pull_step_mt.argtypes = [ctypes.c_uint32, _u32p, _u32p, _u32p, ctypes.c_double,
+                                                ctypes.c_double, ctypes.c_uint32, ctypes.c_uint32, _f64p, _f64p,
+                                                ctypes.c_int]
+            lib.oracle_pull_step_mt.restype = ctypes.c_double
             lib.oracle_in_adjacency.argtypes = [ctypes.c_uint32, _u32p, _u32p, _u32p, _u32p]
             lib.oracle_in_adjacency.restype = None
             lib.oracle_dangling_mass.argtypes = [ctypes.c_uint32, _u32p, _f64p]
@@ -105,12 +113,19 @@ def _ptr(a):
     return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
 
 
+def host_threads() -> int:
+    """Host threads the oracle uses when asked for all cores."""
+    return max(1, len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1))
+
+
 def pagerank(row_ptr, col, d: float = 0.85, iters: int = 20, x0=None, dangling: str = "uniform",
-             history: bool = False):
+             history: bool = False, threads: int = 1):
     """Iterates Eq. 1 ``iters`` times from ``x0`` (uniform 1/n if None).
 
     Returns a dict with ``x`` (final vector), ``resid`` (L1 change per
-    iteration) and, if ``history``, ``hist`` of shape (iters+1, n)."""
+    iteration) and, if ``history``, ``hist`` of shape (iters+1, n). With
+    ``threads`` > 1 each step runs on that many threads over contiguous
+    destination ranges: the same vectors, residuals up to FP64 reassociation."""
     if dangling not in ("uniform", "leak"):
         raise ValueError("dangling must be 'uniform' or 'leak'")
     lib = _load()
@@ -122,8 +137,8 @@ def pagerank(row_ptr, col, d: float = 0.85, iters: int = 20, x0=None, dangling: 
     hist = np.empty((iters + 1, n), dtype=np.float64) if history else None
     x = np.empty(n, dtype=np.float64)
     resid = np.empty(max(iters, 1), dtype=np.float64)
-    rc = lib.oracle_pagerank(n, row_ptr, col, float(d), 1 if dangling == "uniform" else 0, int(iters),
-                             _ptr(x0a), _ptr(hist), _ptr(x), _ptr(resid))
+    rc = lib.oracle_pagerank_mt(n, row_ptr, col, float(d), 1 if dangling == "uniform" else 0, int(iters),
+                                _ptr(x0a), _ptr(hist), _ptr(x), _ptr(resid), int(threads))
     if rc != 0:
         raise MemoryError("oracle_pagerank could not allocate")
     out = {"x": x, "resid": resid[:iters]}
@@ -158,6 +173,18 @@ class Pull:
         dmass = self.dangling_mass(x) if dangling == "uniform" else 0.0
         return lib.oracle_pull_step(self.n, self.row_ptr, self.in_start, self.in_src, float(d), dmass,
                                     int(v_begin), int(v_end), x, y)
+
+    def step_all(self, x, y, d: float = 0.85, dangling: str = "uniform", threads: int = 1, v_begin: int = 0,
+                 v_end=None, dmass=None) -> float:
+        """y[v] = Eq. 1 applied to x for v in [v_begin, v_end) (all nodes by
+        default) on ``threads`` threads over contiguous pieces of the range;
+        returns the L1 change over it. ``dmass``: the dangling mass of x, if
+        already known."""
+        v_end = self.n if v_end is None else v_end
+        if dmass is None:
+            dmass = self.dangling_mass(x) if dangling == "uniform" else 0.0
+        return _load().oracle_pull_step_mt(self.n, self.row_ptr, self.in_start, self.in_src, float(d), float(dmass),
+                                           int(v_begin), int(v_end), x, y, int(threads))
 
 
 def png(row_ptr, col, q: int):

@@ -17,6 +17,13 @@
  *                       mass is spread uniformly over all nodes (default) or
  *                       it leaks, as Eq. 1 literally does.
  *   oracle_pagerank     oracle_pull_step over all nodes, iterated.
+ *   oracle_pull_step_mt oracle_pull_step over all nodes with the destination
+ *                       range cut into `threads` contiguous pieces, one POSIX
+ *                       thread each (every y[v] is computed exactly as in the
+ *                       sequential step; only the order in which the pieces'
+ *                       L1 sums are added differs). oracle_pagerank_mt
+ *                       iterates it. They exist to time the oracle on all host
+ *                       cores and to make full-size checks finish in seconds.
  *   oracle_png_count    first scan of the PNG construction (Sec. 3.3): for each
  *                       source partition p and destination partition p', the
  *                       number of nodes of p with at least one out-neighbour in
@@ -44,6 +51,7 @@
  * sorted ascending.
  */
 #include <math.h>
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -96,12 +104,59 @@ double oracle_pull_step(uint32_t n, const uint32_t* row_ptr, const uint32_t* in_
     return r;
 }
 
-/* Eq. 1 iterated `iters` times from x0 (uniform 1/n when x0 is NULL).
+struct pull_piece {
+    uint32_t n;
+    const uint32_t *row_ptr, *in_start, *in_src;
+    double d, dangling;
+    uint32_t v_begin, v_end;
+    const double* x;
+    double* y;
+    double r;
+};
+
+static void* pull_piece_run(void* arg) {
+    struct pull_piece* a = (struct pull_piece*)arg;
+    a->r = oracle_pull_step(a->n, a->row_ptr, a->in_start, a->in_src, a->d, a->dangling, a->v_begin, a->v_end,
+                            a->x, a->y);
+    return NULL;
+}
+
+/* oracle_pull_step over the destinations [v_begin, v_end) on `threads`
+ * threads (contiguous pieces of the range); the pieces' L1 sums are added in
+ * range order. Returns the L1 change over the range. */
+double oracle_pull_step_mt(uint32_t n, const uint32_t* row_ptr, const uint32_t* in_start, const uint32_t* in_src,
+                           double d, double dangling, uint32_t v_begin, uint32_t v_end, const double* x, double* y,
+                           int threads) {
+    if (threads < 1) threads = 1;
+    if (threads > 512) threads = 512;
+    struct pull_piece pieces[512];
+    pthread_t tid[512];
+    int started[512];
+    for (int i = 0; i < threads; ++i) {
+        const uint64_t len = v_end > v_begin ? (uint64_t)(v_end - v_begin) : 0;
+        struct pull_piece a = {n, row_ptr, in_start, in_src, d, dangling,
+                               v_begin + (uint32_t)(len * i / threads), v_begin + (uint32_t)(len * (i + 1) / threads),
+                               x, y, 0.0};
+        pieces[i] = a;
+    }
+    for (int i = 1; i < threads; ++i) started[i] = pthread_create(&tid[i], NULL, pull_piece_run, &pieces[i]) == 0;
+    pull_piece_run(&pieces[0]);
+    double r = pieces[0].r;
+    for (int i = 1; i < threads; ++i) {
+        if (started[i]) pthread_join(tid[i], NULL);
+        else pull_piece_run(&pieces[i]); /* run it here instead */
+        r += pieces[i].r;
+    }
+    return r;
+}
+
+/* Eq. 1 iterated `iters` times from x0 (uniform 1/n when x0 is NULL), the
+ * pull step on `threads` threads (oracle_pagerank: one).
  * x_hist, when not NULL, receives (iters+1) vectors of n doubles: x_0 .. x_iters.
  * resid[i-1] = sum_v |x_i(v) - x_{i-1}(v)|. Returns 0, or -1 on allocation failure. */
-int oracle_pagerank(uint32_t n, const uint32_t* row_ptr, const uint32_t* col, double d,
-                    int dangling_uniform, int iters, const double* x0,
-                    double* x_hist, double* x_out, double* resid) {
+int oracle_pagerank_mt(uint32_t n, const uint32_t* row_ptr, const uint32_t* col, double d,
+                       int dangling_uniform, int iters, const double* x0,
+                       double* x_hist, double* x_out, double* resid, int threads) {
     uint64_t m = row_ptr[n];
     uint32_t* in_start = (uint32_t*)malloc(((size_t)n + 1) * sizeof(uint32_t));
     uint32_t* in_src = (uint32_t*)malloc((size_t)(m ? m : 1) * sizeof(uint32_t));
@@ -116,7 +171,8 @@ int oracle_pagerank(uint32_t n, const uint32_t* row_ptr, const uint32_t* col, do
     if (x_hist) memcpy(x_hist, x, (size_t)n * sizeof(double));
     for (int it = 1; it <= iters; ++it) {
         double dangling = dangling_uniform ? oracle_dangling_mass(n, row_ptr, x) : 0.0;
-        double r = oracle_pull_step(n, row_ptr, in_start, in_src, d, dangling, 0, n, x, y);
+        double r = threads > 1 ? oracle_pull_step_mt(n, row_ptr, in_start, in_src, d, dangling, 0, n, x, y, threads)
+                               : oracle_pull_step(n, row_ptr, in_start, in_src, d, dangling, 0, n, x, y);
         if (resid) resid[it - 1] = r;
         double* t = x; x = y; y = t;
         if (x_hist) memcpy(x_hist + (size_t)it * n, x, (size_t)n * sizeof(double));
@@ -124,6 +180,12 @@ int oracle_pagerank(uint32_t n, const uint32_t* row_ptr, const uint32_t* col, do
     if (x_out) memcpy(x_out, x, (size_t)n * sizeof(double));
     free(in_start); free(in_src); free(x); free(y);
     return 0;
+}
+
+int oracle_pagerank(uint32_t n, const uint32_t* row_ptr, const uint32_t* col, double d,
+                    int dangling_uniform, int iters, const double* x0,
+                    double* x_hist, double* x_out, double* resid) {
+    return oracle_pagerank_mt(n, row_ptr, col, d, dangling_uniform, iters, x0, x_hist, x_out, resid, 1);
 }
 
 /* First PNG scan. cnt_u and cnt_e are k*k arrays (row = source partition p,

@@ -178,3 +178,24 @@ def test_pull_step_ranges_compose():
     np.testing.assert_array_equal(y, full["x"])
     np.testing.assert_allclose(r, full["resid"][0], rtol=1e-12)
     assert pull.in_edges(0, n) == rp[-1]
+
+
+@pytest.mark.parametrize("threads", [2, 3, 8])
+@pytest.mark.parametrize("dangling", ["uniform", "leak"])
+def test_threaded_oracle_matches_sequential(threads, dangling):
+    # The threaded step computes every y[v] exactly as the sequential one
+    # (same in-neighbour order); only the pieces' L1 sums are added in
+    # another order. Ragged pieces: n is not a multiple of the thread count.
+    rp, col = graphgen.rmat(11, 8, seed=4242)
+    ref = oracle.pagerank(rp, col, D, iters=7, dangling=dangling, history=True)
+    got = oracle.pagerank(rp, col, D, iters=7, dangling=dangling, history=True, threads=threads)
+    np.testing.assert_array_equal(got["hist"], ref["hist"])
+    np.testing.assert_allclose(got["resid"], ref["resid"], rtol=1e-13, atol=0)
+    pull = oracle.Pull(rp, col)
+    x = ref["hist"][3]
+    y1, y2 = np.empty_like(x), np.empty_like(x)
+    r1 = pull.step(x, y1, D, dangling)
+    r2 = pull.step_all(x, y2, D, dangling, threads=threads)
+    np.testing.assert_array_equal(y1, y2)
+    assert abs(r1 - r2) <= 1e-13 * r1
+    assert oracle.host_threads() >= 1
