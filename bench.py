@@ -1,5 +1,5 @@
 #!/usr/bin/env python
-"""PCPM PageRank benchmark: per-iteration GTEPS on one GB300 (or N replicas).
+"""PCPM PageRank benchmark: per-iteration GTEPS on one GB300 (or N destination shards).
 
 Workload (default): RMAT scale 24 (16,777,216 nodes), edge factor 16,
 a, b, c = 0.57, 0.19, 0.19, random node labels, duplicates and self-loops
@@ -696,10 +696,114 @@ def run_ours(a):
     return 0
 
 
+def run_sharded(a):
+    """N > 1 ranks: one graph split by destination partitions over the ranks
+    (pcpm_build_shard), with NCCL exchanging the new ranks' slices and the two
+    FP64 sums after every iteration. The whole graph's edges are processed per
+    step whatever N is, so the scaling is strong."""
+    import torch
+    import torch.distributed as dist
+
+    import paper_1709_07122_gb300 as pcpm
+    from paper_1709_07122_gb300.sharded import ShardedPageRank
+
+    rank, world, local = dist_env()
+    if a.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    pcpm.build()
+    pcpm.lib()
+    rp, col = make_graph(a)  # the same seed on every rank: the same graph
+    n, m = rp.size - 1, int(rp[-1])
+    stream = torch.cuda.current_stream()
+
+    def tmax(x):
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    d_rp, d_col = pcpm.to_device_csr(rp, col)
+    torch.cuda.synchronize()
+    b0 = time.perf_counter()
+    solver = ShardedPageRank(d_rp, d_col, a.part_size, gather_windows=layout_option(a))
+    torch.cuda.synchronize()
+    build_ms = tmax((time.perf_counter() - b0) * 1e3)
+    del d_rp, d_col
+    info = solver.png.info
+    solver.reset()
+    for _ in range(a.warmup):
+        solver.step(a.d)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local).start()
+    time.sleep(0.2)
+    dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.time()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(a.steps):
+        solver.step(a.d)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    dist.barrier()
+    clocks = sampler.stop(t0, t1)
+    iter_ms = tmax(ev0.elapsed_time(ev1) / a.steps)
+
+    out = {
+        "metric": METRIC, "value": m / (iter_ms * 1e-3) / 1e9, "unit": "GTEPS", "n_gpus": world,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": iter_ms, "higher_is_better": True,
+        "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_name(a), "n": n, "m": m, "part_size": a.part_size,
+                   "k": info["num_partitions"], "d": a.d, "gather_layout": a.gather_layout,
+                   "parallelism": f"destination shards x{world} (NCCL all-gather of ranks, FP64 all-reduce)",
+                   "partition_cuts": [int(c) for c in solver.part_bounds],
+                   "l2": "no flush: each iteration moves > 129 MB per GPU"},
+        "build_ms": build_ms,
+        "clocks": clocks,
+        "gpu_launches": 3 * a.steps,
+    }
+    solver.close()
+
+    if not a.no_e2e:
+        e2e_iters = 20
+        prp = torch.empty(n + 1, dtype=torch.int32, pin_memory=True)
+        pcol = torch.empty(max(m, 1), dtype=torch.int32, pin_memory=True)
+        pout = torch.empty(n, dtype=torch.float32, pin_memory=True)
+        prp.numpy()[:] = rp.view(np.int32)
+        pcol.numpy()[:m] = col.view(np.int32)
+        walls = []
+        for rep in range(3):
+            dist.barrier()
+            e0 = time.perf_counter()
+            g_rp = prp.to("cuda", non_blocking=True)
+            g_col = pcol.to("cuda", non_blocking=True)
+            sv = ShardedPageRank(g_rp, g_col, a.part_size, gather_windows=layout_option(a))
+            del g_rp, g_col
+            x, _, _ = sv.pagerank(a.d, max_iters=e2e_iters)
+            pout.copy_(x)
+            torch.cuda.synchronize()
+            walls.append(time.perf_counter() - e0)
+            sv.close()
+        wall = tmax(statistics.median(walls))
+        out["e2e"] = {"value": m * e2e_iters / wall / 1e9, "unit": "GTEPS",
+                      "h2d_bytes_per_step": (n + 1 + m) * 4 / e2e_iters, "d2h_bytes_per_step": n * 4 / e2e_iters,
+                      "call": "ShardedPageRank from pinned host CSR: H2D, shard build, %d iterations with "
+                              "exchange, D2H ranks (every rank)" % e2e_iters, "wall_ms_per_call": wall * 1e3}
+    dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     a = parse_args()
     if a.impl == "reference":
         return run_reference(a)
+    if dist_env()[1] > 1:
+        return run_sharded(a)
     return run_ours(a)
 
 

@@ -101,8 +101,8 @@ typedef struct pcpm_png_info {
     uint32_t n;               /* |V| */
     uint32_t part_size;       /* q, nodes per partition (Sec. 3.1) */
     uint32_t num_partitions;  /* k = ceil(n / q) */
-    uint32_t reserved;
-    uint64_t num_edges;       /* m = |E| */
+    uint32_t shard_part_lo;   /* destination partitions the handle gathers: [shard_part_lo, */
+    uint64_t num_edges;       /* m = |E| (a shard: the edges into its partitions) */
     uint64_t num_updates;     /* |E'|: edges of the PNG = updates per iteration (Sec. 3.3) */
     double compression_ratio; /* r = |E| / |E'| (Sec. 4, Table params) */
     uint64_t device_bytes;    /* device memory held by the handle */
@@ -119,7 +119,7 @@ typedef struct pcpm_png_info {
     uint32_t update_dtype;    /* PCPM_UPDATE_* of the update bins */
     uint32_t update_bytes;    /* bytes per update: 4 or 2 */
     uint32_t gather_windows;  /* 1 if the gather reads the window layout */
-    uint32_t reserved2;
+    uint32_t shard_part_hi;   /*  shard_part_hi); [0, k) unless built by pcpm_build_shard */
     uint64_t num_windows;     /* windows of the window layout */
 } pcpm_png_info;
 
@@ -209,6 +209,73 @@ void pcpm_batch_free(pcpm_batch* batch); /* NULL is a no-op */
 int pcpm_build_weighted(const uint32_t* row_ptr, const uint32_t* col_idx, const float* weights, uint32_t n,
                         uint64_t m, uint32_t part_size, const pcpm_build_options* options, void* stream,
                         pcpm_png** out);
+
+/* ------------------------------------------------------ destination shards
+ * One iteration split over several GPUs (one process each). Every partition of
+ * destinations is gathered and applied independently of the others (Sec. 3.1:
+ * bin p' receives all updates into partition p', and Algorithm 4 reads only
+ * that bin), so each rank builds the bins of a contiguous range of destination
+ * partitions and owns the ranks of their nodes. Its scatter (Algorithm 3) needs
+ * the ranks of every source, so between iterations the ranks exchange their
+ * owned slices of the new vector (an all-gather) and add two FP64 sums (an
+ * all-reduce): the L1 change and the dangling mass. The exchange is the
+ * caller's (NCCL or any collective library); these calls never wait on another
+ * GPU and never read another GPU's memory.
+ *
+ * pcpm_dest_partition_counts: edges per destination partition of a device CSR
+ * (col_idx device uint32[m]; counts host uint64[ceil(n/part_size)]).
+ * Synchronises `stream`. PCPM_EBADGRAPH if a column is >= n.
+ *
+ * pcpm_shard_split (host only, no device work): cuts the k = ceil(n/part_size)
+ * partitions into `nranks` contiguous ranges of near-equal weight, where
+ * partition p weighs ids_per_part[p] plus its node count. part_lo (host,
+ * nranks + 1 entries) receives the cuts: rank r takes [part_lo[r],
+ * part_lo[r+1]), part_lo[0] = 0, part_lo[nranks] = k. Cut r is the partition
+ * boundary b whose prefix weight is nearest r/nranks of the total (ties to
+ * the lower b), moved as little as needed to leave every rank at least one
+ * partition. PCPM_EINVAL if nranks is 0 or above k.
+ *
+ * pcpm_build_shard: pcpm_build_ex restricted to destination partitions
+ * [part_lo, part_hi) (0 <= part_lo < part_hi <= k): the PNG of the edges into
+ * nodes [part_lo*q, min(part_hi*q, n)) from every source node, with the
+ * out-degrees of the whole CSR. Same CSR rules and errors as pcpm_build_ex
+ * (a column >= n anywhere in the CSR gives PCPM_EBADGRAPH). pcpm_png_export of
+ * a shard gives its bins: those of partitions in range equal the whole
+ * graph's, the others are empty. A shard whose range is not all of [0, k)
+ * rejects pcpm_reset, pcpm_iterate, pcpm_iterate_timed, pcpm_pagerank,
+ * pcpm_spmv and batches (PCPM_EINVAL); it runs through the two calls below.
+ * Any handle can run them, a whole-graph one as its own single shard.
+ *
+ * pcpm_shard_init: writes PR_0 to all n entries of pr_out (device float[n]):
+ * pr_init (device float[n], nullable = uniform 1/n). sums (device double[2])
+ * receives {0, dangling mass of PR_0 over the shard's own nodes}.
+ *
+ * pcpm_shard_step: one iteration of Eq. 1 for the shard's own nodes.
+ *   pr_in   device float[n]: PR_i of every node (all shards' slices).
+ *   sums    device double[2], read then written: on entry sums[1] must hold
+ *           the whole graph's dangling mass of pr_in (the all-reduced sums of
+ *           the previous call); on return sums = {sum over own nodes of
+ *           |PR_{i+1}(v) - PR_i(v)|, dangling mass of PR_{i+1} over own nodes}.
+ *   pr_out  device float[n], != pr_in: PR_{i+1} is written to the shard's own
+ *           nodes only; other entries are left as they were.
+ *   flags   PCPM_DANGLING_LEAK or 0 (iterations are always two-phase).
+ * Enqueued on `stream`; does not synchronise. A bounded device wait that gave
+ * up is reported by pcpm_sync_status. */
+int pcpm_dest_partition_counts(const uint32_t* col_idx, uint64_t m, uint32_t n, uint32_t part_size,
+                               uint64_t* counts, void* stream);
+int pcpm_shard_split(const uint64_t* ids_per_part, uint32_t n, uint32_t part_size, uint32_t nranks,
+                     uint32_t* part_lo);
+int pcpm_build_shard(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t n, uint64_t m,
+                     uint32_t part_size, uint32_t part_lo, uint32_t part_hi, const pcpm_build_options* options,
+                     void* stream, pcpm_png** out);
+int pcpm_shard_init(pcpm_png* png, const float* pr_init, float* pr_out, double* sums, void* stream);
+int pcpm_shard_step(pcpm_png* png, float d, uint32_t flags, const float* pr_in, float* pr_out, double* sums,
+                    void* stream);
+
+/* Waits for the handle's last stream and returns the device-side status of
+ * its kernels since the last reset or shard init: PCPM_OK, PCPM_ETIMEOUT (a
+ * bounded wait gave up) or PCPM_EDEVICE. */
+int pcpm_sync_status(const pcpm_png* png);
 
 /* Sparse matrix-vector product over the PNG (Sec. 3.5):
  *   y(v) = sum over edges (u, v) of w(u, v) * x(u)      (y = A^T_w x)

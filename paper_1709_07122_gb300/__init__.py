@@ -41,14 +41,14 @@ class PcpmError(RuntimeError):
 
 class _Info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_uint32), ("part_size", ctypes.c_uint32), ("num_partitions", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32), ("num_edges", ctypes.c_uint64), ("num_updates", ctypes.c_uint64),
+                ("shard_part_lo", ctypes.c_uint32), ("num_edges", ctypes.c_uint64), ("num_updates", ctypes.c_uint64),
                 ("compression_ratio", ctypes.c_double), ("device_bytes", ctypes.c_uint64),
                 ("iterations_done", ctypes.c_int32), ("gather_units", ctypes.c_uint32),
                 ("scatter_units", ctypes.c_uint32), ("gather_cluster", ctypes.c_uint32),
                 ("fused_ok", ctypes.c_uint32), ("canonical_gather", ctypes.c_uint32),
                 ("gather_runs", ctypes.c_uint32), ("merged_adds", ctypes.c_uint64),
                 ("update_dtype", ctypes.c_uint32), ("update_bytes", ctypes.c_uint32),
-                ("gather_windows", ctypes.c_uint32), ("reserved2", ctypes.c_uint32),
+                ("gather_windows", ctypes.c_uint32), ("shard_part_hi", ctypes.c_uint32),
                 ("num_windows", ctypes.c_uint64)]
 
 
@@ -120,6 +120,13 @@ def lib(path: str | None = None):
                 "pcpm_ws_loss_grad": (i32, [vp, vp, vp, u32, vp, vp, vp]),
                 "pcpm_ws_adam": (i32, [vp, vp, vp, vp, i32, f32, f32, f32, f32, vp]),
                 "pcpm_ws_init_ranks": (i32, [vp, u32, vp, vp]),
+                "pcpm_dest_partition_counts": (i32, [vp, u64, u32, u32, vp, vp]),
+                "pcpm_shard_split": (i32, [vp, u32, u32, u32, vp]),
+                "pcpm_build_shard": (i32, [vp, vp, u32, u64, u32, u32, u32, ctypes.POINTER(_Options), vp,
+                                           ctypes.POINTER(vp)]),
+                "pcpm_shard_init": (i32, [vp, vp, vp, vp, vp]),
+                "pcpm_shard_step": (i32, [vp, f32, u32, vp, vp, vp, vp]),
+                "pcpm_sync_status": (i32, [vp]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -212,6 +219,44 @@ class PNG:
                                _stream(stream), ctypes.byref(h)), "pcpm_build")
         self._h = h
         self.n = n
+
+    @classmethod
+    def shard(cls, row_ptr, col, part_size: int, part_lo: int, part_hi: int, stream=None, **options):
+        """The bins of destination partitions [part_lo, part_hi) only
+        (pcpm_build_shard); driven by shard_init / shard_step."""
+        if isinstance(options.get("update_dtype"), str):
+            options = dict(options, update_dtype=UPDATE_DTYPES[options["update_dtype"]])
+        n = row_ptr.numel() - 1
+        m = int(row_ptr[-1].item()) & 0xFFFFFFFF
+        opt = _Options(**{k: int(v) for k, v in options.items()})
+        h = ctypes.c_void_p()
+        _check(lib().pcpm_build_shard(_dev_u32(row_ptr), _dev_u32(col), n, m, int(part_size), int(part_lo),
+                                      int(part_hi), ctypes.byref(opt), _stream(stream), ctypes.byref(h)),
+               "pcpm_build_shard")
+        obj = cls.__new__(cls)
+        obj._h = h
+        obj.n = n
+        return obj
+
+    def shard_init(self, pr_out, sums, pr_init=None, stream=None):
+        """pcpm_shard_init: PR_0 into pr_out (all n), sums = {0, own dangling mass}."""
+        p = None if pr_init is None else ctypes.c_void_p(_f32_dev(pr_init, self.n).data_ptr())
+        _check(lib().pcpm_shard_init(self._h, p, ctypes.c_void_p(_f32_dev(pr_out, self.n).data_ptr()),
+                                     ctypes.c_void_p(_f64_dev(sums, 2).data_ptr()), _stream(stream)),
+               "pcpm_shard_init")
+
+    def shard_step(self, pr_in, pr_out, sums, d: float = 0.85, dangling: str = "uniform", stream=None):
+        """pcpm_shard_step: PR_{i+1} of the shard's own nodes into pr_out;
+        sums[1] must hold the whole graph's dangling mass of pr_in."""
+        _check(lib().pcpm_shard_step(self._h, float(d), _flags(dangling, "two_phase"),
+                                     ctypes.c_void_p(_f32_dev(pr_in, self.n).data_ptr()),
+                                     ctypes.c_void_p(_f32_dev(pr_out, self.n).data_ptr()),
+                                     ctypes.c_void_p(_f64_dev(sums, 2).data_ptr()), _stream(stream)),
+               "pcpm_shard_step")
+
+    def sync_status(self) -> None:
+        """Waits for the handle's stream; raises on a device-side error."""
+        _check(lib().pcpm_sync_status(self._h), "pcpm_sync_status")
 
     @classmethod
     def weighted(cls, row_ptr, col, weights, part_size: int, stream=None, **options):
@@ -367,6 +412,40 @@ def _f32_dev(t, n):
     if t.numel() != n:
         raise ValueError(f"expected {n} elements, got {t.numel()}")
     return t
+
+
+def _f64_dev(t, n):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous CUDA float64 tensor")
+    if t.numel() != n:
+        raise ValueError(f"expected {n} elements, got {t.numel()}")
+    return t
+
+
+def dest_partition_counts(col, n: int, part_size: int, m: int | None = None, stream=None) -> np.ndarray:
+    """Edges per destination partition of a device CSR's columns
+    (pcpm_dest_partition_counts): uint64 [ceil(n / part_size)]. m: the edge
+    count (default col.numel())."""
+    k = (n + part_size - 1) // part_size
+    out = np.zeros(k, np.uint64)
+    m = col.numel() if m is None else int(m)
+    _check(lib().pcpm_dest_partition_counts(_dev_u32(col) if m else None, m, n, int(part_size),
+                                            out.ctypes.data_as(ctypes.c_void_p), _stream(stream)),
+           "pcpm_dest_partition_counts")
+    return out
+
+
+def shard_split(ids_per_part, n: int, part_size: int, nranks: int) -> np.ndarray:
+    """Contiguous destination-partition ranges of near-equal weight
+    (pcpm_shard_split, host only): uint32 [nranks + 1] cut points."""
+    ids = np.ascontiguousarray(ids_per_part, dtype=np.uint64)
+    if ids.size != (n + part_size - 1) // part_size:
+        raise ValueError("ids_per_part needs one count per partition")
+    out = np.zeros(nranks + 1, np.uint32)
+    _check(lib().pcpm_shard_split(ids.ctypes.data_as(ctypes.c_void_p), int(n), int(part_size), int(nranks),
+                                  out.ctypes.data_as(ctypes.c_void_p)), "pcpm_shard_split")
+    return out
 
 
 def pagerank_host(row_ptr: np.ndarray, col: np.ndarray, part_size: int, d: float = 0.85, max_iters: int = 20,

@@ -2,6 +2,7 @@
 // the iteration loop and host-side copies. All arithmetic of the method runs
 // in the kernels of png_build.cu and pcpm_iter.cu.
 #include <algorithm>
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -245,6 +246,10 @@ int iterate_impl(pcpm_png* g, float d, int iters, double tol, uint32_t flags, in
 
 bool bad_damping(float d) { return !(d >= 0.0f && d < 1.0f); }
 
+// A handle that gathers only some destination partitions computes part of an
+// iteration; it is driven by pcpm_shard_init / pcpm_shard_step only.
+bool partial_shard(const pcpm_png* g) { return g->plo != 0 || g->phi != g->k; }
+
 constexpr uint32_t kAllFlags = PCPM_DANGLING_LEAK | PCPM_TWO_PHASE;
 
 }  // namespace
@@ -254,6 +259,7 @@ constexpr uint32_t kAllFlags = PCPM_DANGLING_LEAK | PCPM_TWO_PHASE;
 // dangling term, so the apply returns the bare sum. Leaves the handle after
 // that pass (callers reset before solving).
 int pull_sum(pcpm_png* g, const float* pr_like, float* out, cudaStream_t s) {
+    if (partial_shard(g)) return PCPM_EINVAL;
     g->last_stream = s;
     CK(cudaMemsetAsync(g->state, 0, sizeof(DevState), s));
     CK(cudaMemsetAsync(g->gacc, 0, (size_t)g->n * sizeof(float), s));
@@ -280,8 +286,11 @@ int pcpm_build(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t n, uin
 }
 
 namespace {
+// shard: build only the bins of destination partitions [part_lo, part_hi)
+// from the edges into them (pcpm_build_shard).
 int build_impl(const uint32_t* row_ptr, const uint32_t* col_idx, const float* weights, uint32_t n, uint64_t m,
-               uint32_t part_size, const pcpm_build_options* options, void* stream, pcpm_png** out) {
+               uint32_t part_size, const pcpm_build_options* options, void* stream, pcpm_png** out,
+               bool shard = false, uint32_t part_lo = 0, uint32_t part_hi = 0) {
     if (!out || !row_ptr || n == 0 || n > PCPM_MAX_NODES || part_size == 0 || part_size > PCPM_MAX_PART_SIZE)
         return PCPM_EINVAL;
     pcpm_build_options opt = {};
@@ -301,6 +310,7 @@ int build_impl(const uint32_t* row_ptr, const uint32_t* col_idx, const float* we
     if (m > 0xFFFFFF00ull) return PCPM_EINVAL;
     const uint64_t k = ((uint64_t)n + part_size - 1) / part_size;
     if (k > PCPM_MAX_PARTITIONS) return PCPM_EINVAL;
+    if (shard && (weights || part_lo >= part_hi || part_hi > k)) return PCPM_EINVAL;
     if (!is_device_ptr(row_ptr)) return PCPM_EINVAL;
     if (m > 0 && !is_device_ptr(col_idx)) return PCPM_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
@@ -328,9 +338,28 @@ int build_impl(const uint32_t* row_ptr, const uint32_t* col_idx, const float* we
     g->upd_bytes = opt.update_dtype == PCPM_UPDATE_F32 ? 4u : 2u;
     g->weighted = weights ? 1 : 0;
     g->weights_in = weights;
+    g->plo = shard ? part_lo : 0;
+    g->phi = shard ? part_hi : (uint32_t)k;
     int rc = PCPM_OK;
     if (cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess) rc = PCPM_ECUDA;
-    if (rc == PCPM_OK) rc = build_png(g, row_ptr, col_idx ? col_idx : row_ptr, opt, s);
+    if (shard) {
+        // the shard's own CSR: every source row, only the edges into its nodes
+        uint32_t *rp = nullptr, *cl = nullptr;
+        uint64_t ms = 0;
+        const uint32_t vlo = part_lo * part_size;
+        const uint32_t vhi = (uint32_t)std::min<uint64_t>((uint64_t)part_hi * part_size, n);
+        if (rc == PCPM_OK) rc = shard_filter_csr(row_ptr, col_idx ? col_idx : row_ptr, n, m, vlo, vhi, &rp, &cl, &ms, s);
+        if (rc == PCPM_OK) {
+            g->m = ms;
+            rc = build_png(g, rp, cl, opt, s);
+        }
+        // out-degrees (1/|N_o(u)|) are those of the whole graph
+        if (rc == PCPM_OK) rc = compute_inv_deg(g, row_ptr, s);
+        pool_free(rp, s);
+        pool_free(cl, s);
+    } else if (rc == PCPM_OK) {
+        rc = build_png(g, row_ptr, col_idx ? col_idx : row_ptr, opt, s);
+    }
     if (rc == PCPM_OK) rc = alloc_state(g);
     if (rc == PCPM_OK) rc = configure_kernels(g);
     if (rc == PCPM_OK) {
@@ -360,8 +389,107 @@ int pcpm_build_weighted(const uint32_t* row_ptr, const uint32_t* col_idx, const 
     return build_impl(row_ptr, col_idx, weights, n, m, part_size, options, stream, out);
 }
 
+// ------------------------------------------------------- destination shards
+int pcpm_build_shard(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t n, uint64_t m, uint32_t part_size,
+                     uint32_t part_lo, uint32_t part_hi, const pcpm_build_options* options, void* stream,
+                     pcpm_png** out) {
+    return build_impl(row_ptr, col_idx, nullptr, n, m, part_size, options, stream, out, true, part_lo, part_hi);
+}
+
+int pcpm_dest_partition_counts(const uint32_t* col_idx, uint64_t m, uint32_t n, uint32_t part_size,
+                               uint64_t* counts, void* stream) {
+    if (!counts || n == 0 || n > PCPM_MAX_NODES || part_size == 0 || part_size > PCPM_MAX_PART_SIZE ||
+        m > 0xFFFFFF00ull)
+        return PCPM_EINVAL;
+    if (((uint64_t)n + part_size - 1) / part_size > PCPM_MAX_PARTITIONS) return PCPM_EINVAL;
+    if (m > 0 && !is_device_ptr(col_idx)) return PCPM_EINVAL;
+    return dest_partition_counts(col_idx, m, n, part_size, counts, (cudaStream_t)stream);
+}
+
+int pcpm_shard_split(const uint64_t* ids_per_part, uint32_t n, uint32_t part_size, uint32_t nranks,
+                     uint32_t* part_lo) {
+    if (!ids_per_part || !part_lo || n == 0 || part_size == 0 || nranks == 0) return PCPM_EINVAL;
+    const uint64_t k = ((uint64_t)n + part_size - 1) / part_size;
+    if (nranks > k) return PCPM_EINVAL;
+    // w(p) = destination IDs of bin p + nodes of p: the gather's streamed IDs
+    // plus the apply's per-node work (an edgeless graph splits by nodes).
+    std::vector<uint64_t> pre(k + 1, 0);
+    for (uint64_t p = 0; p < k; ++p) {
+        const uint64_t nodes = std::min<uint64_t>(part_size, (uint64_t)n - p * part_size);
+        pre[p + 1] = pre[p] + ids_per_part[p] + nodes;
+    }
+    const uint64_t W = pre[k];
+    part_lo[0] = 0;
+    for (uint32_t r = 1; r < nranks; ++r) {
+        // the cut nearest r/nranks of the total weight, leaving at least one
+        // partition to this rank and to each later one
+        const long double t = (long double)W * r / nranks;
+        uint64_t b = std::lower_bound(pre.begin(), pre.end(), (uint64_t)std::ceil(t)) - pre.begin();
+        if (b > 0 && (t - (long double)pre[b - 1]) <= ((long double)pre[std::min<uint64_t>(b, k)] - t)) --b;
+        const uint64_t lo = (uint64_t)part_lo[r - 1] + 1, hi = k - (nranks - r);
+        part_lo[r] = (uint32_t)std::min(std::max(b, lo), hi);
+    }
+    part_lo[nranks] = (uint32_t)k;
+    return PCPM_OK;
+}
+
+int pcpm_shard_init(pcpm_png* g, const float* pr_init, float* pr_out, double* sums, void* stream) {
+    if (!g || !is_device_ptr(pr_out) || !is_device_ptr(sums)) return PCPM_EINVAL;
+    if (pr_init && !is_device_ptr(pr_init)) return PCPM_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    g->last_stream = s;
+    const uint32_t vlo = g->plo * g->q, vhi = (uint32_t)std::min<uint64_t>((uint64_t)g->phi * g->q, g->n);
+    CK(cudaMemsetAsync(g->state, 0, sizeof(DevState), s));
+    CK(cudaMemsetAsync(g->gacc, 0, (size_t)g->n * sizeof(float), s));
+    CK(cudaMemsetAsync(g->bin_done, 0, (size_t)g->k * sizeof(uint32_t), s));
+    g->iters_done = 0;
+    g->upd_valid = 0;
+    RC(launch_init_range(g, pr_init, pr_out, vlo, vhi, s));
+    RC(launch_reduce(g, 0.0, -1, s));
+    CK(cudaMemsetAsync(sums, 0, sizeof(double), s));
+    CK(cudaMemcpyAsync(sums + 1, &g->state->dangling, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return PCPM_OK;
+}
+
+int pcpm_shard_step(pcpm_png* g, float d, uint32_t flags, const float* pr_in, float* pr_out, double* sums,
+                    void* stream) {
+    if (!g || bad_damping(d) || (flags & ~kAllFlags)) return PCPM_EINVAL;
+    if (!is_device_ptr(pr_in) || !is_device_ptr(pr_out) || !is_device_ptr(sums) || pr_in == pr_out)
+        return PCPM_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    g->last_stream = s;
+    // the whole graph's dangling mass of pr_in, as the caller summed it
+    CK(cudaMemcpyAsync(&g->state->dangling, sums + 1, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemsetAsync(&g->state->stop, 0, sizeof(int), s));
+    float* const saved[2] = {g->pr[0], g->pr[1]};
+    const int saved_cur = g->cur;
+    g->pr[0] = const_cast<float*>(pr_in);  // only read by the scatter and the apply
+    g->pr[1] = pr_out;
+    g->cur = 0;
+    int rc = launch_scatter(g, s);
+    if (rc == PCPM_OK) rc = launch_gather(g, d, flags | PCPM_TWO_PHASE, /*fused=*/false, s);
+    if (rc == PCPM_OK) rc = launch_reduce(g, 0.0, 0, s, /*record=*/false);
+    g->pr[0] = saved[0];
+    g->pr[1] = saved[1];
+    g->cur = saved_cur;
+    g->upd_valid = 0;
+    if (rc != PCPM_OK) return rc;
+    g->iters_done += 1;
+    CK(cudaMemcpyAsync(sums, &g->state->residual, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(sums + 1, &g->state->dangling, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return PCPM_OK;
+}
+
+int pcpm_sync_status(const pcpm_png* g) {
+    if (!g) return PCPM_EINVAL;
+    CK(cudaStreamSynchronize(g->last_stream));
+    DevState st;
+    CK(cudaMemcpy(&st, g->state, sizeof(DevState), cudaMemcpyDeviceToHost));
+    return check_device_err(st);
+}
+
 int pcpm_spmv(pcpm_png* g, const float* x, float* y, void* stream) {
-    if (!g || !is_device_ptr(x) || !is_device_ptr(y)) return PCPM_EINVAL;
+    if (!g || partial_shard(g) || !is_device_ptr(x) || !is_device_ptr(y)) return PCPM_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     g->last_stream = s;
     CK(cudaMemsetAsync(g->state, 0, sizeof(DevState), s));
@@ -393,7 +521,8 @@ int pcpm_batch_create(pcpm_png* const* handles, int count, float d, int iters, u
     if (!handles || count < 1 || iters < 1 || bad_damping(d) || (flags & ~kAllFlags) || !out) return PCPM_EINVAL;
     std::set<const pcpm_png*> seen;
     for (int i = 0; i < count; ++i)
-        if (!handles[i] || !seen.insert(handles[i]).second) return PCPM_EINVAL;  // no handle twice
+        if (!handles[i] || partial_shard(handles[i]) || !seen.insert(handles[i]).second)
+            return PCPM_EINVAL;  // no handle twice, no destination shard
     // history room for the captured iterations (grows outside the capture)
     for (int i = 0; i < count; ++i) RC(ensure_hist(handles[i], iters, (cudaStream_t)0));
     pcpm_batch* b = new (std::nothrow) pcpm_batch;
@@ -573,6 +702,8 @@ int pcpm_png_get_info(const pcpm_png* g, pcpm_png_info* info) {
     info->update_dtype = (uint32_t)g->upd_dtype;
     info->update_bytes = g->upd_bytes;
     info->gather_windows = (uint32_t)g->gather_windows;
+    info->shard_part_lo = g->plo;
+    info->shard_part_hi = g->phi;
     info->num_windows = g->nwin;
     return PCPM_OK;
 }
@@ -606,7 +737,7 @@ int pcpm_png_export(const pcpm_png* g, uint32_t* cnt_u, uint32_t* cnt_e, uint32_
 }
 
 int pcpm_reset(pcpm_png* g, const float* pr_init, void* stream) {
-    if (!g) return PCPM_EINVAL;
+    if (!g || partial_shard(g)) return PCPM_EINVAL;
     if (pr_init && !is_device_ptr(pr_init)) return PCPM_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     g->last_stream = s;
@@ -623,12 +754,13 @@ int pcpm_reset(pcpm_png* g, const float* pr_init, void* stream) {
 
 int pcpm_iterate(pcpm_png* g, float d, int iters, double tol, uint32_t flags, int* iters_run, double* last_residual,
                  void* stream) {
-    if (!g || iters < 0 || bad_damping(d) || (flags & ~kAllFlags)) return PCPM_EINVAL;
+    if (!g || partial_shard(g) || iters < 0 || bad_damping(d) || (flags & ~kAllFlags)) return PCPM_EINVAL;
     return iterate_impl(g, d, iters, tol, flags, iters_run, last_residual, (cudaStream_t)stream);
 }
 
 int pcpm_iterate_timed(pcpm_png* g, float d, int iters, uint32_t flags, float* kernel_ms, void* stream) {
-    if (!g || iters < 0 || bad_damping(d) || !kernel_ms || (flags & ~kAllFlags)) return PCPM_EINVAL;
+    if (!g || partial_shard(g) || iters < 0 || bad_damping(d) || !kernel_ms || (flags & ~kAllFlags))
+        return PCPM_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     g->last_stream = s;
     std::vector<cudaEvent_t> ev((size_t)4 * iters);
@@ -677,7 +809,7 @@ int pcpm_residual_history(const pcpm_png* g, double* out, int max_count) {
 
 int pcpm_pagerank(pcpm_png* g, float d, int max_iters, double tol, uint32_t flags, const float* pr_init,
                   float* pr_out, int* iters_run, double* final_residual, void* stream) {
-    if (!g || max_iters < 0 || bad_damping(d) || (flags & ~kAllFlags)) return PCPM_EINVAL;
+    if (!g || partial_shard(g) || max_iters < 0 || bad_damping(d) || (flags & ~kAllFlags)) return PCPM_EINVAL;
     if (!is_device_ptr(pr_out)) return PCPM_EINVAL;
     if (pr_init && !is_device_ptr(pr_init)) return PCPM_EINVAL;
     RC(pcpm_reset(g, pr_init, stream));

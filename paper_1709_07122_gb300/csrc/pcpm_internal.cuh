@@ -170,6 +170,10 @@ struct pcpm_png {
     uint32_t* sorder;
     uint32_t nsunits;
     int fused_ok;            // every bin is a single gather unit
+    // Destination shard: the handle holds the bins of destination partitions
+    // [plo, phi) only (all of [0, k) unless built by pcpm_build_shard), gathers
+    // and applies those, and owns nodes [plo * q, min(phi * q, n)).
+    uint32_t plo, phi;
     float* gacc;             // n: partial sums of bins cut into several units
     uint32_t* bin_done;      // k: units of a cut bin that have flushed
     float* inv_deg;          // n: 1/|N_o(u)|, 0 for dangling nodes
@@ -203,6 +207,17 @@ int build_png(pcpm_png* g, const uint32_t* row_ptr, const uint32_t* col, const p
 // temporaries from the pool in s's order. A PCPM_* status.
 int exclusive_scan_u32(const uint32_t* in, uint32_t* out, uint64_t n, cudaStream_t s);
 
+// Destination shards (png_build.cu). keep_counts: per row u, the columns in
+// [vlo, vhi) (a warp per row), with kErrBadGraph in *err for a column >= n or
+// a row whose offsets decrease or pass m. keep_copy: those columns in row
+// order at out_ptr[u]. dest_counts: edges per destination partition (host
+// uint64[k]), kErrBadGraph for a column >= n.
+int shard_filter_csr(const uint32_t* row_ptr, const uint32_t* col, uint32_t n, uint64_t m, uint32_t vlo,
+                     uint32_t vhi, uint32_t** rp_out, uint32_t** col_out, uint64_t* m_out, cudaStream_t s);
+int compute_inv_deg(pcpm_png* g, const uint32_t* row_ptr, cudaStream_t s);
+int dest_partition_counts(const uint32_t* col, uint64_t m, uint32_t n, uint32_t q, uint64_t* counts_host,
+                          cudaStream_t s);
+
 // Iteration kernels (pcpm_iter.cu).
 int configure_kernels(pcpm_png* g);
 int pull_sum(pcpm_png* g, const float* pr_like, float* out, cudaStream_t s);
@@ -212,11 +227,14 @@ void note_cuda_error(cudaError_t e);
 // error and returns PCPM_ECUDA.
 int launch_status();
 int launch_init(pcpm_png* g, const float* pr_init, cudaStream_t s);
+// init into `out` (n floats), with the dangling partial sums over nodes [lo, hi) only.
+int launch_init_range(pcpm_png* g, const float* pr_init, float* out, uint32_t lo, uint32_t hi, cudaStream_t s);
 // raw: stage x itself (SpMV) instead of x * (1/outdeg).
 int launch_scatter(pcpm_png* g, cudaStream_t s, bool raw = false);
 // spmv: the weighted gather of a weighted handle (Sec. 3.5).
 int launch_gather(pcpm_png* g, float d, uint32_t flags, bool fused, cudaStream_t s, bool spmv = false);
-int launch_reduce(pcpm_png* g, double tol, int hist_slot, cudaStream_t s);
+// record = false: the L1 change goes to the device state only, not the history.
+int launch_reduce(pcpm_png* g, double tol, int hist_slot, cudaStream_t s, bool record = true);
 int launch_spr(pcpm_png* g, float* spr, cudaStream_t s);
 size_t partial_slots(const pcpm_png* g);
 

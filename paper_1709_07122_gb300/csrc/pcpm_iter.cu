@@ -354,15 +354,18 @@ __device__ __forceinline__ uint32_t segment_at(const uint32_t* gpre, uint32_t k,
 
 
 // ------------------------------------------------------------------ init
+// PR_0 = pr_init (or 1/n) on all n nodes; the dangling mass of nodes [lo, hi)
+// into the FP64 partials (a destination shard sums only the nodes it owns).
 __global__ void __launch_bounds__(kReduceThreads) init_kernel(uint32_t n, const float* __restrict__ pr_init,
                                                               const float* __restrict__ inv_deg, float* __restrict__ pr,
-                                                              double* __restrict__ partials) {
+                                                              double* __restrict__ partials, uint32_t lo,
+                                                              uint32_t hi) {
     const float uniform = (float)(1.0 / (double)n);
     double dang = 0.0, zero = 0.0;
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         const float x = pr_init ? pr_init[v] : uniform;
         pr[v] = x;
-        if (inv_deg[v] == 0.0f) dang += (double)x;
+        if (inv_deg[v] == 0.0f && v >= lo && v < hi) dang += (double)x;
     }
     block_sum2<kReduceThreads>(zero, dang);
     if (threadIdx.x == 0) {
@@ -1389,7 +1392,7 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_kernel(const double* __
         st->dangling = dg;
         if (hist_slot >= 0) {
             st->residual = r;
-            hist[hist_slot] = r;
+            if (hist) hist[hist_slot] = r;
             st->iters_done += 1;
             if (tol > 0.0 && r < tol) st->stop = 1;
         }
@@ -1548,11 +1551,15 @@ int configure_kernels(pcpm_png* g) {
     return PCPM_ECUDA;
 }
 
-int launch_init(pcpm_png* g, const float* pr_init, cudaStream_t s) {
+int launch_init_range(pcpm_png* g, const float* pr_init, float* out, uint32_t lo, uint32_t hi, cudaStream_t s) {
     const int blocks = (int)std::min<uint64_t>(kInitBlocks, (g->n + kReduceThreads - 1) / kReduceThreads);
-    init_kernel<<<blocks, kReduceThreads, 0, s>>>(g->n, pr_init, g->inv_deg, g->pr[g->cur], g->partials);
+    init_kernel<<<blocks, kReduceThreads, 0, s>>>(g->n, pr_init, g->inv_deg, out, g->partials, lo, hi);
     g->partial_count = blocks;
     return launch_status();
+}
+
+int launch_init(pcpm_png* g, const float* pr_init, cudaStream_t s) {
+    return launch_init_range(g, pr_init, g->pr[g->cur], 0, g->n, s);
 }
 
 int launch_spr(pcpm_png* g, float* spr, cudaStream_t s) {
@@ -1643,8 +1650,9 @@ int launch_gather(pcpm_png* g, float d, uint32_t flags, bool fused, cudaStream_t
     return e == cudaSuccess ? PCPM_OK : PCPM_ECUDA;
 }
 
-int launch_reduce(pcpm_png* g, double tol, int hist_slot, cudaStream_t s) {
-    reduce_kernel<<<1, kReduceThreads, 0, s>>>(g->partials, g->partial_count, g->state, g->hist, hist_slot, tol);
+int launch_reduce(pcpm_png* g, double tol, int hist_slot, cudaStream_t s, bool record) {
+    reduce_kernel<<<1, kReduceThreads, 0, s>>>(g->partials, g->partial_count, g->state, record ? g->hist : nullptr,
+                                               hist_slot, tol);
     return launch_status();
 }
 

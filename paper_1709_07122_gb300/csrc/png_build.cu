@@ -700,6 +700,82 @@ __global__ void inv_deg_kernel(const uint32_t* __restrict__ row_ptr, uint32_t n,
     }
 }
 
+// ------------------------------------------------------ destination shards
+// A destination shard keeps the edges into nodes [vlo, vhi). One warp per row
+// decides with one predicate in both passes (a ballot per 32 columns), so the
+// copy writes exactly the counted columns whatever the row's order; a row
+// whose offsets decrease or pass m, or a column >= n, sets kErrBadGraph and
+// keeps nothing of that row.
+__device__ __forceinline__ bool shard_row(const uint32_t* row_ptr, uint32_t u, uint64_t m, uint32_t& lo,
+                                          uint32_t& hi) {
+    lo = row_ptr[u];
+    hi = row_ptr[u + 1];
+    return hi >= lo && hi <= m;
+}
+
+__global__ void shard_count_kernel(const uint32_t* __restrict__ row_ptr, const uint32_t* __restrict__ col,
+                                   uint32_t n, uint64_t m, uint32_t vlo, uint32_t vhi, uint32_t* __restrict__ cnt,
+                                   int* __restrict__ err) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t u = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
+        uint32_t lo, hi, c = 0;
+        bool bad = !shard_row(row_ptr, (uint32_t)u, m, lo, hi);
+        if (!bad)
+            for (uint32_t e = lo; e < hi; e += 32) {
+                const uint32_t v = e + lane < hi ? col[e + lane] : vlo;
+                bad |= __any_sync(0xffffffffu, e + lane < hi && v >= n);
+                c += __popc(__ballot_sync(0xffffffffu, e + lane < hi && v >= vlo && v < vhi));
+            }
+        if (lane == 0) {
+            cnt[u] = bad ? 0u : c;
+            if (bad) atomicOr(err, kErrBadGraph);
+        }
+    }
+}
+
+__global__ void shard_copy_kernel(const uint32_t* __restrict__ row_ptr, const uint32_t* __restrict__ col,
+                                  uint32_t n, uint64_t m, uint32_t vlo, uint32_t vhi,
+                                  const uint32_t* __restrict__ out_ptr, uint32_t* __restrict__ out) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t u = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
+        uint32_t lo, hi;
+        const uint32_t o0 = out_ptr[u], o1 = out_ptr[u + 1];
+        if (!shard_row(row_ptr, (uint32_t)u, m, lo, hi) || o1 == o0) continue;
+        uint32_t o = o0;
+        for (uint32_t e = lo; e < hi; e += 32) {
+            const uint32_t v = e + lane < hi ? col[e + lane] : vlo;
+            const bool keep = e + lane < hi && v >= vlo && v < vhi && v < n;
+            const uint32_t b = __ballot_sync(0xffffffffu, keep);
+            const uint32_t at = o + __popc(b & ((1u << lane) - 1u));
+            if (keep && at < o1) out[at] = v;
+            o += __popc(b);
+        }
+    }
+}
+
+// Edges per destination partition: a shared-memory histogram per CTA (k <=
+// PCPM_MAX_PARTITIONS counters), added to the global 64-bit counts once.
+__global__ void __launch_bounds__(1024) dest_hist_kernel(const uint32_t* __restrict__ col, uint64_t m, uint32_t n,
+                                                         DivQ div, uint32_t k,
+                                                         unsigned long long* __restrict__ counts,
+                                                         int* __restrict__ err) {
+    __shared__ uint32_t h[PCPM_MAX_PARTITIONS];
+    for (uint32_t p = threadIdx.x; p < k; p += blockDim.x) h[p] = 0;
+    __syncthreads();
+    bool bad = false;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t v = col[e];
+        if (v >= n) bad = true;
+        else atomicAdd(&h[div(v)], 1u);
+    }
+    if (bad) atomicOr(err, kErrBadGraph);
+    __syncthreads();
+    for (uint32_t p = threadIdx.x; p < k; p += blockDim.x)
+        if (h[p]) atomicAdd(&counts[p], (unsigned long long)h[p]);
+}
+
 // In-degree of every node.
 __device__ __forceinline__ unsigned long long block_max_u64(unsigned long long x, unsigned long long* sh) {
 #pragma unroll
@@ -808,13 +884,15 @@ __device__ __forceinline__ void bin_chunks(const uint32_t* bin_e, const uint32_t
 }
 
 // pieces[p] = units of bin p: its chunks cut into runs of at most `per`
-// (an empty bin still gets one unit for its apply).
+// (an empty bin still gets one unit for its apply). Bins outside the
+// handle's destination shard [plo, phi) get none: no other node is applied.
 __global__ void gather_pieces_kernel(const uint32_t* __restrict__ bin_e, const uint32_t* __restrict__ ichunk_start,
-                                     uint32_t k, uint32_t per, uint32_t* __restrict__ pieces) {
+                                     uint32_t k, uint32_t per, uint32_t plo, uint32_t phi,
+                                     uint32_t* __restrict__ pieces) {
     for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < k; p += gridDim.x * blockDim.x) {
         uint32_t first, nch;
         bin_chunks(bin_e, ichunk_start, p, first, nch);
-        pieces[p] = nch ? (nch + per - 1) / per : 1;
+        pieces[p] = (p < plo || p >= phi) ? 0u : nch ? (nch + per - 1) / per : 1u;
     }
 }
 
@@ -1469,6 +1547,75 @@ int exclusive_scan_u32(const uint32_t* in, uint32_t* out, uint64_t n, cudaStream
     return scan_exclusive(in, out, n, tmp, s);
 }
 
+int shard_filter_csr(const uint32_t* row_ptr, const uint32_t* col, uint32_t n, uint64_t m, uint32_t vlo,
+                     uint32_t vhi, uint32_t** rp_out, uint32_t** col_out, uint64_t* m_out, cudaStream_t s) {
+    TempBufs tmp(s);
+    uint32_t* cnt = nullptr;
+    int* d_err = nullptr;
+    BCK(tmp.alloc(&cnt, n));
+    BCK(tmp.alloc(&d_err, 1));
+    BCK(cudaMemsetAsync(d_err, 0, sizeof(int), s));
+    uint32_t* rp = nullptr;
+    BCK(pool_alloc((void**)&rp, ((size_t)n + 1) * sizeof(uint32_t), s));
+    const int grid = grid_for((uint64_t)n * 32, 256, 152 * 16);
+    shard_count_kernel<<<grid, 256, 0, s>>>(row_ptr, col, n, m, vlo, vhi, cnt, d_err);
+    int rc = launch_status();
+    if (rc == PCPM_OK) rc = scan_exclusive(cnt, rp, n, tmp, s);
+    uint32_t total = 0;
+    int h_err = 0;
+    if (rc == PCPM_OK && cudaMemcpyAsync(&total, rp + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        rc = PCPM_ECUDA;
+    if (rc == PCPM_OK) rc = read_err(d_err, s, &h_err);
+    if (rc == PCPM_OK && h_err) rc = PCPM_EBADGRAPH;
+    uint32_t* c = nullptr;
+    if (rc == PCPM_OK) {
+        const cudaError_t e = pool_alloc((void**)&c, std::max<size_t>(total, 1) * sizeof(uint32_t), s);
+        if (e != cudaSuccess) {
+            note_cuda_error(e);
+            rc = e == cudaErrorMemoryAllocation ? PCPM_ENOMEM : PCPM_ECUDA;
+        }
+    }
+    if (rc == PCPM_OK) {
+        shard_copy_kernel<<<grid, 256, 0, s>>>(row_ptr, col, n, m, vlo, vhi, rp, c);
+        rc = launch_status();
+    }
+    if (rc != PCPM_OK) {
+        pool_free(rp, s);
+        pool_free(c, s);
+        return rc;
+    }
+    *rp_out = rp;
+    *col_out = c;
+    *m_out = total;
+    return PCPM_OK;
+}
+
+int compute_inv_deg(pcpm_png* g, const uint32_t* row_ptr, cudaStream_t s) {
+    inv_deg_kernel<<<grid_for(g->n, 256, 4096), 256, 0, s>>>(row_ptr, g->n, g->inv_deg);
+    return launch_status();
+}
+
+int dest_partition_counts(const uint32_t* col, uint64_t m, uint32_t n, uint32_t q, uint64_t* counts_host,
+                          cudaStream_t s) {
+    const uint32_t k = (uint32_t)(((uint64_t)n + q - 1) / q);
+    TempBufs tmp(s);
+    unsigned long long* counts = nullptr;
+    int* d_err = nullptr;
+    BCK(tmp.alloc(&counts, k));
+    BCK(tmp.alloc(&d_err, 1));
+    BCK(cudaMemsetAsync(counts, 0, (size_t)k * sizeof(unsigned long long), s));
+    BCK(cudaMemsetAsync(d_err, 0, sizeof(int), s));
+    if (m) {
+        dest_hist_kernel<<<grid_for(m, 1024, 152 * 2), 1024, 0, s>>>(col, m, n, make_divq(q), k, counts, d_err);
+        BCK(cudaGetLastError());
+    }
+    BCK(cudaMemcpyAsync(counts_host, counts, (size_t)k * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    int h_err = 0;
+    const int rc = read_err(d_err, s, &h_err);
+    if (rc != PCPM_OK) return rc;
+    return h_err ? PCPM_EBADGRAPH : PCPM_OK;
+}
+
 int build_png(pcpm_png* g, const uint32_t* row_ptr, const uint32_t* col, const pcpm_build_options& opt,
               cudaStream_t s) {
     const uint32_t n = g->n, q = g->q, k = g->k;
@@ -1711,7 +1858,7 @@ int build_png(pcpm_png* g, const uint32_t* row_ptr, const uint32_t* col, const p
     const uint32_t gper = !opt.gather_unit_chunks ? gper_default
                           : g->gather_windows     ? (opt.gather_unit_chunks + kWin / kChunk - 1) / (kWin / kChunk)
                                                   : opt.gather_unit_chunks;
-    gather_pieces_kernel<<<grid_for(k, 256, 64), 256, 0, s>>>(g->bin_e, ichunks, k, gper, pieces);
+    gather_pieces_kernel<<<grid_for(k, 256, 64), 256, 0, s>>>(g->bin_e, ichunks, k, gper, g->plo, g->phi, pieces);
     if ((rc = scan_exclusive(pieces, start, k, tmp, s)) != PCPM_OK) return rc;
     src_groups_kernel<<<k, 256, 0, s>>>(g->seg_u, g->cnt_u, k, groups);
     if ((rc = scan_exclusive(groups, gstart, k, tmp, s)) != PCPM_OK) return rc;
@@ -1720,7 +1867,9 @@ int build_png(pcpm_png* g, const uint32_t* row_ptr, const uint32_t* col, const p
     BCK(cudaMemcpyAsync(&totals[1], gstart + k, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     BCK(cudaStreamSynchronize(s));
     g->ngunits = totals[0];
-    g->fused_ok = g->ngunits == k;
+    // The fused iteration scatters every source partition's next updates; a
+    // destination shard gets other shards' ranks only between iterations.
+    g->fused_ok = g->ngunits == k && g->plo == 0 && g->phi == k;
     BCK(tmp.alloc(&sizes, std::max<uint32_t>(g->ngunits, k) + 1));
     BCK(dev_alloc(g, (void**)&g->gunits, (size_t)g->ngunits * sizeof(uint4)));
     BCK(dev_alloc(g, (void**)&g->gorder, (size_t)g->ngunits * sizeof(uint32_t)));

@@ -93,6 +93,25 @@ def test_ppr_autotune_and_pool_entries_check_arguments_on_the_host(L):
     assert L.pcpm_release_cached_memory() == 0  # no pool was created in this process
 
 
+def test_shard_entries_check_arguments_on_the_host(L):
+    h = ctypes.c_void_p()
+    dev = ctypes.c_void_p(16)
+    cuts = (ctypes.c_uint32 * 3)()
+    ids = (ctypes.c_uint64 * 4)(5, 0, 7, 1)
+    assert L.pcpm_build_shard(dev, dev, 40, 0, 10, 2, 2, None, None, ctypes.byref(h)) == -1  # empty range
+    assert L.pcpm_build_shard(dev, dev, 40, 0, 10, 0, 5, None, None, ctypes.byref(h)) == -1  # past k = 4
+    assert L.pcpm_build_shard(dev, dev, 40, 0, 10, 0, 2, None, None, None) == -1
+    assert L.pcpm_shard_init(None, None, dev, dev, None) == -1
+    assert L.pcpm_shard_step(None, 0.85, 0, dev, dev, dev, None) == -1
+    assert L.pcpm_sync_status(None) == -1
+    assert L.pcpm_dest_partition_counts(dev, 0, 0, 10, ids, None) == -1  # n = 0
+    assert L.pcpm_dest_partition_counts(dev, 0, 40, 10, None, None) == -1
+    assert L.pcpm_shard_split(None, 40, 10, 2, cuts) == -1
+    assert L.pcpm_shard_split(ids, 40, 10, 5, cuts) == -1  # more ranks than partitions
+    assert L.pcpm_shard_split(ids, 40, 10, 2, cuts) == 0  # host only: works without a GPU
+    assert list(cuts) == [0, 2, 4]
+
+
 def test_binding_fails_loudly_without_library(tmp_path):
     saved = pcpm._lib
     try:
