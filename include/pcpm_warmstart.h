@@ -11,9 +11,9 @@
  *   1  log1p(outdeg(v))
  *   2  log1p(sum of indeg(u) over in-neighbours u)
  *   3  log1p(sum of outdeg(u) over in-neighbours u)
- * The in-degree and both sums are in-edge sums that the library computes as
- * PCPM passes over the handle (FP32; counts below 2^24 come out exact up to
- * the rounding of 1/outdeg), the logarithms in FP32.
+ * The in-degree and both sums are exact unsigned 32-bit in-edge sums over the
+ * handle's bins (pcpm_ws_degree_sums); the logarithms are FP32 (log1pf of the
+ * count converted to float).
  *   4  log(n * PR_1(v)), PR_1 one Eq. 1 step from the uniform start on the
  *      handle (d = 0.85, dangling mass spread uniformly)
  * Network: standardise x^ = (x - mu) * inv_sigma; h1 = relu(W1 x^ + b1);
@@ -43,20 +43,43 @@ extern "C" {
 #define PCPM_WS_TRAINABLE_OFFSET 10
 
 /* Features of every node of the graph the handle was built from.
- *   row_ptr, col  the device CSR given to pcpm_build (uint32[n+1], uint32[m]).
+ *   row_ptr, col  the device CSR given to pcpm_build (uint32[n+1], uint32[m];
+ *                 col is not read: the sums come from the handle's bins).
  *   features      float[n][5], written.
- * Uses the handle for four passes (three sums, then PR_1) and leaves its
- * solver state after PR_1. Allocates 20 bytes per node of stream-ordered
- * device scratch and frees it. Synchronises. */
+ * Runs the three exact sums of pcpm_ws_degree_sums, then one iteration for
+ * PR_1, and leaves the handle's solver state after PR_1. Allocates 16 bytes per
+ * node of stream-ordered device scratch and frees it. Synchronises.
+ * PCPM_EINVAL for a destination shard (pcpm_build_shard). */
 int pcpm_ws_features(pcpm_png* png, const uint32_t* row_ptr, const uint32_t* col, float* features,
                      void* stream);
+
+/* The integer parts of features 0, 2 and 3, exactly: sums (uint32[3][n]) gets
+ * indeg(v), the sum of indeg(u) and the sum of outdeg(u) over the in-edges
+ * u -> v, each one pass over the handle's canonical bins (every in-edge of a
+ * node of partition p lies in bin p; Sec. 3.1) with unsigned 32-bit
+ * shared-memory sums per bin. The source of each destination ID is that of its
+ * update (Algorithm 4's update index). row_ptr: the CSR given to pcpm_build.
+ * Synchronises; PCPM_EDEVICE if a sum passes 2^32 - 1. */
+int pcpm_ws_degree_sums(pcpm_png* png, const uint32_t* row_ptr, uint32_t* sums, void* stream);
+
+/* Feature statistics for the standardisation, summed in FP64 over all n rows
+ * and added to moments (double[11]: rows, then the sum of each column, then
+ * the sum of squares of each column); zero it before the first graph.
+ * pcpm_ws_standardisation writes params[0..10): mu = the mean and inv_sigma =
+ * 1 / max(population standard deviation, 1e-6) of each column. */
+int pcpm_ws_feature_moments(const float* features, uint32_t n, double* moments, void* stream);
+int pcpm_ws_standardisation(const double* moments, float* params, void* stream);
 
 /* Training targets: target(v) = log(n * pr(v)) computed in FP64 and rounded
  * to float, for ranks pr (float[n], positive) of a graph of n nodes. */
 int pcpm_ws_targets(const float* pr, uint32_t n, float* target, void* stream);
 
 /* Network output for n feature rows, with W1, b1, W2, b2, w3, b3 rounded to
- * bfloat16 (nearest even) and FP32 accumulation.
+ * bfloat16 (nearest even), on the tensor cores (mma m16n8k16, BF16 operands,
+ * FP32 accumulation). The standardised inputs and h1 enter the products as
+ * two BF16 parts each (x = hi + lo, |x - hi - lo| <= 2^-18 |x|), so the
+ * products keep about 16 significant bits of the activations; biases, ReLU
+ * and the output dot product with w3 are FP32.
  *   params float[PCPM_WS_PARAMS]; features float[n][5]; out float[n]. */
 int pcpm_ws_predict(const float* params, const float* features, uint32_t n, float* out, void* stream);
 

@@ -120,6 +120,9 @@ def lib(path: str | None = None):
                 "pcpm_ws_loss_grad": (i32, [vp, vp, vp, u32, vp, vp, vp]),
                 "pcpm_ws_adam": (i32, [vp, vp, vp, vp, i32, f32, f32, f32, f32, vp]),
                 "pcpm_ws_init_ranks": (i32, [vp, u32, vp, vp]),
+                "pcpm_ws_degree_sums": (i32, [vp, vp, vp, vp]),
+                "pcpm_ws_feature_moments": (i32, [vp, u32, vp, vp]),
+                "pcpm_ws_standardisation": (i32, [vp, vp, vp]),
                 "pcpm_dest_partition_counts": (i32, [vp, u64, u32, u32, vp, vp]),
                 "pcpm_shard_split": (i32, [vp, u32, u32, u32, vp]),
                 "pcpm_build_shard": (i32, [vp, vp, u32, u64, u32, u32, u32, ctypes.POINTER(_Options), vp,
@@ -514,6 +517,35 @@ def ws_features(png: "PNG", row_ptr, col, out=None, stream=None):
     _check(lib().pcpm_ws_features(png._h, _dev_u32(row_ptr), _dev_u32(col),
                                   _f32(out, png.n * WS_FEATURES, "features"), _stream(stream)), "pcpm_ws_features")
     return out
+
+
+def ws_degree_sums(png: "PNG", row_ptr, out=None, stream=None):
+    """Exact in-degree, sum of in-neighbours' in-degrees and sum of their
+    out-degrees (pcpm_ws_degree_sums): CUDA int32 [3, n] holding uint32 bits."""
+    import torch
+    out = torch.empty((3, png.n), dtype=torch.int32, device="cuda") if out is None else out
+    if not (out.is_cuda and out.dtype == torch.int32 and out.is_contiguous() and out.numel() == 3 * png.n):
+        raise TypeError("out: expected a contiguous CUDA int32 tensor of 3 * n elements")
+    _check(lib().pcpm_ws_degree_sums(png._h, _dev_u32(row_ptr), ctypes.c_void_p(out.data_ptr()), _stream(stream)),
+           "pcpm_ws_degree_sums")
+    return out
+
+
+def ws_feature_moments(features, moments, stream=None):
+    """Adds the FP64 row count, column sums and sums of squares of the
+    features [n, 5] to moments (CUDA float64 [11]) (pcpm_ws_feature_moments)."""
+    n = features.shape[0]
+    _check(lib().pcpm_ws_feature_moments(_f32(features, n * WS_FEATURES, "features"), n,
+                                         ctypes.c_void_p(_f64_dev(moments, 11).data_ptr()), _stream(stream)),
+           "pcpm_ws_feature_moments")
+
+
+def ws_standardisation(moments, params, stream=None):
+    """mu and inv_sigma from accumulated moments into params[0:10]
+    (pcpm_ws_standardisation)."""
+    _check(lib().pcpm_ws_standardisation(ctypes.c_void_p(_f64_dev(moments, 11).data_ptr()),
+                                         _f32(params, WS_PARAMS, "params"), _stream(stream)),
+           "pcpm_ws_standardisation")
 
 
 def ws_targets(pr, out=None, stream=None):

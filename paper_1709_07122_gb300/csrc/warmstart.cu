@@ -14,6 +14,9 @@
 // CTA's threads split by output entry and add to the global gradient once.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+#include <mutex>
+
 #include "pcpm_internal.cuh"
 #include "pcpm_warmstart.h"
 
@@ -28,32 +31,122 @@ constexpr int OFF_MU = 0, OFF_IS = F, OFF_W1 = 2 * F, OFF_B1 = OFF_W1 + H * F, O
 static_assert(OFF_B3 + 1 == P, "parameter layout");
 static_assert(OFF_W1 == PCPM_WS_TRAINABLE_OFFSET, "parameter layout");
 
-constexpr int kPredictThreads = 256;
 constexpr int kTile = 256;     // nodes per training CTA (one per thread)
 constexpr int kRow = H + 1;    // padded shared-memory row
 
 // ------------------------------------------------------------- features
-// The vectors whose in-edge sums give the degree features: the PCPM pass of
-// pull_sum divides by outdeg(u), so x(u) * outdeg(u) yields sum_u x(u) over
-// in-edges: x = 1 (in-degree), x = indeg(u), x = outdeg(u).
-__global__ void degree_vector_kernel(const uint32_t* __restrict__ row_ptr, uint32_t n, const float* __restrict__ x,
-                                     int power, float* __restrict__ out) {
-    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        const float dout = (float)(row_ptr[v + 1] - row_ptr[v]);
-        out[v] = x ? x[v] * dout : (power == 2 ? dout * dout : dout);
+// Exact in-edge sums over the canonical bins, one CTA per destination bin p
+// (every in-edge of a node of p lies in bin p): acc[v - p q] += val for every
+// destination ID v of the bin, with val = 1 (kMode 0: the in-degree), indeg(u)
+// (1) or outdeg(u) (2) of the ID's source u. The source is that of the ID's
+// update: Algorithm 4's update index, the flagged IDs up to and including the
+// ID minus one, found from the chunk's precomputed base and a ballot per 32
+// IDs. Unsigned 32-bit shared-memory atomics; a sum that passes 2^32 sets
+// kErrBounds in *err.
+constexpr int kDegThreads = 1024;
+
+template <int kMode>
+__global__ void __launch_bounds__(kDegThreads) bin_degree_kernel(
+    const uint32_t* __restrict__ dest, const uint32_t* __restrict__ src, const uint32_t* __restrict__ bin_e,
+    const uint32_t* __restrict__ chunk_base, uint32_t n, uint32_t q, const uint32_t* __restrict__ row_ptr,
+    const uint32_t* __restrict__ indeg, uint32_t* __restrict__ out, int* __restrict__ err) {
+    extern __shared__ uint32_t acc[];
+    const uint32_t p = blockIdx.x;
+    const uint32_t v0 = p * q, len = min(q, n - v0);
+    for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) acc[i] = 0u;
+    __syncthreads();
+    const uint32_t e0 = bin_e[p], e1 = bin_e[p + 1];
+    bool over = false;
+    if (e1 > e0) {
+        const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        const uint32_t c0 = e0 / kChunk, c1 = (e1 - 1) / kChunk;
+        for (uint32_t c = c0 + warp; c <= c1; c += nw) {
+            uint32_t base = chunk_base[c];
+#pragma unroll 2
+            for (uint32_t r = 0; r < kChunk / 32; ++r) {
+                const uint32_t e = c * kChunk + r * 32 + lane;
+                const uint32_t id = e < e1 ? dest[e] : 0u;
+                const uint32_t fl = __ballot_sync(0xffffffffu, (id & kMsb) != 0u);
+                const uint32_t idx = base + __popc(fl & ((2u << lane) - 1u)) - 1u;
+                base += __popc(fl);
+                const uint32_t loc = (id & kIdMask) - v0;
+                if (e >= e0 && e < e1 && loc < len) {
+                    uint32_t val = 1u;
+                    if (kMode != 0) {
+                        const uint32_t u = src[idx];
+                        val = kMode == 1 ? indeg[u] : row_ptr[u + 1] - row_ptr[u];
+                    }
+                    const uint32_t old = atomicAdd(&acc[loc], val);
+                    over |= old + val < old;
+                }
+            }
+        }
     }
+    if (over) atomicOr(err, kErrBounds);
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) out[v0 + i] = acc[i];
 }
 
-__global__ void features_kernel(const uint32_t* __restrict__ row_ptr, uint32_t n, const float* __restrict__ indeg,
-                                const float* __restrict__ s_in, const float* __restrict__ s_out,
+__global__ void features_kernel(const uint32_t* __restrict__ row_ptr, uint32_t n, const uint32_t* __restrict__ sums,
                                 const float* __restrict__ pr1, float* __restrict__ feat) {
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         float* f = feat + (size_t)v * F;
-        f[0] = log1pf(indeg[v]);
+        f[0] = log1pf((float)sums[v]);
         f[1] = log1pf((float)(row_ptr[v + 1] - row_ptr[v]));
-        f[2] = log1pf(s_in[v]);
-        f[3] = log1pf(s_out[v]);
+        f[2] = log1pf((float)sums[(size_t)n + v]);
+        f[3] = log1pf((float)sums[2 * (size_t)n + v]);
         f[4] = logf((float)n * pr1[v]);
+    }
+}
+
+// FP64 moments of the feature columns, accumulated: m[0] += rows, m[1 + f] +=
+// sum of x_f, m[6 + f] += sum of x_f^2.
+constexpr int kMomThreads = 256;
+__global__ void __launch_bounds__(kMomThreads) moments_kernel(const float* __restrict__ feat, uint32_t n,
+                                                              double* __restrict__ m) {
+    double s[F], s2[F];
+#pragma unroll
+    for (int f = 0; f < F; ++f) s[f] = s2[f] = 0.0;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int f = 0; f < F; ++f) {
+            const double x = (double)feat[(size_t)v * F + f];
+            s[f] += x;
+            s2[f] += x * x;
+        }
+    }
+    __shared__ double sh[kMomThreads / 32][2 * F];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s[f] += __shfl_down_sync(0xffffffffu, s[f], o);
+            s2[f] += __shfl_down_sync(0xffffffffu, s2[f], o);
+        }
+        if (lane == 0) {
+            sh[warp][f] = s[f];
+            sh[warp][F + f] = s2[f];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * F) {
+        double t = 0.0;
+        for (int w = 0; w < kMomThreads / 32; ++w) t += sh[w][threadIdx.x];
+        atomicAdd(&m[1 + threadIdx.x], t);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&m[0], (double)n);
+}
+
+// mu = mean, inv_sigma = 1 / max(population std, 1e-6) into params[0, 10).
+__global__ void standardisation_kernel(const double* __restrict__ m, float* __restrict__ params) {
+    const int f = threadIdx.x;
+    if (f < F) {
+        const double rows = m[0] > 0.0 ? m[0] : 1.0;
+        const double mean = m[1 + f] / rows;
+        const double var = fmax(m[1 + F + f] / rows - mean * mean, 0.0);
+        params[OFF_MU + f] = (float)mean;
+        params[OFF_IS + f] = (float)(1.0 / fmax(sqrt(var), 1e-6));
     }
 }
 
@@ -89,61 +182,153 @@ __device__ __forceinline__ void layer1(const float* w, const float* xh, float* h
     }
 }
 
-// Inference keeps W2 at a 16-byte-aligned shared offset (the flat layout puts
-// it at float 394): entries from W2 on move up by kShift floats.
-constexpr int kShift = 2;
-static_assert((OFF_W2 + kShift) % 4 == 0, "W2 rows must start on 16-byte boundaries");
+// ------------------------------------------------------------ inference
+// Inference on the tensor cores: mma.sync m16n8k16 with BF16 operands and
+// FP32 accumulation, one warp per tile of 16 nodes. The weights are BF16 by
+// definition (rounded once, nearest even) and stay in registers as B
+// fragments for the whole kernel. Activations are carried as two BF16 parts,
+// hi = bf16(x) and lo = bf16(x - hi), so every product A B is two MMAs,
+// A_hi B + A_lo B, and the activations keep about 16 significant bits
+// (|x - hi - lo| <= 2^-18 |x|) instead of BF16's 8.
+//
+// Fragment layouts (PTX ISA, mma.m16n8k16, g = lane / 4, t = lane % 4):
+//   A (16 x 16, row-major), 4 registers of two BF16: (row g, k 2t..2t+1),
+//     (row g+8, k 2t..2t+1), (row g, k 2t+8..2t+9), (row g+8, k 2t+8..2t+9);
+//   B (16 x 8), 2 registers: (k 2t..2t+1, n g), (k 2t+8..2t+9, n g);
+//   C (16 x 8, FP32), 4 values: (row g, n 2t..2t+1), (row g+8, n 2t..2t+1).
+// The C fragments of output columns 16k .. 16k+15 (two n-tiles) are exactly
+// the A fragment of input columns 16k .. 16k+15 of the next layer, so h1 goes
+// from layer 1 to layer 2 without leaving the registers.
+constexpr int kPredictWarps = 8;
 
-__global__ void __launch_bounds__(kPredictThreads) predict_kernel(const float* __restrict__ params,
-                                                                  const float* __restrict__ feat, uint32_t n,
-                                                                  float* __restrict__ out) {
-    __shared__ __align__(16) float w[P + kShift];
-    for (int i = threadIdx.x; i < P; i += blockDim.x) {
-        const float x = params[i];
-        w[i < OFF_W2 ? i : i + kShift] = i >= OFF_W1 ? __bfloat162float(__float2bfloat16_rn(x)) : x;
+__device__ __forceinline__ uint32_t bf16x2_bits(__nv_bfloat162 h) { return *reinterpret_cast<uint32_t*>(&h); }
+
+// The two BF16 parts of (a, b), low halves first.
+__device__ __forceinline__ void split_bf16x2(float a, float b, uint32_t& hi, uint32_t& lo) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const float2 hf = __bfloat1622float2(h);
+    hi = bf16x2_bits(h);
+    lo = bf16x2_bits(__floats2bfloat162_rn(a - hf.x, b - hf.y));
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                               uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+__global__ void __launch_bounds__(kPredictWarps * 32) predict_kernel(const float* __restrict__ params,
+                                                                     const float* __restrict__ feat, uint32_t n,
+                                                                     float* __restrict__ out) {
+    __shared__ float sb1[H], sb2[H], sw3[H];
+    for (int i = threadIdx.x; i < H; i += blockDim.x) {
+        sb1[i] = bf16r(params[OFF_B1 + i]);
+        sb2[i] = bf16r(params[OFF_B2 + i]);
+        sw3[i] = bf16r(params[OFF_W3 + i]);
     }
+    const uint32_t lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    // B fragments: layer 1 (K = 5 padded to 16: only k = 2t, 2t+1 < 5 are
+    // nonzero), layer 2 (4 k-tiles x 8 n-tiles)
+    uint32_t bw1[8], bw2[4][8][2];
+#pragma unroll
+    for (int jt = 0; jt < 8; ++jt) {
+        const int nn = 8 * jt + g;
+        const float x0 = 2 * t < F ? params[OFF_W1 + nn * F + 2 * t] : 0.0f;
+        const float x1 = 2 * t + 1 < F ? params[OFF_W1 + nn * F + 2 * t + 1] : 0.0f;
+        bw1[jt] = bf16x2_bits(__floats2bfloat162_rn(x0, x1));
+#pragma unroll
+        for (int kt = 0; kt < 4; ++kt) {
+            const float* r = params + OFF_W2 + nn * H + 16 * kt + 2 * t;
+            bw2[kt][jt][0] = bf16x2_bits(__floats2bfloat162_rn(r[0], r[1]));
+            bw2[kt][jt][1] = bf16x2_bits(__floats2bfloat162_rn(r[8], r[9]));
+        }
+    }
+    float mu[2], is[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const int f = 2 * t + c;
+        mu[c] = f < F ? params[OFF_MU + f] : 0.0f;
+        is[c] = f < F ? params[OFF_IS + f] : 0.0f;
+    }
+    const float b3 = bf16r(params[OFF_B3]);
     __syncthreads();
-    const float* w2 = w + OFF_W2 + kShift;
-    const float* b2 = w2 + H * H;
-    const float* w3 = b2 + H;
-    const float b3 = w3[H];
-    // two nodes per thread: every 16-byte weight load feeds eight FMAs
-    const uint64_t stride = 2ull * gridDim.x * blockDim.x;
-#pragma unroll 1
-    for (uint64_t v0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) * 2; v0 < n; v0 += stride) {
-        asm volatile("" ::: "memory");  // weights stay in shared memory, not in registers across nodes
-        const bool two = v0 + 1 < n;
-        float xa[F], xb[F], ha[H], hb[H];
-        standardise(feat, v0, w, xa);
-        if (two) standardise(feat, v0 + 1, w, xb);
-        else {
+    const uint64_t warps = (uint64_t)gridDim.x * kPredictWarps;
+    const uint64_t ntiles = ((uint64_t)n + 15) / 16;
+    // features of a tile: rows g and g + 8, columns 2t and 2t + 1 (< F)
+    auto load_x = [&](uint64_t tile, float (&x)[4]) {
 #pragma unroll
-            for (int f = 0; f < F; ++f) xb[f] = 0.0f;
+        for (int i = 0; i < 4; ++i) {
+            const uint64_t v = tile * 16 + g + 8 * (i >> 1);
+            const int f = 2 * t + (i & 1);
+            x[i] = (tile < ntiles && v < n && f < F) ? __ldg(feat + v * F + f) : 0.0f;
         }
-        layer1(w, xa, ha);
-        layer1(w, xb, hb);
-        float ya = b3, yb = b3;
+    };
+    uint64_t tile = (uint64_t)blockIdx.x * kPredictWarps + (threadIdx.x >> 5);
+    float xn[4];
+    load_x(tile, xn);
 #pragma unroll 1
-        for (int j = 0; j < H; ++j) {
-            float sa = b2[j], sb = sa;
-            const float4* row = reinterpret_cast<const float4*>(w2 + j * H);
+    for (; tile < ntiles; tile += warps) {
+        float x[4];
 #pragma unroll
-            for (int i4 = 0; i4 < H / 4; ++i4) {
-                const float4 q = row[i4];
-                sa = fmaf(q.x, ha[4 * i4], sa);
-                sa = fmaf(q.y, ha[4 * i4 + 1], sa);
-                sa = fmaf(q.z, ha[4 * i4 + 2], sa);
-                sa = fmaf(q.w, ha[4 * i4 + 3], sa);
-                sb = fmaf(q.x, hb[4 * i4], sb);
-                sb = fmaf(q.y, hb[4 * i4 + 1], sb);
-                sb = fmaf(q.z, hb[4 * i4 + 2], sb);
-                sb = fmaf(q.w, hb[4 * i4 + 3], sb);
+        for (int i = 0; i < 4; ++i) x[i] = xn[i];
+        load_x(tile + warps, xn);  // the next tile's loads overlap this tile
+        // layer 1: standardise, split, 8 n-tiles x 2 parts
+        uint32_t ah[2], al[2];
+        split_bf16x2((x[0] - mu[0]) * is[0], (x[1] - mu[1]) * is[1], ah[0], al[0]);
+        split_bf16x2((x[2] - mu[0]) * is[0], (x[3] - mu[1]) * is[1], ah[1], al[1]);
+        float c1[8][4];
+#pragma unroll
+        for (int jt = 0; jt < 8; ++jt) {
+            c1[jt][0] = c1[jt][1] = c1[jt][2] = c1[jt][3] = 0.0f;
+            mma_bf16_16816(c1[jt], ah[0], ah[1], 0u, 0u, bw1[jt], 0u);
+            mma_bf16_16816(c1[jt], al[0], al[1], 0u, 0u, bw1[jt], 0u);
+        }
+        // h1 = relu(c1 + b1) as the A fragments of layer 2
+        uint32_t a2h[4][4], a2l[4][4];
+#pragma unroll
+        for (int kt = 0; kt < 4; ++kt) {
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const int jt = 2 * kt + half, col = 8 * jt + 2 * t;
+                const float bb0 = sb1[col], bb1 = sb1[col + 1];
+                split_bf16x2(fmaxf(c1[jt][0] + bb0, 0.0f), fmaxf(c1[jt][1] + bb1, 0.0f), a2h[kt][2 * half],
+                             a2l[kt][2 * half]);
+                split_bf16x2(fmaxf(c1[jt][2] + bb0, 0.0f), fmaxf(c1[jt][3] + bb1, 0.0f), a2h[kt][2 * half + 1],
+                             a2l[kt][2 * half + 1]);
             }
-            ya = fmaf(w3[j], fmaxf(sa, 0.0f), ya);
-            yb = fmaf(w3[j], fmaxf(sb, 0.0f), yb);
         }
-        out[v0] = ya;
-        if (two) out[v0 + 1] = yb;
+        // layer 2 and the output dot product, one n-tile at a time
+        float y0 = 0.0f, y1 = 0.0f;
+#pragma unroll
+        for (int jt = 0; jt < 8; ++jt) {
+            float c2[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+            for (int kt = 0; kt < 4; ++kt) {
+                mma_bf16_16816(c2, a2h[kt][0], a2h[kt][1], a2h[kt][2], a2h[kt][3], bw2[kt][jt][0], bw2[kt][jt][1]);
+                mma_bf16_16816(c2, a2l[kt][0], a2l[kt][1], a2l[kt][2], a2l[kt][3], bw2[kt][jt][0], bw2[kt][jt][1]);
+            }
+            const int col = 8 * jt + 2 * t;
+            const float bb0 = sb2[col], bb1 = sb2[col + 1], w0 = sw3[col], w1 = sw3[col + 1];
+            y0 = fmaf(w0, fmaxf(c2[0] + bb0, 0.0f), y0);
+            y0 = fmaf(w1, fmaxf(c2[1] + bb1, 0.0f), y0);
+            y1 = fmaf(w0, fmaxf(c2[2] + bb0, 0.0f), y1);
+            y1 = fmaf(w1, fmaxf(c2[3] + bb1, 0.0f), y1);
+        }
+        // the four lanes of a row group hold disjoint columns
+        y0 += __shfl_xor_sync(0xffffffffu, y0, 1);
+        y0 += __shfl_xor_sync(0xffffffffu, y0, 2);
+        y1 += __shfl_xor_sync(0xffffffffu, y1, 1);
+        y1 += __shfl_xor_sync(0xffffffffu, y1, 2);
+        if (t == 0) {
+            const uint64_t v = tile * 16 + g;
+            if (v < n) out[v] = y0 + b3;
+            if (v + 8 < n) out[v + 8] = y1 + b3;
+        }
     }
 }
 
@@ -285,7 +470,14 @@ __global__ void exp_sum_kernel(const float* __restrict__ pred, uint32_t n, doubl
         s += (double)expf(fminf(fmaxf(pred[v], -80.0f), 80.0f));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(sum, s);
+    __shared__ double sh[32];
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {  // one FP64 atomic per block
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+        atomicAdd(sum, t);
+    }
 }
 
 __global__ void normalise_kernel(const float* __restrict__ pred, uint32_t n, const double* __restrict__ sum,
@@ -315,43 +507,98 @@ size_t train_smem() { return (size_t)(P + 2 * kTile * kRow + kTile * F + kTile) 
 
 using namespace pcpm;
 
+namespace pcpm {
+namespace {
+// The three exact in-edge sums of a whole-graph handle into sums[3][n].
+int degree_sums(pcpm_png* g, const uint32_t* row_ptr, uint32_t* sums, cudaStream_t s) {
+    static std::once_flag attr_once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(attr_once, [] {
+        const size_t smem = PCPM_MAX_PART_SIZE * sizeof(uint32_t);
+        cudaError_t e = cudaFuncSetAttribute(bin_degree_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(bin_degree_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(bin_degree_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr_err = e;
+    });
+    if (attr_err != cudaSuccess) {
+        note_cuda_error(attr_err);
+        return PCPM_ECUDA;
+    }
+    const uint32_t n = g->n;
+    const size_t smem = (size_t)g->q * sizeof(uint32_t);
+    int* err = &g->state->err;
+    if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess) return PCPM_ECUDA;
+    bin_degree_kernel<0><<<g->k, kDegThreads, smem, s>>>(g->dest, g->src, g->bin_e, g->chunk_base, n, g->q, row_ptr,
+                                                          nullptr, sums, err);
+    bin_degree_kernel<1><<<g->k, kDegThreads, smem, s>>>(g->dest, g->src, g->bin_e, g->chunk_base, n, g->q, row_ptr,
+                                                          sums, sums + n, err);
+    bin_degree_kernel<2><<<g->k, kDegThreads, smem, s>>>(g->dest, g->src, g->bin_e, g->chunk_base, n, g->q, row_ptr,
+                                                          nullptr, sums + 2 * (size_t)n, err);
+    return launch_status();
+}
+
+int check_state_err(pcpm_png* g, cudaStream_t s) {
+    int h = 0;
+    if (cudaMemcpyAsync(&h, &g->state->err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return PCPM_ECUDA;
+    return h ? PCPM_EDEVICE : PCPM_OK;
+}
+
+bool whole_graph(const pcpm_png* g) { return g->plo == 0 && g->phi == g->k; }
+}  // namespace
+}  // namespace pcpm
+
+extern "C" int pcpm_ws_degree_sums(pcpm_png* png, const uint32_t* row_ptr, uint32_t* sums, void* stream) {
+    if (!png || !whole_graph(png) || !is_dev(row_ptr) || !is_dev(sums)) return PCPM_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    png->last_stream = s;
+    int rc = degree_sums(png, row_ptr, sums, s);
+    if (rc == PCPM_OK) rc = check_state_err(png, s);
+    return rc;
+}
+
 extern "C" int pcpm_ws_features(pcpm_png* png, const uint32_t* row_ptr, const uint32_t* col, float* features,
                                 void* stream) {
-    pcpm_png_info info;
-    if (!png || pcpm_png_get_info(png, &info) != PCPM_OK) return PCPM_EINVAL;
-    if (!is_dev(row_ptr) || !is_dev(features) || (info.num_edges > 0 && !is_dev(col))) return PCPM_EINVAL;
-    const uint32_t n = info.n;
+    (void)col;
+    if (!png || !whole_graph(png) || !is_dev(row_ptr) || !is_dev(features)) return PCPM_EINVAL;
+    const uint32_t n = png->n;
     cudaStream_t s = (cudaStream_t)stream;
-    // scratch: a staging vector and four sums (in-degree, the two 2-hop sums, PR_1)
-    float* buf = nullptr;
-    if (cudaMallocAsync((void**)&buf, (size_t)5 * n * sizeof(float), s) != cudaSuccess) {
+    png->last_stream = s;
+    // scratch: the three sums (uint32) and PR_1
+    uint32_t* sums = nullptr;
+    if (cudaMallocAsync((void**)&sums, (size_t)4 * n * sizeof(uint32_t), s) != cudaSuccess) {
         cudaGetLastError();
         return PCPM_ENOMEM;
     }
-    float *x = buf, *indeg = buf + (size_t)n, *s_in = buf + 2 * (size_t)n, *s_out = buf + 3 * (size_t)n,
-          *pr1 = buf + 4 * (size_t)n;
-    const int grid = grid_for_n(n, 256);
-    int rc = PCPM_OK;
-    // in-degree: sum of 1 over in-edges
-    degree_vector_kernel<<<grid, 256, 0, s>>>(row_ptr, n, nullptr, 1, x);
-    if (rc == PCPM_OK) rc = pull_sum(png, x, indeg, s);
-    // sum of indeg(u) over in-edges
-    if (rc == PCPM_OK) degree_vector_kernel<<<grid, 256, 0, s>>>(row_ptr, n, indeg, 1, x);
-    if (rc == PCPM_OK) rc = pull_sum(png, x, s_in, s);
-    // sum of outdeg(u) over in-edges
-    if (rc == PCPM_OK) degree_vector_kernel<<<grid, 256, 0, s>>>(row_ptr, n, nullptr, 2, x);
-    if (rc == PCPM_OK) rc = pull_sum(png, x, s_out, s);
+    float* pr1 = reinterpret_cast<float*>(sums + 3 * (size_t)n);
+    int rc = degree_sums(png, row_ptr, sums, s);
+    if (rc == PCPM_OK) rc = check_state_err(png, s);
     // PR_1: one Eq. 1 step from the uniform start
     if (rc == PCPM_OK) rc = pcpm_reset(png, nullptr, stream);
     if (rc == PCPM_OK) rc = pcpm_iterate(png, 0.85f, 1, 0.0, PCPM_TWO_PHASE, nullptr, nullptr, stream);
     if (rc == PCPM_OK) rc = pcpm_ranks(png, pr1, stream);
     if (rc == PCPM_OK) {
-        features_kernel<<<grid, 256, 0, s>>>(row_ptr, n, indeg, s_in, s_out, pr1, features);
+        features_kernel<<<grid_for_n(n, 256), 256, 0, s>>>(row_ptr, n, sums, pr1, features);
         if (cudaGetLastError() != cudaSuccess) rc = PCPM_ECUDA;
     }
-    cudaFreeAsync(buf, s);
+    cudaFreeAsync(sums, s);
     if (rc == PCPM_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = PCPM_ECUDA;
     return rc;
+}
+
+extern "C" int pcpm_ws_feature_moments(const float* features, uint32_t n, double* moments, void* stream) {
+    if (!is_dev(features) || !is_dev(moments) || n == 0) return PCPM_EINVAL;
+    moments_kernel<<<grid_for_n(n, kMomThreads), kMomThreads, 0, (cudaStream_t)stream>>>(features, n, moments);
+    return cudaGetLastError() == cudaSuccess ? PCPM_OK : PCPM_ECUDA;
+}
+
+extern "C" int pcpm_ws_standardisation(const double* moments, float* params, void* stream) {
+    if (!is_dev(moments) || !is_dev(params)) return PCPM_EINVAL;
+    standardisation_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(moments, params);
+    return cudaGetLastError() == cudaSuccess ? PCPM_OK : PCPM_ECUDA;
 }
 
 extern "C" int pcpm_ws_targets(const float* pr, uint32_t n, float* target, void* stream) {
@@ -364,8 +611,9 @@ extern "C" int pcpm_ws_targets(const float* pr, uint32_t n, float* target, void*
 extern "C" int pcpm_ws_predict(const float* params, const float* features, uint32_t n, float* out, void* stream) {
     if (!params || !features || !out) return PCPM_EINVAL;
     if (n == 0) return PCPM_OK;
-    predict_kernel<<<grid_for_n(n, kPredictThreads), kPredictThreads, 0, (cudaStream_t)stream>>>(params, features,
-                                                                                                  n, out);
+    const uint64_t tiles = ((uint64_t)n + 15) / 16;
+    const int blocks = (int)std::min<uint64_t>((tiles + kPredictWarps - 1) / kPredictWarps, 152ull * 8);
+    predict_kernel<<<blocks, kPredictWarps * 32, 0, (cudaStream_t)stream>>>(params, features, n, out);
     return cudaGetLastError() == cudaSuccess ? PCPM_OK : PCPM_ECUDA;
 }
 
@@ -408,7 +656,7 @@ extern "C" int pcpm_ws_init_ranks(const float* pred, uint32_t n, float* pr, void
     int rc = PCPM_OK;
     if (cudaMemsetAsync(sum, 0, sizeof(double), s) != cudaSuccess) rc = PCPM_ECUDA;
     if (rc == PCPM_OK) {
-        exp_sum_kernel<<<grid_for_n(n, 256), 256, 0, s>>>(pred, n, sum);
+        exp_sum_kernel<<<std::min(grid_for_n(n, 256), 152 * 4), 256, 0, s>>>(pred, n, sum);
         normalise_kernel<<<grid_for_n(n, 256), 256, 0, s>>>(pred, n, sum, pr);
         if (cudaGetLastError() != cudaSuccess) rc = PCPM_ECUDA;
     }

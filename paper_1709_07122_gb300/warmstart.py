@@ -9,8 +9,8 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import (PNG, WS_FEATURES, WS_HIDDEN, WS_PARAMS, WS_TRAINABLE, to_device_csr, ws_adam, ws_features,
-               ws_init_ranks, ws_loss_grad, ws_predict, ws_targets)
+from . import (PNG, WS_FEATURES, WS_HIDDEN, WS_PARAMS, WS_TRAINABLE, to_device_csr, ws_adam, ws_feature_moments,
+               ws_features, ws_init_ranks, ws_loss_grad, ws_predict, ws_standardisation, ws_targets)
 
 
 def rmat_params(a: float):
@@ -33,28 +33,25 @@ class Sample:
 
 
 def init_params(samples, seed: int = 0):
-    """Standardisation from the training features (a host sample of rows)
-    and He-normal weights; returns a CUDA float32 tensor [WS_PARAMS]."""
+    """Standardisation from all training features (FP64 moments summed on the
+    device) and He-normal initial weights, which are seeded random inputs
+    drawn on the host; returns a CUDA float32 tensor [WS_PARAMS]."""
     import torch
     rng = np.random.default_rng(seed)
-    rows = []
-    for s in samples:
-        k = min(s.n, 65536)
-        idx = np.sort(rng.choice(s.n, size=k, replace=False))
-        rows.append(s.features.cpu().numpy()[idx])
-    x = np.concatenate(rows).astype(np.float64)
-    mu, sd = x.mean(axis=0), x.std(axis=0)
-    p = np.zeros(WS_PARAMS, np.float32)
     F, H = WS_FEATURES, WS_HIDDEN
-    p[:F] = mu
-    p[F:2 * F] = 1.0 / np.maximum(sd, 1e-6)
+    p = np.zeros(WS_PARAMS, np.float32)
     o = WS_TRAINABLE
     p[o:o + H * F] = rng.standard_normal(H * F) * np.sqrt(2.0 / F)
     o += H * F + H
     p[o:o + H * H] = rng.standard_normal(H * H) * np.sqrt(2.0 / H)
     o += H * H + H
     p[o:o + H] = rng.standard_normal(H) * np.sqrt(1.0 / H)
-    return torch.from_numpy(p).cuda()
+    params = torch.from_numpy(p).cuda()
+    moments = torch.zeros(11, dtype=torch.float64, device="cuda")
+    for s in samples:
+        ws_feature_moments(s.features, moments)
+    ws_standardisation(moments, params)
+    return params
 
 
 def train(params, samples, steps: int = 600, batch: int = 65536, lr: float = 3e-3, seed: int = 1,

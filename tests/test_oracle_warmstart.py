@@ -72,6 +72,37 @@ def test_forward_closed_form_with_zero_weights():
     np.testing.assert_allclose(ws.forward(p, x), want, rtol=1e-14)
 
 
+def test_forward_by_explicit_loops():
+    # The parameter layout read entry by entry: W1[j][f] multiplies input f
+    # into hidden unit j (row j of the flat W1 block), W2[j][i] multiplies h1[i]
+    # into h2[j]. A transposed block or a dropped bias changes the output.
+    rng = np.random.default_rng(4)
+    p = random_params(rng, scale=0.5)
+    x = rng.standard_normal((6, ws.F)) * 2
+    F, H = ws.F, ws.H
+    for r in range(x.shape[0]):
+        xh = [(x[r][f] - p[ws.OFF_MU + f]) * p[ws.OFF_IS + f] for f in range(F)]
+        h1 = []
+        for j in range(H):
+            z = p[ws.OFF_B1 + j]
+            for f in range(F):
+                z += p[ws.OFF_W1 + j * F + f] * xh[f]
+            h1.append(max(z, 0.0))
+        h2 = []
+        for j in range(H):
+            z = p[ws.OFF_B2 + j]
+            for i in range(H):
+                z += p[ws.OFF_W2 + j * H + i] * h1[i]
+            h2.append(max(z, 0.0))
+        y = p[ws.OFF_B3] + sum(p[ws.OFF_W3 + j] * h2[j] for j in range(H))
+        assert abs(ws.forward(p, x[r:r + 1])[0] - y) <= 1e-12 * max(1.0, abs(y))
+    # the hidden layers are not symmetric in their indices: a transposed W2
+    # gives another network
+    q = p.copy()
+    q[ws.OFF_W2:ws.OFF_B2] = p[ws.OFF_W2:ws.OFF_B2].reshape(H, H).T.ravel()
+    assert np.abs(ws.forward(q, x) - ws.forward(p, x)).max() > 1e-3
+
+
 def test_gradient_matches_central_differences():
     rng = np.random.default_rng(2)
     p = random_params(rng)
