@@ -399,6 +399,18 @@ int pcpm_pagerank_host(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_
 int pcpm_scatter_only(pcpm_png* png, void* stream);
 int pcpm_export_state(const pcpm_png* png, float* pr, float* spr, void* updates, double* dangling);
 
+/* Test hook for the bounded device-side waits (PCPM_ETIMEOUT). Sets, on the
+ * current device and for every handle, the bound of the window-layout
+ * gather's waits for work (a free ring stage for the producer, a filled one
+ * for the consumers): `cycles` > 0 SM cycles; 0 restores the default (about
+ * one second); < 0 makes those waits give up at once, as if what they wait for
+ * never happened. A wait that gives up sets PCPM_ETIMEOUT in the handle's
+ * state, stops the CTA's streaming and leaves that launch's ranks undefined;
+ * the copies already in flight are still waited for with the default bound
+ * before the CTA exits. pcpm_reset clears the status. Not for concurrent use
+ * with other work on the device. */
+int pcpm_test_wait_limit(long long cycles);
+
 /* Allocation-free rank statistics. There is no counterpart in the paper: this
  * entry point exists for callers that cannot call cudaMalloc, such as code
  * running inside a custom memory pool or allocator callback that must not

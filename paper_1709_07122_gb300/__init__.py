@@ -130,6 +130,7 @@ def lib(path: str | None = None):
                 "pcpm_shard_init": (i32, [vp, vp, vp, vp, vp]),
                 "pcpm_shard_step": (i32, [vp, f32, u32, vp, vp, vp, vp]),
                 "pcpm_sync_status": (i32, [vp]),
+                "pcpm_test_wait_limit": (i32, [ctypes.c_longlong]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)

@@ -893,6 +893,8 @@ int pcpm_export_state(const pcpm_png* g, float* pr, float* spr, void* updates, d
     return PCPM_OK;
 }
 
+int pcpm_test_wait_limit(long long cycles) { return set_work_wait_limit(cycles); }
+
 const char* pcpm_last_cuda_error(void) { return cudaGetErrorName(g_last_cuda_error); }
 
 const char* pcpm_strerror(int code) {

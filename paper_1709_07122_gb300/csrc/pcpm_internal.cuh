@@ -233,6 +233,8 @@ int launch_init_range(pcpm_png* g, const float* pr_init, float* out, uint32_t lo
 int launch_scatter(pcpm_png* g, cudaStream_t s, bool raw = false);
 // spmv: the weighted gather of a weighted handle (Sec. 3.5).
 int launch_gather(pcpm_png* g, float d, uint32_t flags, bool fused, cudaStream_t s, bool spmv = false);
+// The window gather's bound on waits for work (see pcpm_test_wait_limit).
+int set_work_wait_limit(long long cycles);
 // record = false: the L1 change goes to the device state only, not the history.
 int launch_reduce(pcpm_png* g, double tol, int hist_slot, cudaStream_t s, bool record = true);
 int launch_spr(pcpm_png* g, float* spr, cudaStream_t s);

@@ -135,6 +135,22 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     return true;
 }
 
+// The bound of the window gather's waits for work (a stage to fill, a
+// window to consume), in SM cycles: kWaitLimitCycles unless a test shortens it
+// (pcpm_test_wait_limit); negative: give up without waiting. Waits that drain
+// copies still in flight always keep kWaitLimitCycles, so no copy can land
+// after its CTA has exited.
+__device__ long long g_work_wait_limit = kWaitLimitCycles;
+
+__device__ __forceinline__ bool mbar_wait_work(uint64_t* bar, uint32_t parity, long long limit) {
+    if (limit < 0) return false;
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > limit) return false;
+    return true;
+}
+
 // ------------------------------------------------------------------- cluster
 __device__ __forceinline__ uint32_t cluster_rank() {
     uint32_t r;
@@ -1261,6 +1277,7 @@ __global__ void __launch_bounds__(kWinThreads, 1) gather_win_kernel(const Gather
     const uint32_t nwu = unit.z - unit.y;
     const uint32_t w0 = unit.y + (uint32_t)((uint64_t)nwu * rank / S);
     const uint32_t nmine = unit.y + (uint32_t)((uint64_t)nwu * (rank + 1) / S) - w0;
+    const long long work_limit = g_work_wait_limit;
 
     if (warp == (uint32_t)kWinWarps) {
         if (lane == 0) {  // producer
@@ -1275,7 +1292,7 @@ __global__ void __launch_bounds__(kWinThreads, 1) gather_win_kernel(const Gather
                 const uint4 dsc = next;  // (slice start, slice bytes, word bytes, IDs)
                 if (j + 1 < nmine) next = a.wdesc[w0 + j + 1];
                 const uint32_t s = j % R::kStages;
-                if (j >= (uint32_t)R::kStages && !mbar_wait_bounded(&empty[s], ((j / R::kStages) - 1) & 1u)) {
+                if (j >= (uint32_t)R::kStages && !mbar_wait_work(&empty[s], ((j / R::kStages) - 1) & 1u, work_limit)) {
                     ok = false;
                     break;
                 }
@@ -1287,19 +1304,19 @@ __global__ void __launch_bounds__(kWinThreads, 1) gather_win_kernel(const Gather
                 if (dsc.y)
                     bulk_load_hint(st + R::kUpdOff, static_cast<const T*>(a.upd_in) + dsc.x, dsc.y, &full[s], policy);
             }
-            if (!ok) {
-                // a stage was not released in time: record it and wait
-                // (bounded) for the copies still in flight
-                atomicOr(a.err, kErrTimeout);
-                for (uint32_t jj = j > (uint32_t)R::kStages ? j - R::kStages : 0u; jj < j; ++jj)
-                    (void)mbar_wait_bounded(&full[jj % R::kStages], (jj / R::kStages) & 1u);
-            }
+            // a stage that was not released in time is recorded; either way
+            // the last window issued into each stage has landed (bounded wait)
+            // before this warp reaches the merge: consumers that gave up no
+            // longer wait for them, and no copy may land after the CTA exits
+            if (!ok) atomicOr(a.err, kErrTimeout);
+            for (uint32_t jj = j > (uint32_t)R::kStages ? j - R::kStages : 0u; jj < j; ++jj)
+                (void)mbar_wait_bounded(&full[jj % R::kStages], (jj / R::kStages) & 1u);
         }
         __syncwarp();
     } else {
         for (uint32_t j = 0; j < nmine; ++j) {
             const uint32_t s = j % R::kStages;
-            if (!__all_sync(kFull, mbar_wait_bounded(&full[s], (j / R::kStages) & 1u))) {
+            if (!__all_sync(kFull, mbar_wait_work(&full[s], (j / R::kStages) & 1u, work_limit))) {
                 if (lane == 0) atomicOr(a.err, kErrTimeout);
                 break;
             }
@@ -1648,6 +1665,16 @@ int launch_gather(pcpm_png* g, float d, uint32_t flags, bool fused, cudaStream_t
     g->partial_count = (int)(g->ngunits * g->cluster);
     if (e != cudaSuccess) note_cuda_error(e);
     return e == cudaSuccess ? PCPM_OK : PCPM_ECUDA;
+}
+
+int set_work_wait_limit(long long cycles) {
+    const long long v = cycles == 0 ? kWaitLimitCycles : cycles;
+    const cudaError_t e = cudaMemcpyToSymbol(g_work_wait_limit, &v, sizeof(v));
+    if (e != cudaSuccess) {
+        note_cuda_error(e);
+        return PCPM_ECUDA;
+    }
+    return PCPM_OK;
 }
 
 int launch_reduce(pcpm_png* g, double tol, int hist_slot, cudaStream_t s, bool record) {
