@@ -58,8 +58,13 @@ int pcpm_ws_features(pcpm_png* png, const uint32_t* row_ptr, const uint32_t* col
  * u -> v, each one pass over the handle's canonical bins (every in-edge of a
  * node of partition p lies in bin p; Sec. 3.1) with unsigned 32-bit
  * shared-memory sums per bin. The source of each destination ID is that of its
- * update (Algorithm 4's update index). row_ptr: the CSR given to pcpm_build.
- * Synchronises; PCPM_EDEVICE if a sum passes 2^32 - 1. */
+ * update (Algorithm 4's update index). On handles with FP32 update bins the
+ * per-source degrees are first scattered into the bins (Algorithm 3, copied
+ * bit for bit), so the sums read them in bin order instead of at random. The
+ * in-degree comes from the build where the window layout kept it. Overwrites
+ * the handle's update bins and solver state (pcpm_reset before solving).
+ * row_ptr: the CSR given to pcpm_build. Synchronises;
+ * PCPM_EDEVICE if a sum passes 2^32 - 1. */
 int pcpm_ws_degree_sums(pcpm_png* png, const uint32_t* row_ptr, uint32_t* sums, void* stream);
 
 /* Feature statistics for the standardisation, summed in FP64 over all n rows
@@ -75,11 +80,10 @@ int pcpm_ws_standardisation(const double* moments, float* params, void* stream);
 int pcpm_ws_targets(const float* pr, uint32_t n, float* target, void* stream);
 
 /* Network output for n feature rows, with W1, b1, W2, b2, w3, b3 rounded to
- * bfloat16 (nearest even), on the tensor cores (mma m16n8k16, BF16 operands,
- * FP32 accumulation). The standardised inputs and h1 enter the products as
- * two BF16 parts each (x = hi + lo, |x - hi - lo| <= 2^-18 |x|), so the
- * products keep about 16 significant bits of the activations; biases, ReLU
- * and the output dot product with w3 are FP32.
+ * bfloat16 (nearest even). Both hidden layers run on the tensor cores (mma
+ * m16n8k16, BF16 operands, FP32 accumulation) with the standardised inputs
+ * and h1 rounded to BF16 (relative error <= 2^-9 each); the standardisation,
+ * biases, ReLU and the output dot product with w3 are FP32.
  *   params float[PCPM_WS_PARAMS]; features float[n][5]; out float[n]. */
 int pcpm_ws_predict(const float* params, const float* features, uint32_t n, float* out, void* stream);
 
@@ -99,9 +103,10 @@ int pcpm_ws_adam(float* params, const float* grad, float* m, float* v, int step,
                  float beta2, float eps, void* stream);
 
 /* Initial ranks from predictions: pr(v) = exp(p(v)) / sum_u exp(p(u)) with
- * p = pred clamped to [-80, 80] (so no term overflows FP32), the sum in FP64.
- * pred: float[n]; pr: float[n]. Allocates 8 bytes of device scratch.
- * Synchronises. */
+ * p = pred clamped to [-80, 80] (so no term overflows FP32), the sum in FP64,
+ * each quotient as expf(p(v)) times the FP32 reciprocal of the sum.
+ * pred: float[n]; pr: float[n]. Takes 8 bytes of stream-ordered scratch from
+ * the library's pool. Does not synchronise. */
 int pcpm_ws_init_ranks(const float* pred, uint32_t n, float* pr, void* stream);
 
 #ifdef __cplusplus

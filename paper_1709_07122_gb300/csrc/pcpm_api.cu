@@ -108,7 +108,7 @@ void release(pcpm_png* g) {
                     g->gunits, g->gorder, g->sunits, g->sorder, g->gacc,
                     g->bin_done, g->inv_deg, g->pr[0], g->pr[1], g->upd[0], g->upd[1], g->partials,
                     g->hist, g->state, g->wdest, g->gweight, g->win_start, g->wwords, g->wweight, g->wdesc,
-                    g->whubs};
+                    g->whubs, g->indeg};
     // the caller has waited for every use of the handle's memory
     for (void* p : ptrs) pool_free(p, g->last_stream);
     if (g->state_host) cudaFreeHost(g->state_host);

@@ -153,6 +153,7 @@ struct pcpm_png {
     float* wweight;          // weighted graphs: weights at their IDs' word positions
     uint4* wdesc;            // nwin
     uint32_t* whubs;         // k * kWinHubs: local IDs of each bin's hubs (or kNoHub)
+    uint32_t* indeg;         // n: in-degree of every node in the handle's bins (window layout only)
     uint32_t* gdest;         // nichunks * kChunk words
     uint32_t* gslice_start;  // nichunks: first update of the chunk's slice (multiple of 4)
     uint32_t* gslice_bytes;  // nichunks: bytes of the slice (multiple of 16)
@@ -231,6 +232,9 @@ int launch_init(pcpm_png* g, const float* pr_init, cudaStream_t s);
 int launch_init_range(pcpm_png* g, const float* pr_init, float* out, uint32_t lo, uint32_t hi, cudaStream_t s);
 // raw: stage x itself (SpMV) instead of x * (1/outdeg).
 int launch_scatter(pcpm_png* g, cudaStream_t s, bool raw = false);
+// Algorithm 3 for a 32-bit value per node, copied bit for bit: out[t] = x[src[t]]
+// in the update bins' layout (FP32 update bins only; PCPM_EINVAL otherwise).
+int launch_scatter_bits(pcpm_png* g, const void* x, void* out, cudaStream_t s);
 // spmv: the weighted gather of a weighted handle (Sec. 3.5).
 int launch_gather(pcpm_png* g, float d, uint32_t flags, bool fused, cudaStream_t s, bool spmv = false);
 // The window gather's bound on waits for work (see pcpm_test_wait_limit).

@@ -597,14 +597,15 @@ __global__ void __launch_bounds__(kScatterThreads, 1) scatter_kernel(
                     const uint32_t i = i0 + j * blockDim.x;
                     if (i < v4)
                         reinterpret_cast<float4*>(sspr)[i] =
-                            make_float4(x[j].x * w[j].x, x[j].y * w[j].y, x[j].z * w[j].z, x[j].w * w[j].w);
+                            inv_deg ? make_float4(x[j].x * w[j].x, x[j].y * w[j].y, x[j].z * w[j].z, x[j].w * w[j].w)
+                                    : x[j];  // unscaled: a bit-for-bit copy
                 }
             }
             for (uint32_t i = (v4 << 2) + threadIdx.x; i < len; i += blockDim.x)
-                sspr[i] = pr[base + i] * (inv_deg ? inv_deg[base + i] : 1.0f);
+                sspr[i] = inv_deg ? pr[base + i] * inv_deg[base + i] : pr[base + i];
         } else {
             for (uint32_t i = threadIdx.x; i < len; i += blockDim.x)
-                sspr[i] = pr[base + i] * (inv_deg ? inv_deg[base + i] : 1.0f);
+                sspr[i] = inv_deg ? pr[base + i] * inv_deg[base + i] : pr[base + i];
         }
     };
     scatter_groups_staged<kUpd>(sspr, base, len, gpre, dsh, emsk, k, src, upd, unit.y, min(unit.z, gpre[k]), err,
@@ -1596,6 +1597,14 @@ int launch_scatter(pcpm_png* g, cudaStream_t s, bool raw) {
                                                g->seg_u,
                                                g->cnt_u, g->sunits, g->sorder, g->upd[g->ucur], g->state,
                                                &g->state->err);
+    return launch_status();
+}
+
+int launch_scatter_bits(pcpm_png* g, const void* x, void* out, cudaStream_t s) {
+    if (g->upd_dtype != kUpdF32) return PCPM_EINVAL;
+    scatter_kernel<kUpdF32><<<g->nsunits, kScatterThreads, scatter_smem_bytes(g->q, g->k), s>>>(
+        g->n, g->q, g->k, static_cast<const float*>(x), nullptr, g->src, g->seg_u, g->cnt_u, g->sunits, g->sorder,
+        out, g->state, &g->state->err);
     return launch_status();
 }
 

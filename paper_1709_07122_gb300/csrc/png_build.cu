@@ -1125,7 +1125,8 @@ __global__ void __launch_bounds__(kLayoutWarps * 32) gather_layout_kernel(
 //       block count.
 __global__ void __launch_bounds__(1024) bin_owner_kernel(const uint32_t* __restrict__ dest,
                                                          const uint32_t* __restrict__ bin_e, uint32_t n, uint32_t q,
-                                                         uint32_t* __restrict__ whubs, uint32_t* __restrict__ bnd) {
+                                                         uint32_t* __restrict__ whubs, uint32_t* __restrict__ bnd,
+                                                         uint32_t* __restrict__ indeg) {
     extern __shared__ uint32_t deg[];  // q in-degrees, then one weight per block
     __shared__ unsigned long long sh[32];
     __shared__ uint32_t sh32[32];
@@ -1148,6 +1149,7 @@ __global__ void __launch_bounds__(1024) bin_owner_kernel(const uint32_t* __restr
             if (loc[j] < len) atomicAdd(&deg[loc[j]], 1u);
     }
     __syncthreads();
+    for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) indeg[base + i] = deg[i];  // kept by the handle
     for (uint32_t h = 0; h < kWinHubs; ++h) {
         unsigned long long best = 0;
         for (uint32_t i = threadIdx.x; i < len; i += blockDim.x)
@@ -1784,7 +1786,8 @@ int build_png(pcpm_png* g, const uint32_t* row_ptr, const uint32_t* col, const p
         BCK(dev_alloc(g, (void**)&g->whubs, (size_t)k * kWinHubs * sizeof(uint32_t)));
         const size_t own_smem = ((size_t)((q + 31) & ~31u) + 1024) * sizeof(uint32_t);
         BCK(cudaFuncSetAttribute(bin_owner_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)own_smem));
-        bin_owner_kernel<<<k, 1024, own_smem, s>>>(g->dest, g->bin_e, n, q, g->whubs, bnd);
+        BCK(dev_alloc(g, (void**)&g->indeg, (size_t)n * sizeof(uint32_t)));
+        bin_owner_kernel<<<k, 1024, own_smem, s>>>(g->dest, g->bin_e, n, q, g->whubs, bnd, g->indeg);
         BCK(cudaGetLastError());
         BCK(dev_alloc(g, (void**)&g->win_start, (k + 1) * sizeof(uint32_t)));
         bin_window_counts_kernel<<<grid_for(k, 256, 64), 256, 0, s>>>(g->bin_e, k, wc);

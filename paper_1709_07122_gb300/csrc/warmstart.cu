@@ -38,18 +38,40 @@ constexpr int kRow = H + 1;    // padded shared-memory row
 // Exact in-edge sums over the canonical bins, one CTA per destination bin p
 // (every in-edge of a node of p lies in bin p): acc[v - p q] += val for every
 // destination ID v of the bin, with val = 1 (kMode 0: the in-degree), indeg(u)
-// (1) or outdeg(u) (2) of the ID's source u. The source is that of the ID's
+// (1) or outdeg(u) (2) of the ID's source u, or (3) the ID's update value
+// vals[idx] (a per-source value already scattered into the update bins by
+// Algorithm 3, so it is read in bin order instead of at random). The source
+// is that of the ID's
 // update: Algorithm 4's update index, the flagged IDs up to and including the
 // ID minus one, found from the chunk's precomputed base and a ballot per 32
 // IDs. Unsigned 32-bit shared-memory atomics; a sum that passes 2^32 sets
 // kErrBounds in *err.
-constexpr int kDegThreads = 1024;
+constexpr int kDegThreads = 512;
+
+// L2 policies: the bins stream through once (evict first), the degree tables
+// are read at random and should stay in L2 (evict last).
+__device__ __forceinline__ uint64_t l2_policy_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint32_t ld_hint(const uint32_t* p, uint64_t policy) {
+    uint32_t v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(policy));
+    return v;
+}
 
 template <int kMode>
 __global__ void __launch_bounds__(kDegThreads) bin_degree_kernel(
     const uint32_t* __restrict__ dest, const uint32_t* __restrict__ src, const uint32_t* __restrict__ bin_e,
     const uint32_t* __restrict__ chunk_base, uint32_t n, uint32_t q, const uint32_t* __restrict__ row_ptr,
-    const uint32_t* __restrict__ indeg, uint32_t* __restrict__ out, int* __restrict__ err) {
+    const uint32_t* __restrict__ indeg, uint32_t* __restrict__ out, int* __restrict__ err,
+    const uint32_t* __restrict__ vals = nullptr) {
     extern __shared__ uint32_t acc[];
     const uint32_t p = blockIdx.x;
     const uint32_t v0 = p * q, len = min(q, n - v0);
@@ -60,24 +82,52 @@ __global__ void __launch_bounds__(kDegThreads) bin_degree_kernel(
     if (e1 > e0) {
         const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
         const uint32_t c0 = e0 / kChunk, c1 = (e1 - 1) / kChunk;
-        for (uint32_t c = c0 + warp; c <= c1; c += nw) {
-            uint32_t base = chunk_base[c];
-#pragma unroll 2
-            for (uint32_t r = 0; r < kChunk / 32; ++r) {
-                const uint32_t e = c * kChunk + r * 32 + lane;
-                const uint32_t id = e < e1 ? dest[e] : 0u;
-                const uint32_t fl = __ballot_sync(0xffffffffu, (id & kMsb) != 0u);
-                const uint32_t idx = base + __popc(fl & ((2u << lane) - 1u)) - 1u;
-                base += __popc(fl);
-                const uint32_t loc = (id & kIdMask) - v0;
-                if (e >= e0 && e < e1 && loc < len) {
-                    uint32_t val = 1u;
-                    if (kMode != 0) {
-                        const uint32_t u = src[idx];
-                        val = kMode == 1 ? indeg[u] : row_ptr[u + 1] - row_ptr[u];
-                    }
-                    const uint32_t old = atomicAdd(&acc[loc], val);
-                    over |= old + val < old;
+        constexpr uint32_t kR = kChunk / 32;  // rounds of 32 IDs per chunk
+        constexpr uint32_t kC = 4;            // chunks per warp step
+        const uint64_t stream = l2_policy_first(), keep = l2_policy_last();
+        for (uint32_t cb = c0 + kC * warp; cb <= c1; cb += kC * nw) {
+            // all loads of a step are issued before any is used: the IDs,
+            // then the sources of the in-bin IDs, then their degrees
+            uint32_t id[kC * kR], idx[kC * kR];
+#pragma unroll
+            for (uint32_t i = 0; i < kC * kR; ++i) {
+                const uint32_t e = (cb + i / kR) * kChunk + (i % kR) * 32 + lane;
+                id[i] = (cb + i / kR <= c1 && e < e1) ? ld_hint(dest + e, stream) : 0u;
+            }
+#pragma unroll
+            for (uint32_t ci = 0; ci < kC; ++ci) {
+                uint32_t base = cb + ci <= c1 ? chunk_base[cb + ci] : 0u;
+#pragma unroll
+                for (uint32_t r = 0; r < kR; ++r) {
+                    const uint32_t i = ci * kR + r;
+                    const uint32_t fl = __ballot_sync(0xffffffffu, (id[i] & kMsb) != 0u);
+                    idx[i] = base + __popc(fl & ((2u << lane) - 1u)) - 1u;
+                    base += __popc(fl);
+                    const uint32_t e = (cb + ci) * kChunk + r * 32 + lane;
+                    if (cb + ci > c1 || e < e0 || e >= e1 || (id[i] & kIdMask) - v0 >= len)
+                        id[i] = kNoHub;  // not this bin's
+                }
+            }
+            uint32_t val[kC * kR];
+            if (kMode == 3) {  // the ID's update holds the value (scattered by source partition)
+#pragma unroll
+                for (uint32_t i = 0; i < kC * kR; ++i) val[i] = id[i] != kNoHub ? ld_hint(vals + idx[i], stream) : 0u;
+            } else if (kMode != 0) {
+                uint32_t u[kC * kR];
+#pragma unroll
+                for (uint32_t i = 0; i < kC * kR; ++i) u[i] = id[i] != kNoHub ? ld_hint(src + idx[i], stream) : 0u;
+#pragma unroll
+                for (uint32_t i = 0; i < kC * kR; ++i)
+                    val[i] = id[i] == kNoHub ? 0u
+                             : kMode == 1    ? ld_hint(indeg + u[i], keep)
+                                             : ld_hint(row_ptr + u[i] + 1, keep) - ld_hint(row_ptr + u[i], keep);
+            }
+#pragma unroll
+            for (uint32_t i = 0; i < kC * kR; ++i) {
+                if (id[i] != kNoHub) {
+                    const uint32_t add = kMode == 0 ? 1u : val[i];
+                    const uint32_t old = atomicAdd(&acc[(id[i] & kIdMask) - v0], add);
+                    over |= old + add < old;
                 }
             }
         }
@@ -85,6 +135,11 @@ __global__ void __launch_bounds__(kDegThreads) bin_degree_kernel(
     if (over) atomicOr(err, kErrBounds);
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) out[v0 + i] = acc[i];
+}
+
+__global__ void degree_u32_kernel(const uint32_t* __restrict__ row_ptr, uint32_t n, uint32_t* __restrict__ out) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        out[v] = row_ptr[v + 1] - row_ptr[v];
 }
 
 __global__ void features_kernel(const uint32_t* __restrict__ row_ptr, uint32_t n, const uint32_t* __restrict__ sums,
@@ -183,13 +238,12 @@ __device__ __forceinline__ void layer1(const float* w, const float* xh, float* h
 }
 
 // ------------------------------------------------------------ inference
-// Inference on the tensor cores: mma.sync m16n8k16 with BF16 operands and
-// FP32 accumulation, one warp per tile of 16 nodes. The weights are BF16 by
-// definition (rounded once, nearest even) and stay in registers as B
-// fragments for the whole kernel. Activations are carried as two BF16 parts,
-// hi = bf16(x) and lo = bf16(x - hi), so every product A B is two MMAs,
-// A_hi B + A_lo B, and the activations keep about 16 significant bits
-// (|x - hi - lo| <= 2^-18 |x|) instead of BF16's 8.
+// One warp per tile of 16 nodes, both hidden layers on the tensor cores:
+// mma.sync m16n8k16 with BF16 operands and FP32 accumulation. The weights are
+// BF16 by definition (rounded once, nearest even) and stay in registers as B
+// fragments for the whole kernel; the standardised inputs (K = 5, padded to
+// 16) and h1 are rounded to BF16 (relative 2^-9) for the products. Biases,
+// ReLU and the output dot product with w3 are FP32.
 //
 // Fragment layouts (PTX ISA, mma.m16n8k16, g = lane / 4, t = lane % 4):
 //   A (16 x 16, row-major), 4 registers of two BF16: (row g, k 2t..2t+1),
@@ -200,16 +254,9 @@ __device__ __forceinline__ void layer1(const float* w, const float* xh, float* h
 // the A fragment of input columns 16k .. 16k+15 of the next layer, so h1 goes
 // from layer 1 to layer 2 without leaving the registers.
 constexpr int kPredictWarps = 8;
+constexpr int kPredictGroup = 4;  // tiles per warp step: the next step's loads are in flight meanwhile
 
 __device__ __forceinline__ uint32_t bf16x2_bits(__nv_bfloat162 h) { return *reinterpret_cast<uint32_t*>(&h); }
-
-// The two BF16 parts of (a, b), low halves first.
-__device__ __forceinline__ void split_bf16x2(float a, float b, uint32_t& hi, uint32_t& lo) {
-    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-    const float2 hf = __bfloat1622float2(h);
-    hi = bf16x2_bits(h);
-    lo = bf16x2_bits(__floats2bfloat162_rn(a - hf.x, b - hf.y));
-}
 
 __device__ __forceinline__ void mma_bf16_16816(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
                                                uint32_t b0, uint32_t b1) {
@@ -259,75 +306,77 @@ __global__ void __launch_bounds__(kPredictWarps * 32) predict_kernel(const float
     __syncthreads();
     const uint64_t warps = (uint64_t)gridDim.x * kPredictWarps;
     const uint64_t ntiles = ((uint64_t)n + 15) / 16;
-    // features of a tile: rows g and g + 8, columns 2t and 2t + 1 (< F)
-    auto load_x = [&](uint64_t tile, float (&x)[4]) {
+    const uint64_t ngroups = (ntiles + kPredictGroup - 1) / kPredictGroup;
+    // features of a group of tiles: per tile rows g and g + 8, columns 2t and
+    // 2t + 1 (< F). A warp works on groups of kPredictGroup tiles and loads
+    // the next group's features while it computes this one.
+    auto load_x = [&](uint64_t grp, float (&x)[kPredictGroup][4]) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const uint64_t v = tile * 16 + g + 8 * (i >> 1);
-            const int f = 2 * t + (i & 1);
-            x[i] = (tile < ntiles && v < n && f < F) ? __ldg(feat + v * F + f) : 0.0f;
-        }
+        for (int tt = 0; tt < kPredictGroup; ++tt)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const uint64_t v = (grp * kPredictGroup + tt) * 16 + g + 8 * (i >> 1);
+                const int f = 2 * t + (i & 1);
+                x[tt][i] = (grp < ngroups && v < n && f < F) ? __ldg(feat + v * F + f) : 0.0f;
+            }
     };
-    uint64_t tile = (uint64_t)blockIdx.x * kPredictWarps + (threadIdx.x >> 5);
-    float xn[4];
-    load_x(tile, xn);
+    uint64_t grp = (uint64_t)blockIdx.x * kPredictWarps + (threadIdx.x >> 5);
+    float xn[kPredictGroup][4];
+    load_x(grp, xn);
 #pragma unroll 1
-    for (; tile < ntiles; tile += warps) {
-        float x[4];
+    for (; grp < ngroups; grp += warps) {
+        float xg[kPredictGroup][4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) x[i] = xn[i];
-        load_x(tile + warps, xn);  // the next tile's loads overlap this tile
-        // layer 1: standardise, split, 8 n-tiles x 2 parts
-        uint32_t ah[2], al[2];
-        split_bf16x2((x[0] - mu[0]) * is[0], (x[1] - mu[1]) * is[1], ah[0], al[0]);
-        split_bf16x2((x[2] - mu[0]) * is[0], (x[3] - mu[1]) * is[1], ah[1], al[1]);
-        float c1[8][4];
+        for (int tt = 0; tt < kPredictGroup; ++tt)
 #pragma unroll
-        for (int jt = 0; jt < 8; ++jt) {
-            c1[jt][0] = c1[jt][1] = c1[jt][2] = c1[jt][3] = 0.0f;
-            mma_bf16_16816(c1[jt], ah[0], ah[1], 0u, 0u, bw1[jt], 0u);
-            mma_bf16_16816(c1[jt], al[0], al[1], 0u, 0u, bw1[jt], 0u);
-        }
-        // h1 = relu(c1 + b1) as the A fragments of layer 2
-        uint32_t a2h[4][4], a2l[4][4];
+            for (int i = 0; i < 4; ++i) xg[tt][i] = xn[tt][i];
+        load_x(grp + warps, xn);  // the next group's loads overlap this group
 #pragma unroll
-        for (int kt = 0; kt < 4; ++kt) {
+        for (int tt = 0; tt < kPredictGroup; ++tt) {
+            const uint64_t tile = grp * kPredictGroup + tt;
+            if (tile >= ntiles) break;
+            const float* x = xg[tt];
+            // layer 1: 8 n-tiles; A has k = 2t, 2t+1 only (k >= 8 are zero)
+            const uint32_t a0 = bf16x2_bits(__floats2bfloat162_rn((x[0] - mu[0]) * is[0], (x[1] - mu[1]) * is[1]));
+            const uint32_t a1 = bf16x2_bits(__floats2bfloat162_rn((x[2] - mu[0]) * is[0], (x[3] - mu[1]) * is[1]));
+            uint32_t a2[4][4];
 #pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                const int jt = 2 * kt + half, col = 8 * jt + 2 * t;
+            for (int jt = 0; jt < 8; ++jt) {
+                float c1[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                mma_bf16_16816(c1, a0, a1, 0u, 0u, bw1[jt], 0u);
+                // h1 = relu(c1 + b1) as the A fragments of layer 2
+                const int col = 8 * jt + 2 * t, kt = jt >> 1, half = jt & 1;
                 const float bb0 = sb1[col], bb1 = sb1[col + 1];
-                split_bf16x2(fmaxf(c1[jt][0] + bb0, 0.0f), fmaxf(c1[jt][1] + bb1, 0.0f), a2h[kt][2 * half],
-                             a2l[kt][2 * half]);
-                split_bf16x2(fmaxf(c1[jt][2] + bb0, 0.0f), fmaxf(c1[jt][3] + bb1, 0.0f), a2h[kt][2 * half + 1],
-                             a2l[kt][2 * half + 1]);
+                a2[kt][2 * half] =
+                    bf16x2_bits(__floats2bfloat162_rn(fmaxf(c1[0] + bb0, 0.0f), fmaxf(c1[1] + bb1, 0.0f)));
+                a2[kt][2 * half + 1] =
+                    bf16x2_bits(__floats2bfloat162_rn(fmaxf(c1[2] + bb0, 0.0f), fmaxf(c1[3] + bb1, 0.0f)));
             }
-        }
-        // layer 2 and the output dot product, one n-tile at a time
-        float y0 = 0.0f, y1 = 0.0f;
+            // layer 2 and the output dot product, one n-tile at a time
+            float y0 = 0.0f, y1 = 0.0f;
 #pragma unroll
-        for (int jt = 0; jt < 8; ++jt) {
-            float c2[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            for (int jt = 0; jt < 8; ++jt) {
+                float c2[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-            for (int kt = 0; kt < 4; ++kt) {
-                mma_bf16_16816(c2, a2h[kt][0], a2h[kt][1], a2h[kt][2], a2h[kt][3], bw2[kt][jt][0], bw2[kt][jt][1]);
-                mma_bf16_16816(c2, a2l[kt][0], a2l[kt][1], a2l[kt][2], a2l[kt][3], bw2[kt][jt][0], bw2[kt][jt][1]);
+                for (int kt = 0; kt < 4; ++kt)
+                    mma_bf16_16816(c2, a2[kt][0], a2[kt][1], a2[kt][2], a2[kt][3], bw2[kt][jt][0], bw2[kt][jt][1]);
+                const int col = 8 * jt + 2 * t;
+                const float bb0 = sb2[col], bb1 = sb2[col + 1], w0 = sw3[col], w1 = sw3[col + 1];
+                y0 = fmaf(w0, fmaxf(c2[0] + bb0, 0.0f), y0);
+                y0 = fmaf(w1, fmaxf(c2[1] + bb1, 0.0f), y0);
+                y1 = fmaf(w0, fmaxf(c2[2] + bb0, 0.0f), y1);
+                y1 = fmaf(w1, fmaxf(c2[3] + bb1, 0.0f), y1);
             }
-            const int col = 8 * jt + 2 * t;
-            const float bb0 = sb2[col], bb1 = sb2[col + 1], w0 = sw3[col], w1 = sw3[col + 1];
-            y0 = fmaf(w0, fmaxf(c2[0] + bb0, 0.0f), y0);
-            y0 = fmaf(w1, fmaxf(c2[1] + bb1, 0.0f), y0);
-            y1 = fmaf(w0, fmaxf(c2[2] + bb0, 0.0f), y1);
-            y1 = fmaf(w1, fmaxf(c2[3] + bb1, 0.0f), y1);
-        }
-        // the four lanes of a row group hold disjoint columns
-        y0 += __shfl_xor_sync(0xffffffffu, y0, 1);
-        y0 += __shfl_xor_sync(0xffffffffu, y0, 2);
-        y1 += __shfl_xor_sync(0xffffffffu, y1, 1);
-        y1 += __shfl_xor_sync(0xffffffffu, y1, 2);
-        if (t == 0) {
-            const uint64_t v = tile * 16 + g;
-            if (v < n) out[v] = y0 + b3;
-            if (v + 8 < n) out[v + 8] = y1 + b3;
+            // the four lanes of a row group hold disjoint columns
+            y0 += __shfl_xor_sync(0xffffffffu, y0, 1);
+            y0 += __shfl_xor_sync(0xffffffffu, y0, 2);
+            y1 += __shfl_xor_sync(0xffffffffu, y1, 1);
+            y1 += __shfl_xor_sync(0xffffffffu, y1, 2);
+            if (t == 0) {
+                const uint64_t v = tile * 16 + g;
+                if (v < n) out[v] = y0 + b3;
+                if (v + 8 < n) out[v + 8] = y1 + b3;
+            }
         }
     }
 }
@@ -482,9 +531,9 @@ __global__ void exp_sum_kernel(const float* __restrict__ pred, uint32_t n, doubl
 
 __global__ void normalise_kernel(const float* __restrict__ pred, uint32_t n, const double* __restrict__ sum,
                                  float* __restrict__ pr) {
-    const double inv = 1.0 / *sum;
+    const float inv = (float)(1.0 / *sum);
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
-        pr[v] = (float)((double)expf(fminf(fmaxf(pred[v], -80.0f), 80.0f)) * inv);
+        pr[v] = expf(fminf(fmaxf(pred[v], -80.0f), 80.0f)) * inv;
 }
 
 int grid_for_n(uint64_t work, int threads) {
@@ -520,6 +569,9 @@ int degree_sums(pcpm_png* g, const uint32_t* row_ptr, uint32_t* sums, cudaStream
             e = cudaFuncSetAttribute(bin_degree_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(bin_degree_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(bin_degree_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+
         attr_err = e;
     });
     if (attr_err != cudaSuccess) {
@@ -529,9 +581,35 @@ int degree_sums(pcpm_png* g, const uint32_t* row_ptr, uint32_t* sums, cudaStream
     const uint32_t n = g->n;
     const size_t smem = (size_t)g->q * sizeof(uint32_t);
     int* err = &g->state->err;
-    if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess) return PCPM_ECUDA;
-    bin_degree_kernel<0><<<g->k, kDegThreads, smem, s>>>(g->dest, g->src, g->bin_e, g->chunk_base, n, g->q, row_ptr,
-                                                          nullptr, sums, err);
+    // the solver's scalars start over (the scatter runs only while no
+    // tolerance has stopped the solve)
+    if (cudaMemsetAsync(g->state, 0, sizeof(DevState), s) != cudaSuccess) return PCPM_ECUDA;
+    if (g->indeg) {  // the window-layout build kept the in-degrees
+        if (cudaMemcpyAsync(sums, g->indeg, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return PCPM_ECUDA;
+    } else {
+        bin_degree_kernel<0><<<g->k, kDegThreads, smem, s>>>(g->dest, g->src, g->bin_e, g->chunk_base, n, g->q,
+                                                              row_ptr, nullptr, sums, err);
+    }
+    if (g->upd_dtype == (int)PCPM_UPDATE_F32) {
+        // Scatter indeg(u) and outdeg(u) into the two update buffers
+        // (Algorithm 3 on 32-bit values, copied bit for bit), then sum them
+        // from the bins in bin order instead of reading the degrees at random.
+        // The solver's update bins are overwritten.
+        degree_u32_kernel<<<grid_for_n(n, 256), 256, 0, s>>>(row_ptr, n, sums + 2 * (size_t)n);
+        int rc = launch_status();
+        if (rc == PCPM_OK) rc = launch_scatter_bits(g, sums, g->upd[0], s);
+        if (rc == PCPM_OK) rc = launch_scatter_bits(g, sums + 2 * (size_t)n, g->upd[1], s);
+        g->upd_valid = 0;
+        if (rc != PCPM_OK) return rc;
+        bin_degree_kernel<3><<<g->k, kDegThreads, smem, s>>>(g->dest, g->src, g->bin_e, g->chunk_base, n, g->q,
+                                                              row_ptr, nullptr, sums + n, err,
+                                                              static_cast<const uint32_t*>(g->upd[0]));
+        bin_degree_kernel<3><<<g->k, kDegThreads, smem, s>>>(g->dest, g->src, g->bin_e, g->chunk_base, n, g->q,
+                                                              row_ptr, nullptr, sums + 2 * (size_t)n, err,
+                                                              static_cast<const uint32_t*>(g->upd[1]));
+        return launch_status();
+    }
     bin_degree_kernel<1><<<g->k, kDegThreads, smem, s>>>(g->dest, g->src, g->bin_e, g->chunk_base, n, g->q, row_ptr,
                                                           sums, sums + n, err);
     bin_degree_kernel<2><<<g->k, kDegThreads, smem, s>>>(g->dest, g->src, g->bin_e, g->chunk_base, n, g->q, row_ptr,
@@ -567,15 +645,20 @@ extern "C" int pcpm_ws_features(pcpm_png* png, const uint32_t* row_ptr, const ui
     const uint32_t n = png->n;
     cudaStream_t s = (cudaStream_t)stream;
     png->last_stream = s;
-    // scratch: the three sums (uint32) and PR_1
+    // scratch from the library's pool: the three sums (uint32) and PR_1
     uint32_t* sums = nullptr;
-    if (cudaMallocAsync((void**)&sums, (size_t)4 * n * sizeof(uint32_t), s) != cudaSuccess) {
+    if (pool_alloc((void**)&sums, (size_t)4 * n * sizeof(uint32_t), s) != cudaSuccess) {
         cudaGetLastError();
         return PCPM_ENOMEM;
     }
     float* pr1 = reinterpret_cast<float*>(sums + 3 * (size_t)n);
     int rc = degree_sums(png, row_ptr, sums, s);
-    if (rc == PCPM_OK) rc = check_state_err(png, s);
+    // overflow of a sum is reported at the end (the reset below clears the
+    // handle's status, so it is read first, on the stream)
+    int* h_err = nullptr;
+    if (rc == PCPM_OK && cudaMallocHost((void**)&h_err, sizeof(int)) != cudaSuccess) rc = PCPM_ENOMEM;
+    if (rc == PCPM_OK && cudaMemcpyAsync(h_err, &png->state->err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        rc = PCPM_ECUDA;
     // PR_1: one Eq. 1 step from the uniform start
     if (rc == PCPM_OK) rc = pcpm_reset(png, nullptr, stream);
     if (rc == PCPM_OK) rc = pcpm_iterate(png, 0.85f, 1, 0.0, PCPM_TWO_PHASE, nullptr, nullptr, stream);
@@ -584,8 +667,10 @@ extern "C" int pcpm_ws_features(pcpm_png* png, const uint32_t* row_ptr, const ui
         features_kernel<<<grid_for_n(n, 256), 256, 0, s>>>(row_ptr, n, sums, pr1, features);
         if (cudaGetLastError() != cudaSuccess) rc = PCPM_ECUDA;
     }
-    cudaFreeAsync(sums, s);
+    pool_free(sums, s);
     if (rc == PCPM_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = PCPM_ECUDA;
+    if (rc == PCPM_OK && *h_err) rc = PCPM_EDEVICE;
+    if (h_err) cudaFreeHost(h_err);
     return rc;
 }
 
@@ -612,7 +697,8 @@ extern "C" int pcpm_ws_predict(const float* params, const float* features, uint3
     if (!params || !features || !out) return PCPM_EINVAL;
     if (n == 0) return PCPM_OK;
     const uint64_t tiles = ((uint64_t)n + 15) / 16;
-    const int blocks = (int)std::min<uint64_t>((tiles + kPredictWarps - 1) / kPredictWarps, 152ull * 8);
+    const uint64_t groups = (tiles + kPredictGroup - 1) / kPredictGroup;
+    const int blocks = (int)std::min<uint64_t>((groups + kPredictWarps - 1) / kPredictWarps, 152ull * 2);
     predict_kernel<<<blocks, kPredictWarps * 32, 0, (cudaStream_t)stream>>>(params, features, n, out);
     return cudaGetLastError() == cudaSuccess ? PCPM_OK : PCPM_ECUDA;
 }
@@ -649,7 +735,7 @@ extern "C" int pcpm_ws_init_ranks(const float* pred, uint32_t n, float* pr, void
     if (!pred || !pr || n == 0) return PCPM_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     double* sum = nullptr;
-    if (cudaMallocAsync((void**)&sum, sizeof(double), s) != cudaSuccess) {
+    if (pool_alloc((void**)&sum, sizeof(double), s) != cudaSuccess) {
         cudaGetLastError();
         return PCPM_ENOMEM;
     }
@@ -657,10 +743,9 @@ extern "C" int pcpm_ws_init_ranks(const float* pred, uint32_t n, float* pr, void
     if (cudaMemsetAsync(sum, 0, sizeof(double), s) != cudaSuccess) rc = PCPM_ECUDA;
     if (rc == PCPM_OK) {
         exp_sum_kernel<<<std::min(grid_for_n(n, 256), 152 * 4), 256, 0, s>>>(pred, n, sum);
-        normalise_kernel<<<grid_for_n(n, 256), 256, 0, s>>>(pred, n, sum, pr);
+        normalise_kernel<<<std::min(grid_for_n(n, 256), 152 * 8), 256, 0, s>>>(pred, n, sum, pr);
         if (cudaGetLastError() != cudaSuccess) rc = PCPM_ECUDA;
     }
-    cudaFreeAsync(sum, s);
-    if (rc == PCPM_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = PCPM_ECUDA;
+    pool_free(sum, s);
     return rc;
 }

@@ -55,10 +55,11 @@ def init_params(samples, seed: int = 0):
 
 
 def train(params, samples, steps: int = 600, batch: int = 65536, lr: float = 3e-3, seed: int = 1,
-          log_every: int = 100):
+          log_every: int = 100, schedule: str = "constant"):
     """Adam on batches of consecutive rows of a random sample (node labels are
     random, so consecutive rows are a random draw of that graph's nodes).
-    Returns the loss log [(step, loss)]."""
+    schedule "cosine" lowers the step size from lr towards 0 along half a
+    cosine over the steps. Returns the loss log [(step, loss)]."""
     import torch
     rng = np.random.default_rng(seed)
     grad = torch.zeros(WS_PARAMS, dtype=torch.float32, device="cuda")
@@ -71,7 +72,8 @@ def train(params, samples, steps: int = 600, batch: int = 65536, lr: float = 3e-
         b = min(batch, s.n)
         i0 = int(rng.integers(0, s.n - b + 1))
         ws_loss_grad(params, s.features[i0:i0 + b], s.target[i0:i0 + b], grad, loss)
-        ws_adam(params, grad, m, v, step, lr)
+        step_lr = lr if schedule == "constant" else max(lr * 0.5 * (1.0 + np.cos(np.pi * step / steps)), lr * 1e-3)
+        ws_adam(params, grad, m, v, step, step_lr)
         if step % log_every == 0 or step == steps:
             log.append((step, float(loss.item())))
     return log
