@@ -75,6 +75,22 @@ extern "C" {
  * several units whose partial sums meet in global memory), iterations run in
  * the two-phase form whatever the flag says. */
 #define PCPM_TWO_PHASE 0x2u
+/* Delta iterations (not in the paper; meant for 16-bit update bins). After
+ * the first iteration since pcpm_reset, each iteration scatters the change
+ * of SPR since the previous iteration instead of SPR itself, and the apply
+ * adds it to the current ranks, which Eq. 1 allows by linearity:
+ *   PR_{i+1} = PR_i + d * (A^T (SPR_i - SPR_{i-1}) + (D_i - D_{i-1}) / n)
+ * (D the dangling mass; 0 under PCPM_DANGLING_LEAK). The changes shrink as the
+ * iteration converges, so the rounding of 16-bit bins shrinks with them
+ * instead of leaving a floor; FP16 bins store each change times 2^E with
+ * E = floor(log2(65504 / r)), r the last L1 change (which bounds every change
+ * of SPR), and the gather divides by 2^E. With 16-bit bins every iteration of
+ * such a solve, the first included, adds to each node's stored value what the
+ * rounding of its previous one left out (error feedback, one FP32 per node),
+ * so the stored values sum to the true ones up to the last rounding. The FP32
+ * rounding of the ranks is not damped away as in the plain form: it adds up
+ * over the iterations. Iterations run in the two-phase form. */
+#define PCPM_DELTA 0x4u
 
 /* Kernels timed by pcpm_iterate_timed, in this order. In fused mode the
  * standalone scatter runs only when needed and the gather phase includes the

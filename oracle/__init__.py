@@ -235,7 +235,7 @@ _F16_MAX = 65504.0
 def store_updates(values_f32, dtype: str) -> np.ndarray:
     """Stored form of FP32 update values. f32: unchanged. f16: binary16 of
     value * 2^15 (an exact power-of-two scaling), rounded to nearest even,
-    saturating at the largest finite half (numpy's float32 -> float16 cast
+    saturating at +-the largest finite half (numpy's float32 -> float16 cast
     rounds to nearest even). bf16: the 16-bit pattern of binary32 rounded to
     nearest even at bit 16, returned as uint16."""
     v = np.ascontiguousarray(values_f32, dtype=np.float32)
@@ -243,7 +243,7 @@ def store_updates(values_f32, dtype: str) -> np.ndarray:
         return v.copy()
     if dtype == "f16":
         scaled = v * np.float32(2.0 ** F16_SCALE_LOG2)
-        return np.minimum(scaled, np.float32(_F16_MAX)).astype(np.float16)
+        return np.clip(scaled, np.float32(-_F16_MAX), np.float32(_F16_MAX)).astype(np.float16)
     if dtype == "bf16":
         bits = v.view(np.uint32).astype(np.uint64)
         # round to nearest, ties to even: add 0x7FFF plus the lowest kept bit

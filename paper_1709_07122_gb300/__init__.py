@@ -23,6 +23,7 @@ PCPM_OK = 0
 PCPM_NOT_CONVERGED = 1
 DANGLING_LEAK = 0x1
 TWO_PHASE = 0x2
+DELTA = 0x4
 NUM_PHASES = 3
 PHASES = ("scatter", "gather_apply", "reduce")
 
@@ -165,11 +166,14 @@ def _dev_u32(t):
 
 
 def _flags(dangling: str, mode: str = "fused") -> int:
+    """mode: "fused", "two_phase", or "delta" (two-phase iterations that
+    scatter the change of SPR, PCPM_DELTA)."""
     if dangling not in ("uniform", "leak"):
         raise ValueError("dangling must be 'uniform' or 'leak'")
-    if mode not in ("fused", "two_phase"):
-        raise ValueError("mode must be 'fused' or 'two_phase'")
-    return (DANGLING_LEAK if dangling == "leak" else 0) | (TWO_PHASE if mode == "two_phase" else 0)
+    if mode not in ("fused", "two_phase", "delta"):
+        raise ValueError("mode must be 'fused', 'two_phase' or 'delta'")
+    return ((DANGLING_LEAK if dangling == "leak" else 0) | (TWO_PHASE if mode != "fused" else 0)
+            | (DELTA if mode == "delta" else 0))
 
 
 def autotune(row_ptr, col, part_sizes=(2048, 4096, 8192, 16384, 32768), d: float = 0.85, warmup: int = 2,

@@ -108,7 +108,7 @@ void release(pcpm_png* g) {
                     g->gunits, g->gorder, g->sunits, g->sorder, g->gacc,
                     g->bin_done, g->inv_deg, g->pr[0], g->pr[1], g->upd[0], g->upd[1], g->partials,
                     g->hist, g->state, g->wdest, g->gweight, g->win_start, g->wwords, g->wweight, g->wdesc,
-                    g->whubs, g->indeg};
+                    g->whubs, g->indeg, g->dq_err};
     // the caller has waited for every use of the handle's memory
     for (void* p : ptrs) pool_free(p, g->last_stream);
     if (g->state_host) cudaFreeHost(g->state_host);
@@ -131,6 +131,10 @@ int alloc_state(pcpm_png* g) {
     CK(dev_alloc(g, (void**)&g->partials, 2 * partial_slots(g) * sizeof(double)));
     CK(dev_alloc(g, (void**)&g->gacc, (size_t)n * sizeof(float)));
     CK(dev_alloc(g, (void**)&g->bin_done, (size_t)g->k * sizeof(uint32_t)));
+    if (g->upd_bytes == 2) {  // the rounding carried between delta iterations
+        CK(dev_alloc(g, (void**)&g->dq_err, (size_t)2 * n * sizeof(float)));
+        CK(cudaMemsetAsync(g->dq_err, 0, (size_t)2 * n * sizeof(float), s));
+    }
     CK(cudaMemsetAsync(g->gacc, 0, (size_t)n * sizeof(float), s));
     CK(cudaMemsetAsync(g->bin_done, 0, (size_t)g->k * sizeof(uint32_t), s));
     g->hist_cap = 1024;
@@ -181,12 +185,15 @@ int sync_state(pcpm_png* g, cudaStream_t s) {
 int run_iterations(pcpm_png* g, float d, int iters, double tol, uint32_t flags, cudaStream_t s,
                    std::vector<cudaEvent_t>* ev) {
     RC(ensure_hist(g, g->iters_done + iters, s));
-    const bool fused = !(flags & PCPM_TWO_PHASE) && g->fused_ok;
+    const bool fused = !(flags & (PCPM_TWO_PHASE | PCPM_DELTA)) && g->fused_ok;
     for (int i = 0; i < iters; ++i) {
+        // the delta form needs the ranks before the current ones: from the
+        // second iteration since the reset on
+        const bool delta = (flags & PCPM_DELTA) && g->iters_done + i >= 1;
         if (ev) CK(cudaEventRecord((*ev)[4 * i], s));
-        if (!fused || !g->upd_valid) RC(launch_scatter(g, s));
+        if (!fused || !g->upd_valid) RC(launch_scatter(g, s, false, delta, (flags & PCPM_DELTA) != 0));
         if (ev) CK(cudaEventRecord((*ev)[4 * i + 1], s));
-        RC(launch_gather(g, d, flags, fused, s));
+        RC(launch_gather(g, d, flags, fused, s, false, delta));
         if (ev) CK(cudaEventRecord((*ev)[4 * i + 2], s));
         RC(launch_reduce(g, tol, g->iters_done + i, s));
         if (ev) CK(cudaEventRecord((*ev)[4 * i + 3], s));
@@ -208,6 +215,7 @@ int iterate_impl(pcpm_png* g, float d, int iters, double tol, uint32_t flags, in
     const int start_done = g->iters_done;
     const int start_cur = g->cur;
     const int start_ucur = g->ucur;
+    const int start_dq = g->dq_cur;
     const int start_valid = g->upd_valid;
     const bool need_sync = tol > 0.0 || iters_run || last_residual;
     if (tol > 0.0) {
@@ -231,7 +239,8 @@ int iterate_impl(pcpm_png* g, float d, int iters, double tol, uint32_t flags, in
         const int done = g->state_host->iters_done - start_done;
         g->iters_done = g->state_host->iters_done;
         g->cur = start_cur ^ (done & 1);
-        if (!(flags & PCPM_TWO_PHASE) && g->fused_ok) {
+        if ((flags & PCPM_DELTA) && g->dq_err) g->dq_cur = start_dq ^ (done & 1);  // one scatter per iteration
+        if (!(flags & (PCPM_TWO_PHASE | PCPM_DELTA)) && g->fused_ok) {
             g->ucur = start_ucur ^ (done & 1);
             g->upd_valid = done > 0 ? 1 : start_valid;
         } else if (done > 0) {
@@ -250,7 +259,7 @@ bool bad_damping(float d) { return !(d >= 0.0f && d < 1.0f); }
 // iteration; it is driven by pcpm_shard_init / pcpm_shard_step only.
 bool partial_shard(const pcpm_png* g) { return g->plo != 0 || g->phi != g->k; }
 
-constexpr uint32_t kAllFlags = PCPM_DANGLING_LEAK | PCPM_TWO_PHASE;
+constexpr uint32_t kAllFlags = PCPM_DANGLING_LEAK | PCPM_TWO_PHASE | PCPM_DELTA;
 
 }  // namespace
 
@@ -453,7 +462,7 @@ int pcpm_shard_init(pcpm_png* g, const float* pr_init, float* pr_out, double* su
 
 int pcpm_shard_step(pcpm_png* g, float d, uint32_t flags, const float* pr_in, float* pr_out, double* sums,
                     void* stream) {
-    if (!g || bad_damping(d) || (flags & ~kAllFlags)) return PCPM_EINVAL;
+    if (!g || bad_damping(d) || (flags & ~kAllFlags) || (flags & PCPM_DELTA)) return PCPM_EINVAL;
     if (!is_device_ptr(pr_in) || !is_device_ptr(pr_out) || !is_device_ptr(sums) || pr_in == pr_out)
         return PCPM_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
@@ -742,6 +751,8 @@ int pcpm_reset(pcpm_png* g, const float* pr_init, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     g->last_stream = s;
     CK(cudaMemsetAsync(g->state, 0, sizeof(DevState), s));
+    if (g->dq_err) CK(cudaMemsetAsync(g->dq_err, 0, (size_t)2 * g->n * sizeof(float), s));
+    g->dq_cur = 0;
     CK(cudaMemsetAsync(g->gacc, 0, (size_t)g->n * sizeof(float), s));
     CK(cudaMemsetAsync(g->bin_done, 0, (size_t)g->k * sizeof(uint32_t), s));
     g->cur = 0;

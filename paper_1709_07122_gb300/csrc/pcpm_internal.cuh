@@ -100,12 +100,13 @@ constexpr int kErrBadGraph = 4;
 
 // Solver scalars kept on the device.
 struct DevState {
-    double dangling;  // sum of PR over dangling nodes for the current ranks
-    double residual;  // L1 change of the last iteration
-    int stop;         // set once residual < tol (tol > 0)
-    int iters_done;   // iterations applied since reset
-    int err;          // kErr* bits
+    double dangling;       // sum of PR over dangling nodes for the current ranks
+    double residual;       // L1 change of the last iteration
+    int stop;              // set once residual < tol (tol > 0)
+    int iters_done;        // iterations applied since reset
+    int err;               // kErr* bits
     int pad;
+    double dangling_prev;  // the dangling mass of the ranks before the current ones
 };
 
 }  // namespace pcpm
@@ -178,6 +179,10 @@ struct pcpm_png {
     float* gacc;             // n: partial sums of bins cut into several units
     uint32_t* bin_done;      // k: units of a cut bin that have flushed
     float* inv_deg;          // n: 1/|N_o(u)|, 0 for dangling nodes
+    float* dq_err;           // 2n (16-bit update bins): rounding left out of each node's last stored value
+                             // (delta solves), carried into its next one; read from half dq_cur, written to
+                             // the other; zeroed by a reset
+    int dq_cur;
     // solver state
     float* pr[2];            // ranks ping-pong
     int cur;                 // pr[cur] holds PR_i
@@ -231,12 +236,16 @@ int launch_init(pcpm_png* g, const float* pr_init, cudaStream_t s);
 // init into `out` (n floats), with the dangling partial sums over nodes [lo, hi) only.
 int launch_init_range(pcpm_png* g, const float* pr_init, float* out, uint32_t lo, uint32_t hi, cudaStream_t s);
 // raw: stage x itself (SpMV) instead of x * (1/outdeg).
-int launch_scatter(pcpm_png* g, cudaStream_t s, bool raw = false);
+// delta: scatter the change of SPR since the previous ranks (PCPM_DELTA);
+// feedback: 16-bit bins carry each node's rounding left-over (dq_err) into
+// its next stored value (every iteration of a PCPM_DELTA solve).
+int launch_scatter(pcpm_png* g, cudaStream_t s, bool raw = false, bool delta = false, bool feedback = false);
 // Algorithm 3 for a 32-bit value per node, copied bit for bit: out[t] = x[src[t]]
 // in the update bins' layout (FP32 update bins only; PCPM_EINVAL otherwise).
 int launch_scatter_bits(pcpm_png* g, const void* x, void* out, cudaStream_t s);
 // spmv: the weighted gather of a weighted handle (Sec. 3.5).
-int launch_gather(pcpm_png* g, float d, uint32_t flags, bool fused, cudaStream_t s, bool spmv = false);
+int launch_gather(pcpm_png* g, float d, uint32_t flags, bool fused, cudaStream_t s, bool spmv = false,
+                  bool delta = false);
 // The window gather's bound on waits for work (see pcpm_test_wait_limit).
 int set_work_wait_limit(long long cycles);
 // record = false: the L1 change goes to the device state only, not the history.

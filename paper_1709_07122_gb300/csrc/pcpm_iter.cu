@@ -239,6 +239,8 @@ struct Upd<kUpdF32> {
     static constexpr float acc_scale = 1.0f;
     __device__ static float load(const T* p, uint32_t i) { return p[i]; }
     __device__ static T from(float x) { return x; }
+    // the value whose from() is q, in the units from() takes
+    __device__ static float back(T q) { return q; }
     __device__ static void store4(T* p, uint32_t e, float a, float b, float c, float d) {
         st_stream_f4(p + e, make_float4(a, b, c, d));
     }
@@ -248,7 +250,8 @@ struct Upd<kUpdF16> {
     using T = __half;
     static constexpr float acc_scale = 1.0f / kF16Scale;
     __device__ static float load(const T* p, uint32_t i) { return __half2float(p[i]); }
-    __device__ static T from(float x) { return __float2half_rn(fminf(x * kF16Scale, 65504.0f)); }
+    __device__ static T from(float x) { return __float2half_rn(fmaxf(fminf(x * kF16Scale, 65504.0f), -65504.0f)); }
+    __device__ static float back(T q) { return __half2float(q) * (1.0f / kF16Scale); }
     __device__ static void store4(T* p, uint32_t e, float a, float b, float c, float d) {
         st_stream_u2(p + e, (uint32_t)__half_as_ushort(from(a)) | ((uint32_t)__half_as_ushort(from(b)) << 16),
                      (uint32_t)__half_as_ushort(from(c)) | ((uint32_t)__half_as_ushort(from(d)) << 16));
@@ -260,12 +263,37 @@ struct Upd<kUpdBF16> {
     static constexpr float acc_scale = 1.0f;
     __device__ static float load(const T* p, uint32_t i) { return __bfloat162float(p[i]); }
     __device__ static T from(float x) { return __float2bfloat16_rn(x); }
+    __device__ static float back(T q) { return __bfloat162float(q); }
     __device__ static void store4(T* p, uint32_t e, float a, float b, float c, float d) {
         st_stream_u2(p + e,
                      (uint32_t)__bfloat16_as_ushort(from(a)) | ((uint32_t)__bfloat16_as_ushort(from(b)) << 16),
                      (uint32_t)__bfloat16_as_ushort(from(c)) | ((uint32_t)__bfloat16_as_ushort(from(d)) << 16));
     }
 };
+
+// Delta iterations (PCPM_DELTA): the bins carry the change of SPR since the
+// previous iteration, bounded by the last L1 change r (|dSPR(u)| <=
+// |dPR(u)| <= r). FP16 bins rescale it by 2^E, E = floor(log2(65504 / r)),
+// so the largest possible change maps to the top of the FP16 range and the
+// shrinking changes keep their relative precision; FP32 and BF16 bins need no
+// scale. delta_stage_scale multiplies the change before Upd::from (which
+// itself multiplies FP16 values by 2^15); the gather's sums are multiplied by
+// delta_acc_scale (instead of Upd::acc_scale).
+template <int kUpd>
+__device__ __forceinline__ int delta_exponent(const DevState* st) {
+    if (kUpd != kUpdF16) return 0;
+    const double r = st->residual;
+    if (!(r > 0.0)) return 100;  // no change to carry
+    return max(-100, min(100, (int)floor(log2(65504.0 / r))));
+}
+template <int kUpd>
+__device__ __forceinline__ float delta_stage_scale(const DevState* st) {
+    return kUpd == kUpdF16 ? ldexpf(1.0f, delta_exponent<kUpd>(st) - PCPM_F16_SCALE_LOG2) : 1.0f;
+}
+template <int kUpd>
+__device__ __forceinline__ float delta_acc_scale(const DevState* st) {
+    return kUpd == kUpdF16 ? ldexpf(1.0f, -delta_exponent<kUpd>(st)) : 1.0f;
+}
 
 // Deterministic block sum of two doubles; result valid in thread 0. `scratch`
 // is 2 * kThreads / 32 doubles of shared memory.
@@ -553,11 +581,14 @@ __global__ void __launch_bounds__(kScatterThreads, 1) scatter_kernel(
     uint32_t n, uint32_t q, uint32_t k, const float* __restrict__ pr, const float* __restrict__ inv_deg,
     const uint32_t* __restrict__ src, const uint32_t* __restrict__ seg_u, const uint32_t* __restrict__ cnt_u,
     const uint4* __restrict__ units, const uint32_t* __restrict__ order, void* __restrict__ upd,
-    const DevState* __restrict__ st, int* __restrict__ err) {
+    const DevState* __restrict__ st, int* __restrict__ err, const float* __restrict__ pr_prev,
+    const float* __restrict__ dq_in, float* __restrict__ dq_out) {
     if (st->stop) return;
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ uint32_t sh32[32];
     __shared__ __align__(8) uint64_t bars[2 * (kScatterThreads / 32)];
+    // delta form: the change of SPR since pr_prev, scaled for the bins' format
+    const float dsc = pr_prev ? delta_stage_scale<kUpd>(st) : 1.0f;
     float* sspr = reinterpret_cast<float*>(smraw);
     const size_t gpre_off = (size_t)((q + 3) & ~3u) * sizeof(float);
     uint32_t* gpre = reinterpret_cast<uint32_t*>(smraw + gpre_off);
@@ -578,7 +609,28 @@ __global__ void __launch_bounds__(kScatterThreads, 1) scatter_kernel(
     // loads of each array in flight per thread.
     auto stage_spr = [&] {
         constexpr int kIlp = 2;
-        if ((base & 3) == 0) {
+        if (dq_in) {
+            // error feedback (16-bit bins in a delta solve): SPR, or from the
+            // second iteration on its change, plus what the rounding of this
+            // node's previous stored value left out, rounded to the bins'
+            // format here (every update of the node carries the same value);
+            // what this rounding leaves out goes into the next change, so the
+            // stored values sum to the true ones up to the last rounding
+            // instead of piling up. Every unit of the partition computes the
+            // same values from dq_in; its first unit alone writes dq_out.
+            using U = Upd<kUpd>;
+            const bool writer = unit.y == 0;
+            for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) {
+                const float x = pr_prev ? pr[base + i] - pr_prev[base + i] : pr[base + i];
+                const float v = x * inv_deg[base + i] + dq_in[base + i];
+                const float sq = U::back(U::from(v * dsc));  // what the stores below will write
+                sspr[i] = sq;
+                if (writer) dq_out[base + i] = v - sq / dsc;
+            }
+        } else if (pr_prev) {  // delta form: (PR - PR_prev) / outdeg, scaled
+            for (uint32_t i = threadIdx.x; i < len; i += blockDim.x)
+                sspr[i] = (pr[base + i] - pr_prev[base + i]) * inv_deg[base + i] * dsc;
+        } else if ((base & 3) == 0) {
             const uint32_t v4 = len >> 2;
             const float4* pr4 = reinterpret_cast<const float4*>(pr + base);
             const float4* in4 = reinterpret_cast<const float4*>(inv_deg ? inv_deg + base : pr + base);
@@ -641,6 +693,7 @@ struct GatherArgs {
     int* err;
     float d;
     int uniform_dangling;
+    int delta;  // PR' = PR + d (A^T dSPR + dD / n): the bins hold changes (PCPM_DELTA)
     // fused scatter of the next iteration
     const uint32_t* src;
     const uint32_t* seg_u;
@@ -726,14 +779,20 @@ __device__ __forceinline__ void gather_finish(const GatherArgs& a, unsigned char
     };
 
     const double D = a.uniform_dangling ? a.st->dangling : 0.0;
-    const float cst = (float)((1.0 - (double)a.d) / (double)a.n + (double)a.d * D / (double)a.n);
-    const float d_acc = a.d * U::acc_scale;  // exact: the scale is a power of two
+    // delta form: PR' = PR + d * (acc + (D - D_prev) / n), acc the sum of the
+    // changes of SPR (their scale removed)
+    const double Dd = a.uniform_dangling ? a.st->dangling - a.st->dangling_prev : 0.0;
+    const float cst = a.delta ? (float)((double)a.d * Dd / (double)a.n)
+                              : (float)((1.0 - (double)a.d) / (double)a.n + (double)a.d * D / (double)a.n);
+    // exact: the scales are powers of two
+    const float d_acc = a.d * (a.delta ? delta_acc_scale<kUpd>(a.st) : U::acc_scale);
+    const float keep = a.delta ? 1.0f : 0.0f;  // the delta form adds the old rank
     // Per-thread partial sums of at most len / blockDim terms in FP32 (FP64
     // arithmetic is slow on this part); thread and block totals in FP64.
     float res_f = 0.0f, dg_f = 0.0f;
     // Apply to one node: PR', residual and dangling terms, SPR' for the fused scatter.
     auto apply1 = [&](uint32_t i, float s, float old, float inv) -> float {
-        const float x = fmaf(d_acc, s, cst);
+        const float x = fmaf(keep, old, fmaf(d_acc, s, cst));
         if (kFused) acc[i] = x * inv;
         res_f += fabsf(x - old);
         if (inv == 0.0f) dg_f += x;
@@ -856,7 +915,7 @@ __device__ __forceinline__ void gather_finish(const GatherArgs& a, unsigned char
                 for (int j = 0; j < kApplyIlp; ++j) {
                     const uint32_t i = i0 + j * blockDim.x;
                     if (i < len) {
-                        const float x = fmaf(d_acc, s[j], cst);
+                        const float x = fmaf(keep, old[j], fmaf(d_acc, s[j], cst));
                         a.gacc[vbase + i] = 0.0f;
                         a.pr_out[vbase + i] = x;
                         res_f += fabsf(x - old[j]);
@@ -1407,6 +1466,7 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_kernel(const double* __
     }
     block_sum2<kReduceThreads>(r, dg);
     if (threadIdx.x == 0) {
+        st->dangling_prev = st->dangling;
         st->dangling = dg;
         if (hist_slot >= 0) {
             st->residual = r;
@@ -1586,17 +1646,22 @@ int launch_spr(pcpm_png* g, float* spr, cudaStream_t s) {
     return launch_status();
 }
 
-int launch_scatter(pcpm_png* g, cudaStream_t s, bool raw) {
+int launch_scatter(pcpm_png* g, cudaStream_t s, bool raw, bool delta, bool feedback) {
+    feedback = feedback && g->dq_err && !raw;
     const size_t smem = scatter_smem_bytes(g->q, g->k);
     void (*f)(uint32_t, uint32_t, uint32_t, const float*, const float*, const uint32_t*, const uint32_t*,
-              const uint32_t*, const uint4*, const uint32_t*, void*, const DevState*, int*) =
+              const uint32_t*, const uint4*, const uint32_t*, void*, const DevState*, int*, const float*,
+              const float*, float*) =
         g->upd_dtype == kUpdF16 ? scatter_kernel<kUpdF16>
         : g->upd_dtype == kUpdBF16 ? scatter_kernel<kUpdBF16>
                                    : scatter_kernel<kUpdF32>;
     f<<<g->nsunits, kScatterThreads, smem, s>>>(g->n, g->q, g->k, g->pr[g->cur], raw ? nullptr : g->inv_deg, g->src,
                                                g->seg_u,
                                                g->cnt_u, g->sunits, g->sorder, g->upd[g->ucur], g->state,
-                                               &g->state->err);
+                                               &g->state->err, delta ? g->pr[g->cur ^ 1] : nullptr,
+                                               feedback ? g->dq_err + (size_t)g->dq_cur * g->n : nullptr,
+                                               feedback ? g->dq_err + (size_t)(g->dq_cur ^ 1) * g->n : nullptr);
+    if (feedback) g->dq_cur ^= 1;
     return launch_status();
 }
 
@@ -1604,13 +1669,14 @@ int launch_scatter_bits(pcpm_png* g, const void* x, void* out, cudaStream_t s) {
     if (g->upd_dtype != kUpdF32) return PCPM_EINVAL;
     scatter_kernel<kUpdF32><<<g->nsunits, kScatterThreads, scatter_smem_bytes(g->q, g->k), s>>>(
         g->n, g->q, g->k, static_cast<const float*>(x), nullptr, g->src, g->seg_u, g->cnt_u, g->sunits, g->sorder,
-        out, g->state, &g->state->err);
+        out, g->state, &g->state->err, nullptr, nullptr, nullptr);
     return launch_status();
 }
 
-int launch_gather(pcpm_png* g, float d, uint32_t flags, bool fused, cudaStream_t s, bool spmv) {
+int launch_gather(pcpm_png* g, float d, uint32_t flags, bool fused, cudaStream_t s, bool spmv, bool delta) {
     const bool weighted = spmv && g->weighted;  // only SpMV applies the weights
     GatherArgs a;
+    a.delta = delta ? 1 : 0;
     a.gweight = g->gweight;
     a.n = g->n;
     a.q = g->q;

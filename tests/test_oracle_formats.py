@@ -37,6 +37,9 @@ def test_f16_saturates_and_keeps_subnormals():
     assert f16_bits([4.0, 65504 * S]) == [0x7BFF, 0x7BFF]
     # the smallest binary16 subnormal is 2^-24: stored value 2^-24 -> 0x0001
     assert f16_bits([2.0 ** -24 * S]) == [0x0001]
+    # changes of SPR (delta iterations) are signed: -65504 = 0xFBFF saturates
+    # the other way, -1.0 = 0xBC00, -2^-24 = 0x8001
+    assert f16_bits([-4.0, -1 * S, -(2.0 ** -24) * S]) == [0xFBFF, 0xBC00, 0x8001]
 
 
 def test_bf16_exact_and_ties():
