@@ -444,12 +444,15 @@ def batched_leg(a, graphs: int = 256, iters: int = 20):
     gen_s = time.perf_counter() - t0
     dev = [pcpm.to_device_csr(rp, col) for rp, col in data]
     edges = sum(int(rp[-1]) for rp, _ in data)
-    # partition size per scale (pcpm_autotune on the first graph of that scale)
-    best_q = {}
+    # partition size and tile shape per scale (pcpm_autotune_ex on the first
+    # graph of that scale)
+    best_q, best_opts = {}, {}
+    shapes = ({}, {"gather_cluster": 1}, {"gather_unit_chunks": 64})
     for s in sorted(set(scales)):
         i = scales.index(s)
-        best_q[s], _ = pcpm.autotune(*dev[i], (2048, 8192, 32768), a.d, warmup=2, iters=5, mode="two_phase")
-    handles = [pcpm.PNG(*dev[i], best_q[s]) for i, s in enumerate(scales)]
+        best_q[s], best_opts[s], _ = pcpm.autotune_tiles(*dev[i], (2048, 8192, 32768), shapes, a.d, warmup=2,
+                                                         iters=5, mode="two_phase")
+    handles = [pcpm.PNG(*dev[i], best_q[s], **best_opts[s]) for i, s in enumerate(scales)]
     del dev
     t1 = time.perf_counter()
     batch = pcpm.Batch(handles, a.d, iters, mode="two_phase")
@@ -479,6 +482,7 @@ def batched_leg(a, graphs: int = 256, iters: int = 20):
         h.close()
     return {"graphs": graphs, "scales": "10-18", "iterations_each": iters, "edges_total": edges,
             "partition_size_per_scale": {str(k): v for k, v in sorted(best_q.items())},
+            "tile_shape_per_scale": {str(k): v for k, v in sorted(best_opts.items())},
             "one_graph_launch_ms": graph_ms, "gteps": edges * iters / (graph_ms * 1e-3) / 1e9,
             "call_by_call_ms": seq_ms, "call_by_call_gteps": edges * iters / (seq_ms * 1e-3) / 1e9,
             "capture_ms": capture_s * 1e3, "generate_s": gen_s}
@@ -681,6 +685,15 @@ def run_ours(a):
                 dts[dt_name]["time_to_residual"] = {"tol": 1e-7, "iters": its, "ms": e0.elapsed_time(e1),
                                                     "final_residual": res, "reached": res < 1e-7}
                 conv_ranks[dt_name] = xr.cpu().numpy()
+                if dt_name != "f32":  # delta iterations with rounding feedback (PCPM_DELTA)
+                    torch.cuda.synchronize()
+                    e0.record()
+                    xd, itd, resd = gu.pagerank(a.d, max_iters=300, tol=1e-7, mode="delta")
+                    e1.record()
+                    torch.cuda.synchronize()
+                    dts[dt_name]["time_to_residual_delta"] = {"tol": 1e-7, "iters": itd, "ms": e0.elapsed_time(e1),
+                                                              "final_residual": resd, "reached": resd < 1e-7}
+                    conv_ranks[dt_name + "_delta"] = xd.cpu().numpy()
             gu.close()
         del d_rp, d_col
         out["update_dtypes"] = dts
@@ -703,8 +716,9 @@ def run_ours(a):
             out["update_dtypes"][dt_name]["l1_first_iteration_vs_fp64_oracle"] = float(
                 np.abs(x1.astype(np.float64) - y_ref).sum())
         if "f32" in conv_ranks:  # converged ranks of each format against the FP32 solve's
-            for dt_name, xr in conv_ranks.items():
-                out["update_dtypes"][dt_name]["time_to_residual"]["l1_vs_f32_converged"] = float(
+            for key, xr in conv_ranks.items():
+                dt_name, leg = (key[:-6], "time_to_residual_delta") if key.endswith("_delta") else (key, "time_to_residual")
+                out["update_dtypes"][dt_name][leg]["l1_vs_f32_converged"] = float(
                     np.abs(xr.astype(np.float64) - conv_ranks["f32"].astype(np.float64)).sum())
     ranks.close()
     if rank == 0:

@@ -334,6 +334,19 @@ int pcpm_autotune(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t n, 
                   const uint32_t* part_sizes, int count, float d, int warmup, int iters, uint32_t flags,
                   void* stream, uint32_t* best_part_size, float* ms_per_iter);
 
+/* The autotuner over partition sizes and tile shapes: every partition size
+ * with every build option set (the work decomposition: gather_unit_chunks,
+ * scatter_unit_groups, gather_cluster, gather layout; results do not depend
+ * on them, only speed), timed as in pcpm_autotune.
+ *   options      host, `noptions` >= 1 option sets (NULL: one automatic set).
+ *   best_option  host; receives the index of the fastest option set.
+ *   ms_per_iter  host, count * noptions floats (row = partition size),
+ *                nullable; -1 where the build rejected the combination. */
+int pcpm_autotune_ex(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t n, uint64_t m,
+                     const uint32_t* part_sizes, int count, const pcpm_build_options* options, int noptions,
+                     float d, int warmup, int iters, uint32_t flags, void* stream, uint32_t* best_part_size,
+                     int* best_option, float* ms_per_iter);
+
 /* Returns the memory that the library's pools hold but no live handle uses
  * to the driver (cudaMemPoolTrimTo 0 on every device the library used).
  * PCPM_ECUDA if a trim fails. */

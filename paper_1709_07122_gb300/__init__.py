@@ -102,6 +102,8 @@ def lib(path: str | None = None):
                 "pcpm_release_cached_memory": (i32, []),
                 "pcpm_autotune": (i32, [vp, vp, u32, u64, vp, i32, f32, i32, i32, u32, vp, ctypes.POINTER(u32),
                                         vp]),
+                "pcpm_autotune_ex": (i32, [vp, vp, u32, u64, vp, i32, ctypes.POINTER(_Options), i32, f32, i32,
+                                           i32, u32, vp, ctypes.POINTER(u32), pi, vp]),
                 "pcpm_ppr_create": (i32, [vp, vp, vp, vp, ctypes.POINTER(vp)]),
                 "pcpm_ppr_run": (i32, [vp, f32, i32, vp]),
                 "pcpm_ppr_residuals": (i32, [vp, vp, i32]),
@@ -190,6 +192,35 @@ def autotune(row_ptr, col, part_sizes=(2048, 4096, 8192, 16384, 32768), d: float
                                _stream(stream), ctypes.byref(best), ms.ctypes.data_as(ctypes.c_void_p)),
            "pcpm_autotune")
     return best.value, {int(q): (float(t) if t >= 0 else None) for q, t in zip(cand, ms)}
+
+
+# Tile shapes the autotuner tries by default: the automatic decomposition,
+# one gather CTA per unit, four-CTA clusters, small and large gather units,
+# and the chunk layout.
+TILE_SHAPES = ({}, {"gather_cluster": 1}, {"gather_cluster": 4}, {"gather_unit_chunks": 64},
+               {"gather_unit_chunks": 1024}, {"scatter_unit_groups": 4096}, {"gather_windows": 2})
+
+
+def autotune_tiles(row_ptr, col, part_sizes=(8192, 16384, 32768), tile_shapes=TILE_SHAPES, d: float = 0.85,
+                   warmup: int = 2, iters: int = 5, dangling: str = "uniform", mode: str = "two_phase",
+                   stream=None):
+    """Partition size and tile shape (pcpm_autotune_ex) on a device CSR:
+    returns (best part size, best build options dict, {(part size, shape
+    index): ms per iteration, or None if rejected})."""
+    cand = np.ascontiguousarray(part_sizes, dtype=np.uint32)
+    shapes = list(tile_shapes)
+    opts = (_Options * len(shapes))(*[_Options(**{k: int(v) for k, v in o.items()}) for o in shapes])
+    ms = np.empty(cand.size * len(shapes), np.float32)
+    best_q, best_o = ctypes.c_uint32(0), ctypes.c_int(0)
+    n = row_ptr.numel() - 1
+    m = int(row_ptr[-1].item()) & 0xFFFFFFFF
+    _check(lib().pcpm_autotune_ex(_dev_u32(row_ptr), _dev_u32(col), n, m, cand.ctypes.data_as(ctypes.c_void_p),
+                                  int(cand.size), opts, len(shapes), float(d), int(warmup), int(iters),
+                                  _flags(dangling, mode), _stream(stream), ctypes.byref(best_q),
+                                  ctypes.byref(best_o), ms.ctypes.data_as(ctypes.c_void_p)), "pcpm_autotune_ex")
+    table = {(int(q), j): (float(ms[i * len(shapes) + j]) if ms[i * len(shapes) + j] >= 0 else None)
+             for i, q in enumerate(cand) for j in range(len(shapes))}
+    return best_q.value, dict(shapes[best_o.value]), table
 
 
 def release_cached_memory() -> None:

@@ -651,27 +651,41 @@ void pcpm_free(pcpm_png* png) {
 int pcpm_autotune(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t n, uint64_t m,
                   const uint32_t* part_sizes, int count, float d, int warmup, int iters, uint32_t flags,
                   void* stream, uint32_t* best_part_size, float* ms_per_iter) {
-    if (!part_sizes || count < 1 || !best_part_size || warmup < 0 || iters < 1 || bad_damping(d) ||
-        (flags & ~kAllFlags))
+    if (!best_part_size) return PCPM_EINVAL;
+    int best_opt = 0;
+    return pcpm_autotune_ex(row_ptr, col_idx, n, m, part_sizes, count, nullptr, 1, d, warmup, iters, flags, stream,
+                            best_part_size, &best_opt, ms_per_iter);
+}
+
+int pcpm_autotune_ex(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t n, uint64_t m,
+                     const uint32_t* part_sizes, int count, const pcpm_build_options* options, int noptions,
+                     float d, int warmup, int iters, uint32_t flags, void* stream, uint32_t* best_part_size,
+                     int* best_option, float* ms_per_iter) {
+    if (!part_sizes || count < 1 || noptions < 1 || !best_part_size || !best_option || warmup < 0 || iters < 1 ||
+        bad_damping(d) || (flags & ~kAllFlags))
         return PCPM_EINVAL;
     float best = -1.0f;
     for (int i = 0; i < count; ++i) {
-        if (ms_per_iter) ms_per_iter[i] = -1.0f;
-        pcpm_png* g = nullptr;
-        int rc = pcpm_build(row_ptr, col_idx, n, m, part_sizes[i], stream, &g);
-        if (rc == PCPM_EINVAL) continue;
-        if (rc != PCPM_OK) return rc;
-        float kms[PCPM_NUM_PHASES + 1] = {};
-        rc = pcpm_reset(g, nullptr, stream);
-        if (rc == PCPM_OK && warmup > 0) rc = pcpm_iterate(g, d, warmup, 0.0, flags, nullptr, nullptr, stream);
-        if (rc == PCPM_OK) rc = pcpm_iterate_timed(g, d, iters, flags, kms, stream);
-        pcpm_free(g);
-        if (rc != PCPM_OK) return rc;
-        const float ms = kms[PCPM_NUM_PHASES] / (float)iters;
-        if (ms_per_iter) ms_per_iter[i] = ms;
-        if (best < 0.0f || ms < best) {
-            best = ms;
-            *best_part_size = part_sizes[i];
+        for (int j = 0; j < noptions; ++j) {
+            float* slot = ms_per_iter ? ms_per_iter + (size_t)i * noptions + j : nullptr;
+            if (slot) *slot = -1.0f;
+            pcpm_png* g = nullptr;
+            int rc = pcpm_build_ex(row_ptr, col_idx, n, m, part_sizes[i], options ? options + j : nullptr, stream, &g);
+            if (rc == PCPM_EINVAL) continue;  // this partition size or tile shape does not apply
+            if (rc != PCPM_OK) return rc;
+            float kms[PCPM_NUM_PHASES + 1] = {};
+            rc = pcpm_reset(g, nullptr, stream);
+            if (rc == PCPM_OK && warmup > 0) rc = pcpm_iterate(g, d, warmup, 0.0, flags, nullptr, nullptr, stream);
+            if (rc == PCPM_OK) rc = pcpm_iterate_timed(g, d, iters, flags, kms, stream);
+            pcpm_free(g);
+            if (rc != PCPM_OK) return rc;
+            const float ms = kms[PCPM_NUM_PHASES] / (float)iters;
+            if (slot) *slot = ms;
+            if (best < 0.0f || ms < best) {
+                best = ms;
+                *best_part_size = part_sizes[i];
+                *best_option = j;
+            }
         }
     }
     return best < 0.0f ? PCPM_EINVAL : PCPM_OK;

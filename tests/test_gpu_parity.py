@@ -266,6 +266,24 @@ def test_autotune_picks_the_fastest_valid_part_size():
         pcpm.autotune(d_rp, d_col, (40000, 0))
 
 
+def test_autotune_over_tile_shapes_picks_the_fastest_valid_pair():
+    rp, col = graphgen.rmat(14, 16, seed=40)
+    d_rp, d_col = pcpm.to_device_csr(rp, col)
+    shapes = ({}, {"gather_cluster": 1}, {"gather_unit_chunks": 64}, {"gather_windows": 2},
+              {"gather_cluster": 3})  # 3 is not a cluster size: rejected
+    best_q, best_opts, table = pcpm.autotune_tiles(d_rp, d_col, (2048, 8192), shapes, iters=3)
+    assert all(table[(q, 4)] is None for q in (2048, 8192))
+    valid = {k: t for k, t in table.items() if t is not None}
+    assert len(valid) == 8 and all(t > 0 for t in valid.values())
+    q, j = min(valid, key=valid.get)
+    assert (best_q, best_opts) == (q, shapes[j])
+    # the chosen pair solves like any other
+    ref = oracle.pagerank(rp, col, 0.85, iters=5)["x"]
+    with pcpm.PNG(d_rp, d_col, best_q, **best_opts) as g:
+        x, _, _ = g.pagerank(0.85, max_iters=5)
+    assert l1(x.cpu().numpy(), ref) <= L1_TOL
+
+
 def test_errors_from_bad_inputs():
     rp = np.array([0, 2, 3, 3], np.uint32)
     unsorted = np.array([2, 1, 0], np.uint32)
