@@ -91,6 +91,8 @@ def _load():
             lib.oracle_png_fill_weights.restype = None
             lib.oracle_spmv.argtypes = [ctypes.c_uint32, _u32p, _u32p, _f64p, _f64p, _f64p]
             lib.oracle_spmv.restype = None
+            lib.oracle_spmv_rect.argtypes = [ctypes.c_uint32, ctypes.c_uint32, _u32p, _u32p, _f64p, _f64p, _f64p]
+            lib.oracle_spmv_rect.restype = None
             lib.oracle_weighted_gather.argtypes = [ctypes.c_uint32, ctypes.c_uint32, _u32p, _u32p, _u32p, _u32p,
                                                    _f64p, _f64p, _f64p]
             lib.oracle_weighted_gather.restype = None
@@ -287,6 +289,19 @@ def spmv(row_ptr, col, weights, x) -> np.ndarray:
     lib.oracle_spmv(n, row_ptr, col if col.size else np.zeros(1, np.uint32), w if w.size else np.zeros(1),
                     np.ascontiguousarray(x, dtype=np.float64), y)
     return y
+
+
+def spmv_rect(row_ptr, col, weights, x, n_cols: int) -> np.ndarray:
+    """Non-square A (rows = row_ptr.size - 1, n_cols columns) in CSR:
+    y(c) = sum over entries (r, c) of w * x(r), FP64 (Sec. 3.5)."""
+    lib = _load()
+    row_ptr, col = _csr(row_ptr, col)
+    n_rows = row_ptr.size - 1
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    y = np.empty(max(n_cols, 1), dtype=np.float64)
+    lib.oracle_spmv_rect(n_rows, int(n_cols), row_ptr, col if col.size else np.zeros(1, np.uint32),
+                         w if w.size else np.zeros(1), np.ascontiguousarray(x, dtype=np.float64), y)
+    return y[:n_cols]
 
 
 def weighted_scatter_gather(g: dict, wbin, x) -> np.ndarray:

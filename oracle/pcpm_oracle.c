@@ -319,6 +319,15 @@ void oracle_spmv(uint32_t n, const uint32_t* row_ptr, const uint32_t* col, const
         for (uint32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) y[col[e]] += weights[e] * x[u];
 }
 
+/* Sec. 3.5, a non-square matrix A (n_rows x n_cols) in CSR:
+ * y(c) = sum over the entries (r, c) of w * x(r), for c < n_cols. */
+void oracle_spmv_rect(uint32_t n_rows, uint32_t n_cols, const uint32_t* row_ptr, const uint32_t* col,
+                      const double* weights, const double* x, double* y) {
+    memset(y, 0, (size_t)n_cols * sizeof(double));
+    for (uint32_t r = 0; r < n_rows; ++r)
+        for (uint32_t e = row_ptr[r]; e < row_ptr[r + 1]; ++e) y[col[e]] += weights[e] * x[r];
+}
+
 /* Sec. 3.5 with Algorithms 3 and 4: update[t] = x[src_idx[t]]; the gather
  * walks each bin's IDs with the update pointer of Algorithm 4 and adds
  * weight * update to the destination. */

@@ -55,3 +55,36 @@ def test_bin_weights_follow_the_destination_ids():
         g = oracle.png(rp, col, q)
         np.testing.assert_array_equal(g["dest_ids"] & 0x7FFFFFFF, col[order])
         np.testing.assert_array_equal(oracle.bin_weights(rp, col, q, w, g), w[order])
+
+
+def rect(rows, cols, nnz, seed):
+    rng = np.random.default_rng(seed)
+    r = rng.integers(0, rows, nnz)
+    c = rng.integers(0, cols, nnz)
+    key = np.unique(r.astype(np.int64) * cols + c)
+    r, c = key // cols, key % cols
+    rp = np.zeros(rows + 1, np.uint32)
+    np.add.at(rp, r + 1, 1)
+    return np.cumsum(rp).astype(np.uint32), c.astype(np.uint32)
+
+
+def test_rect_spmv_equals_dense_product():
+    # a rows x cols matrix written out entry by entry: y = A^T x
+    rng = np.random.default_rng(10)
+    for rows, cols, nnz in ((7, 3, 12), (3, 11, 20), (50, 200, 900), (300, 40, 2000), (1, 5, 3)):
+        rp, col = rect(rows, cols, nnz, rows * 31 + cols)
+        w = rng.standard_normal(int(rp[-1]))
+        x = rng.standard_normal(rows)
+        A = np.zeros((rows, cols))
+        for r in range(rows):
+            for e in range(int(rp[r]), int(rp[r + 1])):
+                A[r, int(col[e])] += w[e]
+        np.testing.assert_allclose(oracle.spmv_rect(rp, col, w, x, cols), A.T @ x, rtol=1e-12, atol=1e-12)
+
+
+def test_rect_spmv_of_a_square_matrix_is_spmv():
+    rng = np.random.default_rng(11)
+    (rp, col), _ = next(graphs())
+    w = rng.standard_normal(int(rp[-1]))
+    x = rng.standard_normal(rp.size - 1)
+    np.testing.assert_array_equal(oracle.spmv_rect(rp, col, w, x, rp.size - 1), oracle.spmv(rp, col, w, x))
