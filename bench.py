@@ -365,7 +365,26 @@ def spmv_leg(a, rp, col, m):
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / reps
             res[name] = {"ms": ms, "gteps": m / (ms * 1e-3) / 1e9}
-    del d_rp, d_col, w, x
+    # a non-square matrix: the first half of the rows, all columns (Sec. 3.5)
+    rows = (rp.size - 1) // 2
+    mr = int(rp[rows])
+    r_rp, r_col = pcpm.to_device_csr(rp[:rows + 1], col[:mr])
+    xr = torch.from_numpy(rng.random(rows, dtype=np.float32)).cuda()
+    with pcpm.PNG.rect(r_rp, r_col, rp.size - 1, q, w[:mr].contiguous()) as gr:
+        for _ in range(3):
+            gr.spmv_rect(xr)
+        reps = 20
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            gr.spmv_rect(xr)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        res["rect_weighted"] = {"rows": rows, "cols": rp.size - 1, "entries": mr, "ms": ms,
+                                "gteps": mr / (ms * 1e-3) / 1e9}
+    del d_rp, d_col, w, x, r_rp, r_col, xr
     torch.cuda.empty_cache()
     res["part_size"] = q
     res["note"] = "one scatter of x (no 1/outdeg) + one gather; weighted stages 4 extra bytes per edge"

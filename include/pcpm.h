@@ -303,6 +303,25 @@ int pcpm_sync_status(const pcpm_png* png);
  * (pcpm_reset before solving). Enqueued on `stream`; does not synchronise. */
 int pcpm_spmv(pcpm_png* png, const float* x, float* y, void* stream);
 
+/* Non-square matrices (Sec. 3.5): rows and columns are partitioned
+ * separately; the scatter runs over the row partitions and the gather over
+ * the column partitions. A is n_rows x n_cols in CSR (rows are the sources):
+ *   row_ptr  device, uint32[n_rows + 1];  col_idx  device, uint32[m], each
+ *            < n_cols, sorted within the row;  weights  device float[m] or
+ *            NULL (all 1; then the PCPM_MAX_PART_SIZE limit applies, else
+ *            PCPM_MAX_WEIGHTED_PART_SIZE).
+ * Rows and columns share one range of n = max(n_rows, n_cols) IDs and the
+ * part size q: k = ceil(n / q) partitions, of which the first ceil(n_rows / q)
+ * hold sources and the first ceil(n_cols / q) are gathered. PCPM_EBADGRAPH if a
+ * column is >= n_cols; other errors as pcpm_build_ex. The handle runs
+ * pcpm_spmv_rect only (PageRank needs a square matrix).
+ * pcpm_spmv_rect: y = A^T_w x, x device float[n_rows], y device float[n_cols],
+ * one scatter and one gather (FP32 accumulation). Enqueued on `stream`. */
+int pcpm_build_rect(const uint32_t* row_ptr, const uint32_t* col_idx, const float* weights, uint32_t n_rows,
+                    uint32_t n_cols, uint64_t m, uint32_t part_size, const pcpm_build_options* options, void* stream,
+                    pcpm_png** out);
+int pcpm_spmv_rect(pcpm_png* png, const float* x, float* y, void* stream);
+
 /* Test hook: the weights in canonical bin order, host float[m] (the position
  * of each weight matches pcpm_png_export's dest_ids). Synchronises.
  * PCPM_EINVAL for an unweighted handle. */

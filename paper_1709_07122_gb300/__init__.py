@@ -133,6 +133,9 @@ def lib(path: str | None = None):
                 "pcpm_shard_init": (i32, [vp, vp, vp, vp, vp]),
                 "pcpm_shard_step": (i32, [vp, f32, u32, vp, vp, vp, vp]),
                 "pcpm_sync_status": (i32, [vp]),
+                "pcpm_build_rect": (i32, [vp, vp, vp, u32, u32, u64, u32, ctypes.POINTER(_Options), vp,
+                                          ctypes.POINTER(vp)]),
+                "pcpm_spmv_rect": (i32, [vp, vp, vp, vp]),
                 "pcpm_test_wait_limit": (i32, [ctypes.c_longlong]),
             }
             for name, (res, args) in sig.items():
@@ -276,6 +279,36 @@ class PNG:
         obj._h = h
         obj.n = n
         return obj
+
+    @classmethod
+    def rect(cls, row_ptr, col, n_cols: int, part_size: int, weights=None, stream=None, **options):
+        """A non-square matrix (rows = row_ptr.numel() - 1, n_cols columns)
+        for pcpm_spmv_rect (Sec. 3.5); weights: CUDA float32 per entry or None."""
+        if isinstance(options.get("update_dtype"), str):
+            options = dict(options, update_dtype=UPDATE_DTYPES[options["update_dtype"]])
+        n_rows = row_ptr.numel() - 1
+        m = int(row_ptr[-1].item()) & 0xFFFFFFFF
+        opt = _Options(**{k: int(v) for k, v in options.items()})
+        w = None
+        if weights is not None and m:
+            w = ctypes.c_void_p(_f32(weights, m, "weights").value)
+        h = ctypes.c_void_p()
+        _check(lib().pcpm_build_rect(_dev_u32(row_ptr), _dev_u32(col) if m else None, w, n_rows, int(n_cols), m,
+                                     int(part_size), ctypes.byref(opt), _stream(stream), ctypes.byref(h)),
+               "pcpm_build_rect")
+        obj = cls.__new__(cls)
+        obj._h = h
+        obj.n = max(n_rows, int(n_cols))
+        obj.n_rows, obj.n_cols = n_rows, int(n_cols)
+        return obj
+
+    def spmv_rect(self, x, out=None, stream=None):
+        """y = A^T_w x of a non-square handle (pcpm_spmv_rect)."""
+        import torch
+        out = torch.empty(self.n_cols, dtype=torch.float32, device="cuda") if out is None else out
+        _check(lib().pcpm_spmv_rect(self._h, _f32(x, self.n_rows, "x"), _f32(out, self.n_cols, "out"),
+                                    _stream(stream)), "pcpm_spmv_rect")
+        return out
 
     def shard_init(self, pr_out, sums, pr_init=None, stream=None):
         """pcpm_shard_init: PR_0 into pr_out (all n), sums = {0, own dangling mass}."""

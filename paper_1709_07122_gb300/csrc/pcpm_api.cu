@@ -256,8 +256,9 @@ int iterate_impl(pcpm_png* g, float d, int iters, double tol, uint32_t flags, in
 bool bad_damping(float d) { return !(d >= 0.0f && d < 1.0f); }
 
 // A handle that gathers only some destination partitions computes part of an
-// iteration; it is driven by pcpm_shard_init / pcpm_shard_step only.
-bool partial_shard(const pcpm_png* g) { return g->plo != 0 || g->phi != g->k; }
+// iteration; it is driven by pcpm_shard_init / pcpm_shard_step only. A
+// non-square matrix has no PageRank; it is driven by pcpm_spmv_rect only.
+bool partial_shard(const pcpm_png* g) { return g->plo != 0 || g->phi != g->k || g->rect; }
 
 constexpr uint32_t kAllFlags = PCPM_DANGLING_LEAK | PCPM_TWO_PHASE | PCPM_DELTA;
 
@@ -299,7 +300,8 @@ namespace {
 // from the edges into them (pcpm_build_shard).
 int build_impl(const uint32_t* row_ptr, const uint32_t* col_idx, const float* weights, uint32_t n, uint64_t m,
                uint32_t part_size, const pcpm_build_options* options, void* stream, pcpm_png** out,
-               bool shard = false, uint32_t part_lo = 0, uint32_t part_hi = 0) {
+               bool shard = false, uint32_t part_lo = 0, uint32_t part_hi = 0, uint32_t rect_rows = 0,
+               uint32_t rect_cols = 0) {
     if (!out || !row_ptr || n == 0 || n > PCPM_MAX_NODES || part_size == 0 || part_size > PCPM_MAX_PART_SIZE)
         return PCPM_EINVAL;
     pcpm_build_options opt = {};
@@ -349,6 +351,12 @@ int build_impl(const uint32_t* row_ptr, const uint32_t* col_idx, const float* we
     g->weights_in = weights;
     g->plo = shard ? part_lo : 0;
     g->phi = shard ? part_hi : (uint32_t)k;
+    if (rect_cols) {  // gather the column partitions only
+        g->rect = 1;
+        g->n_rows = rect_rows;
+        g->n_cols = rect_cols;
+        g->phi = (rect_cols + part_size - 1) / part_size;
+    }
     int rc = PCPM_OK;
     if (cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess) rc = PCPM_ECUDA;
     if (shard) {
@@ -398,6 +406,64 @@ int pcpm_build_weighted(const uint32_t* row_ptr, const uint32_t* col_idx, const 
     return build_impl(row_ptr, col_idx, weights, n, m, part_size, options, stream, out);
 }
 
+// ----------------------------------------------------- non-square matrices
+namespace pcpm_rect {
+__global__ void extend_rows_kernel(const uint32_t* __restrict__ row_ptr, uint32_t rows, uint32_t n,
+                                   uint32_t* __restrict__ out) {
+    const uint32_t end = row_ptr[rows];
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v <= n; v += gridDim.x * blockDim.x)
+        out[v] = v <= rows ? row_ptr[v] : end;
+}
+}  // namespace pcpm_rect
+
+int pcpm_build_rect(const uint32_t* row_ptr, const uint32_t* col_idx, const float* weights, uint32_t n_rows,
+                    uint32_t n_cols, uint64_t m, uint32_t part_size, const pcpm_build_options* options, void* stream,
+                    pcpm_png** out) {
+    if (!out || !row_ptr || n_rows == 0 || n_cols == 0 || part_size == 0 || part_size > PCPM_MAX_PART_SIZE)
+        return PCPM_EINVAL;
+    const uint32_t n = std::max(n_rows, n_cols);
+    if (n > PCPM_MAX_NODES || ((uint64_t)n + part_size - 1) / part_size > PCPM_MAX_PARTITIONS || m > 0xFFFFFF00ull)
+        return PCPM_EINVAL;
+    if (!is_device_ptr(row_ptr) || (m > 0 && !is_device_ptr(col_idx))) return PCPM_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    // every column index below n_cols (the build itself checks < n)
+    if (m > 0) {
+        std::vector<uint64_t> counts(((uint64_t)n_cols + part_size - 1) / part_size);
+        RC(dest_partition_counts(col_idx, m, n_cols, part_size, counts.data(), s));
+    }
+    if (n_cols <= n_rows)
+        return build_impl(row_ptr, col_idx, weights, n, m, part_size, options, stream, out, false, 0, 0, n_rows,
+                          n_cols);
+    // more columns than rows: rows n_rows .. n-1 are empty
+    uint32_t* rp = nullptr;
+    CK(pool_alloc((void**)&rp, ((size_t)n + 1) * sizeof(uint32_t), s));
+    pcpm_rect::extend_rows_kernel<<<(int)std::min<uint64_t>(4096, ((uint64_t)n + 256) / 256), 256, 0, s>>>(row_ptr, n_rows, n,
+                                                                                                 rp);
+    int rc = launch_status();
+    if (rc == PCPM_OK)
+        rc = build_impl(rp, col_idx, weights, n, m, part_size, options, stream, out, false, 0, 0, n_rows, n_cols);
+    cudaStreamSynchronize(s);
+    pool_free(rp, s);
+    return rc;
+}
+
+int pcpm_spmv_rect(pcpm_png* g, const float* x, float* y, void* stream) {
+    if (!g || !g->rect || !is_device_ptr(x) || !is_device_ptr(y)) return PCPM_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    g->last_stream = s;
+    CK(cudaMemsetAsync(g->state, 0, sizeof(DevState), s));
+    CK(cudaMemsetAsync(g->gacc, 0, (size_t)g->n * sizeof(float), s));
+    CK(cudaMemsetAsync(g->bin_done, 0, (size_t)g->k * sizeof(uint32_t), s));
+    g->cur = 0;
+    g->iters_done = 0;
+    g->upd_valid = 0;
+    RC(launch_copy_pad(x, g->n_rows, g->pr[0], g->n, s));  // x on the rows, 0 past them
+    RC(launch_scatter(g, s, /*raw=*/true));                // update[t] = x[src[t]], the row partitions
+    RC(launch_gather(g, 1.0f, PCPM_DANGLING_LEAK, /*fused=*/false, s, /*spmv=*/true));  // the column partitions
+    CK(cudaMemcpyAsync(y, g->pr[1], (size_t)g->n_cols * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    return PCPM_OK;
+}
+
 // ------------------------------------------------------- destination shards
 int pcpm_build_shard(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t n, uint64_t m, uint32_t part_size,
                      uint32_t part_lo, uint32_t part_hi, const pcpm_build_options* options, void* stream,
@@ -443,7 +509,7 @@ int pcpm_shard_split(const uint64_t* ids_per_part, uint32_t n, uint32_t part_siz
 }
 
 int pcpm_shard_init(pcpm_png* g, const float* pr_init, float* pr_out, double* sums, void* stream) {
-    if (!g || !is_device_ptr(pr_out) || !is_device_ptr(sums)) return PCPM_EINVAL;
+    if (!g || g->rect || !is_device_ptr(pr_out) || !is_device_ptr(sums)) return PCPM_EINVAL;
     if (pr_init && !is_device_ptr(pr_init)) return PCPM_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     g->last_stream = s;
@@ -462,7 +528,7 @@ int pcpm_shard_init(pcpm_png* g, const float* pr_init, float* pr_out, double* su
 
 int pcpm_shard_step(pcpm_png* g, float d, uint32_t flags, const float* pr_in, float* pr_out, double* sums,
                     void* stream) {
-    if (!g || bad_damping(d) || (flags & ~kAllFlags) || (flags & PCPM_DELTA)) return PCPM_EINVAL;
+    if (!g || g->rect || bad_damping(d) || (flags & ~kAllFlags) || (flags & PCPM_DELTA)) return PCPM_EINVAL;
     if (!is_device_ptr(pr_in) || !is_device_ptr(pr_out) || !is_device_ptr(sums) || pr_in == pr_out)
         return PCPM_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;

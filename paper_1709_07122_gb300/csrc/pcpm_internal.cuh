@@ -176,6 +176,11 @@ struct pcpm_png {
     // [plo, phi) only (all of [0, k) unless built by pcpm_build_shard), gathers
     // and applies those, and owns nodes [plo * q, min(phi * q, n)).
     uint32_t plo, phi;
+    // Non-square matrix (pcpm_build_rect, Sec. 3.5): rows [0, n_rows) are the
+    // sources, columns [0, n_cols) the destinations, over n = max of the two
+    // IDs; the gather runs the column partitions only (phi = ceil(n_cols / q)).
+    int rect;
+    uint32_t n_rows, n_cols;
     float* gacc;             // n: partial sums of bins cut into several units
     uint32_t* bin_done;      // k: units of a cut bin that have flushed
     float* inv_deg;          // n: 1/|N_o(u)|, 0 for dangling nodes
@@ -233,6 +238,8 @@ void note_cuda_error(cudaError_t e);
 // error and returns PCPM_ECUDA.
 int launch_status();
 int launch_init(pcpm_png* g, const float* pr_init, cudaStream_t s);
+// out[v] = x[v] for v < len, 0 for len <= v < n (a non-square matrix's rows).
+int launch_copy_pad(const float* x, uint32_t len, float* out, uint32_t n, cudaStream_t s);
 // init into `out` (n floats), with the dangling partial sums over nodes [lo, hi) only.
 int launch_init_range(pcpm_png* g, const float* pr_init, float* out, uint32_t lo, uint32_t hi, cudaStream_t s);
 // raw: stage x itself (SpMV) instead of x * (1/outdeg).

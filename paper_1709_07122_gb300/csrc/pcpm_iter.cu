@@ -1636,6 +1636,16 @@ int launch_init_range(pcpm_png* g, const float* pr_init, float* out, uint32_t lo
     return launch_status();
 }
 
+__global__ void copy_pad_kernel(const float* __restrict__ x, uint32_t len, float* __restrict__ out, uint32_t n) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        out[v] = v < len ? x[v] : 0.0f;
+}
+
+int launch_copy_pad(const float* x, uint32_t len, float* out, uint32_t n, cudaStream_t s) {
+    copy_pad_kernel<<<(int)std::min<uint64_t>(4096, ((uint64_t)n + 255) / 256), 256, 0, s>>>(x, len, out, n);
+    return launch_status();
+}
+
 int launch_init(pcpm_png* g, const float* pr_init, cudaStream_t s) {
     return launch_init_range(g, pr_init, g->pr[g->cur], 0, g->n, s);
 }

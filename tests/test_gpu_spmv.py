@@ -107,3 +107,62 @@ def test_bad_weighted_options_rejected():
         with pytest.raises(pcpm.PcpmError) as e:
             weighted(rp, col, w, q, **opts)
         assert e.value.code == -1
+
+
+def rect_matrix(rows, cols, nnz, seed):
+    """A rows x cols CSR with sorted, distinct columns per row."""
+    rng = np.random.default_rng(seed)
+    r = rng.integers(0, rows, nnz)
+    c = rng.integers(0, cols, nnz)
+    key = np.unique(r.astype(np.int64) * cols + c)
+    r, c = key // cols, key % cols
+    rp = np.zeros(rows + 1, np.int64)
+    np.add.at(rp, r + 1, 1)
+    return np.cumsum(rp).astype(np.uint32), c.astype(np.uint32)
+
+
+RECT = {
+    "tall_5000x700_q256": (5000, 700, 40000, 256),
+    "wide_600x9000_q1000": (600, 9000, 30000, 1000),
+    "wide_ragged_1000x33001_q4096": (1000, 33001, 50000, 4096),
+    "tall_one_col_partition_40000x300_q16384": (40000, 300, 200000, 16384),
+    "single_row_1x5000_q7": (1, 5000, 3000, 7),
+}
+
+
+@pytest.mark.parametrize("opts", [{}, {"gather_windows": 2}, {"gather_unit_chunks": 1, "gather_cluster": 1}],
+                         ids=["windows", "chunks", "cut_bins"])
+@pytest.mark.parametrize("weights", [True, False], ids=["weighted", "unit"])
+@pytest.mark.parametrize("name", sorted(RECT))
+def test_rect_spmv_matches_oracle(name, weights, opts):
+    rows, cols, nnz, q = RECT[name]
+    rp, col = rect_matrix(rows, cols, nnz, seed=rows + cols)
+    m = int(rp[-1])
+    rng = np.random.default_rng(89)
+    w = rng.standard_normal(m).astype(np.float32) if weights else np.ones(m, np.float32)
+    x = rng.standard_normal(rows).astype(np.float32)
+    want = oracle.spmv_rect(rp, col, w.astype(np.float64), x.astype(np.float64), cols)
+    k = np.bincount(col, minlength=cols)
+    mag = oracle.spmv_rect(rp, col, np.abs(w.astype(np.float64)), np.abs(x.astype(np.float64)), cols)
+    drp, dcol = pcpm.to_device_csr(rp, col)
+    wq = min(q, 16384) if weights else q
+    g = pcpm.PNG.rect(drp, dcol, cols, wq, torch.from_numpy(w).cuda() if weights else None, **opts)
+    with g:
+        assert g.info["shard_part_hi"] == -(-cols // wq)  # only the column partitions are gathered
+        for _ in range(2):  # the handle is reusable
+            y = g.spmv_rect(torch.from_numpy(x).cuda()).cpu().numpy().astype(np.float64)
+            assert y.shape == (cols,)
+            assert np.all(np.abs(y - want) <= (k + 4) * U * mag + 1e-30)
+
+
+def test_rect_rejects_pagerank_and_columns_out_of_range():
+    rp, col = rect_matrix(300, 100, 1000, seed=5)
+    drp, dcol = pcpm.to_device_csr(rp, col)
+    with pcpm.PNG.rect(drp, dcol, 100, 64) as g:
+        for call in (lambda: g.pagerank(0.85, 2), lambda: g.reset(), lambda: g.spmv(torch.ones(g.n, device="cuda"))):
+            with pytest.raises(pcpm.PcpmError) as e:
+                call()
+            assert e.value.code == -1
+    with pytest.raises(pcpm.PcpmError) as e:
+        pcpm.PNG.rect(drp, dcol, 50, 64)  # columns up to 99 but only 50 declared
+    assert e.value.code == -6
