@@ -451,8 +451,11 @@ def batched_leg(a, graphs: int = 256, iters: int = 20):
     """Many small independent graphs (RMAT, scales drawn from 10-18, random
     labels) solved for `iters` iterations each by one captured CUDA graph
     launch, against the same solves issued call by call on one stream. The
-    partition size is picked per scale from {2048, 8192, 32768} by the
-    library's autotuner (five timed iterations on the first graph of that scale)."""
+    partition size and tile shape are picked per scale from {2048, 8192,
+    32768} by the library's autotuner (five timed iterations on the first
+    graph of that scale); each of the three part sizes for all graphs is
+    timed too. Graphs that share a part size and cluster size run each phase
+    as one launch over all their units."""
     import torch
     import paper_1709_07122_gb300 as pcpm
     import graphgen
@@ -471,22 +474,36 @@ def batched_leg(a, graphs: int = 256, iters: int = 20):
         i = scales.index(s)
         best_q[s], best_opts[s], _ = pcpm.autotune_tiles(*dev[i], (2048, 8192, 32768), shapes, a.d, warmup=2,
                                                          iters=5, mode="two_phase")
+
+    def time_batch(batch):
+        batch.launch()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            batch.launch()
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
+
+    # one part size for every graph (default tiles): the fewest batch groups
+    one_q = {}
+    for q in (2048, 8192, 32768):
+        hs = [pcpm.PNG(rp, col, q) for rp, col in dev]
+        with pcpm.Batch(hs, a.d, iters, mode="two_phase") as b:
+            one_q[str(q)] = {"ms": time_batch(b), "kernel_launches": b.kernel_launches}
+        for h in hs:
+            h.close()
     handles = [pcpm.PNG(*dev[i], best_q[s], **best_opts[s]) for i, s in enumerate(scales)]
     del dev
     t1 = time.perf_counter()
     batch = pcpm.Batch(handles, a.d, iters, mode="two_phase")
     capture_s = time.perf_counter() - t1
-    batch.launch()
-    torch.cuda.synchronize()
-    ms = []
-    for _ in range(3):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        batch.launch()
-        e1.record()
-        torch.cuda.synchronize()
-        ms.append(e0.elapsed_time(e1))
-    graph_ms = statistics.median(ms)
+    graph_ms = time_batch(batch)
+    launches = batch.kernel_launches
+    best_one_q = min(one_q, key=lambda q: one_q[q]["ms"])
     # the same work, one call after another
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
@@ -503,6 +520,10 @@ def batched_leg(a, graphs: int = 256, iters: int = 20):
             "partition_size_per_scale": {str(k): v for k, v in sorted(best_q.items())},
             "tile_shape_per_scale": {str(k): v for k, v in sorted(best_opts.items())},
             "one_graph_launch_ms": graph_ms, "gteps": edges * iters / (graph_ms * 1e-3) / 1e9,
+            "kernel_launches": launches,
+            "one_part_size": one_q,
+            "one_part_size_best": {"part_size": int(best_one_q), "ms": one_q[best_one_q]["ms"],
+                                   "gteps": edges * iters / (one_q[best_one_q]["ms"] * 1e-3) / 1e9},
             "call_by_call_ms": seq_ms, "call_by_call_gteps": edges * iters / (seq_ms * 1e-3) / 1e9,
             "capture_ms": capture_s * 1e3, "generate_s": gen_s}
 

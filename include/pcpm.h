@@ -207,12 +207,24 @@ int pcpm_build_ex(const uint32_t* row_ptr, const uint32_t* col_idx, uint32_t n, 
  *   handles  host array of `count` distinct handles (PCPM_EINVAL otherwise),
  *            which must outlive the batch.
  * pcpm_batch_create synchronises the default stream if a handle's residual
- * history has to grow (it captures on private streams). */
+ * history has to grow (it captures on private streams). The L1 changes reach
+ * each handle's history at every launch, also after later pcpm_iterate calls
+ * have grown it. pcpm_batch_free waits for the device before it releases
+ * the batch's buffers. */
 typedef struct pcpm_batch pcpm_batch;
 int pcpm_batch_create(pcpm_png* const* handles, int count, float d, int iters, uint32_t flags,
                       pcpm_batch** out);
 int pcpm_batch_launch(pcpm_batch* batch, void* stream);
 void pcpm_batch_free(pcpm_batch* batch); /* NULL is a no-op */
+/* The number of kernels one pcpm_batch_launch runs (the kernel nodes of its
+ * CUDA graph) into *launches. When every handle has the window layout, FP32
+ * bins and no weights, and the flags ask for plain two-phase iterations,
+ * each phase is a single launch over the units of all graphs that share a
+ * part size and a gather cluster size: 2 + 3 iters launches per distinct
+ * (part size, cluster size) pair (reset, its reduction, then scatter,
+ * gather, reduction per iteration) plus one copy of the histories. Otherwise each handle's work is captured as
+ * pcpm_reset and pcpm_iterate enqueue it. PCPM_EINVAL for NULL arguments. */
+int pcpm_batch_kernel_launches(const pcpm_batch* batch, int* launches);
 
 /* Weighted graphs and SpMV (Sec. 3.5): pcpm_build with an edge weight per
  * column index.

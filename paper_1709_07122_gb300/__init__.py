@@ -116,6 +116,7 @@ def lib(path: str | None = None):
                 "pcpm_batch_create": (i32, [vp, i32, f32, i32, u32, ctypes.POINTER(vp)]),
                 "pcpm_batch_launch": (i32, [vp, vp]),
                 "pcpm_batch_free": (None, [vp]),
+                "pcpm_batch_kernel_launches": (i32, [vp, ctypes.POINTER(i32)]),
                 "pcpm_export_weights": (i32, [vp, vp]),
                 "pcpm_ws_features": (i32, [vp, vp, vp, vp, vp]),
                 "pcpm_ws_predict": (i32, [vp, vp, u32, vp, vp]),
@@ -681,6 +682,13 @@ class Batch:
 
     def launch(self, stream=None):
         _check(lib().pcpm_batch_launch(self._b, _stream(stream)), "pcpm_batch_launch")
+
+    @property
+    def kernel_launches(self) -> int:
+        """Kernels one launch runs (pcpm_batch_kernel_launches)."""
+        k = ctypes.c_int32()
+        _check(lib().pcpm_batch_kernel_launches(self._b, ctypes.byref(k)), "pcpm_batch_kernel_launches")
+        return int(k.value)
 
     def close(self):
         if getattr(self, "_b", None) is not None and self._b.value:

@@ -581,13 +581,22 @@ int pcpm_spmv(pcpm_png* g, const float* x, float* y, void* stream) {
 }
 
 // ------------------------------------------------------------------ batches
+// The captured work writes each handle's L1 changes into the batch's own
+// history rows; the graph's last kernel copies them to the handles' history
+// buffers through a device table of pointers, refreshed at launch when a
+// handle's history has grown (moved) since the capture.
 struct pcpm_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    pcpm::BatchKernels* kernels = nullptr;  // one launch per phase over all graphs, else per-handle work
+    double* hist = nullptr;                 // count x iters
+    double** hist_dst = nullptr;            // count device pointers
+    std::vector<double*> hist_dst_host;
+    int iters = 0;
     // each handle's host-side solver state right after the captured work
     struct After {
         pcpm_png* g;
-        int cur, ucur, upd_valid, iters_done;
+        int cur, ucur, upd_valid, iters_done, dq_cur;
     };
     std::vector<After> after;
 };
@@ -598,10 +607,11 @@ int pcpm_batch_create(pcpm_png* const* handles, int count, float d, int iters, u
     for (int i = 0; i < count; ++i)
         if (!handles[i] || partial_shard(handles[i]) || !seen.insert(handles[i]).second)
             return PCPM_EINVAL;  // no handle twice, no destination shard
-    // history room for the captured iterations (grows outside the capture)
+    // history room for the batch's iterations (grows outside the capture)
     for (int i = 0; i < count; ++i) RC(ensure_hist(handles[i], iters, (cudaStream_t)0));
     pcpm_batch* b = new (std::nothrow) pcpm_batch;
     if (!b) return PCPM_ENOMEM;
+    b->iters = iters;
     const int nb = std::min(count, kBatchStreams);
     std::vector<cudaStream_t> streams(nb, nullptr);
     std::vector<cudaEvent_t> joins(nb, nullptr);
@@ -609,53 +619,67 @@ int pcpm_batch_create(pcpm_png* const* handles, int count, float d, int iters, u
     cudaEvent_t fork = nullptr;
     int rc = PCPM_OK;
     bool capturing = false;
-    if (cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess)
-        rc = PCPM_ECUDA;
-    for (int j = 0; j < nb && rc == PCPM_OK; ++j)
-        if (cudaStreamCreateWithFlags(&streams[j], cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&joins[j], cudaEventDisableTiming) != cudaSuccess)
-            rc = PCPM_ECUDA;
-    if (rc == PCPM_OK) {
-        const cudaError_t e = cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal);
-        if (e != cudaSuccess) {
-            note_cuda_error(e);
-            rc = PCPM_ECUDA;
-        }
-    }
-    capturing = rc == PCPM_OK;
     auto ok = [&](cudaError_t e) {
         if (e != cudaSuccess) {
             note_cuda_error(e);
-            rc = PCPM_ECUDA;
+            if (rc == PCPM_OK) rc = e == cudaErrorMemoryAllocation ? PCPM_ENOMEM : PCPM_ECUDA;
         }
         return rc == PCPM_OK;
     };
-    if (rc == PCPM_OK) ok(cudaEventRecord(fork, origin));
-    for (int j = 0; j < nb && rc == PCPM_OK; ++j) ok(cudaStreamWaitEvent(streams[j], fork, 0));
-    // handle i on branch i % nb: independent graphs run side by side
-    for (int i = 0; i < count && rc == PCPM_OK; ++i) {
-        pcpm_png* g = handles[i];
-        cudaStream_t s = streams[i % nb];
-        rc = pcpm_reset(g, nullptr, s);
-        if (rc == PCPM_OK) rc = run_iterations(g, d, iters, 0.0, flags, s, nullptr);
-        if (rc == PCPM_OK) {
-            g->iters_done = iters;
-            b->after.push_back({g, g->cur, g->ucur, g->upd_valid, g->iters_done});
+    if (ok(cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking)))
+        ok(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    if (rc == PCPM_OK && ok(pool_alloc((void**)&b->hist, (size_t)count * iters * sizeof(double), origin)) &&
+        ok(pool_alloc((void**)&b->hist_dst, (size_t)count * sizeof(double*), origin))) {
+        for (int i = 0; i < count; ++i) b->hist_dst_host.push_back(handles[i]->hist);
+        if (ok(cudaMemcpyAsync(b->hist_dst, b->hist_dst_host.data(), (size_t)count * sizeof(double*),
+                               cudaMemcpyHostToDevice, origin)))
+            ok(cudaStreamSynchronize(origin));
+    }
+    const bool one_launch = rc == PCPM_OK && batch_kernels_ok(handles, count, flags);
+    if (one_launch) rc = batch_kernels_create(handles, count, d, flags, b->hist, iters, origin, &b->kernels);
+    for (int j = 0; j < nb && rc == PCPM_OK; ++j)
+        if (ok(cudaStreamCreateWithFlags(&streams[j], cudaStreamNonBlocking)))
+            ok(cudaEventCreateWithFlags(&joins[j], cudaEventDisableTiming));
+    if (rc == PCPM_OK) capturing = ok(cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal));
+    if (rc == PCPM_OK && ok(cudaEventRecord(fork, origin)))
+        for (int j = 0; j < nb && rc == PCPM_OK; ++j) ok(cudaStreamWaitEvent(streams[j], fork, 0));
+    if (one_launch && rc == PCPM_OK) {
+        // each (part size, cluster size) group on its own branch
+        rc = batch_kernels_record(b->kernels, iters, streams.data(),
+                                  std::max(1, std::min(nb, batch_kernels_groups(b->kernels))));
+        for (int i = 0; i < count && rc == PCPM_OK; ++i) {
+            pcpm_png* g = handles[i];
+            // as pcpm_reset then `iters` two-phase iterations leave it
+            b->after.push_back({g, iters & 1, g->ucur, 0, iters, 0});
+        }
+    } else if (rc == PCPM_OK) {
+        // handle i on branch i % nb: independent graphs run side by side
+        for (int i = 0; i < count && rc == PCPM_OK; ++i) {
+            pcpm_png* g = handles[i];
+            cudaStream_t s = streams[i % nb];
+            double* const own_hist = g->hist;
+            const int own_cap = g->hist_cap;
+            g->hist = b->hist + (size_t)i * iters;  // the captured reductions write the batch's rows
+            g->hist_cap = iters;
+            rc = pcpm_reset(g, nullptr, s);
+            if (rc == PCPM_OK) rc = run_iterations(g, d, iters, 0.0, flags, s, nullptr);
+            g->hist = own_hist;
+            g->hist_cap = own_cap;
+            if (rc == PCPM_OK) {
+                g->iters_done = iters;
+                b->after.push_back({g, g->cur, g->ucur, g->upd_valid, g->iters_done, g->dq_cur});
+            }
         }
     }
     for (int j = 0; j < nb && rc == PCPM_OK; ++j)
         if (ok(cudaEventRecord(joins[j], streams[j]))) ok(cudaStreamWaitEvent(origin, joins[j], 0));
+    if (rc == PCPM_OK) rc = launch_hist_copy(b->hist, b->hist_dst, iters, count, origin);
     if (capturing) {
         cudaGraph_t graph = nullptr;
         const cudaError_t e = cudaStreamEndCapture(origin, &graph);
         if (rc == PCPM_OK && e == cudaSuccess) {
             b->graph = graph;
-            const cudaError_t ei = cudaGraphInstantiate(&b->exec, graph, 0);
-            if (ei != cudaSuccess) {
-                note_cuda_error(ei);
-                rc = PCPM_ECUDA;
-            }
+            ok(cudaGraphInstantiate(&b->exec, graph, 0));
         } else {
             if (e != cudaSuccess) note_cuda_error(e);
             if (graph) cudaGraphDestroy(graph);
@@ -668,7 +692,10 @@ int pcpm_batch_create(pcpm_png* const* handles, int count, float d, int iters, u
         if (streams[j]) cudaStreamDestroy(streams[j]);
     }
     if (fork) cudaEventDestroy(fork);
-    if (origin) cudaStreamDestroy(origin);
+    if (origin) {
+        cudaStreamSynchronize(origin);
+        cudaStreamDestroy(origin);
+    }
     for (int i = 0; i < count; ++i) handles[i]->last_stream = nullptr;
     if (rc != PCPM_OK) {
         pcpm_batch_free(b);
@@ -681,21 +708,56 @@ int pcpm_batch_create(pcpm_png* const* handles, int count, float d, int iters, u
 int pcpm_batch_launch(pcpm_batch* b, void* stream) {
     if (!b || !b->exec) return PCPM_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
+    bool moved = false;
+    for (size_t i = 0; i < b->after.size(); ++i) {
+        pcpm_png* g = b->after[i].g;
+        RC(ensure_hist(g, b->iters, s));
+        if (g->hist != b->hist_dst_host[i]) {
+            b->hist_dst_host[i] = g->hist;
+            moved = true;
+        }
+    }
+    if (moved)
+        CK(cudaMemcpyAsync(b->hist_dst, b->hist_dst_host.data(), b->hist_dst_host.size() * sizeof(double*),
+                           cudaMemcpyHostToDevice, s));
     CK(cudaGraphLaunch(b->exec, s));
     for (const auto& a : b->after) {
         a.g->cur = a.cur;
         a.g->ucur = a.ucur;
         a.g->upd_valid = a.upd_valid;
         a.g->iters_done = a.iters_done;
+        a.g->dq_cur = a.dq_cur;
         a.g->last_stream = s;
     }
     return PCPM_OK;
 }
 
+int pcpm_batch_kernel_launches(const pcpm_batch* b, int* launches) {
+    if (!b || !b->graph || !launches) return PCPM_EINVAL;
+    size_t count = 0;
+    CK(cudaGraphGetNodes(b->graph, nullptr, &count));
+    std::vector<cudaGraphNode_t> nodes(count);
+    if (count) CK(cudaGraphGetNodes(b->graph, nodes.data(), &count));
+    int k = 0;
+    for (cudaGraphNode_t node : nodes) {
+        cudaGraphNodeType t;
+        CK(cudaGraphNodeGetType(node, &t));
+        if (t == cudaGraphNodeTypeKernel) ++k;
+    }
+    *launches = k;
+    return PCPM_OK;
+}
+
 void pcpm_batch_free(pcpm_batch* b) {
     if (!b) return;
+    // the batch's buffers return to the pool only once no launch can still use them
+    cudaDeviceSynchronize();
+    cudaGetLastError();
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
+    pcpm::batch_kernels_free(b->kernels);
+    if (b->hist) pool_free(b->hist, nullptr);
+    if (b->hist_dst) pool_free(b->hist_dst, nullptr);
     delete b;
 }
 

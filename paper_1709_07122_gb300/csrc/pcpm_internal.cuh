@@ -253,6 +253,22 @@ int launch_scatter_bits(pcpm_png* g, const void* x, void* out, cudaStream_t s);
 // spmv: the weighted gather of a weighted handle (Sec. 3.5).
 int launch_gather(pcpm_png* g, float d, uint32_t flags, bool fused, cudaStream_t s, bool spmv = false,
                   bool delta = false);
+// Batched solves with one launch per phase over the units of all graphs
+// (pcpm_batch_*) of each (part size, cluster size) group: usable when every
+// handle has the window layout, FP32 bins, no weights and the whole square
+// graph, and the iterations are plain two-phase ones. batch_kernels_free
+// wants the device idle.
+struct BatchKernels;
+bool batch_kernels_ok(pcpm_png* const* hs, int count, uint32_t flags);
+// hist: count x iters doubles, row i the L1 changes of hs[i].
+int batch_kernels_create(pcpm_png* const* hs, int count, float d, uint32_t flags, double* hist, int iters,
+                         cudaStream_t s, BatchKernels** out);
+int batch_kernels_groups(const BatchKernels* b);
+// group i recorded on streams[i % nstreams]: groups run side by side
+int batch_kernels_record(BatchKernels* b, int iters, const cudaStream_t* streams, int nstreams);
+void batch_kernels_free(BatchKernels* b);
+// dst[i][t] = src[i * iters + t] for t < iters (dst: device table of count pointers).
+int launch_hist_copy(const double* src, double* const* dst, int iters, int count, cudaStream_t s);
 // The window gather's bound on waits for work (see pcpm_test_wait_limit).
 int set_work_wait_limit(long long cycles);
 // record = false: the L1 change goes to the device state only, not the history.

@@ -33,6 +33,8 @@
 
 #include <algorithm>
 #include <mutex>
+#include <utility>
+#include <vector>
 
 #include "pcpm_internal.cuh"
 
@@ -577,12 +579,12 @@ __host__ __device__ constexpr uint32_t scatter_stage_bytes(uint32_t q, uint32_t 
     return fit < kScatterStageBytes ? (uint32_t)fit : kScatterStageBytes;
 }
 template <int kUpd>
-__global__ void __launch_bounds__(kScatterThreads, 1) scatter_kernel(
+__device__ __forceinline__ void scatter_body(
     uint32_t n, uint32_t q, uint32_t k, const float* __restrict__ pr, const float* __restrict__ inv_deg,
     const uint32_t* __restrict__ src, const uint32_t* __restrict__ seg_u, const uint32_t* __restrict__ cnt_u,
     const uint4* __restrict__ units, const uint32_t* __restrict__ order, void* __restrict__ upd,
     const DevState* __restrict__ st, int* __restrict__ err, const float* __restrict__ pr_prev,
-    const float* __restrict__ dq_in, float* __restrict__ dq_out) {
+    const float* __restrict__ dq_in, float* __restrict__ dq_out, uint32_t upos) {
     if (st->stop) return;
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ uint32_t sh32[32];
@@ -595,7 +597,7 @@ __global__ void __launch_bounds__(kScatterThreads, 1) scatter_kernel(
     uint32_t* dsh = reinterpret_cast<uint32_t*>(smraw + gpre_off + scatter_gpre_bytes(k));
     uint8_t* emsk = smraw + gpre_off + scatter_gpre_bytes(k) + scatter_dsh_bytes(k);
     unsigned char* stages = smraw + gpre_off + scatter_table_bytes(k);
-    const uint4 unit = units[order[blockIdx.x]];  // (partition, first group, end group, pieces)
+    const uint4 unit = units[order[upos]];  // (partition, first group, end group, pieces)
     const uint32_t p = unit.x;
     const uint32_t base = p * q, len = min(q, n - base);
     const uint32_t* segrow = seg_u + (size_t)p * k;
@@ -662,6 +664,42 @@ __global__ void __launch_bounds__(kScatterThreads, 1) scatter_kernel(
     };
     scatter_groups_staged<kUpd>(sspr, base, len, gpre, dsh, emsk, k, src, upd, unit.y, min(unit.z, gpre[k]), err,
                                 stages, scatter_stage_bytes(q, k), bars, stage_spr);
+}
+
+template <int kUpd>
+__global__ void __launch_bounds__(kScatterThreads, 1) scatter_kernel(
+    uint32_t n, uint32_t q, uint32_t k, const float* __restrict__ pr, const float* __restrict__ inv_deg,
+    const uint32_t* __restrict__ src, const uint32_t* __restrict__ seg_u, const uint32_t* __restrict__ cnt_u,
+    const uint4* __restrict__ units, const uint32_t* __restrict__ order, void* __restrict__ upd,
+    const DevState* __restrict__ st, int* __restrict__ err, const float* __restrict__ pr_prev,
+    const float* __restrict__ dq_in, float* __restrict__ dq_out) {
+    scatter_body<kUpd>(n, q, k, pr, inv_deg, src, seg_u, cnt_u, units, order, upd, st, err, pr_prev, dq_in, dq_out,
+                       blockIdx.x);
+}
+
+// The scatter of one graph of a batch (plain FP32 form).
+struct ScatterArgs {
+    uint32_t n, q, k;
+    const float* pr;
+    const float* inv_deg;
+    const uint32_t* src;
+    const uint32_t* seg_u;
+    const uint32_t* cnt_u;
+    const uint4* units;
+    const uint32_t* order;
+    void* upd;
+    const DevState* st;
+    int* err;
+};
+
+// Many graphs in one launch: block b takes item b (graph, position of the
+// unit in that graph's order).
+__global__ void __launch_bounds__(kScatterThreads, 1) scatter_batch_kernel(const ScatterArgs* __restrict__ tab,
+                                                                          const uint2* __restrict__ items) {
+    const uint2 it = items[blockIdx.x];
+    const ScatterArgs a = tab[it.x];
+    scatter_body<kUpdF32>(a.n, a.q, a.k, a.pr, a.inv_deg, a.src, a.seg_u, a.cnt_u, a.units, a.order, a.upd, a.st,
+                          a.err, nullptr, nullptr, nullptr, it.y);
 }
 
 // ---------------------------------------------------------- gather+apply
@@ -733,7 +771,7 @@ template <bool kFused, int kUpd, int kThreads>
 __device__ __forceinline__ void gather_finish(const GatherArgs& a, unsigned char* ring, size_t ring_bytes,
                                               uint64_t* sbars, unsigned char* sarea, size_t sarea_bytes, float* acc,
                                               uint32_t* sh32, uint32_t S, uint32_t rank, uint32_t pd,
-                                              uint32_t npieces, uint32_t vbase, uint32_t len) {
+                                              uint32_t npieces, uint32_t vbase, uint32_t len, uint32_t pslot) {
     using U = Upd<kUpd>;
     constexpr size_t kSumScratch = 2 * (kThreads / 32) * sizeof(double);
     cluster_sync();  // every CTA of the cluster has finished its accumulator
@@ -929,8 +967,8 @@ __device__ __forceinline__ void gather_finish(const GatherArgs& a, unsigned char
     double res = (double)res_f, dg = (double)dg_f;
     block_sum2<kThreads>(res, dg, reinterpret_cast<double*>(ring + ring_bytes - kSumScratch));
     if (threadIdx.x == 0) {
-        a.partials[2 * blockIdx.x] = res;
-        a.partials[2 * blockIdx.x + 1] = dg;
+        a.partials[2 * pslot] = res;
+        a.partials[2 * pslot + 1] = dg;
     }
 
     if constexpr (kFused) {
@@ -1251,7 +1289,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 1) gather_kernel(const Gath
     static_assert(R::kBytes >= scatter_table_bytes(PCPM_MAX_PARTITIONS) + 2 * kGatherWarps * 16 * 16,
                   "the fused scatter's stages must hold at least 16 groups beside the largest segment tables");
     gather_finish<kFused, kUpd, kGatherWarps * 32>(a, ring, R::kBytes, reinterpret_cast<uint64_t*>(meta), ring,
-                                                   R::kBytes, acc, sh32, S, rank, pd, npieces, vbase, len);
+                                                   R::kBytes, acc, sh32, S, rank, pd, npieces, vbase, len, blockIdx.x);
 }
 
 
@@ -1298,8 +1336,10 @@ static_assert(2 * (kWinThreads / 32) * sizeof(uint64_t) <= kWinScatterBars, "sca
 // lane and window remains of the one per ID of a racing layout. Then the hub
 // slots of all warps are summed into the hubs in warp order, and
 // gather_finish merges, applies and (fused) scatters.
+// uslot: the unit's position in a.order; pslot: this CTA's pair of FP64
+// partial sums in a.partials.
 template <bool kFused, int kUpd, bool kW>
-__global__ void __launch_bounds__(kWinThreads, 1) gather_win_kernel(const GatherArgs a) {
+__device__ __forceinline__ void gather_win_body(const GatherArgs& a, uint32_t uslot, uint32_t pslot) {
     using U = Upd<kUpd>;
     using R = WinRing<kUpd, kW>;
     using T = typename U::T;
@@ -1313,7 +1353,7 @@ __global__ void __launch_bounds__(kWinThreads, 1) gather_win_kernel(const Gather
     float* acc = reinterpret_cast<float*>(smraw + R::kAcc);
 
     const uint32_t S = cluster_size(), rank = cluster_rank();
-    const uint4 unit = a.units[a.order[blockIdx.x / S]];  // (bin, first window, end window, pieces of the bin)
+    const uint4 unit = a.units[a.order[uslot]];  // (bin, first window, end window, pieces of the bin)
     const uint32_t pd = unit.x, npieces = unit.w;
     const uint32_t vbase = pd * a.q, len = min(a.q, a.n - vbase);
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1451,13 +1491,87 @@ __global__ void __launch_bounds__(kWinThreads, 1) gather_win_kernel(const Gather
                   "the fused scatter's stages must hold at least 16 groups beside the largest segment tables");
     gather_finish<kFused, kUpd, kWinThreads>(a, ring, R::kBytes, reinterpret_cast<uint64_t*>(ring),
                                              ring + kWinScatterBars, R::kBytes - kWinScatterBars, acc, sh32, S, rank,
-                                             pd, npieces, vbase, len);
+                                             pd, npieces, vbase, len, pslot);
+}
+
+template <bool kFused, int kUpd, bool kW>
+__global__ void __launch_bounds__(kWinThreads, 1) gather_win_kernel(const GatherArgs a) {
+    gather_win_body<kFused, kUpd, kW>(a, blockIdx.x / cluster_size(), blockIdx.x);
+}
+
+// Many graphs in one launch (batched solves): item b / S of `items` names a
+// graph (its arguments in tab) and one of its gather units; the CTA's partial
+// sums go to that graph's slot unit * S + rank, as in its own launch.
+__global__ void __launch_bounds__(kWinThreads, 1) gather_win_batch_kernel(const GatherArgs* __restrict__ tab,
+                                                                          const uint2* __restrict__ items) {
+    const uint32_t S = cluster_size();
+    const uint2 it = items[blockIdx.x / S];
+    const GatherArgs a = tab[it.x];
+    gather_win_body<false, kUpdF32, false>(a, it.y, it.y * S + cluster_rank());
 }
 
 // ---------------------------------------------------------------- reduce
+__device__ __forceinline__ void reduce_body(const double* __restrict__ partials, int count, DevState* __restrict__ st,
+                                            double* __restrict__ hist, int hist_slot, double tol);
+
 __global__ void __launch_bounds__(kReduceThreads) reduce_kernel(const double* __restrict__ partials, int count,
                                                                 DevState* __restrict__ st, double* __restrict__ hist,
                                                                 int hist_slot, double tol) {
+    reduce_body(partials, count, st, hist, hist_slot, tol);
+}
+
+// The reduction of one graph of a batch; block b takes graph b.
+struct ReduceArgs {
+    const double* partials;
+    int count;
+    DevState* st;
+    double* hist;
+};
+__global__ void __launch_bounds__(kReduceThreads) reduce_batch_kernel(const ReduceArgs* __restrict__ tab,
+                                                                      int hist_slot) {
+    const ReduceArgs a = tab[blockIdx.x];
+    reduce_body(a.partials, a.count, a.st, a.hist, hist_slot, 0.0);
+}
+
+// A batch's reset, graph blockIdx.y: PR_0 = 1/n, the dangling mass of PR_0
+// into the partials of its first gridDim.x blocks, the solver scalars zeroed,
+// and the cut bins' global sums and counters cleared.
+struct InitArgs {
+    uint32_t n, k;
+    const float* inv_deg;
+    float* pr;
+    double* partials;
+    DevState* st;
+    float* gacc;
+    uint32_t* bin_done;
+};
+__global__ void __launch_bounds__(kReduceThreads) init_batch_kernel(const InitArgs* __restrict__ tab) {
+    const InitArgs a = tab[blockIdx.y];
+    const float uniform = (float)(1.0 / (double)a.n);
+    double dang = 0.0, zero = 0.0;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < a.n; v += gridDim.x * blockDim.x) {
+        a.pr[v] = uniform;
+        a.gacc[v] = 0.0f;
+        if (a.inv_deg[v] == 0.0f) dang += (double)uniform;
+    }
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < a.k; p += gridDim.x * blockDim.x) a.bin_done[p] = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.st->dangling = 0.0;
+        a.st->residual = 0.0;
+        a.st->stop = 0;
+        a.st->iters_done = 0;
+        a.st->err = 0;
+        a.st->dangling_prev = 0.0;
+    }
+    block_sum2<kReduceThreads>(zero, dang);
+    if (threadIdx.x == 0) {
+        a.partials[2 * blockIdx.x] = 0.0;
+        a.partials[2 * blockIdx.x + 1] = dang;
+    }
+}
+
+__device__ __forceinline__ void reduce_body(const double* __restrict__ partials, int count, DevState* __restrict__ st,
+                                            double* __restrict__ hist, int hist_slot, double tol) {
     if (st->stop) return;
     double r = 0.0, dg = 0.0;
     for (int i = threadIdx.x; i < count; i += blockDim.x) {
@@ -1683,8 +1797,9 @@ int launch_scatter_bits(pcpm_png* g, const void* x, void* out, cudaStream_t s) {
     return launch_status();
 }
 
-int launch_gather(pcpm_png* g, float d, uint32_t flags, bool fused, cudaStream_t s, bool spmv, bool delta) {
-    const bool weighted = spmv && g->weighted;  // only SpMV applies the weights
+namespace {
+// The gather's arguments for the handle's ranks pr[cur] -> pr[cur ^ 1].
+GatherArgs gather_args(pcpm_png* g, float d, uint32_t flags, bool delta, int cur) {
     GatherArgs a;
     a.delta = delta ? 1 : 0;
     a.gweight = g->gweight;
@@ -1703,9 +1818,9 @@ int launch_gather(pcpm_png* g, float d, uint32_t flags, bool fused, cudaStream_t
     a.gacc = g->gacc;
     a.bin_done = g->bin_done;
     a.upd_in = g->upd[g->ucur];
-    a.pr_in = g->pr[g->cur];
+    a.pr_in = g->pr[cur];
     a.inv_deg = g->inv_deg;
-    a.pr_out = g->pr[g->cur ^ 1];
+    a.pr_out = g->pr[cur ^ 1];
     a.partials = g->partials;
     a.st = g->state;
     a.err = &g->state->err;
@@ -1719,6 +1834,13 @@ int launch_gather(pcpm_png* g, float d, uint32_t flags, bool fused, cudaStream_t
     a.wweight = g->wweight;
     a.wdesc = g->wdesc;
     a.whubs = g->whubs;
+    return a;
+}
+}  // namespace
+
+int launch_gather(pcpm_png* g, float d, uint32_t flags, bool fused, cudaStream_t s, bool spmv, bool delta) {
+    const bool weighted = spmv && g->weighted;  // only SpMV applies the weights
+    const GatherArgs a = gather_args(g, d, flags, delta, g->cur);
 
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
@@ -1768,4 +1890,230 @@ int launch_reduce(pcpm_png* g, double tol, int hist_slot, cudaStream_t s, bool r
     return launch_status();
 }
 
+}  // namespace pcpm
+
+// ------------------------------------------------------------ batch kernels
+namespace pcpm {
+
+struct BatchKernels {
+    struct Group {
+        int count = 0;
+        int S = 1;
+        size_t gsmem = 0, ssmem = 0;
+        GatherArgs* gtab = nullptr;   // [2][count]: from pr[0] and from pr[1]
+        ScatterArgs* stab = nullptr;  // [2][count]
+        ReduceArgs* rtab = nullptr;   // [count] after an iteration
+        ReduceArgs* rtab0 = nullptr;  // [count] after the reset (init partials)
+        InitArgs* itab = nullptr;     // [count]
+        uint2* gitems = nullptr;
+        uint32_t ngitems = 0;
+        uint2* sitems = nullptr;
+        uint32_t nsitems = 0;
+        int init_blocks = 1;
+    };
+    std::vector<Group> groups;
+    std::vector<void*> allocs;
+};
+
+bool batch_kernels_ok(pcpm_png* const* hs, int count, uint32_t flags) {
+    if (!(flags & PCPM_TWO_PHASE) || (flags & PCPM_DELTA) || count > 65535) return false;
+    for (int i = 0; i < count; ++i) {
+        const pcpm_png* g = hs[i];
+        if (!g->gather_windows || g->upd_dtype != kUpdF32 || g->weighted || g->rect || g->plo != 0 || g->phi != g->k)
+            return false;
+    }
+    return true;
+}
+
+void batch_kernels_free(BatchKernels* b) {
+    if (!b) return;
+    for (void* p : b->allocs) pool_free(p, nullptr);
+    delete b;
+}
+
+namespace {
+template <class T>
+int upload(BatchKernels* b, const std::vector<T>& host, T** dev, cudaStream_t s) {
+    void* p = nullptr;
+    cudaError_t e = pool_alloc(&p, std::max<size_t>(host.size(), 1) * sizeof(T), s);
+    if (e == cudaSuccess) {
+        b->allocs.push_back(p);
+        if (!host.empty()) e = cudaMemcpyAsync(p, host.data(), host.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+    }
+    if (e != cudaSuccess) {
+        note_cuda_error(e);
+        return e == cudaErrorMemoryAllocation ? PCPM_ENOMEM : PCPM_ECUDA;
+    }
+    *dev = static_cast<T*>(p);
+    return PCPM_OK;
+}
+
+// (graph, position in its order) of every unit, largest first
+int batch_items(const std::vector<pcpm_png*>& gs, bool gather, std::vector<uint2>& items, cudaStream_t s) {
+    std::vector<std::pair<uint32_t, uint2>> all;
+    for (size_t j = 0; j < gs.size(); ++j) {
+        pcpm_png* g = gs[j];
+        const uint32_t nu = gather ? g->ngunits : g->nsunits;
+        std::vector<uint4> units(nu);
+        std::vector<uint32_t> order(nu);
+        cudaError_t e = cudaMemcpyAsync(units.data(), gather ? g->gunits : g->sunits, nu * sizeof(uint4),
+                                        cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(order.data(), gather ? g->gorder : g->sorder, nu * sizeof(uint32_t),
+                                cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            note_cuda_error(e);
+            return PCPM_ECUDA;
+        }
+        for (uint32_t r = 0; r < nu; ++r) {
+            const uint4 u = units[order[r]];
+            all.push_back({u.z - u.y, make_uint2((uint32_t)j, r)});
+        }
+    }
+    std::stable_sort(all.begin(), all.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+    items.clear();
+    for (const auto& x : all) items.push_back(x.second);
+    return PCPM_OK;
+}
+}  // namespace
+
+int batch_kernels_create(pcpm_png* const* hs, int count, float d, uint32_t flags, double* hist, int iters,
+                         cudaStream_t s, BatchKernels** out) {
+    BatchKernels* b = new (std::nothrow) BatchKernels;
+    if (!b) return PCPM_ENOMEM;
+    // one group per (part size, cluster size): the launch's shared memory
+    // follows q, its cluster dimension the handle's CTAs per gather unit
+    std::vector<std::pair<uint32_t, int>> keys;
+    for (int i = 0; i < count; ++i) {
+        const std::pair<uint32_t, int> key(hs[i]->q, hs[i]->cluster);
+        if (std::find(keys.begin(), keys.end(), key) == keys.end()) keys.push_back(key);
+    }
+    int rc = PCPM_OK;
+    for (const auto& key : keys) {
+        const uint32_t q = key.first;
+        std::vector<pcpm_png*> gs;
+        std::vector<int> idx;  // position in hs: the graph's history rows
+        for (int i = 0; i < count; ++i)
+            if (hs[i]->q == q && hs[i]->cluster == key.second) {
+                gs.push_back(hs[i]);
+                idx.push_back(i);
+            }
+        BatchKernels::Group G;
+        G.count = (int)gs.size();
+        G.S = gs[0]->cluster;
+        G.gsmem = win_smem_bytes(q, kUpdF32, false);
+        uint32_t nmax = 0;
+        std::vector<GatherArgs> gt(2 * gs.size());
+        std::vector<ScatterArgs> st(2 * gs.size());
+        std::vector<ReduceArgs> rt(gs.size()), rt0(gs.size());
+        std::vector<InitArgs> it(gs.size());
+        for (size_t j = 0; j < gs.size(); ++j) {
+            pcpm_png* g = gs[j];
+            G.ssmem = std::max(G.ssmem, scatter_smem_bytes(q, g->k));
+            nmax = std::max(nmax, g->n);
+            for (int c = 0; c < 2; ++c) {
+                gt[c * gs.size() + j] = gather_args(g, d, flags, false, c);
+                ScatterArgs& a = st[c * gs.size() + j];
+                a = ScatterArgs{g->n, g->q, g->k, g->pr[c], g->inv_deg, g->src, g->seg_u, g->cnt_u, g->sunits,
+                                g->sorder, g->upd[g->ucur], g->state, &g->state->err};
+            }
+            rt[j] = ReduceArgs{g->partials, (int)(g->ngunits * g->cluster), g->state, hist + (size_t)idx[j] * iters};
+            it[j] = InitArgs{g->n, g->k, g->inv_deg, g->pr[0], g->partials, g->state, g->gacc, g->bin_done};
+        }
+        G.init_blocks = (int)std::min<uint64_t>(kInitBlocks, ((uint64_t)nmax + kReduceThreads - 1) / kReduceThreads);
+        for (size_t j = 0; j < gs.size(); ++j) rt0[j] = ReduceArgs{gs[j]->partials, G.init_blocks, gs[j]->state, nullptr};
+        std::vector<uint2> gi, si;
+        if (rc == PCPM_OK) rc = batch_items(gs, true, gi, s);
+        if (rc == PCPM_OK) rc = batch_items(gs, false, si, s);
+        if (rc == PCPM_OK) rc = upload(b, gt, &G.gtab, s);
+        if (rc == PCPM_OK) rc = upload(b, st, &G.stab, s);
+        if (rc == PCPM_OK) rc = upload(b, rt, &G.rtab, s);
+        if (rc == PCPM_OK) rc = upload(b, rt0, &G.rtab0, s);
+        if (rc == PCPM_OK) rc = upload(b, it, &G.itab, s);
+        if (rc == PCPM_OK) rc = upload(b, gi, &G.gitems, s);
+        if (rc == PCPM_OK) rc = upload(b, si, &G.sitems, s);
+        G.ngitems = (uint32_t)gi.size();
+        G.nsitems = (uint32_t)si.size();
+        if (rc == PCPM_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = PCPM_ECUDA;  // host tables go out of scope
+        if (rc == PCPM_OK) {
+            cudaError_t e = raise_smem_limit((const void*)gather_win_batch_kernel, G.gsmem);
+            if (e == cudaSuccess) e = raise_smem_limit((const void*)scatter_batch_kernel, G.ssmem);
+            if (e != cudaSuccess) {
+                note_cuda_error(e);
+                rc = PCPM_ECUDA;
+            }
+        }
+        if (rc != PCPM_OK) break;
+        b->groups.push_back(G);
+    }
+    if (rc != PCPM_OK) {
+        cudaStreamSynchronize(s);
+        batch_kernels_free(b);
+        return rc;
+    }
+    *out = b;
+    return PCPM_OK;
+}
+
+int batch_kernels_groups(const BatchKernels* b) { return (int)b->groups.size(); }
+
+// The reset and `iters` two-phase iterations of every graph, one launch per
+// phase and group; group i on streams[i % nstreams].
+int batch_kernels_record(BatchKernels* b, int iters, const cudaStream_t* streams, int nstreams) {
+    for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+        const auto& G = b->groups[gi];
+        cudaStream_t s = streams[gi % nstreams];
+        init_batch_kernel<<<dim3(G.init_blocks, G.count), kReduceThreads, 0, s>>>(G.itab);
+        reduce_batch_kernel<<<G.count, kReduceThreads, 0, s>>>(G.rtab0, -1);
+        for (int i = 0; i < iters; ++i) {
+            const int c = i & 1;
+            if (G.nsitems)
+                scatter_batch_kernel<<<G.nsitems, kScatterThreads, G.ssmem, s>>>(G.stab + (size_t)c * G.count,
+                                                                                 G.sitems);
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = G.S;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.gridDim = dim3(G.ngitems * G.S);
+            cfg.blockDim = dim3(kWinThreads);
+            cfg.dynamicSmemBytes = G.gsmem;
+            cfg.stream = s;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            const cudaError_t e =
+                G.ngitems ? cudaLaunchKernelEx(&cfg, gather_win_batch_kernel,
+                                               (const GatherArgs*)(G.gtab + (size_t)c * G.count),
+                                               (const uint2*)G.gitems)
+                          : cudaSuccess;
+            if (e != cudaSuccess) {
+                note_cuda_error(e);
+                return PCPM_ECUDA;
+            }
+            reduce_batch_kernel<<<G.count, kReduceThreads, 0, s>>>(G.rtab, i);
+        }
+        const int rc = launch_status();
+        if (rc != PCPM_OK) return rc;
+    }
+    return PCPM_OK;
+}
+
+}  // namespace pcpm
+
+namespace pcpm {
+namespace {
+// Row i of the batch's history (iters values) to dst[i].
+__global__ void hist_copy_kernel(const double* __restrict__ src, double* const* __restrict__ dst, int iters,
+                                 int count) {
+    for (int i = blockIdx.x; i < count; i += gridDim.x)
+        for (int t = threadIdx.x; t < iters; t += blockDim.x) dst[i][t] = src[(size_t)i * iters + t];
+}
+}  // namespace
+
+int launch_hist_copy(const double* src, double* const* dst, int iters, int count, cudaStream_t s) {
+    hist_copy_kernel<<<std::min(count, 1024), 128, 0, s>>>(src, dst, iters, count);
+    return launch_status();
+}
 }  // namespace pcpm
