@@ -450,12 +450,13 @@ def ppr_leg(a, iters: int = 20):
 def batched_leg(a, graphs: int = 256, iters: int = 20):
     """Many small independent graphs (RMAT, scales drawn from 10-18, random
     labels) solved for `iters` iterations each by one captured CUDA graph
-    launch, against the same solves issued call by call on one stream. The
-    partition size and tile shape are picked per scale from {2048, 8192,
-    32768} by the library's autotuner (five timed iterations on the first
-    graph of that scale); each of the three part sizes for all graphs is
-    timed too. Graphs that share a part size and cluster size run each phase
-    as one launch over all their units."""
+    launch, against the same solves issued call by call on one stream.
+    Graphs that share a part size and cluster size run each phase as one
+    launch over all their units, so the configuration is tuned for the batch
+    as a whole: one part size for every graph (2048, 8192 or 32768, default
+    tiles), or part size and tile shape per scale as the single-graph
+    autotuner picks them (five timed iterations on the first graph of that
+    scale). The fastest configuration is the leg's number."""
     import torch
     import paper_1709_07122_gb300 as pcpm
     import graphgen
@@ -466,14 +467,6 @@ def batched_leg(a, graphs: int = 256, iters: int = 20):
     gen_s = time.perf_counter() - t0
     dev = [pcpm.to_device_csr(rp, col) for rp, col in data]
     edges = sum(int(rp[-1]) for rp, _ in data)
-    # partition size and tile shape per scale (pcpm_autotune_ex on the first
-    # graph of that scale)
-    best_q, best_opts = {}, {}
-    shapes = ({}, {"gather_cluster": 1}, {"gather_unit_chunks": 64})
-    for s in sorted(set(scales)):
-        i = scales.index(s)
-        best_q[s], best_opts[s], _ = pcpm.autotune_tiles(*dev[i], (2048, 8192, 32768), shapes, a.d, warmup=2,
-                                                         iters=5, mode="two_phase")
 
     def time_batch(batch):
         batch.launch()
@@ -488,22 +481,37 @@ def batched_leg(a, graphs: int = 256, iters: int = 20):
             ms.append(e0.elapsed_time(e1))
         return statistics.median(ms)
 
-    # one part size for every graph (default tiles): the fewest batch groups
-    one_q = {}
-    for q in (2048, 8192, 32768):
-        hs = [pcpm.PNG(rp, col, q) for rp, col in dev]
-        with pcpm.Batch(hs, a.d, iters, mode="two_phase") as b:
-            one_q[str(q)] = {"ms": time_batch(b), "kernel_launches": b.kernel_launches}
-        for h in hs:
-            h.close()
-    handles = [pcpm.PNG(*dev[i], best_q[s], **best_opts[s]) for i, s in enumerate(scales)]
+    # part size and tile shape per scale (pcpm_autotune_ex on the first graph
+    # of that scale)
+    best_q, best_opts = {}, {}
+    shapes = ({}, {"gather_cluster": 1}, {"gather_unit_chunks": 64})
+    for s in sorted(set(scales)):
+        i = scales.index(s)
+        best_q[s], best_opts[s], _ = pcpm.autotune_tiles(*dev[i], (2048, 8192, 32768), shapes, a.d, warmup=2,
+                                                         iters=5, mode="two_phase")
+    configs = {"part_size_%d" % q: [(q, {})] * graphs for q in (2048, 8192, 32768)}
+    configs["per_scale_autotuned"] = [(best_q[s], best_opts[s]) for s in scales]
+    results, best = {}, None
+    for name, cfg in configs.items():
+        handles = [pcpm.PNG(*dev[i], q, **opts) for i, (q, opts) in enumerate(cfg)]
+        t1 = time.perf_counter()
+        batch = pcpm.Batch(handles, a.d, iters, mode="two_phase")
+        capture_ms = (time.perf_counter() - t1) * 1e3
+        ms = time_batch(batch)
+        results[name] = {"ms": ms, "gteps": edges * iters / (ms * 1e-3) / 1e9,
+                         "kernel_launches": batch.kernel_launches, "capture_ms": capture_ms}
+        if best is None or ms < results[best[0]]["ms"]:
+            if best is not None:
+                best[1].close()
+                for h in best[2]:
+                    h.close()
+            best = (name, batch, handles)
+        else:
+            batch.close()
+            for h in handles:
+                h.close()
     del dev
-    t1 = time.perf_counter()
-    batch = pcpm.Batch(handles, a.d, iters, mode="two_phase")
-    capture_s = time.perf_counter() - t1
-    graph_ms = time_batch(batch)
-    launches = batch.kernel_launches
-    best_one_q = min(one_q, key=lambda q: one_q[q]["ms"])
+    name, batch, handles = best
     # the same work, one call after another
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
@@ -516,16 +524,14 @@ def batched_leg(a, graphs: int = 256, iters: int = 20):
     batch.close()
     for h in handles:
         h.close()
+    r = results[name]
     return {"graphs": graphs, "scales": "10-18", "iterations_each": iters, "edges_total": edges,
-            "partition_size_per_scale": {str(k): v for k, v in sorted(best_q.items())},
-            "tile_shape_per_scale": {str(k): v for k, v in sorted(best_opts.items())},
-            "one_graph_launch_ms": graph_ms, "gteps": edges * iters / (graph_ms * 1e-3) / 1e9,
-            "kernel_launches": launches,
-            "one_part_size": one_q,
-            "one_part_size_best": {"part_size": int(best_one_q), "ms": one_q[best_one_q]["ms"],
-                                   "gteps": edges * iters / (one_q[best_one_q]["ms"] * 1e-3) / 1e9},
+            "config": name, "one_graph_launch_ms": r["ms"], "gteps": r["gteps"],
+            "kernel_launches": r["kernel_launches"], "configs": results,
+            "per_scale_autotuned": {"partition_size": {str(k): v for k, v in sorted(best_q.items())},
+                                    "tile_shape": {str(k): v for k, v in sorted(best_opts.items())}},
             "call_by_call_ms": seq_ms, "call_by_call_gteps": edges * iters / (seq_ms * 1e-3) / 1e9,
-            "capture_ms": capture_s * 1e3, "generate_s": gen_s}
+            "generate_s": gen_s}
 
 
 def warm_start_leg(a, rp, col):
