@@ -456,7 +456,9 @@ def batched_leg(a, graphs: int = 256, iters: int = 20):
     as a whole: one part size for every graph (2048, 8192 or 32768, default
     tiles), or part size and tile shape per scale as the single-graph
     autotuner picks them (five timed iterations on the first graph of that
-    scale). The fastest configuration is the leg's number."""
+    scale), or each graph's node count rounded into [2048, 32768] (one
+    partition per graph up to scale 15). The fastest configuration is the
+    leg's number."""
     import torch
     import paper_1709_07122_gb300 as pcpm
     import graphgen
@@ -490,6 +492,9 @@ def batched_leg(a, graphs: int = 256, iters: int = 20):
         best_q[s], best_opts[s], _ = pcpm.autotune_tiles(*dev[i], (2048, 8192, 32768), shapes, a.d, warmup=2,
                                                          iters=5, mode="two_phase")
     configs = {"part_size_%d" % q: [(q, {})] * graphs for q in (2048, 8192, 32768)}
+    # each graph in one partition where it fits: n = 2^scale rounded into
+    # [2048, 32768], so small graphs' CTAs reserve small accumulators
+    configs["part_size_fit"] = [(min(32768, max(2048, 1 << s)), {}) for s in scales]
     configs["per_scale_autotuned"] = [(best_q[s], best_opts[s]) for s in scales]
     results, best = {}, None
     for name, cfg in configs.items():

@@ -217,13 +217,16 @@ int pcpm_batch_create(pcpm_png* const* handles, int count, float d, int iters, u
 int pcpm_batch_launch(pcpm_batch* batch, void* stream);
 void pcpm_batch_free(pcpm_batch* batch); /* NULL is a no-op */
 /* The number of kernels one pcpm_batch_launch runs (the kernel nodes of its
- * CUDA graph) into *launches. When every handle has the window layout, FP32
- * bins and no weights, and the flags ask for plain two-phase iterations,
- * each phase is a single launch over the units of all graphs that share a
- * part size and a gather cluster size: 2 + 3 iters launches per distinct
- * (part size, cluster size) pair (reset, its reduction, then scatter,
- * gather, reduction per iteration) plus one copy of the histories. Otherwise each handle's work is captured as
- * pcpm_reset and pcpm_iterate enqueue it. PCPM_EINVAL for NULL arguments. */
+ * CUDA graph) into *launches. When every handle has the window layout and no
+ * weights, and the flags ask for two-phase or fused iterations (not delta
+ * ones; fused only if every handle can fuse), each phase is a single launch
+ * over the units of all graphs that share a part size, a gather cluster size
+ * and a bin format: per such group 2 + 3 iters launches for two-phase
+ * iterations (reset, its reduction, then scatter, gather, reduction per
+ * iteration) or 3 + 2 iters for fused ones (one scatter, then gather with
+ * the next scatter, and reduction per iteration), plus one copy of the
+ * histories. Otherwise each handle's work is captured as pcpm_reset and
+ * pcpm_iterate enqueue it. PCPM_EINVAL for NULL arguments. */
 int pcpm_batch_kernel_launches(const pcpm_batch* batch, int* launches);
 
 /* Weighted graphs and SpMV (Sec. 3.5): pcpm_build with an edge weight per

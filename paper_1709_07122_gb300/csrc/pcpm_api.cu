@@ -647,10 +647,11 @@ int pcpm_batch_create(pcpm_png* const* handles, int count, float d, int iters, u
         // each (part size, cluster size) group on its own branch
         rc = batch_kernels_record(b->kernels, iters, streams.data(),
                                   std::max(1, std::min(nb, batch_kernels_groups(b->kernels))));
+        const bool fused = batch_kernels_fused(b->kernels);
         for (int i = 0; i < count && rc == PCPM_OK; ++i) {
             pcpm_png* g = handles[i];
-            // as pcpm_reset then `iters` two-phase iterations leave it
-            b->after.push_back({g, iters & 1, g->ucur, 0, iters, 0});
+            // as pcpm_reset then `iters` iterations leave it
+            b->after.push_back({g, iters & 1, fused ? g->ucur ^ (iters & 1) : g->ucur, fused ? 1 : 0, iters, 0});
         }
     } else if (rc == PCPM_OK) {
         // handle i on branch i % nb: independent graphs run side by side

@@ -254,12 +254,13 @@ int launch_scatter_bits(pcpm_png* g, const void* x, void* out, cudaStream_t s);
 int launch_gather(pcpm_png* g, float d, uint32_t flags, bool fused, cudaStream_t s, bool spmv = false,
                   bool delta = false);
 // Batched solves with one launch per phase over the units of all graphs
-// (pcpm_batch_*) of each (part size, cluster size) group: usable when every
-// handle has the window layout, FP32 bins, no weights and the whole square
-// graph, and the iterations are plain two-phase ones. batch_kernels_free
-// wants the device idle.
+// (pcpm_batch_*) of each (part size, cluster size, bin format) group: usable
+// when every handle has the window layout, no weights and the whole square
+// graph, the iterations are not delta ones, and (fused iterations) every
+// handle can fuse. batch_kernels_free wants the device idle.
 struct BatchKernels;
 bool batch_kernels_ok(pcpm_png* const* hs, int count, uint32_t flags);
+bool batch_kernels_fused(const BatchKernels* b);
 // hist: count x iters doubles, row i the L1 changes of hs[i].
 int batch_kernels_create(pcpm_png* const* hs, int count, float d, uint32_t flags, double* hist, int iters,
                          cudaStream_t s, BatchKernels** out);

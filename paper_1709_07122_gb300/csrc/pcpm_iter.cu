@@ -694,12 +694,13 @@ struct ScatterArgs {
 
 // Many graphs in one launch: block b takes item b (graph, position of the
 // unit in that graph's order).
+template <int kUpd>
 __global__ void __launch_bounds__(kScatterThreads, 1) scatter_batch_kernel(const ScatterArgs* __restrict__ tab,
                                                                           const uint2* __restrict__ items) {
     const uint2 it = items[blockIdx.x];
     const ScatterArgs a = tab[it.x];
-    scatter_body<kUpdF32>(a.n, a.q, a.k, a.pr, a.inv_deg, a.src, a.seg_u, a.cnt_u, a.units, a.order, a.upd, a.st,
-                          a.err, nullptr, nullptr, nullptr, it.y);
+    scatter_body<kUpd>(a.n, a.q, a.k, a.pr, a.inv_deg, a.src, a.seg_u, a.cnt_u, a.units, a.order, a.upd, a.st,
+                       a.err, nullptr, nullptr, nullptr, it.y);
 }
 
 // ---------------------------------------------------------- gather+apply
@@ -1502,12 +1503,13 @@ __global__ void __launch_bounds__(kWinThreads, 1) gather_win_kernel(const Gather
 // Many graphs in one launch (batched solves): item b / S of `items` names a
 // graph (its arguments in tab) and one of its gather units; the CTA's partial
 // sums go to that graph's slot unit * S + rank, as in its own launch.
+template <bool kFused, int kUpd>
 __global__ void __launch_bounds__(kWinThreads, 1) gather_win_batch_kernel(const GatherArgs* __restrict__ tab,
                                                                           const uint2* __restrict__ items) {
     const uint32_t S = cluster_size();
     const uint2 it = items[blockIdx.x / S];
     const GatherArgs a = tab[it.x];
-    gather_win_body<false, kUpdF32, false>(a, it.y, it.y * S + cluster_rank());
+    gather_win_body<kFused, kUpd, false>(a, it.y, it.y * S + cluster_rank());
 }
 
 // ---------------------------------------------------------------- reduce
@@ -1799,7 +1801,7 @@ int launch_scatter_bits(pcpm_png* g, const void* x, void* out, cudaStream_t s) {
 
 namespace {
 // The gather's arguments for the handle's ranks pr[cur] -> pr[cur ^ 1].
-GatherArgs gather_args(pcpm_png* g, float d, uint32_t flags, bool delta, int cur) {
+GatherArgs gather_args(pcpm_png* g, float d, uint32_t flags, bool delta, int cur, int ucur) {
     GatherArgs a;
     a.delta = delta ? 1 : 0;
     a.gweight = g->gweight;
@@ -1817,7 +1819,7 @@ GatherArgs gather_args(pcpm_png* g, float d, uint32_t flags, bool delta, int cur
     a.hubs = g->hubs;
     a.gacc = g->gacc;
     a.bin_done = g->bin_done;
-    a.upd_in = g->upd[g->ucur];
+    a.upd_in = g->upd[ucur];
     a.pr_in = g->pr[cur];
     a.inv_deg = g->inv_deg;
     a.pr_out = g->pr[cur ^ 1];
@@ -1829,7 +1831,7 @@ GatherArgs gather_args(pcpm_png* g, float d, uint32_t flags, bool delta, int cur
     a.src = g->src;
     a.seg_u = g->seg_u;
     a.cnt_u = g->cnt_u;
-    a.upd_out = g->upd[g->ucur ^ 1];
+    a.upd_out = g->upd[ucur ^ 1];
     a.wwords = g->wwords;
     a.wweight = g->wweight;
     a.wdesc = g->wdesc;
@@ -1840,7 +1842,7 @@ GatherArgs gather_args(pcpm_png* g, float d, uint32_t flags, bool delta, int cur
 
 int launch_gather(pcpm_png* g, float d, uint32_t flags, bool fused, cudaStream_t s, bool spmv, bool delta) {
     const bool weighted = spmv && g->weighted;  // only SpMV applies the weights
-    const GatherArgs a = gather_args(g, d, flags, delta, g->cur);
+    const GatherArgs a = gather_args(g, d, flags, delta, g->cur, g->ucur);
 
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
@@ -1899,6 +1901,7 @@ struct BatchKernels {
     struct Group {
         int count = 0;
         int S = 1;
+        int upd = kUpdF32;
         size_t gsmem = 0, ssmem = 0;
         GatherArgs* gtab = nullptr;   // [2][count]: from pr[0] and from pr[1]
         ScatterArgs* stab = nullptr;  // [2][count]
@@ -1913,17 +1916,37 @@ struct BatchKernels {
     };
     std::vector<Group> groups;
     std::vector<void*> allocs;
+    bool fused = false;  // gather + apply + next scatter per iteration
 };
 
 bool batch_kernels_ok(pcpm_png* const* hs, int count, uint32_t flags) {
-    if (!(flags & PCPM_TWO_PHASE) || (flags & PCPM_DELTA) || count > 65535) return false;
+    if ((flags & PCPM_DELTA) || count > 65535) return false;
+    const bool fused = !(flags & PCPM_TWO_PHASE);
     for (int i = 0; i < count; ++i) {
         const pcpm_png* g = hs[i];
-        if (!g->gather_windows || g->upd_dtype != kUpdF32 || g->weighted || g->rect || g->plo != 0 || g->phi != g->k)
+        if (!g->gather_windows || g->weighted || g->rect || g->plo != 0 || g->phi != g->k || (fused && !g->fused_ok))
             return false;
     }
     return true;
 }
+
+bool batch_kernels_fused(const BatchKernels* b) { return b->fused; }
+
+namespace {
+using BatchGatherFn = void (*)(const GatherArgs*, const uint2*);
+using BatchScatterFn = void (*)(const ScatterArgs*, const uint2*);
+template <bool kFused>
+BatchGatherFn pick_batch_gather(int upd) {
+    return upd == kUpdF16    ? gather_win_batch_kernel<kFused, kUpdF16>
+           : upd == kUpdBF16 ? gather_win_batch_kernel<kFused, kUpdBF16>
+                             : gather_win_batch_kernel<kFused, kUpdF32>;
+}
+BatchScatterFn pick_batch_scatter(int upd) {
+    return upd == kUpdF16    ? scatter_batch_kernel<kUpdF16>
+           : upd == kUpdBF16 ? scatter_batch_kernel<kUpdBF16>
+                             : scatter_batch_kernel<kUpdF32>;
+}
+}  // namespace
 
 void batch_kernels_free(BatchKernels* b) {
     if (!b) return;
@@ -1982,27 +2005,33 @@ int batch_kernels_create(pcpm_png* const* hs, int count, float d, uint32_t flags
                          cudaStream_t s, BatchKernels** out) {
     BatchKernels* b = new (std::nothrow) BatchKernels;
     if (!b) return PCPM_ENOMEM;
-    // one group per (part size, cluster size): the launch's shared memory
-    // follows q, its cluster dimension the handle's CTAs per gather unit
-    std::vector<std::pair<uint32_t, int>> keys;
+    b->fused = !(flags & PCPM_TWO_PHASE);
+    // one group per (part size, cluster size, bin format): the launch's
+    // shared memory follows q, its cluster dimension the handle's CTAs per
+    // gather unit, its instantiation the bins' format
+    std::vector<uint3> keys;
     for (int i = 0; i < count; ++i) {
-        const std::pair<uint32_t, int> key(hs[i]->q, hs[i]->cluster);
-        if (std::find(keys.begin(), keys.end(), key) == keys.end()) keys.push_back(key);
+        const uint3 key = make_uint3(hs[i]->q, (uint32_t)hs[i]->cluster, (uint32_t)hs[i]->upd_dtype);
+        if (std::find_if(keys.begin(), keys.end(), [&](const uint3& x) {
+                return x.x == key.x && x.y == key.y && x.z == key.z;
+            }) == keys.end())
+            keys.push_back(key);
     }
     int rc = PCPM_OK;
     for (const auto& key : keys) {
-        const uint32_t q = key.first;
+        const uint32_t q = key.x;
         std::vector<pcpm_png*> gs;
         std::vector<int> idx;  // position in hs: the graph's history rows
         for (int i = 0; i < count; ++i)
-            if (hs[i]->q == q && hs[i]->cluster == key.second) {
+            if (hs[i]->q == q && (uint32_t)hs[i]->cluster == key.y && (uint32_t)hs[i]->upd_dtype == key.z) {
                 gs.push_back(hs[i]);
                 idx.push_back(i);
             }
         BatchKernels::Group G;
         G.count = (int)gs.size();
         G.S = gs[0]->cluster;
-        G.gsmem = win_smem_bytes(q, kUpdF32, false);
+        G.upd = gs[0]->upd_dtype;
+        G.gsmem = win_smem_bytes(q, G.upd, false);
         uint32_t nmax = 0;
         std::vector<GatherArgs> gt(2 * gs.size());
         std::vector<ScatterArgs> st(2 * gs.size());
@@ -2013,10 +2042,13 @@ int batch_kernels_create(pcpm_png* const* hs, int count, float d, uint32_t flags
             G.ssmem = std::max(G.ssmem, scatter_smem_bytes(q, g->k));
             nmax = std::max(nmax, g->n);
             for (int c = 0; c < 2; ++c) {
-                gt[c * gs.size() + j] = gather_args(g, d, flags, false, c);
+                // iteration i reads pr[i & 1]; the fused form also swaps the
+                // update buffers every iteration
+                const int u = b->fused ? g->ucur ^ c : g->ucur;
+                gt[c * gs.size() + j] = gather_args(g, d, flags, false, c, u);
                 ScatterArgs& a = st[c * gs.size() + j];
                 a = ScatterArgs{g->n, g->q, g->k, g->pr[c], g->inv_deg, g->src, g->seg_u, g->cnt_u, g->sunits,
-                                g->sorder, g->upd[g->ucur], g->state, &g->state->err};
+                                g->sorder, g->upd[u], g->state, &g->state->err};
             }
             rt[j] = ReduceArgs{g->partials, (int)(g->ngunits * g->cluster), g->state, hist + (size_t)idx[j] * iters};
             it[j] = InitArgs{g->n, g->k, g->inv_deg, g->pr[0], g->partials, g->state, g->gacc, g->bin_done};
@@ -2037,8 +2069,10 @@ int batch_kernels_create(pcpm_png* const* hs, int count, float d, uint32_t flags
         G.nsitems = (uint32_t)si.size();
         if (rc == PCPM_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = PCPM_ECUDA;  // host tables go out of scope
         if (rc == PCPM_OK) {
-            cudaError_t e = raise_smem_limit((const void*)gather_win_batch_kernel, G.gsmem);
-            if (e == cudaSuccess) e = raise_smem_limit((const void*)scatter_batch_kernel, G.ssmem);
+            const void* gf = b->fused ? (const void*)pick_batch_gather<true>(G.upd)
+                                      : (const void*)pick_batch_gather<false>(G.upd);
+            cudaError_t e = raise_smem_limit(gf, G.gsmem);
+            if (e == cudaSuccess) e = raise_smem_limit((const void*)pick_batch_scatter(G.upd), G.ssmem);
             if (e != cudaSuccess) {
                 note_cuda_error(e);
                 rc = PCPM_ECUDA;
@@ -2058,19 +2092,22 @@ int batch_kernels_create(pcpm_png* const* hs, int count, float d, uint32_t flags
 
 int batch_kernels_groups(const BatchKernels* b) { return (int)b->groups.size(); }
 
-// The reset and `iters` two-phase iterations of every graph, one launch per
-// phase and group; group i on streams[i % nstreams].
+// The reset and `iters` iterations of every graph, one launch per phase and
+// group; group i on streams[i % nstreams]. Two-phase: scatter, gather,
+// reduce per iteration. Fused: one scatter, then gather (with the next
+// iteration's scatter) and reduce per iteration.
 int batch_kernels_record(BatchKernels* b, int iters, const cudaStream_t* streams, int nstreams) {
     for (size_t gi = 0; gi < b->groups.size(); ++gi) {
         const auto& G = b->groups[gi];
         cudaStream_t s = streams[gi % nstreams];
         init_batch_kernel<<<dim3(G.init_blocks, G.count), kReduceThreads, 0, s>>>(G.itab);
         reduce_batch_kernel<<<G.count, kReduceThreads, 0, s>>>(G.rtab0, -1);
+        const BatchScatterFn sf = pick_batch_scatter(G.upd);
+        const BatchGatherFn gf = b->fused ? pick_batch_gather<true>(G.upd) : pick_batch_gather<false>(G.upd);
         for (int i = 0; i < iters; ++i) {
             const int c = i & 1;
-            if (G.nsitems)
-                scatter_batch_kernel<<<G.nsitems, kScatterThreads, G.ssmem, s>>>(G.stab + (size_t)c * G.count,
-                                                                                 G.sitems);
+            if (G.nsitems && (!b->fused || i == 0))
+                sf<<<G.nsitems, kScatterThreads, G.ssmem, s>>>(G.stab + (size_t)c * G.count, G.sitems);
             cudaLaunchConfig_t cfg = {};
             cudaLaunchAttribute attr[1];
             attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -2084,8 +2121,7 @@ int batch_kernels_record(BatchKernels* b, int iters, const cudaStream_t* streams
             cfg.attrs = attr;
             cfg.numAttrs = 1;
             const cudaError_t e =
-                G.ngitems ? cudaLaunchKernelEx(&cfg, gather_win_batch_kernel,
-                                               (const GatherArgs*)(G.gtab + (size_t)c * G.count),
+                G.ngitems ? cudaLaunchKernelEx(&cfg, gf, (const GatherArgs*)(G.gtab + (size_t)c * G.count),
                                                (const uint2*)G.gitems)
                           : cudaSuccess;
             if (e != cudaSuccess) {
