@@ -1197,7 +1197,7 @@ __global__ void bin_window_counts_kernel(const uint32_t* __restrict__ bin_e, uin
         cnt[p] = (bin_e[p + 1] - bin_e[p] + kWin - 1) / kWin;
 }
 
-constexpr int kWlThreads = 256;
+constexpr int kWlThreads = 512;
 constexpr int kWlWarps = kWlThreads / 32;
 constexpr uint32_t kWlSpan = kWin / kWlWarps;   // consecutive items per warp
 constexpr uint32_t kWlSteps = kWlSpan / 32;     // 32-item steps per warp
