@@ -527,10 +527,28 @@ def batched_leg(a, graphs: int = 256, iters: int = 20):
     torch.cuda.synchronize()
     seq_ms = e0.elapsed_time(e1)
     batch.close()
+    # equal accuracy: the fewest iterations after which every graph's L1
+    # change is below 1e-7 (read from one long batch), then that batch timed
+    tol, long_iters = 1e-7, 80
+    with pcpm.Batch(handles, a.d, long_iters, mode="two_phase") as lb:
+        lb.launch()
+        torch.cuda.synchronize()
+        need = []
+        for h in handles:
+            hist = h.residual_history()
+            below = np.nonzero(hist < tol)[0]
+            need.append(int(below[0]) + 1 if below.size else None)
+    to_tol = {"tol": tol, "reached": all(x is not None for x in need)}
+    if to_tol["reached"]:
+        k_tol = max(need)
+        with pcpm.Batch(handles, a.d, k_tol, mode="two_phase") as tb:
+            to_tol.update({"iters": k_tol, "ms": time_batch(tb),
+                           "iters_per_graph_min_median_max": [min(need), int(np.median(need)), k_tol]})
     for h in handles:
         h.close()
     r = results[name]
     return {"graphs": graphs, "scales": "10-18", "iterations_each": iters, "edges_total": edges,
+            "time_to_residual": to_tol,
             "config": name, "one_graph_launch_ms": r["ms"], "gteps": r["gteps"],
             "kernel_launches": r["kernel_launches"], "configs": results,
             "per_scale_autotuned": {"partition_size": {str(k): v for k, v in sorted(best_q.items())},
