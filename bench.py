@@ -209,9 +209,13 @@ def algorithmic_bytes(info, mode="fused"):
         nchunks = -(-m // 256)
         gather = 4 * m + ub * ne + 4 * nchunks + 8 * (k + 1) + 8 * k  # destIDs, updates, chunk bases, bins, hubs
     apply = 12 * n  # PR_old and 1/outdeg read, PR' written
-    scatter = (4 + ub) * ne + 8 * k * k  # srcIdx read + update write, segment starts/counts
     if mode == "fused":
+        # the fused gather's scatter reads 4-byte global source IDs
+        scatter = (4 + ub) * ne + 8 * k * k  # srcIdx read + update write, segment starts/counts
         return {"scatter": 0, "gather_apply": gather + apply + scatter, "reduce": 16 * k}
+    # the scatter kernel reads 2-byte local source indices (u - p q) with
+    # FP32 bins, 4-byte global ones with 16-bit bins
+    scatter = ((2 if ub == 4 else 4) + ub) * ne + 8 * k * k
     return {"scatter": scatter + 8 * n, "gather_apply": gather + apply, "reduce": 16 * k}
 
 

@@ -103,7 +103,7 @@ bool is_device_ptr(const void* p) {
 
 void release(pcpm_png* g) {
     if (!g) return;
-    void* ptrs[] = {g->dest, g->src, g->bin_u, g->bin_e, g->seg_u, g->cnt_u, g->seg_e, g->cnt_e,
+    void* ptrs[] = {g->dest, g->src, g->src16, g->bin_u, g->bin_e, g->seg_u, g->cnt_u, g->seg_e, g->cnt_e,
                     g->chunk_base, g->hubs, g->gdest, g->gslice_start, g->gslice_bytes, g->ichunk_start,
                     g->gunits, g->gorder, g->sunits, g->sorder, g->gacc,
                     g->bin_done, g->inv_deg, g->pr[0], g->pr[1], g->upd[0], g->upd[1], g->partials,

@@ -121,6 +121,7 @@ struct pcpm_png {
     // PNG
     uint32_t* dest;          // m destination IDs in bin order (padded to whole chunks)
     uint32_t* src;           // ne source IDs in bin order (padded)
+    uint16_t* src16;         // the same as indices within their source partition (ne + 16)
     uint32_t* bin_u;         // k+1 starts of update bins
     uint32_t* bin_e;         // k+1 starts of destination-ID bins
     uint32_t* seg_u;         // k*k absolute start of segment (p, p') in the update array

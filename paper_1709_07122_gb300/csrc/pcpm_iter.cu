@@ -439,27 +439,92 @@ __global__ void spr_kernel(uint32_t n, const float* __restrict__ pr, const float
 // stages are in flight and before any is read, followed by a block barrier:
 // the scatter kernel fills sspr there. The barriers `bars` (two per warp) must
 // be initialised and visible to the block.
-template <int kUpd, class Prologue>
+//
+// kIdx16: src holds 16-bit local indices src[t] - base (Sec. 3.3 allows them
+// for q <= 2^16), so a group is 8 bytes. A bulk copy must start and end on
+// 16-byte boundaries: every piece is copied from the even group at or below
+// its first group to the even group above its last, and each lane keeps, for
+// the piece of segment sg + lane, the offset from a group's global index to
+// its position in the stage (a stage holds at most 32 pieces).
+template <int kUpd, bool kIdx16, class Prologue>
 __device__ void scatter_groups_staged(const float* sspr, uint32_t base, uint32_t len, const uint32_t* gpre,
                                       const uint32_t* dsh, const uint8_t* emsk, uint32_t k,
-                                      const uint32_t* __restrict__ src,
+                                      const void* __restrict__ src_raw,
                                       void* __restrict__ upd_raw, uint32_t f_lo, uint32_t f_hi, int* err,
                                       unsigned char* stages, uint32_t stage_bytes, uint64_t* bars,
                                       Prologue prologue) {
     using U = Upd<kUpd>;
     typename U::T* upd = reinterpret_cast<typename U::T*>(upd_raw);
+    const uint32_t* src = static_cast<const uint32_t*>(src_raw);
+    const uint16_t* src16 = static_cast<const uint16_t*>(src_raw);
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const uint32_t span = f_hi - f_lo;
     const uint32_t w_lo = f_lo + (uint32_t)((uint64_t)span * warp / nw);
     const uint32_t w_hi = f_lo + (uint32_t)((uint64_t)span * (warp + 1) / nw);
-    const uint32_t cap = stage_bytes / 16;
+    const uint32_t cap = stage_bytes / (kIdx16 ? 8 : 16);  // groups (16-bit: 8-byte units) per stage
     unsigned char* wst = stages + (size_t)warp * 2 * stage_bytes;
     uint64_t* wb = bars + 2 * warp;
     const uint64_t policy = policy_evict_first();
     // per slot (warp-uniform): groups, first flattened group, its segment
     uint32_t n0 = 0, n1 = 0, fb0 = 0, fb1 = 0, sg0 = 0, sg1 = 0, ph0 = 0, ph1 = 0;
+    // kIdx16, per slot: one piece (warp-uniform), and per lane the stage
+    // offset of the piece of segment sg + lane (group f of segment j sits at
+    // 8-byte unit f + dsh[j] + off)
+    bool one0 = true, one1 = true;
+    uint32_t off0 = 0, off1 = 0;
     uint32_t pf = w_lo, ppd = 0;
+    auto issue16 = [&](int slot) -> bool {  // warp-collective
+        if (pf >= w_hi) return false;
+        ppd = segment_at(gpre, k, ppd, pf);  // gpre[ppd] <= pf < gpre[ppd + 1]
+        unsigned char* dst = wst + (size_t)slot * stage_bytes;
+        const uint32_t lim = min(w_hi, pf + cap - 2);  // two units for the rounding of one piece
+        uint32_t f_end, off;
+        bool one;
+        if (gpre[ppd + 1] >= lim) {  // a piece of one segment fills the stage
+            one = true;
+            f_end = lim;
+            const uint32_t dd = dsh[ppd];
+            const uint32_t a0 = (pf + dd) & ~1u, a1 = (lim + dd + 1) & ~1u;
+            if (lane == 0) {
+                mbar_arrive_expect_tx(&wb[slot], (a1 - a0) * 8u);
+                bulk_load_hint(dst, src16 + (size_t)a0 * 4, (a1 - a0) * 8u, &wb[slot], policy);
+            }
+            off = 0u - a0;
+        } else {  // the rest of segment ppd, then whole segments while they fit (at most 32 pieces)
+            one = false;
+            const uint32_t j = ppd + lane;
+            uint32_t units = 0, a0 = 0;
+            if (j < k) {
+                const uint32_t fs = max(pf, gpre[j]), fe = gpre[j + 1];
+                if (fe > fs) {
+                    a0 = (fs + dsh[j]) & ~1u;
+                    units = ((fe + dsh[j] + 1) & ~1u) - a0;
+                }
+            }
+            uint32_t incl = units;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(kFull, incl, o);
+                if (lane >= (uint32_t)o) incl += y;
+            }
+            // a prefix of the lanes: incl, gpre[j + 1] and j all rise with the lane
+            const uint32_t c = __popc(__ballot_sync(kFull, j < k && incl <= cap && gpre[j + 1] <= w_hi));
+            f_end = gpre[ppd + c];  // c >= 1: the first piece is under lim - pf + 2 <= cap units
+            const uint32_t total = __shfl_sync(kFull, incl, c - 1);
+            if (lane == 0) mbar_arrive_expect_tx(&wb[slot], total * 8u);
+            __syncwarp();
+            const uint32_t excl = incl - units;
+            if (lane < c && units)
+                bulk_load_hint(dst + (size_t)excl * 8u, src16 + (size_t)a0 * 4, units * 8u, &wb[slot], policy);
+            off = excl - a0;
+        }
+        if (slot) { n1 = f_end - pf; fb1 = pf; sg1 = ppd; one1 = one; off1 = off; }
+        else { n0 = f_end - pf; fb0 = pf; sg0 = ppd; one0 = one; off0 = off; }
+        pf = f_end;
+        return true;
+    };
     auto issue = [&](int slot) -> bool {  // warp-collective
+        if constexpr (kIdx16) return issue16(slot);
         if (pf >= w_hi) return false;
         ppd = segment_at(gpre, k, ppd, pf);  // gpre[ppd] <= pf < gpre[ppd + 1]
         // The stage holds a piece of one segment that alone fills it (the
@@ -509,6 +574,47 @@ __device__ void scatter_groups_staged(const float* sspr, uint32_t base, uint32_t
         const uint32_t n = slot ? n1 : n0, fb = slot ? fb1 : fb0;
         uint32_t pd = slot ? sg1 : sg0;
         const uint4* ids = reinterpret_cast<const uint4*>(wst + (size_t)slot * stage_bytes);
+        if constexpr (kIdx16) {
+            const uint2* ids16 = reinterpret_cast<const uint2*>(wst + (size_t)slot * stage_bytes);
+            const uint32_t off = slot ? off1 : off0;
+            // one group of four local indices: as put below
+            auto put16 = [&](uint32_t f, uint32_t u, uint32_t dd, uint32_t glo, uint32_t ghi, uint32_t em) {
+                const uint32_t e = (f + dd) << 2;
+                const uint2 w = ids16[u];
+                const uint32_t i0 = w.x & 0xFFFFu, i1 = w.x >> 16, i2 = w.y & 0xFFFFu, i3 = w.y >> 16;
+                if (f != glo && f + 1 != ghi) {
+                    if (i0 < len && i1 < len && i2 < len && i3 < len)
+                        U::store4(upd, e, sspr[i0], sspr[i1], sspr[i2], sspr[i3]);
+                    else
+                        atomicOr(err, kErrBounds);
+                } else {
+                    const uint32_t jlo = f == glo ? (em & 3u) : 0u, jhi = f + 1 == ghi ? (em >> 2) : 4u;
+                    const uint32_t v[4] = {i0, i1, i2, i3};
+#pragma unroll
+                    for (uint32_t jj = 0; jj < 4; ++jj) {
+                        if (jj >= jlo && jj < jhi) {
+                            if (v[jj] < len) upd[e + jj] = U::from(sspr[v[jj]]); else atomicOr(err, kErrBounds);
+                        }
+                    }
+                }
+            };
+            if (slot ? one1 : one0) {  // one piece: the same segment and offset for every group
+                const uint32_t glo = gpre[pd], ghi = gpre[pd + 1], dd = dsh[pd], em = emsk[pd];
+                for (uint32_t g = lane; g < n; g += 32) put16(fb + g, fb + g + dd + off, dd, glo, ghi, em);
+            } else {
+                uint32_t hint = pd;
+                for (uint32_t g0 = 0; g0 < n; g0 += 32) {  // uniform trips: the offsets come by shuffle
+                    const uint32_t g = g0 + lane, f = fb + g;
+                    const bool act = g < n;
+                    if (act) hint = segment_at(gpre, k, hint, f);
+                    const uint32_t o = __shfl_sync(kFull, off, act ? hint - pd : 0u);
+                    if (act) put16(f, f + dsh[hint] + o, dsh[hint], gpre[hint], gpre[hint + 1], emsk[hint]);
+                }
+            }
+            __syncwarp();  // every lane is done with the slot before it is refilled
+            if (slot) has1 = issue(1); else has0 = issue(0);
+            return true;
+        }
         // one group: interior groups lie inside their segment; a segment's
         // first or last group holds its entries [jlo, jhi) only
         auto put = [&](uint32_t f, uint32_t g, uint32_t dd, uint32_t glo, uint32_t ghi, uint32_t em) {
@@ -581,7 +687,8 @@ __host__ __device__ constexpr uint32_t scatter_stage_bytes(uint32_t q, uint32_t 
 template <int kUpd>
 __device__ __forceinline__ void scatter_body(
     uint32_t n, uint32_t q, uint32_t k, const float* __restrict__ pr, const float* __restrict__ inv_deg,
-    const uint32_t* __restrict__ src, const uint32_t* __restrict__ seg_u, const uint32_t* __restrict__ cnt_u,
+    const uint32_t* __restrict__ src, const uint16_t* __restrict__ src16, const uint32_t* __restrict__ seg_u,
+    const uint32_t* __restrict__ cnt_u,
     const uint4* __restrict__ units, const uint32_t* __restrict__ order, void* __restrict__ upd,
     const DevState* __restrict__ st, int* __restrict__ err, const float* __restrict__ pr_prev,
     const float* __restrict__ dq_in, float* __restrict__ dq_out, uint32_t upos) {
@@ -662,19 +769,25 @@ __device__ __forceinline__ void scatter_body(
                 sspr[i] = inv_deg ? pr[base + i] * inv_deg[base + i] : pr[base + i];
         }
     };
-    scatter_groups_staged<kUpd>(sspr, base, len, gpre, dsh, emsk, k, src, upd, unit.y, min(unit.z, gpre[k]), err,
-                                stages, scatter_stage_bytes(q, k), bars, stage_spr);
+    // 16-bit local indices with FP32 bins, where they save time; with 16-bit
+    // bins the 32-bit ones measured faster
+    constexpr bool kIdx16 = kUpd == kUpdF32;
+    scatter_groups_staged<kUpd, kIdx16>(sspr, base, len, gpre, dsh, emsk, k,
+                                        kIdx16 ? static_cast<const void*>(src16) : static_cast<const void*>(src), upd,
+                                        unit.y, min(unit.z, gpre[k]), err, stages, scatter_stage_bytes(q, k), bars,
+                                        stage_spr);
 }
 
 template <int kUpd>
 __global__ void __launch_bounds__(kScatterThreads, 1) scatter_kernel(
     uint32_t n, uint32_t q, uint32_t k, const float* __restrict__ pr, const float* __restrict__ inv_deg,
-    const uint32_t* __restrict__ src, const uint32_t* __restrict__ seg_u, const uint32_t* __restrict__ cnt_u,
+    const uint32_t* __restrict__ src, const uint16_t* __restrict__ src16, const uint32_t* __restrict__ seg_u,
+    const uint32_t* __restrict__ cnt_u,
     const uint4* __restrict__ units, const uint32_t* __restrict__ order, void* __restrict__ upd,
     const DevState* __restrict__ st, int* __restrict__ err, const float* __restrict__ pr_prev,
     const float* __restrict__ dq_in, float* __restrict__ dq_out) {
-    scatter_body<kUpd>(n, q, k, pr, inv_deg, src, seg_u, cnt_u, units, order, upd, st, err, pr_prev, dq_in, dq_out,
-                       blockIdx.x);
+    scatter_body<kUpd>(n, q, k, pr, inv_deg, src, src16, seg_u, cnt_u, units, order, upd, st, err, pr_prev, dq_in,
+                       dq_out, blockIdx.x);
 }
 
 // The scatter of one graph of a batch (plain FP32 form).
@@ -683,6 +796,7 @@ struct ScatterArgs {
     const float* pr;
     const float* inv_deg;
     const uint32_t* src;
+    const uint16_t* src16;
     const uint32_t* seg_u;
     const uint32_t* cnt_u;
     const uint4* units;
@@ -699,8 +813,8 @@ __global__ void __launch_bounds__(kScatterThreads, 1) scatter_batch_kernel(const
                                                                           const uint2* __restrict__ items) {
     const uint2 it = items[blockIdx.x];
     const ScatterArgs a = tab[it.x];
-    scatter_body<kUpd>(a.n, a.q, a.k, a.pr, a.inv_deg, a.src, a.seg_u, a.cnt_u, a.units, a.order, a.upd, a.st,
-                       a.err, nullptr, nullptr, nullptr, it.y);
+    scatter_body<kUpd>(a.n, a.q, a.k, a.pr, a.inv_deg, a.src, a.src16, a.seg_u, a.cnt_u, a.units, a.order, a.upd,
+                       a.st, a.err, nullptr, nullptr, nullptr, it.y);
 }
 
 // ---------------------------------------------------------- gather+apply
@@ -1015,7 +1129,7 @@ __device__ __forceinline__ void gather_finish(const GatherArgs& a, unsigned char
         // stages: the scatter area after the segment table
         const size_t st_off = scatter_table_bytes(a.k);
         const uint32_t stage_bytes = (uint32_t)(((sarea_bytes - st_off) / (2 * kWarps)) & ~(size_t)15);
-        scatter_groups_staged<kUpd>(acc, vbase, len, gpre, dsh, emsk, a.k, a.src, a.upd_out, f_lo, f_hi, a.err,
+        scatter_groups_staged<kUpd, false>(acc, vbase, len, gpre, dsh, emsk, a.k, a.src, a.upd_out, f_lo, f_hi, a.err,
                                     sarea + st_off, stage_bytes, sbars, [] {});
     } else {
         if (!push) cluster_sync();  // remote loads of this CTA's shared memory are done
@@ -1775,13 +1889,15 @@ int launch_spr(pcpm_png* g, float* spr, cudaStream_t s) {
 int launch_scatter(pcpm_png* g, cudaStream_t s, bool raw, bool delta, bool feedback) {
     feedback = feedback && g->dq_err && !raw;
     const size_t smem = scatter_smem_bytes(g->q, g->k);
-    void (*f)(uint32_t, uint32_t, uint32_t, const float*, const float*, const uint32_t*, const uint32_t*,
+    void (*f)(uint32_t, uint32_t, uint32_t, const float*, const float*, const uint32_t*, const uint16_t*,
+              const uint32_t*,
               const uint32_t*, const uint4*, const uint32_t*, void*, const DevState*, int*, const float*,
               const float*, float*) =
         g->upd_dtype == kUpdF16 ? scatter_kernel<kUpdF16>
         : g->upd_dtype == kUpdBF16 ? scatter_kernel<kUpdBF16>
                                    : scatter_kernel<kUpdF32>;
     f<<<g->nsunits, kScatterThreads, smem, s>>>(g->n, g->q, g->k, g->pr[g->cur], raw ? nullptr : g->inv_deg, g->src,
+                                               g->src16,
                                                g->seg_u,
                                                g->cnt_u, g->sunits, g->sorder, g->upd[g->ucur], g->state,
                                                &g->state->err, delta ? g->pr[g->cur ^ 1] : nullptr,
@@ -1794,7 +1910,8 @@ int launch_scatter(pcpm_png* g, cudaStream_t s, bool raw, bool delta, bool feedb
 int launch_scatter_bits(pcpm_png* g, const void* x, void* out, cudaStream_t s) {
     if (g->upd_dtype != kUpdF32) return PCPM_EINVAL;
     scatter_kernel<kUpdF32><<<g->nsunits, kScatterThreads, scatter_smem_bytes(g->q, g->k), s>>>(
-        g->n, g->q, g->k, static_cast<const float*>(x), nullptr, g->src, g->seg_u, g->cnt_u, g->sunits, g->sorder,
+        g->n, g->q, g->k, static_cast<const float*>(x), nullptr, g->src, g->src16, g->seg_u, g->cnt_u, g->sunits,
+        g->sorder,
         out, g->state, &g->state->err, nullptr, nullptr, nullptr);
     return launch_status();
 }
@@ -2047,7 +2164,7 @@ int batch_kernels_create(pcpm_png* const* hs, int count, float d, uint32_t flags
                 const int u = b->fused ? g->ucur ^ c : g->ucur;
                 gt[c * gs.size() + j] = gather_args(g, d, flags, false, c, u);
                 ScatterArgs& a = st[c * gs.size() + j];
-                a = ScatterArgs{g->n, g->q, g->k, g->pr[c], g->inv_deg, g->src, g->seg_u, g->cnt_u, g->sunits,
+                a = ScatterArgs{g->n, g->q, g->k, g->pr[c], g->inv_deg, g->src, g->src16, g->seg_u, g->cnt_u, g->sunits,
                                 g->sorder, g->upd[u], g->state, &g->state->err};
             }
             rt[j] = ReduceArgs{g->partials, (int)(g->ngunits * g->cluster), g->state, hist + (size_t)idx[j] * iters};

@@ -1455,6 +1455,16 @@ __global__ void __launch_bounds__(kWlThreads, 2) window_layout_kernel(
     if (lane == 0 && nbad) atomicAdd(&stats[1], (unsigned long long)nbad);
 }
 
+// src16[t] = src[t] - p q, p = src[t] / q: the index within its source
+// partition.
+__global__ void src_local_kernel(const uint32_t* __restrict__ src, uint64_t ne, DivQ divq,
+                                 uint16_t* __restrict__ src16) {
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < ne; t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t v = src[t];
+        src16[t] = (uint16_t)(v - divq(v) * divq.q);
+    }
+}
+
 __global__ void scatter_pieces_kernel(const uint32_t* __restrict__ groups, uint32_t k, uint32_t per,
                                       uint32_t* __restrict__ pieces) {
     for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < k; p += gridDim.x * blockDim.x)
@@ -1728,6 +1738,14 @@ int build_png(pcpm_png* g, const uint32_t* row_ptr, const uint32_t* col, const p
                                                                     tab_e, tab_u, g->bin_e, g->bin_u, g->dest,
                                                                     g->src, d_err, g->weights_in, g->wdest);
         }
+        BCK(cudaGetLastError());
+    }
+    // 16-bit local source indices for the scatter (Sec. 3.3: u - p q fits
+    // 16 bits for q <= 2^16), with room for copies rounded to 16 bytes
+    BCK(dev_alloc(g, (void**)&g->src16, (g->ne + 16) * sizeof(uint16_t)));
+    BCK(cudaMemsetAsync(g->src16, 0, (g->ne + 16) * sizeof(uint16_t), s));
+    if (g->ne) {
+        src_local_kernel<<<grid_for(g->ne, 256, sms * 8), 256, 0, s>>>(g->src, g->ne, divq, g->src16);
         BCK(cudaGetLastError());
     }
 
