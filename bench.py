@@ -715,18 +715,18 @@ def run_ours(a):
         prp.numpy()[:] = rp.view(np.int32)
         pcol.numpy()[:m] = col.view(np.int32)
         hrp, hcol, hout = prp.numpy().view(np.uint32), pcol.numpy().view(np.uint32)[:m], pout.numpy()
-        pcpm.pagerank_host(hrp, hcol, a.part_size, a.d, 3, pr_out=hout)  # warm-up call
+        pcpm.pagerank_host(hrp, hcol, a.part_size, a.d, 3, pr_out=hout, mode=a.mode)  # warm-up call
         barrier()
         walls = []
         for _ in range(3):
             e0 = time.perf_counter()
-            pcpm.pagerank_host(hrp, hcol, a.part_size, a.d, e2e_iters, pr_out=hout)
+            pcpm.pagerank_host(hrp, hcol, a.part_size, a.d, e2e_iters, pr_out=hout, mode=a.mode)
             walls.append(time.perf_counter() - e0)
         wall = max_over_ranks(statistics.median(walls))
         out["e2e"] = {"value": world * m * e2e_iters / wall / 1e9, "unit": "GTEPS",
                       "h2d_bytes_per_step": (n + 1 + m) * 4 / e2e_iters, "d2h_bytes_per_step": n * 4 / e2e_iters,
-                      "call": "pcpm_pagerank_host: H2D CSR (pinned) + PNG build + %d iterations + D2H ranks"
-                              % e2e_iters, "wall_ms_per_call": wall * 1e3}
+                      "call": "pcpm_pagerank_host: H2D CSR (pinned) + PNG build + %d %s iterations + D2H ranks"
+                              % (e2e_iters, a.mode), "wall_ms_per_call": wall * 1e3}
 
     # Reduced-precision update bins (not in the paper): speed, bytes per edge,
     # and the first iteration's distance to the FP64 oracle's (below).
