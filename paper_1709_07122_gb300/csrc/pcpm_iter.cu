@@ -790,7 +790,7 @@ __global__ void __launch_bounds__(kScatterThreads, 1) scatter_kernel(
                        dq_out, blockIdx.x);
 }
 
-// The scatter of one graph of a batch (plain FP32 form).
+// The scatter of one graph of a batch (its bins in any format).
 struct ScatterArgs {
     uint32_t n, q, k;
     const float* pr;
